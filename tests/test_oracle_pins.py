@@ -1,0 +1,334 @@
+"""Pins for the CPU oracle: each test checks it against something the paper or the
+mathematics fixes, not against a second copy of its own formulas.
+
+* hand example (Eq. 1, Eq. 2, Algorithm 1, Eq. 11, §5.3), values worked out by hand;
+* SplitMix64 published reference outputs;
+* Eq. 1 / Eq. 2 collision probabilities 1 - theta/pi and (1 - theta/pi)^K, by brute force;
+* Theorem 1 (§3.3): the count estimator is unbiased for S(q, D) = sum_i p_i^K (Eq. 3);
+* invariants: every array sums to the number of inserts; the Q identity of Eq. 11;
+  H(2^k x) = H(x); negation flips every bit whose projection is non-zero;
+* library routines: numpy's float64 matmul signs, bincount, mean and population std.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1706_06664_gb300 import workloads
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+# ------------------------------------------------------------------------------------------
+# Hand example
+# ------------------------------------------------------------------------------------------
+def _hand():
+    g = _load("hand_example.json")
+    W = np.array(g["W_columns"], dtype=np.float32).T.copy()  # d x KL, column c = W[:, c]
+    X = np.array(g["X"], dtype=np.float32)
+    return g, W, X
+
+
+def test_hand_example_projections_and_ids():
+    g, W, X = _hand()
+    s = oracle.project(X, W)
+    assert s.tolist() == g["projections"]
+    ids = oracle.hash_ids(X, W, g["K"], g["L"])
+    assert ids.tolist() == g["ids"]
+
+
+def test_hand_example_insert_score_flag():
+    g, W, X = _hand()
+    det = oracle.Detector(g["d"], g["K"], g["L"], W=W)
+    scores, sums, flags = det.insert_score(X, g["alpha"])
+    assert det.counts.tolist() == g["counts"]
+    assert sums.tolist() == g["sums"]
+    assert scores.tolist() == g["scores"]
+    assert flags.tolist() == g["flags"]
+    st = det.stats(g["alpha"])
+    assert st["Q"] == g["Q"]
+    assert st["mu_ins"] == g["mu_ins"]
+    assert st["mu"] == g["mu"]
+    # sqrt, a division and a subtraction: each within half an ulp of its exact result
+    assert st["sigma"] == pytest.approx(g["sigma"], rel=4 * 2.0**-53, abs=0)
+    assert st["threshold"] == pytest.approx(g["threshold"], rel=4 * 2.0**-53, abs=0)
+
+
+def test_hand_example_incremental_mean_eq11():
+    g, W, X = _hand()
+    ids = oracle.hash_ids(X, W, g["K"], g["L"])
+    counts = np.zeros((g["L"], 1 << g["K"]), dtype=np.uint32)
+    mu, trace = oracle.mu_incremental(ids, counts, g["K"])
+    assert np.allclose(trace, g["mu_incremental_trace"], rtol=1e-15, atol=0)
+    assert counts.tolist() == g["counts"]
+    # the literal post-increment reading of Algorithm 1 would give 3.0 after x1
+    assert trace[0] != g["mu_after_first_point_literal_post_increment_reading"]
+
+
+# ------------------------------------------------------------------------------------------
+# Generator
+# ------------------------------------------------------------------------------------------
+def test_splitmix64_reference_vectors():
+    for v in _load("splitmix64.json")["vectors"]:
+        assert oracle.splitmix64_draw(v["seed"], v["t"]) == v["out"]
+
+
+def test_projection_from_seed_is_standard_normal():
+    W = oracle.projection_from_seed(64, 16, 256, seed=12345).astype(np.float64).ravel()
+    assert W.size == 64 * 16 * 256
+    m, v = W.mean(), W.var()
+    se = 1.0 / math.sqrt(W.size)
+    assert abs(m) < 5 * se
+    assert abs(v - 1.0) < 5 * math.sqrt(2.0) * se
+    kurt = np.mean((W - m) ** 4) / v**2
+    assert abs(kurt - 3.0) < 5 * math.sqrt(24.0) * se
+    scipy_stats = pytest.importorskip("scipy.stats")
+    ks = scipy_stats.kstest(W, "norm")
+    assert ks.pvalue > 1e-4
+    # even and odd flat indices (cos and sin halves) are each N(0,1) and uncorrelated
+    e, o = W[0::2], W[1::2]
+    assert abs(np.corrcoef(e, o)[0, 1]) < 5 * math.sqrt(2.0) * se
+    assert scipy_stats.kstest(e, "norm").pvalue > 1e-4
+    assert scipy_stats.kstest(o, "norm").pvalue > 1e-4
+
+
+def test_projection_from_seed_deterministic_and_seed_dependent():
+    a = oracle.projection_from_seed(5, 3, 4, seed=7)
+    b = oracle.projection_from_seed(5, 3, 4, seed=7)
+    c = oracle.projection_from_seed(5, 3, 4, seed=8)
+    assert np.array_equal(a, b)
+    assert not np.array_equal(a, c)
+    # the matrix is a prefix-stable function of the flat index: a larger L extends it
+    big = oracle.projection_from_seed(5, 3, 8, seed=7)
+    assert np.array_equal(big.ravel()[:4], a.ravel()[:4])
+
+
+# ------------------------------------------------------------------------------------------
+# Eq. 1 / Eq. 2 collision probabilities
+# ------------------------------------------------------------------------------------------
+def _pair_at_angle(theta, d):
+    x = np.zeros(d, dtype=np.float32)
+    y = np.zeros(d, dtype=np.float32)
+    x[0] = 1.0
+    y[0] = np.float32(math.cos(theta))
+    y[1] = np.float32(math.sin(theta))
+    return np.stack([x, y])
+
+
+@pytest.mark.parametrize("theta", [math.pi / 6, math.pi / 3, math.pi / 2, 2 * math.pi / 3])
+@pytest.mark.parametrize("source", ["seed", "numpy"])
+def test_srp_collision_probability_eq1(theta, source):
+    d, M = 4, 1 << 17
+    W = oracle.projection_from_seed(d, 1, M, seed=99) if source == "seed" else workloads.gaussian_w(d, 1, M, 99)
+    X = _pair_at_angle(theta, d)
+    ids = oracle.hash_ids(X, W, 1, M)
+    # recompute theta from the binary32 inputs actually hashed
+    xd, yd = X.astype(np.float64)
+    th = math.acos(float(xd @ yd) / (np.linalg.norm(xd) * np.linalg.norm(yd)))
+    p = 1.0 - th / math.pi
+    frac = float(np.mean(ids[0] == ids[1]))
+    assert abs(frac - p) < 5 * math.sqrt(p * (1 - p) / M)
+
+
+@pytest.mark.parametrize("K", [2, 4])
+def test_srp_collision_probability_eq2(K):
+    d, L = 4, 1 << 15
+    theta = math.pi / 4
+    W = oracle.projection_from_seed(d, K, L, seed=2024 + K)
+    X = _pair_at_angle(theta, d)
+    ids = oracle.hash_ids(X, W, K, L)
+    xd, yd = X.astype(np.float64)
+    th = math.acos(float(xd @ yd) / (np.linalg.norm(xd) * np.linalg.norm(yd)))
+    p = (1.0 - th / math.pi) ** K
+    frac = float(np.mean(ids[0] == ids[1]))
+    assert abs(frac - p) < 5 * math.sqrt(p * (1 - p) / L)
+
+
+# ------------------------------------------------------------------------------------------
+# Theorem 1: E[S^(q)] = sum_i p_i^K
+# ------------------------------------------------------------------------------------------
+def test_theorem1_unbiased():
+    rng = np.random.default_rng(5)
+    d, K, L = 3, 2, 100_000
+    D = rng.standard_normal((6, d)).astype(np.float32)
+    q = rng.standard_normal((1, d)).astype(np.float32)
+    det = oracle.Detector(d, K, L, seed=77)
+    det.insert(D)
+    scores, sums, _ = det.score(q, 1.0)
+    Dd, qd = D.astype(np.float64), q[0].astype(np.float64)
+    cos = Dd @ qd / (np.linalg.norm(Dd, axis=1) * np.linalg.norm(qd))
+    p = 1.0 - np.arccos(np.clip(cos, -1, 1)) / math.pi
+    S = float(np.sum(p**K))
+    # Var of one array's count <= E[A^2] <= n * S; the estimator averages L independent arrays
+    se = math.sqrt(len(D) * S / L)
+    assert abs(scores[0] - S) < 5 * se
+
+
+# ------------------------------------------------------------------------------------------
+# Invariants and library-routine cross-checks
+# ------------------------------------------------------------------------------------------
+def test_hash_matches_float64_matmul_signs():
+    rng = np.random.default_rng(11)
+    n, d, K, L = 300, 37, 7, 9
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    W = workloads.gaussian_w(d, K, L, 3)
+    ids = oracle.hash_ids(X, W, K, L)
+    S = X.astype(np.float64) @ W.astype(np.float64)
+    margin = np.abs(S) > 1e-9 * (np.abs(X.astype(np.float64)) @ np.abs(W.astype(np.float64)))
+    bits = (S > 0).astype(np.uint32).reshape(n, L, K)
+    ref = (bits << np.arange(K, dtype=np.uint32)).sum(axis=2)
+    got_bits = (ids[:, :, None] >> np.arange(K, dtype=np.uint32)) & 1
+    ok = margin.reshape(n, L, K)
+    assert np.all(got_bits[ok] == bits[ok])
+    assert ok.mean() > 0.999
+    assert np.array_equal(ids[ok.all(axis=2)], ref[ok.all(axis=2)])
+
+
+def test_counts_match_bincount_and_sum_to_n():
+    w = workloads.small(seed=3, n=3000)
+    det = oracle.Detector(w["d"], w["K"], w["L"], seed=5)
+    ids = det.insert(w["X"])
+    for j in range(w["L"]):
+        assert np.array_equal(det.counts[j], np.bincount(ids[:, j], minlength=1 << w["K"]))
+        assert int(det.counts[j].sum()) == 3000
+    ids2 = det.insert(w["X"][:777])
+    for j in range(w["L"]):
+        assert int(det.counts[j].sum()) == 3777
+
+
+def test_mu_identity_three_ways():
+    """Eq. 11 point by point == Q/(nL) == mean score of the inserted set at final counts."""
+    w = workloads.small(seed=4, n=2000)
+    det = oracle.Detector(w["d"], w["K"], w["L"], seed=6)
+    ids = det.insert(w["X"])
+    counts = np.zeros_like(det.counts)
+    mu_inc, _ = oracle.mu_incremental(ids, counts, w["K"])
+    assert np.array_equal(counts, det.counts)
+    Q = det.q()
+    assert Q == int(np.sum(det.counts.astype(np.int64) ** 2))
+    mu_q = det.stats()["mu_ins"]
+    sums = oracle.gather(ids, det.counts, w["K"])
+    mu_scores = float(np.mean(sums.astype(np.float64) / w["L"]))
+    assert mu_q == pytest.approx(mu_scores, rel=1e-14)
+    assert mu_inc == pytest.approx(mu_q, rel=1e-12)
+    assert int(sums.sum()) == Q  # sum over points of their counts = sum over buckets of count^2
+
+
+def test_power_of_two_scaling_invariance():
+    rng = np.random.default_rng(12)
+    X = rng.standard_normal((50, 20)).astype(np.float32)
+    W = workloads.gaussian_w(20, 6, 5, 1)
+    base = oracle.hash_ids(X, W, 6, 5)
+    for k in (-7, -1, 3, 20):
+        assert np.array_equal(oracle.hash_ids(X * np.float32(2.0**k), W, 6, 5), base)
+
+
+def test_negation_flips_nonzero_bits():
+    rng = np.random.default_rng(13)
+    X = rng.standard_normal((40, 8)).astype(np.float32)
+    X[0] = 0.0
+    X[1, :] = [1, 1, 1, 0, 0, 0, 0, 0]
+    W = workloads.gaussian_w(8, 5, 6, 2)
+    W[:, 0] = [1, -1, 0, 0, 0, 0, 0, 0]  # x[1] projects to exactly 0 on column 0
+    K, L = 5, 6
+    s = oracle.project(X, W)
+    a = oracle.hash_ids(X, W, K, L)
+    b = oracle.hash_ids(-X, W, K, L)
+    ba = ((a[:, :, None] >> np.arange(K, dtype=np.uint32)) & 1).reshape(40, K * L)
+    bb = ((b[:, :, None] >> np.arange(K, dtype=np.uint32)) & 1).reshape(40, K * L)
+    nz = s != 0
+    assert np.all(ba[nz] + bb[nz] == 1)
+    assert np.all(ba[~nz] == 0) and np.all(bb[~nz] == 0)
+    assert np.all(a[0] == 0)  # the zero vector goes to bucket 0 of every array
+    assert ba[1, 0] == 0 and bb[1, 0] == 0
+
+
+def test_stats_match_numpy_mean_and_population_std():
+    w = workloads.small(seed=8, n=5000)
+    det = oracle.Detector(w["d"], w["K"], w["L"], seed=9)
+    scores, sums, flags = det.insert_score(w["X"], 1.0)
+    st = det.stats(1.0)
+    assert st["mu"] == pytest.approx(float(np.mean(scores)), rel=1e-13)
+    assert st["sigma"] == pytest.approx(float(np.std(scores)), rel=1e-12)
+    assert st["threshold"] == pytest.approx(st["mu"] - st["sigma"], rel=1e-15)
+    assert np.array_equal(flags.astype(bool), scores < st["threshold"])
+    # with "insert everything, then score everything", mu equals the inserted-set mean
+    assert st["mu"] == pytest.approx(st["mu_ins"], rel=1e-14)
+
+
+def test_running_stats_span_batches():
+    w = workloads.small(seed=10, n=3000)
+    det = oracle.Detector(w["d"], w["K"], w["L"], seed=11)
+    det.insert(w["X"])
+    s1, _, _ = det.score(w["X"][:1000], 2.0)
+    s2, _, f2 = det.score(w["X"][1000:], 2.0)
+    allsc = np.concatenate([s1, s2])
+    st = det.stats(2.0)
+    assert st["n_scored"] == 3000
+    assert st["mu"] == pytest.approx(float(allsc.mean()), rel=1e-13)
+    assert st["sigma"] == pytest.approx(float(allsc.std()), rel=1e-12)
+    assert np.array_equal(f2.astype(bool), s2 < st["threshold"])
+
+
+def test_score_does_not_insert_and_insert_score_order():
+    w = workloads.small(seed=12, n=1000)
+    a = oracle.Detector(w["d"], w["K"], w["L"], seed=13)
+    a.score(w["X"], 1.0)
+    assert int(a.counts.sum()) == 0 and a.n_ins == 0
+    b = oracle.Detector(w["d"], w["K"], w["L"], seed=13)
+    c = oracle.Detector(w["d"], w["K"], w["L"], seed=13)
+    sb, ub, fb = b.insert_score(w["X"], 1.0)
+    c.insert(w["X"])
+    sc, uc, fc = c.score(w["X"], 1.0)
+    assert np.array_equal(ub, uc) and np.array_equal(fb, fc)
+
+
+def test_insert_order_independent():
+    w = workloads.small(seed=14, n=1500)
+    a = oracle.Detector(w["d"], w["K"], w["L"], seed=15)
+    b = oracle.Detector(w["d"], w["K"], w["L"], seed=15)
+    a.insert(w["X"])
+    b.insert(w["X"][::-1].copy())
+    assert np.array_equal(a.counts, b.counts)
+
+
+def test_empty_batch_and_overflow():
+    det = oracle.Detector(4, 3, 2, seed=1)
+    ids = det.insert(np.zeros((0, 4), dtype=np.float32))
+    assert ids.shape == (0, 2) and int(det.counts.sum()) == 0
+    det.counts[0, 0] = np.uint32(2**32 - 1)
+    before = det.counts.copy()
+    with pytest.raises(OverflowError):
+        det.insert(np.zeros((1, 4), dtype=np.float32))  # the zero vector hits bucket 0
+    assert np.array_equal(det.counts, before)
+
+
+def test_bf16_inputs_hash_like_their_float32_values():
+    rng = np.random.default_rng(21)
+    Xf = rng.standard_normal((64, 48)).astype(np.float32)
+    Xb = workloads.to_bf16_bits(Xf)
+    W = workloads.gaussian_w(48, 8, 4, 5)
+    a = oracle.hash_ids(Xb, W, 8, 4)
+    b = oracle.hash_ids(workloads.bf16_bits_to_f32(Xb), W, 8, 4)
+    assert np.array_equal(a, b)
+
+
+def test_nonfinite_inputs_follow_binary64_semantics():
+    # NaN anywhere makes every projection NaN, and NaN > 0 is false: bucket 0 everywhere.
+    W = workloads.gaussian_w(5, 4, 3, 8)
+    X = np.zeros((2, 5), dtype=np.float32)
+    X[0, 2] = np.nan
+    X[1, 0] = np.inf
+    ids = oracle.hash_ids(X, W, 4, 3)
+    assert np.all(ids[0] == 0)
+    bits = ((ids[1][:, None] >> np.arange(4, dtype=np.uint32)) & 1).ravel()
+    expect = (W[0] > 0).astype(np.uint32)  # inf * w has the sign of w (w != 0)
+    assert np.array_equal(bits, expect)
