@@ -1,0 +1,178 @@
+/*
+ * ace.h — C ABI of the GB300 (sm_103a) ACE hot path.
+ *
+ * ACE (Arrays of locality-sensitive Count Estimators; Luo & Shrivastava) keeps L arrays
+ * A_1..A_L of 2^K counters.  A point x is hashed by K*L signed random projections
+ * (Eq. 1: h_w(x) = sign(w^T x), w ~ N(0, I)); each group of K bits forms a bucket id
+ * H_j(x) (Eq. 2).  Inserting x increments A_j[H_j(x)] for every j (Algorithm 1,
+ * pre-processing phase, §3.2); the score of a query q is (1/L) sum_j A_j[H_j(q)]
+ * (Algorithm 1, query phase, §3.2); a point is reported when its score is below
+ * mu - alpha*sigma of the scores (§5.3 uses alpha = 1).
+ *
+ * Definitions this library computes exactly (the same as the project's CPU reference):
+ *   - SRP bit of column c for point x:  [ s > 0 ], s = the binary64 sum, in index order
+ *     i = 0..d-1, of (double)x_i * (double)W[i][c].  A zero projection gives bit 0.
+ *   - bucket id  H_j(x) = sum_{k<K} bit(c = j*K + k) * 2^k   (first bit is the LSB).
+ *   - counts are uint32; sums c = sum_j A_j[H_j(q)] are uint32; scores are c / L (binary64).
+ *   - mu = S1/(N L), sigma = sqrt(N S2 - S1^2)/(N L), threshold = mu - alpha*sigma, where
+ *     N, S1 = sum c, S2 = sum c^2 run over every point scored by this detector, the
+ *     current call included; flag = score < threshold.  Each is one correctly rounded
+ *     binary64 operation on exact integers, so the values are bit-reproducible.
+ * The projection itself runs in binary32 (SIMT) or bfloat16 (tensor cores) with a
+ * rigorous error bound; every projection whose magnitude is inside the bound is recomputed
+ * in binary64 in index order, so bucket ids never depend on the fast path.
+ *
+ * Conventions
+ *   - Every device pointer is a CUDA global-memory address on the detector's device,
+ *     row-major and contiguous, aligned to its element size; the caller owns it.
+ *   - X is n x d: binary32 (ACE_F32) or bfloat16 bit patterns (ACE_BF16).
+ *   - Calls that take a stream are asynchronous on it (a cudaStream_t; NULL = legacy
+ *     default stream).  Only ace_stats, ace_get_counts, ace_get_projection and the *_host
+ *     entry points block, and they block on that stream only.
+ *   - A handle may be used from one host thread at a time; calls on one handle must be
+ *     ordered (same stream, or the caller orders the streams).
+ *   - Every function returns ACE_OK or an error code; ace_last_error() gives this
+ *     thread's last message.  No C++ exception crosses the ABI.  On any error other than
+ *     ACE_ERR_CUDA the detector's state is unchanged.
+ */
+#ifndef ACE_GB300_H
+#define ACE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ace_detector* ace_handle;
+
+enum {
+  ACE_OK = 0,
+  ACE_ERR_ARG = 1,      /* invalid argument (sizes, null pointer, dtype)                */
+  ACE_ERR_OOM = 2,      /* a device or host allocation failed                           */
+  ACE_ERR_OVERFLOW = 3, /* a count, a per-point sum or N*S2 would not fit its width     */
+  ACE_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up                           */
+  ACE_ERR_CUDA = 5,     /* a CUDA runtime call failed (message in ace_last_error)       */
+  ACE_ERR_UNSUPPORTED = 6 /* the requested path is not available for this shape/device  */
+};
+
+enum { ACE_F32 = 0, ACE_BF16 = 1 };
+
+/* Projection precision (the sign bits are exact on every path; this picks the engine). */
+enum {
+  ACE_PROJ_AUTO = -1, /* fastest available path for the detector's shape (default)       */
+  ACE_PROJ_FP32 = 0,  /* binary32 FMA on the SIMT cores                                   */
+  ACE_PROJ_BF16 = 1   /* bfloat16 split operands on tcgen05 tensor cores, binary32 accum.  */
+};
+
+/* Device-status bits reported by ace_stats (sticky until ace_reset). */
+enum {
+  ACE_STATUS_SUM_OVERFLOW = 1u, /* some per-point sum c did not fit in uint32            */
+  ACE_STATUS_TIMEOUT = 2u       /* a bounded device wait gave up                          */
+};
+
+typedef struct {
+  uint64_t n_ins;           /* points inserted                                          */
+  uint64_t n_scored;        /* N: points scored (every score / insert_score call)       */
+  uint64_t Q_lo, Q_hi;      /* Q = sum_j sum_b A_j[b]^2 (128-bit)                       */
+  uint64_t S1_lo, S1_hi;    /* S1 = sum of per-point sums c over scored points           */
+  uint64_t S2_lo, S2_hi;    /* S2 = sum of c^2                                           */
+  double mu_ins;            /* mean score of the inserted set: Q / (n_ins L) (Eq. 11)    */
+  double mu;                /* S1 / (N L)                                                */
+  double sigma;             /* sqrt(N S2 - S1^2) / (N L), population                     */
+  uint64_t rechecks;        /* projections recomputed in binary64 (inside the bound)     */
+  uint64_t nonfinite_points;/* points with a NaN/Inf coordinate or an overflowing norm   */
+  uint32_t status;          /* ACE_STATUS_* bits                                         */
+  int32_t precision;        /* ACE_PROJ_* path used by the last hash                     */
+} ace_stats_t;
+
+/*
+ * ace_create — Algorithm 1 "Hash Initialize" (§3.2) and array allocation.
+ * Draws the d x (K*L) projection matrix W, w ~ N(0,1) (§2.1), from `seed` with SplitMix64
+ * in counter mode (draw t = SplitMix64 output for state seed + (t+1)*0x9E3779B97F4A7C15)
+ * and Box-Muller on pairs of draws (u1 = (draw_2p >> 11) + 1) * 2^-53, u2 = (draw_2p+1 >> 11)
+ * * 2^-53, r = sqrt(-2 ln u1), W.flat[2p] = r cos(2 pi u2), W.flat[2p+1] = r sin(2 pi u2),
+ * each rounded to binary32; W.flat[i*K*L + c] = W[i][c]), and zeroes L arrays of 2^K
+ * uint32 counters on the current CUDA device.
+ * Limits: d >= 1, 1 <= K <= 24, L >= 1, K*L <= 65536.  *out receives the handle.
+ * Errors: ACE_ERR_ARG, ACE_ERR_OOM, ACE_ERR_CUDA.
+ */
+int ace_create(int d, int K, int L, uint64_t seed, ace_handle* out);
+
+/* As ace_create, with an explicit host d x (K*L) row-major binary32 W (copied). */
+int ace_create_with_projection(int d, int K, int L, const float* W_host, ace_handle* out);
+
+/* Frees the handle and its device memory (synchronises the device first).  NULL is ok. */
+int ace_destroy(ace_handle h);
+
+/* Zeroes the arrays and every running statistic; keeps W.  Asynchronous on `stream`. */
+int ace_reset(ace_handle h, void* stream);
+
+/* Selects the projection engine (ACE_PROJ_*).  Results do not depend on it. */
+int ace_set_precision(ace_handle h, int precision);
+
+/*
+ * ace_insert — counting phase (Algorithm 1 pre-processing; §3.2 "Counting Phase"):
+ * for every point x of X (n x d), A_j[H_j(x)] += 1 for j = 1..L.  The result does not
+ * depend on the order of the points.  n = 0 is a no-op.
+ * Errors: ACE_ERR_ARG; ACE_ERR_OVERFLOW if n_ins + n would exceed 2^32 - 1 (a count could
+ * then overflow; nothing is inserted); ACE_ERR_CUDA.
+ */
+int ace_insert(ace_handle h, const void* X_dev, int64_t n, int dtype, void* stream);
+
+/*
+ * ace_score — query phase (Algorithm 1; §3.2 "Real-time (query) Phase") and the §5.3
+ * threshold rule, against the arrays as they stand at the start of the call (scoring
+ * never inserts).  For each point: sums_dev[i] = c_i = sum_j A_j[H_j(x_i)] (uint32),
+ * scores_dev[i] = c_i / L (binary64), flags_dev[i] = 1 if scores_dev[i] < mu - alpha*sigma
+ * else 0, with mu and sigma over every point scored so far including this call.
+ * Any of the three outputs may be NULL.  Errors: ACE_ERR_ARG, ACE_ERR_OOM, ACE_ERR_CUDA.
+ */
+int ace_score(ace_handle h, const void* X_dev, int64_t n, int dtype, double alpha,
+              double* scores_dev, uint32_t* sums_dev, uint8_t* flags_dev, void* stream);
+
+/* Inserts the whole batch, then scores it against the updated arrays (same outputs). */
+int ace_insert_score(ace_handle h, const void* X_dev, int64_t n, int dtype, double alpha,
+                     double* scores_dev, uint32_t* sums_dev, uint8_t* flags_dev, void* stream);
+
+/*
+ * ace_insert_score_host — ace_insert_score on HOST buffers: X_host (n x d, pinned or
+ * pageable) is copied to the device, processed, and the outputs copied back to host
+ * (any of them may be NULL).  Blocks until the outputs are in host memory.
+ */
+int ace_insert_score_host(ace_handle h, const void* X_host, int64_t n, int dtype, double alpha,
+                          double* scores_host, uint32_t* sums_host, uint8_t* flags_host,
+                          void* stream);
+
+/*
+ * ace_hash — Eq. 1 + Eq. 2 only: ids_dev[i*L + j] = H_j(x_i) (uint32, n x L).  No state
+ * changes except the recheck counter.
+ */
+int ace_hash(ace_handle h, const void* X_dev, int64_t n, int dtype, uint32_t* ids_dev,
+             void* stream);
+
+/* Synchronises `stream`, then fills *out (Q is computed from the arrays here). */
+int ace_stats(ace_handle h, void* stream, ace_stats_t* out);
+
+/* Copies the L x 2^K counts (row j = A_j) to host memory.  Synchronises `stream`. */
+int ace_get_counts(ace_handle h, uint32_t* counts_host, void* stream);
+
+/* Copies the d x (K*L) binary32 W to host memory. */
+int ace_get_projection(ace_handle h, float* W_host);
+
+/* Detector shape. */
+int ace_get_shape(ace_handle h, int* d, int* K, int* L);
+
+/* This thread's last error message ("" if none).  The pointer stays valid until the
+ * next call on this thread. */
+const char* ace_last_error(void);
+
+/* Library version string. */
+const char* ace_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ACE_GB300_H */

@@ -1,0 +1,240 @@
+"""ctypes binding of the C ABI in include/ace.h (argument marshalling only).
+
+Every step of the hot path runs in the CUDA library; torch is used for device buffers and
+streams.  If the library has not been built, the first call raises — there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libace_gb300.so")
+
+ACE_OK, ACE_ERR_ARG, ACE_ERR_OOM, ACE_ERR_OVERFLOW, ACE_ERR_TIMEOUT, ACE_ERR_CUDA, ACE_ERR_UNSUPPORTED = range(7)
+ACE_F32, ACE_BF16 = 0, 1
+ACE_PROJ_AUTO, ACE_PROJ_FP32, ACE_PROJ_BF16 = -1, 0, 1
+PRECISIONS = {"auto": ACE_PROJ_AUTO, "fp32": ACE_PROJ_FP32, "bf16": ACE_PROJ_BF16}
+
+# Every symbol include/ace.h declares (checked by the tests).
+EXPORTS = [
+    "ace_create", "ace_create_with_projection", "ace_destroy", "ace_reset", "ace_set_precision",
+    "ace_insert", "ace_score", "ace_insert_score", "ace_insert_score_host", "ace_hash", "ace_stats",
+    "ace_get_counts", "ace_get_projection", "ace_get_shape", "ace_last_error", "ace_version",
+]
+
+
+class AceError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"ace error {code}: {msg}")
+        self.code = code
+
+
+class ace_stats_t(ctypes.Structure):
+    _fields_ = [
+        ("n_ins", ctypes.c_uint64), ("n_scored", ctypes.c_uint64),
+        ("Q_lo", ctypes.c_uint64), ("Q_hi", ctypes.c_uint64),
+        ("S1_lo", ctypes.c_uint64), ("S1_hi", ctypes.c_uint64),
+        ("S2_lo", ctypes.c_uint64), ("S2_hi", ctypes.c_uint64),
+        ("mu_ins", ctypes.c_double), ("mu", ctypes.c_double), ("sigma", ctypes.c_double),
+        ("rechecks", ctypes.c_uint64), ("nonfinite_points", ctypes.c_uint64),
+        ("status", ctypes.c_uint32), ("precision", ctypes.c_int32),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libace_gb300.so and declares the ABI (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+        lib = ctypes.CDLL(path)
+        P, i32, i64, u64, f64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        H = ctypes.c_void_p
+        decl = {
+            "ace_create": ([i32, i32, i32, u64, ctypes.POINTER(H)], i32),
+            "ace_create_with_projection": ([i32, i32, i32, P, ctypes.POINTER(H)], i32),
+            "ace_destroy": ([H], i32),
+            "ace_reset": ([H, P], i32),
+            "ace_set_precision": ([H, i32], i32),
+            "ace_insert": ([H, P, i64, i32, P], i32),
+            "ace_score": ([H, P, i64, i32, f64, P, P, P, P], i32),
+            "ace_insert_score": ([H, P, i64, i32, f64, P, P, P, P], i32),
+            "ace_insert_score_host": ([H, P, i64, i32, f64, P, P, P, P], i32),
+            "ace_hash": ([H, P, i64, i32, P, P], i32),
+            "ace_stats": ([H, P, ctypes.POINTER(ace_stats_t)], i32),
+            "ace_get_counts": ([H, P, P], i32),
+            "ace_get_projection": ([H, P], i32),
+            "ace_get_shape": ([H, P, P, P], i32),
+            "ace_last_error": ([], ctypes.c_char_p),
+            "ace_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in decl.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != ACE_OK:
+        raise AceError(rc, _lib.ace_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _x_dtype(X):
+    torch = _torch()
+    if X.dtype == torch.float32:
+        return ACE_F32
+    if X.dtype in (torch.bfloat16, torch.int16, torch.uint16):
+        return ACE_BF16
+    raise TypeError("X must be float32 or bfloat16 (or int16/uint16 bfloat16 bit patterns)")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+class Detector:
+    """One ACE detector (W, L count arrays of 2^K uint32, running score statistics) on the
+    current CUDA device."""
+
+    def __init__(self, d: int, K: int, L: int, seed: int = 0, W: np.ndarray | None = None,
+                 precision: str = "auto"):
+        lib = load_library()
+        self.d, self.K, self.L = int(d), int(K), int(L)
+        h = ctypes.c_void_p()
+        if W is None:
+            _check(lib.ace_create(self.d, self.K, self.L, ctypes.c_uint64(int(seed) & (2**64 - 1)), ctypes.byref(h)))
+        else:
+            Wc = np.ascontiguousarray(W, dtype=np.float32)
+            assert Wc.shape == (self.d, self.K * self.L)
+            _check(lib.ace_create_with_projection(self.d, self.K, self.L, Wc.ctypes.data_as(ctypes.c_void_p),
+                                                  ctypes.byref(h)))
+        self._h = h
+        self.set_precision(precision)
+
+    # -- lifecycle ---------------------------------------------------------------------
+    def close(self):
+        if self._h is not None and self._h.value:
+            load_library().ace_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_precision(self, precision):
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        _check(load_library().ace_set_precision(self._h, p))
+
+    def reset(self, stream=None):
+        _check(load_library().ace_reset(self._h, _stream_ptr(stream)))
+
+    # -- hot path ------------------------------------------------------------------------
+    def _xcheck(self, X):
+        assert X.is_cuda and X.is_contiguous() and X.dim() == 2 and X.shape[1] == self.d, "X must be n x d on CUDA"
+
+    def insert(self, X, stream=None):
+        self._xcheck(X)
+        _check(load_library().ace_insert(self._h, _ptr(X), X.shape[0], _x_dtype(X), _stream_ptr(stream)))
+
+    def _outs(self, n, scores, sums, flags, device):
+        torch = _torch()
+        sc = torch.empty(n, dtype=torch.float64, device=device) if scores is True else (scores or None)
+        su = torch.empty(n, dtype=torch.int32, device=device) if sums is True else (sums or None)
+        fl = torch.empty(n, dtype=torch.uint8, device=device) if flags is True else (flags or None)
+        return sc, su, fl
+
+    def score(self, X, alpha: float = 1.0, scores=True, sums=True, flags=True, stream=None):
+        """Returns (scores float64, sums int32 holding uint32 bits, flags uint8) tensors."""
+        self._xcheck(X)
+        sc, su, fl = self._outs(X.shape[0], scores, sums, flags, X.device)
+        _check(load_library().ace_score(self._h, _ptr(X), X.shape[0], _x_dtype(X), float(alpha), _ptr(sc),
+                                        _ptr(su), _ptr(fl), _stream_ptr(stream)))
+        return sc, su, fl
+
+    def insert_score(self, X, alpha: float = 1.0, scores=True, sums=True, flags=True, stream=None):
+        self._xcheck(X)
+        sc, su, fl = self._outs(X.shape[0], scores, sums, flags, X.device)
+        _check(load_library().ace_insert_score(self._h, _ptr(X), X.shape[0], _x_dtype(X), float(alpha), _ptr(sc),
+                                               _ptr(su), _ptr(fl), _stream_ptr(stream)))
+        return sc, su, fl
+
+    def insert_score_host(self, X: np.ndarray, alpha: float = 1.0, scores=None, sums=None, flags=None,
+                          stream=None):
+        """Host buffers in, host buffers out (copies are part of the call)."""
+        n = X.shape[0]
+        dt = ACE_F32 if X.dtype == np.float32 else ACE_BF16
+        if X.dtype not in (np.float32, np.uint16):
+            raise TypeError("X must be float32 or uint16 bfloat16 bits")
+
+        def p(a):
+            return ctypes.c_void_p(a.ctypes.data) if a is not None else ctypes.c_void_p(0)
+
+        _check(load_library().ace_insert_score_host(self._h, ctypes.c_void_p(X.ctypes.data), n, dt, float(alpha),
+                                                    p(scores), p(sums), p(flags), _stream_ptr(stream)))
+        return scores, sums, flags
+
+    def hash(self, X, stream=None):
+        """n x L bucket ids (int32 tensor holding uint32 values)."""
+        self._xcheck(X)
+        torch = _torch()
+        ids = torch.empty((X.shape[0], self.L), dtype=torch.int32, device=X.device)
+        _check(load_library().ace_hash(self._h, _ptr(X), X.shape[0], _x_dtype(X), _ptr(ids), _stream_ptr(stream)))
+        return ids
+
+    # -- introspection -----------------------------------------------------------------
+    def stats(self, stream=None) -> dict:
+        st = ace_stats_t()
+        _check(load_library().ace_stats(self._h, _stream_ptr(stream), ctypes.byref(st)))
+        return {
+            "n_ins": st.n_ins, "n_scored": st.n_scored,
+            "Q": st.Q_lo | (st.Q_hi << 64), "S1": st.S1_lo | (st.S1_hi << 64), "S2": st.S2_lo | (st.S2_hi << 64),
+            "mu_ins": st.mu_ins, "mu": st.mu, "sigma": st.sigma, "rechecks": st.rechecks,
+            "nonfinite_points": st.nonfinite_points, "status": st.status, "precision": st.precision,
+        }
+
+    def counts(self, stream=None) -> np.ndarray:
+        out = np.empty((self.L, 1 << self.K), dtype=np.uint32)
+        _check(load_library().ace_get_counts(self._h, ctypes.c_void_p(out.ctypes.data), _stream_ptr(stream)))
+        return out
+
+    def projection(self) -> np.ndarray:
+        out = np.empty((self.d, self.K * self.L), dtype=np.float32)
+        _check(load_library().ace_get_projection(self._h, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+
+def u32(t) -> np.ndarray:
+    """int32 tensor holding uint32 bit patterns -> numpy uint32."""
+    return t.cpu().numpy().view(np.uint32)

@@ -1,0 +1,432 @@
+// C ABI and host runtime: detector handles, device memory, guard constants, launches.
+#include <cfloat>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ace_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(ACE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define ACE_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+}  // namespace
+
+struct ace_detector {
+  int d = 0, K = 0, L = 0, KL = 0, device = 0;
+  int precision = ACE_PROJ_AUTO;
+  int last_precision = ACE_PROJ_FP32;
+  float* W = nullptr;       // [d][KL]
+  float* Wt = nullptr;      // [KL][d]
+  float* cB = nullptr;      // [KL]
+  float xfac = 1.f, xabs = 0.f, babs = 0.f;
+  uint32_t* counts = nullptr;  // [L][2^K]
+  ace::DevStats* st = nullptr;
+  void* ids = nullptr;
+  size_t ids_cap = 0;  // bytes
+  uint32_t* sums = nullptr;
+  size_t sums_cap = 0;  // elements
+  void* xstage = nullptr;
+  size_t xstage_cap = 0;  // bytes
+  double* scstage = nullptr;
+  uint8_t* flstage = nullptr;
+  size_t stage_cap = 0;  // elements
+  uint64_t n_ins = 0;
+  std::vector<float> Wh;  // host copy of W
+};
+
+namespace {
+
+size_t count_elems(const ace_detector* h) { return (static_cast<size_t>(1) << h->K) * static_cast<size_t>(h->L); }
+
+void free_all(ace_detector* h) {
+  cudaFree(h->W);
+  cudaFree(h->Wt);
+  cudaFree(h->cB);
+  cudaFree(h->counts);
+  cudaFree(h->st);
+  cudaFree(h->ids);
+  cudaFree(h->sums);
+  cudaFree(h->xstage);
+  cudaFree(h->scstage);
+  cudaFree(h->flstage);
+}
+
+// Guard constants of the binary32 paths (see hash_simt.cu): both gammas, ||w_c|| rounded
+// up, and a 2% margin that covers the few binary32 roundings of the bound itself.
+void guard_constants(const std::vector<float>& W, int d, int KL, std::vector<float>& cB, float& xfac, float& xabs,
+                     float& babs) {
+  const double u32 = std::ldexp(1.0, -24), u64 = std::ldexp(1.0, -53);
+  const double g32 = d * u32 / (1.0 - d * u32);
+  const double g64 = d * u64 / (1.0 - d * u64);
+  const double gam = (g32 + g64) * 1.02;
+  cB.resize(KL);
+  for (int c = 0; c < KL; ++c) {
+    double s = 0.0;
+    for (int i = 0; i < d; ++i) {
+      const double w = W[static_cast<size_t>(i) * KL + c];
+      s += w * w;
+    }
+    const double nw = std::sqrt(s) * (1.0 + 1e-12);
+    cB[c] = std::nextafter(static_cast<float>(gam * nw), FLT_MAX);
+  }
+  xfac = std::nextafter(static_cast<float>(1.0 + 2.0 * g32 + std::ldexp(1.0, -20)), FLT_MAX);
+  xabs = static_cast<float>(std::ldexp(static_cast<double>(d), -149));
+  babs = static_cast<float>(std::ldexp(static_cast<double>(d), -148));
+  if (xabs == 0.f) xabs = std::ldexp(1.0f, -149);
+  if (babs == 0.f) babs = std::ldexp(1.0f, -148);
+}
+
+int make_detector(int d, int K, int L, const float* Wsrc, uint64_t seed, bool from_seed, ace_handle* out) {
+  if (!out) return fail(ACE_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (d < 1 || K < 1 || K > 24 || L < 1 || static_cast<long long>(K) * L > 65536)
+    return fail(ACE_ERR_ARG, "invalid shape d=%d K=%d L=%d (need d>=1, 1<=K<=24, L>=1, K*L<=65536)", d, K, L);
+  if (!from_seed && !Wsrc) return fail(ACE_ERR_ARG, "W_host is NULL");
+  ace_detector* h = new (std::nothrow) ace_detector();
+  if (!h) return fail(ACE_ERR_OOM, "host allocation failed");
+  h->d = d;
+  h->K = K;
+  h->L = L;
+  h->KL = K * L;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  const size_t dkl = static_cast<size_t>(d) * h->KL;
+  try {
+    h->Wh.resize(dkl);
+  } catch (...) {
+    delete h;
+    return fail(ACE_ERR_OOM, "host allocation of W failed");
+  }
+  if (from_seed) ace::generate_projection(d, K, L, seed, h->Wh.data());
+  else std::memcpy(h->Wh.data(), Wsrc, dkl * sizeof(float));
+  for (size_t i = 0; i < dkl; ++i)
+    if (!std::isfinite(h->Wh[i])) {
+      delete h;
+      return fail(ACE_ERR_ARG, "W has a non-finite entry at flat index %zu", i);
+    }
+  std::vector<float> Wt(dkl), cB;
+  for (int i = 0; i < d; ++i)
+    for (int c = 0; c < h->KL; ++c) Wt[static_cast<size_t>(c) * d + i] = h->Wh[static_cast<size_t>(i) * h->KL + c];
+  guard_constants(h->Wh, d, h->KL, cB, h->xfac, h->xabs, h->babs);
+
+  auto bad = [&](cudaError_t err, const char* what) {
+    free_all(h);
+    delete h;
+    return err == cudaErrorMemoryAllocation ? fail(ACE_ERR_OOM, "%s: out of device memory", what)
+                                            : cuda_fail(err, what);
+  };
+  if ((e = cudaMalloc(&h->W, dkl * sizeof(float))) != cudaSuccess) return bad(e, "cudaMalloc W");
+  if ((e = cudaMalloc(&h->Wt, dkl * sizeof(float))) != cudaSuccess) return bad(e, "cudaMalloc Wt");
+  if ((e = cudaMalloc(&h->cB, h->KL * sizeof(float))) != cudaSuccess) return bad(e, "cudaMalloc cB");
+  if ((e = cudaMalloc(&h->counts, count_elems(h) * sizeof(uint32_t))) != cudaSuccess) return bad(e, "cudaMalloc counts");
+  if ((e = cudaMalloc(&h->st, sizeof(ace::DevStats))) != cudaSuccess) return bad(e, "cudaMalloc stats");
+  if ((e = cudaMemcpy(h->W, h->Wh.data(), dkl * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bad(e, "copy W");
+  if ((e = cudaMemcpy(h->Wt, Wt.data(), dkl * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bad(e, "copy Wt");
+  if ((e = cudaMemcpy(h->cB, cB.data(), h->KL * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bad(e, "copy cB");
+  if ((e = cudaMemset(h->counts, 0, count_elems(h) * sizeof(uint32_t))) != cudaSuccess) return bad(e, "zero counts");
+  if ((e = cudaMemset(h->st, 0, sizeof(ace::DevStats))) != cudaSuccess) return bad(e, "zero stats");
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bad(e, "create sync");
+  *out = h;
+  return ACE_OK;
+}
+
+int check_x(ace_handle h, const void* X, long long n, int dtype) {
+  if (!h) return fail(ACE_ERR_ARG, "handle is NULL");
+  if (n < 0) return fail(ACE_ERR_ARG, "n < 0");
+  if (dtype != ACE_F32 && dtype != ACE_BF16) return fail(ACE_ERR_ARG, "unknown dtype %d", dtype);
+  if (n > 0 && !X) return fail(ACE_ERR_ARG, "X is NULL");
+  const size_t esz = dtype == ACE_F32 ? 4 : 2;
+  if (reinterpret_cast<uintptr_t>(X) % esz) return fail(ACE_ERR_ARG, "X is not aligned to its element size");
+  if (n > (1LL << 40)) return fail(ACE_ERR_ARG, "n too large");
+  return ACE_OK;
+}
+
+// Grow a device buffer (synchronises `s` before freeing the old one).
+int grow(void** p, size_t* cap, size_t need, cudaStream_t s, const char* what) {
+  if (need <= *cap) return ACE_OK;
+  size_t ncap = need + need / 2;
+  if (*p) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+  }
+  cudaError_t e = cudaMalloc(p, ncap);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    if (e == cudaErrorMemoryAllocation) return fail(ACE_ERR_OOM, "%s: out of device memory (%zu bytes)", what, ncap);
+    return cuda_fail(e, what);
+  }
+  *cap = ncap;
+  return ACE_OK;
+}
+
+ace::HashArgs hash_args(ace_handle h, const void* X, long long n, int dtype, int mode) {
+  ace::HashArgs a{};
+  a.X = X;
+  a.x_bf16 = dtype == ACE_BF16;
+  a.n = n;
+  a.d = h->d;
+  a.K = h->K;
+  a.L = h->L;
+  a.KL = h->KL;
+  a.W = h->W;
+  a.Wt = h->Wt;
+  a.cB = h->cB;
+  a.xfac = h->xfac;
+  a.xabs = h->xabs;
+  a.babs = h->babs;
+  a.mode = mode;
+  a.ids = h->ids;
+  a.ld = n;
+  a.ids_rm = nullptr;
+  a.counts = h->counts;
+  a.st = h->st;
+  return a;
+}
+
+size_t id_bytes(ace_handle h) { return h->K <= 16 ? 2 : 4; }
+
+int run_hash(ace_handle h, const ace::HashArgs& a, cudaStream_t s) {
+  h->last_precision = ACE_PROJ_FP32;
+  cudaError_t e = ace::launch_hash_simt(a, s);
+  if (e != cudaSuccess) return cuda_fail(e, "hash kernel launch");
+  return ACE_OK;
+}
+
+int score_common(ace_handle h, const void* X, long long n, int dtype, double alpha, double* scores, uint32_t* sums,
+                 uint8_t* flags, cudaStream_t s, bool insert) {
+  int rc = check_x(h, X, n, dtype);
+  if (rc) return rc;
+  if (!std::isfinite(alpha)) return fail(ACE_ERR_ARG, "alpha must be finite");
+  if (insert && h->n_ins + static_cast<uint64_t>(n) > 0xFFFFFFFFull)
+    return fail(ACE_ERR_OVERFLOW, "inserting %lld points would allow a count above 2^32-1", n);
+  if (n == 0) return ACE_OK;
+  if ((rc = grow(&h->ids, &h->ids_cap, static_cast<size_t>(n) * h->L * id_bytes(h), s, "ids scratch"))) return rc;
+  uint32_t* sum_out = sums;
+  if (!sum_out) {
+    void* p = h->sums;
+    if ((rc = grow(&p, &h->sums_cap, static_cast<size_t>(n) * sizeof(uint32_t), s, "sums scratch"))) return rc;
+    h->sums = static_cast<uint32_t*>(p);
+    sum_out = h->sums;
+  }
+  ace::HashArgs a = hash_args(h, X, n, dtype, ace::kStoreIds | (insert ? ace::kInsert : 0));
+  if ((rc = run_hash(h, a, s))) return rc;
+  if (insert) h->n_ins += static_cast<uint64_t>(n);
+  cudaError_t e = ace::launch_score_gather(h->ids, h->K <= 16, n, n, h->K, h->L, h->counts, sum_out, h->st, s);
+  if (e != cudaSuccess) return cuda_fail(e, "score kernel launch");
+  e = ace::launch_flags(sum_out, (scores || flags) ? n : 0, h->L, alpha, h->st, scores, flags, s);
+  if (e != cudaSuccess) return cuda_fail(e, "flags kernel launch");
+  return ACE_OK;
+}
+
+using u128 = unsigned __int128;
+
+}  // namespace
+
+extern "C" {
+
+int ace_create(int d, int K, int L, uint64_t seed, ace_handle* out) {
+  return make_detector(d, K, L, nullptr, seed, true, out);
+}
+
+int ace_create_with_projection(int d, int K, int L, const float* W_host, ace_handle* out) {
+  return make_detector(d, K, L, W_host, 0, false, out);
+}
+
+int ace_destroy(ace_handle h) {
+  if (!h) return ACE_OK;
+  cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+  return ACE_OK;
+}
+
+int ace_reset(ace_handle h, void* stream) {
+  if (!h) return fail(ACE_ERR_ARG, "handle is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ACE_CUDA(cudaMemsetAsync(h->counts, 0, count_elems(h) * sizeof(uint32_t), s));
+  ACE_CUDA(cudaMemsetAsync(h->st, 0, sizeof(ace::DevStats), s));
+  h->n_ins = 0;
+  return ACE_OK;
+}
+
+int ace_set_precision(ace_handle h, int precision) {
+  if (!h) return fail(ACE_ERR_ARG, "handle is NULL");
+  if (precision != ACE_PROJ_AUTO && precision != ACE_PROJ_FP32 && precision != ACE_PROJ_BF16)
+    return fail(ACE_ERR_ARG, "unknown precision %d", precision);
+  h->precision = precision;
+  return ACE_OK;
+}
+
+int ace_insert(ace_handle h, const void* X_dev, int64_t n, int dtype, void* stream) {
+  int rc = check_x(h, X_dev, n, dtype);
+  if (rc) return rc;
+  if (h->n_ins + static_cast<uint64_t>(n) > 0xFFFFFFFFull)
+    return fail(ACE_ERR_OVERFLOW, "inserting %lld points would allow a count above 2^32-1", static_cast<long long>(n));
+  if (n == 0) return ACE_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ace::HashArgs a = hash_args(h, X_dev, n, dtype, ace::kInsert);
+  if ((rc = run_hash(h, a, s))) return rc;
+  h->n_ins += static_cast<uint64_t>(n);
+  return ACE_OK;
+}
+
+int ace_score(ace_handle h, const void* X_dev, int64_t n, int dtype, double alpha, double* scores_dev,
+              uint32_t* sums_dev, uint8_t* flags_dev, void* stream) {
+  return score_common(h, X_dev, n, dtype, alpha, scores_dev, sums_dev, flags_dev, static_cast<cudaStream_t>(stream),
+                      false);
+}
+
+int ace_insert_score(ace_handle h, const void* X_dev, int64_t n, int dtype, double alpha, double* scores_dev,
+                     uint32_t* sums_dev, uint8_t* flags_dev, void* stream) {
+  return score_common(h, X_dev, n, dtype, alpha, scores_dev, sums_dev, flags_dev, static_cast<cudaStream_t>(stream),
+                      true);
+}
+
+int ace_insert_score_host(ace_handle h, const void* X_host, int64_t n, int dtype, double alpha, double* scores_host,
+                          uint32_t* sums_host, uint8_t* flags_host, void* stream) {
+  int rc = check_x(h, X_host, n, dtype);
+  if (rc) return rc;
+  if (n == 0) return ACE_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t xbytes = static_cast<size_t>(n) * h->d * (dtype == ACE_F32 ? 4 : 2);
+  if ((rc = grow(&h->xstage, &h->xstage_cap, xbytes, s, "X staging"))) return rc;
+  if (static_cast<size_t>(n) > h->stage_cap) {
+    ACE_CUDA(cudaStreamSynchronize(s));
+    cudaFree(h->scstage);
+    cudaFree(h->flstage);
+    h->scstage = nullptr;
+    h->flstage = nullptr;
+    h->stage_cap = 0;
+    const size_t cap = static_cast<size_t>(n) + static_cast<size_t>(n) / 2;
+    cudaError_t e = cudaMalloc(&h->scstage, cap * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->flstage, cap);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ACE_ERR_OOM, "output staging: %s", cudaGetErrorString(e));
+    }
+    h->stage_cap = cap;
+  }
+  void* p = h->sums;
+  if ((rc = grow(&p, &h->sums_cap, static_cast<size_t>(n) * sizeof(uint32_t), s, "sums scratch"))) return rc;
+  h->sums = static_cast<uint32_t*>(p);
+  ACE_CUDA(cudaMemcpyAsync(h->xstage, X_host, xbytes, cudaMemcpyHostToDevice, s));
+  rc = score_common(h, h->xstage, n, dtype, alpha, scores_host ? h->scstage : nullptr, h->sums,
+                    flags_host ? h->flstage : nullptr, s, true);
+  if (rc) return rc;
+  if (scores_host) ACE_CUDA(cudaMemcpyAsync(scores_host, h->scstage, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (sums_host) ACE_CUDA(cudaMemcpyAsync(sums_host, h->sums, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  if (flags_host) ACE_CUDA(cudaMemcpyAsync(flags_host, h->flstage, n, cudaMemcpyDeviceToHost, s));
+  ACE_CUDA(cudaStreamSynchronize(s));
+  return ACE_OK;
+}
+
+int ace_hash(ace_handle h, const void* X_dev, int64_t n, int dtype, uint32_t* ids_dev, void* stream) {
+  int rc = check_x(h, X_dev, n, dtype);
+  if (rc) return rc;
+  if (n > 0 && !ids_dev) return fail(ACE_ERR_ARG, "ids_dev is NULL");
+  if (n == 0) return ACE_OK;
+  ace::HashArgs a = hash_args(h, X_dev, n, dtype, ace::kStoreIdsRowMajor);
+  a.ids_rm = ids_dev;
+  return run_hash(h, a, static_cast<cudaStream_t>(stream));
+}
+
+int ace_stats(ace_handle h, void* stream, ace_stats_t* out) {
+  if (!h || !out) return fail(ACE_ERR_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ACE_CUDA(cudaMemsetAsync(h->st->Q, 0, sizeof(h->st->Q), s));
+  cudaError_t e = ace::launch_sum_squares(h->counts, static_cast<long long>(count_elems(h)), h->st, s);
+  if (e != cudaSuccess) return cuda_fail(e, "sum of squares launch");
+  ace::DevStats st;
+  ACE_CUDA(cudaMemcpyAsync(&st, h->st, sizeof st, cudaMemcpyDeviceToHost, s));
+  ACE_CUDA(cudaStreamSynchronize(s));
+  std::memset(out, 0, sizeof *out);
+  out->n_ins = h->n_ins;
+  out->n_scored = st.n_scored;
+  out->Q_lo = st.Q[0];
+  out->Q_hi = st.Q[1];
+  out->S1_lo = st.S1[0];
+  out->S1_hi = st.S1[1];
+  out->S2_lo = st.S2[0];
+  out->S2_hi = st.S2[1];
+  const u128 Q = (static_cast<u128>(st.Q[1]) << 64) | st.Q[0];
+  out->mu_ins = h->n_ins ? static_cast<double>(Q) / (static_cast<double>(h->n_ins) * static_cast<double>(h->L)) : 0.0;
+  // mu and sigma from the exact sums, the same binary64 steps as the flags kernel
+  const u128 S1 = (static_cast<u128>(st.S1[1]) << 64) | st.S1[0];
+  const u128 S2 = (static_cast<u128>(st.S2[1]) << 64) | st.S2[0];
+  const uint64_t N = st.n_scored;
+  if (N > 0 && (S2 == 0 || static_cast<u128>(N) <= (~static_cast<u128>(0)) / S2)) {
+    const double NL = static_cast<double>(N) * static_cast<double>(h->L);
+    out->mu = static_cast<double>(S1) / NL;
+    out->sigma = std::sqrt(static_cast<double>(static_cast<u128>(N) * S2 - S1 * S1)) / NL;
+  } else if (N > 0) {
+    out->mu = out->sigma = std::nan("");
+  }
+  out->rechecks = st.rechecks;
+  out->nonfinite_points = st.nonfinite;
+  out->status = st.status;
+  out->precision = h->last_precision;
+  return ACE_OK;
+}
+
+int ace_get_counts(ace_handle h, uint32_t* counts_host, void* stream) {
+  if (!h || !counts_host) return fail(ACE_ERR_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ACE_CUDA(cudaMemcpyAsync(counts_host, h->counts, count_elems(h) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  ACE_CUDA(cudaStreamSynchronize(s));
+  return ACE_OK;
+}
+
+int ace_get_projection(ace_handle h, float* W_host) {
+  if (!h || !W_host) return fail(ACE_ERR_ARG, "NULL argument");
+  std::memcpy(W_host, h->Wh.data(), h->Wh.size() * sizeof(float));
+  return ACE_OK;
+}
+
+int ace_get_shape(ace_handle h, int* d, int* K, int* L) {
+  if (!h) return fail(ACE_ERR_ARG, "handle is NULL");
+  if (d) *d = h->d;
+  if (K) *K = h->K;
+  if (L) *L = h->L;
+  return ACE_OK;
+}
+
+const char* ace_last_error(void) { return g_err.c_str(); }
+
+const char* ace_version(void) { return "ace-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "../../include/ace.h"
+
+namespace ace {
+
+// Device-resident running state of one detector.  All sums are exact integers; the three
+// doubles are the statistics of the last score call (for ace_stats).
+struct DevStats {
+  unsigned long long n_scored;   // N
+  unsigned long long S1[2];      // lo, hi
+  unsigned long long S2[2];      // lo, hi
+  unsigned long long Q[2];       // scratch for ace_stats: sum of count^2
+  unsigned long long rechecks;   // binary64 recomputations
+  unsigned long long nonfinite;  // points with a non-finite squared norm
+  unsigned int status;           // ACE_STATUS_* bits
+  unsigned int pad;
+  double mu, sigma, threshold;
+};
+
+enum HashMode : int {
+  kStoreIds = 1,      // write ids to the table-major scratch [L][ld]
+  kInsert = 2,        // increment the count arrays
+  kStoreIdsRowMajor = 4  // write uint32 ids point-major [n][L] (ace_hash)
+};
+
+// Everything a hash kernel needs.  Columns c = j*K + k; W is d x KL row-major.
+struct HashArgs {
+  const void* X;        // n x d, binary32 or bfloat16 bits
+  int x_bf16;           // 0: binary32, 1: bfloat16
+  long long n;
+  int d, K, L, KL;
+  const float* W;       // [d][KL] binary32
+  const float* Wt;      // [KL][d] binary32 (columns contiguous, for the binary64 recheck)
+  const float* cB;      // [KL] guard coefficient: margin * gamma * ||w_c|| (rounded up)
+  float xfac;           // squared-norm inflation (1 + 2 gamma_d + slack)
+  float xabs;           // squared-norm underflow allowance
+  float babs;           // absolute allowance in the projection bound
+  int mode;             // HashMode bits
+  void* ids;            // scratch ids (uint16 when K <= 16, else uint32), [L][ld]
+  long long ld;         // leading dimension of the scratch ids (>= n)
+  uint32_t* ids_rm;     // [n][L] uint32 (kStoreIdsRowMajor)
+  uint32_t* counts;     // [L][2^K]
+  DevStats* st;
+};
+
+// Kernels launched from the runtime (each returns the launch error).
+cudaError_t launch_hash_simt(const HashArgs& a, cudaStream_t s);
+cudaError_t launch_score_gather(const void* ids, int ids16, long long ld, long long n, int K, int L,
+                                const uint32_t* counts, uint32_t* sums, DevStats* st, cudaStream_t s);
+cudaError_t launch_flags(const uint32_t* sums, long long n, int L, double alpha, DevStats* st,
+                         double* scores, uint8_t* flags, cudaStream_t s);
+cudaError_t launch_sum_squares(const uint32_t* counts, long long total, DevStats* st, cudaStream_t s);
+
+// Host-side generator of the projection matrix (SplitMix64 counter mode + Box-Muller).
+void generate_projection(int d, int K, int L, uint64_t seed, float* W);
+
+}  // namespace ace

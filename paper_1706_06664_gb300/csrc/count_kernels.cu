@@ -1,0 +1,204 @@
+// Query phase and score statistics.
+//
+//   score_gather  Algorithm 1 query phase (§3.2): c_i = sum_j A_j[H_j(q_i)] from the cached
+//                 table-major ids; folds N += n, S1 += sum c, S2 += sum c^2 (exact 128-bit).
+//   flags         §5.3 threshold: mu = S1/(N L), sigma = sqrt(N S2 - S1^2)/(N L),
+//                 t = mu - alpha*sigma, score = c/L, flag = score < t.  Every binary64 step
+//                 is an explicit correctly rounded intrinsic, so no contraction can change it.
+//   sum_squares   Q = sum over all counters of A^2 (the closed form of Eq. 11 summed over
+//                 the inserts: mu_ins = Q / (n_ins L)).
+#include "ace_internal.h"
+
+namespace ace {
+namespace {
+
+__device__ __forceinline__ void add128(unsigned long long& lo, unsigned long long& hi, unsigned long long l2,
+                                       unsigned long long h2) {
+  const unsigned long long s = lo + l2;
+  hi += h2 + (s < lo ? 1ull : 0ull);
+  lo = s;
+}
+
+// Exact: the sum modulo 2^128 is independent of the order of the atomics.
+__device__ __forceinline__ void atomic_add128(unsigned long long* p, unsigned long long lo, unsigned long long hi) {
+  if (lo) {
+    const unsigned long long old = atomicAdd(p, lo);
+    if (old + lo < old) hi += 1ull;
+  }
+  if (hi) atomicAdd(p + 1, hi);
+}
+
+// Block-wide sum of (s1 as 64-bit, s2 as 128-bit); thread 0 adds it to the globals.
+__device__ void block_fold(unsigned long long s1, unsigned long long s2lo, unsigned long long s2hi,
+                           unsigned long long* S1, unsigned long long* S2) {
+  __shared__ unsigned long long sh[3][32];
+  unsigned long long s1hi = 0;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long a = __shfl_down_sync(0xFFFFFFFFu, s1, off);
+    const unsigned long long b = __shfl_down_sync(0xFFFFFFFFu, s1hi, off);
+    const unsigned long long c = __shfl_down_sync(0xFFFFFFFFu, s2lo, off);
+    const unsigned long long d = __shfl_down_sync(0xFFFFFFFFu, s2hi, off);
+    add128(s1, s1hi, a, b);
+    add128(s2lo, s2hi, c, d);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ unsigned long long sh1hi[32];
+  if (lane == 0) {
+    sh[0][w] = s1;
+    sh1hi[w] = s1hi;
+    sh[1][w] = s2lo;
+    sh[2][w] = s2hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long a = 0, ah = 0, b = 0, bh = 0;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) {
+      add128(a, ah, sh[0][i], sh1hi[i]);
+      add128(b, bh, sh[1][i], sh[2][i]);
+    }
+    atomic_add128(S1, a, ah);
+    atomic_add128(S2, b, bh);
+  }
+}
+
+template <typename IdT>
+__global__ void __launch_bounds__(256) score_gather_kernel(const IdT* __restrict__ ids, long long ld, long long n, int K,
+                                                           int L, const uint32_t* __restrict__ counts,
+                                                           uint32_t* __restrict__ sums, DevStats* st) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  unsigned long long c = 0;
+  if (i < n) {
+    const IdT* col = ids + i;
+#pragma unroll 10
+    for (int j = 0; j < L; ++j) {
+      const uint32_t id = col[static_cast<size_t>(j) * ld];
+      c += __ldg(counts + (static_cast<size_t>(j) << K) + id);
+    }
+    if (c > 0xFFFFFFFFull) atomicOr(&st->status, static_cast<unsigned>(ACE_STATUS_SUM_OVERFLOW));
+    sums[i] = static_cast<uint32_t>(c);
+  }
+  block_fold(c, c * c, __umul64hi(c, c), st->S1, st->S2);
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&st->n_scored, static_cast<unsigned long long>(n));
+}
+
+// Correctly rounded (nearest-even) conversion of a 128-bit unsigned integer to binary64.
+__device__ double u128_to_f64(unsigned long long lo, unsigned long long hi) {
+  if (hi == 0) return __ull2double_rn(lo);
+  const int s = __clzll(static_cast<long long>(hi));
+  unsigned long long top = s == 0 ? hi : ((hi << s) | (lo >> (64 - s)));
+  const unsigned long long rest = lo << s;
+  top |= rest != 0 ? 1ull : 0ull;  // sticky bit, below the rounding position of a 64-bit value
+  const double scale = __longlong_as_double(static_cast<long long>(1023 + 64 - s) << 52);
+  return __dmul_rn(__ull2double_rn(top), scale);
+}
+
+__global__ void __launch_bounds__(256) flags_kernel(const uint32_t* __restrict__ sums, long long n, int L, double alpha,
+                                                    DevStats* st, double* __restrict__ scores,
+                                                    uint8_t* __restrict__ flags) {
+  __shared__ double t_sh;
+  if (threadIdx.x == 0) {
+    const unsigned long long N = st->n_scored;
+    const unsigned long long s1lo = st->S1[0], s1hi = st->S1[1], s2lo = st->S2[0], s2hi = st->S2[1];
+    // N * S2 as 128 bits, with overflow detection
+    const unsigned long long plo = N * s2lo;
+    const unsigned long long pmid = __umul64hi(N, s2lo);
+    const unsigned long long hlo = N * s2hi;
+    const bool ovf = __umul64hi(N, s2hi) != 0 || pmid + hlo < pmid || s1hi != 0 || N == 0;
+    const unsigned long long phi = pmid + hlo;
+    // S1^2 (S1 < 2^64 whenever N*S2 < 2^128, by Cauchy-Schwarz)
+    const unsigned long long qlo = s1lo * s1lo, qhi = __umul64hi(s1lo, s1lo);
+    const unsigned long long vlo = plo - qlo;
+    const unsigned long long vhi = phi - qhi - (plo < qlo ? 1ull : 0ull);
+    double mu, sigma, t;
+    if (ovf) {
+      if (N != 0) atomicOr(&st->status, static_cast<unsigned>(ACE_STATUS_SUM_OVERFLOW));
+      mu = sigma = t = __longlong_as_double(0x7ff8000000000000LL);
+    } else {
+      const double NL = __dmul_rn(__ull2double_rn(N), static_cast<double>(L));
+      mu = __ddiv_rn(u128_to_f64(s1lo, s1hi), NL);
+      sigma = __ddiv_rn(__dsqrt_rn(u128_to_f64(vlo, vhi)), NL);
+      t = __dsub_rn(mu, __dmul_rn(alpha, sigma));
+    }
+    t_sh = t;
+    if (blockIdx.x == 0) {
+      st->mu = mu;
+      st->sigma = sigma;
+      st->threshold = t;
+    }
+  }
+  __syncthreads();
+  const double t = t_sh;
+  const double Ld = static_cast<double>(L);
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const double sc = __ddiv_rn(__uint2double_rn(sums[i]), Ld);
+    if (scores) scores[i] = sc;
+    if (flags) flags[i] = sc < t ? 1 : 0;
+  }
+}
+
+__global__ void __launch_bounds__(256) sum_squares_kernel(const uint32_t* __restrict__ counts, long long total,
+                                                          DevStats* st) {
+  unsigned long long lo = 0, hi = 0;
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const unsigned long long c = counts[i];
+    add128(lo, hi, c * c, 0ull);
+  }
+  // reuse the 128-bit fold: (0, Q) -> S1 slot unused
+  __shared__ unsigned long long sh[2][32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long a = __shfl_down_sync(0xFFFFFFFFu, lo, off);
+    const unsigned long long b = __shfl_down_sync(0xFFFFFFFFu, hi, off);
+    add128(lo, hi, a, b);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    sh[0][w] = lo;
+    sh[1][w] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long a = 0, ah = 0;
+    for (int i = 0; i < static_cast<int>((blockDim.x + 31) >> 5); ++i) add128(a, ah, sh[0][i], sh[1][i]);
+    atomic_add128(st->Q, a, ah);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_score_gather(const void* ids, int ids16, long long ld, long long n, int K, int L,
+                                const uint32_t* counts, uint32_t* sums, DevStats* st, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long blocks = (n + 255) / 256;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (ids16)
+    score_gather_kernel<uint16_t><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
+        static_cast<const uint16_t*>(ids), ld, n, K, L, counts, sums, st);
+  else
+    score_gather_kernel<uint32_t><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
+        static_cast<const uint32_t*>(ids), ld, n, K, L, counts, sums, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flags(const uint32_t* sums, long long n, int L, double alpha, DevStats* st, double* scores,
+                         uint8_t* flags, cudaStream_t s) {
+  long long blocks = (n + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  flags_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(sums, n, L, alpha, st, scores, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_squares(const uint32_t* counts, long long total, DevStats* st, cudaStream_t s) {
+  long long blocks = (total + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  sum_squares_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(counts, total, st);
+  return cudaGetLastError();
+}
+
+}  // namespace ace

@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element by element,
+on the same seeded inputs.  Ids, counts, sums, flags and scores are compared bit-exactly;
+mu and sigma are compared bit-exactly too (tighter than the 1e-12 relative bar), because both
+sides take the same correctly rounded binary64 steps on the same exact integers."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1706_06664_gb300 import ace, workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PRECS = ["fp32"]
+
+
+def _dev(X):
+    if X.dtype == np.uint16:
+        return torch.from_numpy(X.view(np.int16)).cuda()
+    return torch.from_numpy(X).cuda()
+
+
+def _pair(d, K, L, seed=None, W=None, precision="fp32"):
+    det = ace.Detector(d, K, L, seed=seed or 0, W=W, precision=precision)
+    ref = oracle.Detector(d, K, L, seed=seed, W=W if W is not None else det.projection())
+    return det, ref
+
+
+def _compare_score(out, ref_out):
+    sc, su, fl = out
+    rs, ru, rf = ref_out
+    torch.cuda.synchronize()
+    assert np.array_equal(ace.u32(su), ru)
+    assert np.array_equal(sc.cpu().numpy(), rs)
+    assert np.array_equal(fl.cpu().numpy(), rf)
+
+
+def _compare_stats(det, ref, alpha=1.0):
+    s, r = det.stats(), ref.stats(alpha)
+    for k in ("n_ins", "n_scored", "Q", "S1", "S2"):
+        assert s[k] == r[k], k
+    for k in ("mu_ins", "mu", "sigma"):
+        assert s[k] == r[k], (k, s[k], r[k])
+    assert s["status"] == 0
+
+
+def test_projection_generator_matches_oracle():
+    for (d, K, L, seed) in [(32, 10, 20, 1), (41, 15, 50, 2), (7, 3, 5, 2**63 + 12345)]:
+        det = ace.Detector(d, K, L, seed=seed)
+        assert np.array_equal(det.projection(), oracle.projection_from_seed(d, K, L, seed))
+        det.close()
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_hand_example(precision):
+    import json, os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_example.json")))
+    W = np.array(g["W_columns"], dtype=np.float32).T.copy()
+    X = np.array(g["X"], dtype=np.float32)
+    det = ace.Detector(3, 2, 2, W=W, precision=precision)
+    ids = ace.u32(det.hash(_dev(X)))
+    assert ids.tolist() == g["ids"]
+    sc, su, fl = det.insert_score(_dev(X), 1.0)
+    torch.cuda.synchronize()
+    assert det.counts().tolist() == g["counts"]
+    assert ace.u32(su).tolist() == g["sums"]
+    assert sc.cpu().numpy().tolist() == g["scores"]
+    assert fl.cpu().numpy().tolist() == g["flags"]
+    st = det.stats()
+    assert st["Q"] == g["Q"] and st["mu_ins"] == g["mu_ins"] and st["mu"] == g["mu"]
+    ref = oracle.Detector(3, 2, 2, W=W)
+    ref.insert_score(X, 1.0)
+    assert st["sigma"] == ref.stats()["sigma"]
+    assert st["rechecks"] >= 1  # x1 projects to exactly 0 on column 3
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_small_config_full_size(precision):
+    """Config 'small' at its full size: n=10,000, d=32, K=10, L=20; insert all, score all."""
+    w = workloads.small(seed=1)
+    det, ref = _pair(w["d"], w["K"], w["L"], seed=17, precision=precision)
+    Xd = _dev(w["X"])
+    assert np.array_equal(ace.u32(det.hash(Xd)), ref.hash(w["X"]))
+    det.insert(Xd)
+    ref.insert(w["X"])
+    assert np.array_equal(det.counts(), ref.counts)
+    _compare_score(det.score(Xd, w["alpha"]), ref.score(w["X"], w["alpha"]))
+    _compare_stats(det, ref)
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_kdd_shaped_reduced(precision):
+    """KDD-shaped recipe (d=41, K=15, L=50) at n=20,011: many tiles and a ragged tail."""
+    w = workloads.kdd(seed=2, n=20_011)
+    det, ref = _pair(w["d"], w["K"], w["L"], seed=5, precision=precision)
+    Xd = _dev(w["X"])
+    _compare_score(det.insert_score(Xd, 1.0), ref.insert_score(w["X"], 1.0))
+    assert np.array_equal(det.counts(), ref.counts)
+    _compare_stats(det, ref)
+    # a second batch: scores use the running statistics over both batches
+    w2 = workloads.kdd(seed=3, n=3001)
+    _compare_score(det.score(_dev(w2["X"]), 2.0), ref.score(w2["X"], 2.0))
+    _compare_stats(det, ref, 2.0)
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_highdim_bf16_reduced(precision):
+    """High-dimensional recipe (bfloat16 inputs, d=1024, K=16, L=64) at n=1,500."""
+    w = workloads.highdim(seed=3, n=1500)
+    det, ref = _pair(w["d"], w["K"], w["L"], seed=9, precision=precision)
+    Xd = _dev(w["X"])
+    assert np.array_equal(ace.u32(det.hash(Xd)), ref.hash(w["X"]))
+    _compare_score(det.insert_score(Xd, 1.0), ref.insert_score(w["X"], 1.0))
+    assert np.array_equal(det.counts(), ref.counts)
+    _compare_stats(det, ref)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (3, 24, 2), (5, 17, 3), (64, 2, 100), (33, 7, 40), (130, 13, 11)])
+def test_shapes_and_ragged_batches(shape):
+    d, K, L = shape
+    rng = np.random.default_rng(sum(shape))
+    det, ref = _pair(d, K, L, seed=d * 1000 + K)
+    for n in (1, 127, 129, 300):
+        X = rng.standard_normal((n, d)).astype(np.float32)
+        _compare_score(det.insert_score(_dev(X), 1.0), ref.insert_score(X, 1.0))
+    assert np.array_equal(det.counts(), ref.counts)
+    _compare_stats(det, ref)
+
+
+def test_edge_values_exact_zeros_nonfinite_subnormal_huge():
+    d, K, L = 6, 4, 5
+    W = workloads.gaussian_w(d, K, L, 3)
+    W[:, 0] = [1, -1, 0, 0, 0, 0]
+    X = np.zeros((12, d), dtype=np.float32)
+    X[1] = [1, 1, 0, 0, 0, 0]             # exact zero on column 0
+    X[2, 3] = np.nan                        # NaN -> every projection NaN -> bucket 0
+    X[3, 0] = np.inf                        # +inf
+    X[4, 1] = -np.inf
+    X[5] = 1e-40                            # subnormal coordinates
+    X[6] = [3e38, -3e38, 1e38, 0, 0, 0]     # squared norm overflows binary32
+    X[7] = [2.0**-140, 0, 0, 0, 0, 0]
+    X[8] = 1.0
+    X[9] = -1.0
+    X[10, 5] = 1.0
+    X[11] = [1, 1, 1e-7, -1e-7, 0, 0]
+    det, ref = _pair(d, K, L, W=W)
+    Xd = _dev(X)
+    assert np.array_equal(ace.u32(det.hash(Xd)), ref.hash(X))
+    _compare_score(det.insert_score(Xd, 1.0), ref.insert_score(X, 1.0))
+    st = det.stats()
+    assert st["nonfinite_points"] >= 4
+    assert st["rechecks"] > 0
+
+
+def test_zero_column_and_zero_batch():
+    d, K, L = 4, 3, 2
+    W = workloads.gaussian_w(d, K, L, 4)
+    W[:, 2] = 0.0
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((50, d)).astype(np.float32)
+    det, ref = _pair(d, K, L, W=W)
+    det.insert(_dev(np.zeros((0, d), dtype=np.float32)))
+    _compare_score(det.insert_score(_dev(X), 0.5), ref.insert_score(X, 0.5))
+    _compare_stats(det, ref, 0.5)
+
+
+def test_score_does_not_insert_and_reset():
+    w = workloads.small(seed=5, n=2000)
+    det, ref = _pair(w["d"], w["K"], w["L"], seed=3)
+    Xd = _dev(w["X"])
+    det.score(Xd, 1.0)
+    torch.cuda.synchronize()
+    assert int(det.counts().sum()) == 0
+    det.insert(Xd)
+    det.reset()
+    st = det.stats()
+    assert st["n_ins"] == 0 and st["n_scored"] == 0 and int(det.counts().sum()) == 0
+
+
+def test_host_entry_point_matches_device_path():
+    w = workloads.kdd(seed=6, n=7777)
+    a, ref = _pair(w["d"], w["K"], w["L"], seed=8)
+    n = w["X"].shape[0]
+    sc = np.empty(n, dtype=np.float64)
+    su = np.empty(n, dtype=np.uint32)
+    fl = np.empty(n, dtype=np.uint8)
+    a.insert_score_host(w["X"], 1.0, sc, su, fl)
+    rs, ru, rf = ref.insert_score(w["X"], 1.0)
+    assert np.array_equal(su, ru) and np.array_equal(sc, rs) and np.array_equal(fl, rf)
+    _compare_stats(a, ref)
+
+
+def test_kdd_full_size_sampled():
+    """KDD-shaped recipe at its full size (n=500,000), in the bench's launch configuration:
+    ids of a sample of points against the oracle, plus invariants that hold at any size."""
+    w = workloads.kdd(seed=2)
+    X = w["X"]
+    n = X.shape[0]
+    det = ace.Detector(w["d"], w["K"], w["L"], seed=5)
+    Xd = _dev(X)
+    ids = ace.u32(det.hash(Xd))
+    rng = np.random.default_rng(0)
+    sample = np.sort(rng.choice(n, size=3000, replace=False))
+    sample = np.unique(np.concatenate([sample, [0, n - 1]]))
+    ref_ids = oracle.hash_ids(X[sample], det.projection(), w["K"], w["L"])
+    assert np.array_equal(ids[sample], ref_ids)
+    sc, su, fl = det.insert_score(Xd, 1.0)
+    torch.cuda.synchronize()
+    counts = det.counts()
+    assert np.all(counts.sum(axis=1, dtype=np.uint64) == n)
+    # counts equal the per-table histogram of the GPU ids (itself checked on the sample)
+    for j in (0, 17, 49):
+        assert np.array_equal(counts[j], np.bincount(ids[:, j], minlength=1 << w["K"]))
+    sums = ace.u32(su).astype(np.int64)
+    expect = np.zeros(n, dtype=np.int64)
+    for j in range(w["L"]):
+        expect += counts[j][ids[:, j]]
+    assert np.array_equal(sums, expect)
+    st = det.stats()
+    assert st["Q"] == int(sums.sum())
+    ref = oracle.Detector(w["d"], w["K"], w["L"], W=det.projection())
+    ref.counts[:] = counts
+    ref.n_ins = n
+    ref_sc, ref_su, ref_fl = ref._score_ids(ids, 1.0)
+    assert np.array_equal(ref_su, ace.u32(su))
+    assert np.array_equal(sc.cpu().numpy(), ref_sc) and np.array_equal(fl.cpu().numpy(), ref_fl)
+    assert st["mu"] == ref.stats()["mu"] and st["sigma"] == ref.stats()["sigma"]
