@@ -168,6 +168,21 @@ int ace_get_shape(ace_handle h, int* d, int* K, int* L);
  * next call on this thread. */
 const char* ace_last_error(void);
 
+/*
+ * Per-phase timing hook.  While enabled, the library brackets each kernel it launches with
+ * a pair of CUDA events on the caller's stream; ace_profile_read() waits for them and
+ * returns the summed durations per phase (and clears them).  The launch counters count
+ * every kernel the library launched on this handle since creation or the last read.
+ */
+enum { ACE_PHASE_HASH = 0, ACE_PHASE_SCORE = 1, ACE_PHASE_FLAGS = 2, ACE_PHASE_OTHER = 3, ACE_NPHASE = 4 };
+typedef struct {
+  uint64_t launches[ACE_NPHASE]; /* kernels launched per phase                           */
+  double ms[ACE_NPHASE];         /* summed event time per phase (enabled periods only)   */
+  uint64_t timed[ACE_NPHASE];    /* launches that were timed                              */
+} ace_profile_t;
+int ace_profile_enable(ace_handle h, int enable);
+int ace_profile_read(ace_handle h, ace_profile_t* out);
+
 /* Library version string. */
 const char* ace_version(void);
 

@@ -24,7 +24,9 @@ EXPORTS = [
     "ace_create", "ace_create_with_projection", "ace_destroy", "ace_reset", "ace_set_precision",
     "ace_insert", "ace_score", "ace_insert_score", "ace_insert_score_host", "ace_hash", "ace_stats",
     "ace_get_counts", "ace_get_projection", "ace_get_shape", "ace_last_error", "ace_version",
+    "ace_profile_enable", "ace_profile_read",
 ]
+PHASES = ("hash", "score", "flags", "other")
 
 
 class AceError(RuntimeError):
@@ -43,6 +45,10 @@ class ace_stats_t(ctypes.Structure):
         ("rechecks", ctypes.c_uint64), ("nonfinite_points", ctypes.c_uint64),
         ("status", ctypes.c_uint32), ("precision", ctypes.c_int32),
     ]
+
+
+class ace_profile_t(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64 * 4), ("ms", ctypes.c_double * 4), ("timed", ctypes.c_uint64 * 4)]
 
 
 _lib = None
@@ -75,6 +81,8 @@ def load_library(path: str = LIB_PATH):
             "ace_get_counts": ([H, P, P], i32),
             "ace_get_projection": ([H, P], i32),
             "ace_get_shape": ([H, P, P, P], i32),
+            "ace_profile_enable": ([H, i32], i32),
+            "ace_profile_read": ([H, ctypes.POINTER(ace_profile_t)], i32),
             "ace_last_error": ([], ctypes.c_char_p),
             "ace_version": ([], ctypes.c_char_p),
         }
@@ -170,10 +178,13 @@ class Detector:
 
     def _outs(self, n, scores, sums, flags, device):
         torch = _torch()
-        sc = torch.empty(n, dtype=torch.float64, device=device) if scores is True else (scores or None)
-        su = torch.empty(n, dtype=torch.int32, device=device) if sums is True else (sums or None)
-        fl = torch.empty(n, dtype=torch.uint8, device=device) if flags is True else (flags or None)
-        return sc, su, fl
+
+        def pick(v, dt):
+            if v is True:
+                return torch.empty(n, dtype=dt, device=device)
+            return None if (v is None or v is False) else v
+
+        return pick(scores, torch.float64), pick(sums, torch.int32), pick(flags, torch.uint8)
 
     def score(self, X, alpha: float = 1.0, scores=True, sums=True, flags=True, stream=None):
         """Returns (scores float64, sums int32 holding uint32 bits, flags uint8) tensors."""
@@ -228,6 +239,16 @@ class Detector:
         out = np.empty((self.L, 1 << self.K), dtype=np.uint32)
         _check(load_library().ace_get_counts(self._h, ctypes.c_void_p(out.ctypes.data), _stream_ptr(stream)))
         return out
+
+    def profile(self, enable: bool = True):
+        _check(load_library().ace_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """Per-phase kernel launches and summed CUDA-event milliseconds since the last read."""
+        p = ace_profile_t()
+        _check(load_library().ace_profile_read(self._h, ctypes.byref(p)))
+        return {name: {"launches": int(p.launches[i]), "ms": float(p.ms[i]), "timed": int(p.timed[i])}
+                for i, name in enumerate(PHASES)}
 
     def projection(self) -> np.ndarray:
         out = np.empty((self.d, self.K * self.L), dtype=np.float32)

@@ -57,13 +57,59 @@ struct ace_detector {
   size_t stage_cap = 0;  // elements
   uint64_t n_ins = 0;
   std::vector<float> Wh;  // host copy of W
+  // profiling hook
+  bool prof = false;
+  uint64_t launches[ACE_NPHASE] = {0, 0, 0, 0};
+  struct Mark {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> pool;
 };
 
 namespace {
 
+// Brackets one library kernel launch with events when profiling is on.
+struct PhaseScope {
+  ace_detector* h;
+  int phase;
+  cudaStream_t s;
+  cudaEvent_t b = nullptr;
+  cudaEvent_t take() {
+    if (!h->pool.empty()) {
+      cudaEvent_t e = h->pool.back();
+      h->pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  PhaseScope(ace_detector* h_, int phase_, cudaStream_t s_) : h(h_), phase(phase_), s(s_) {
+    h->launches[phase] += 1;
+    if (h->prof) {
+      cudaEvent_t a = take();
+      b = take();
+      cudaEventRecord(a, s);
+      h->marks.push_back({phase, a, b});
+    }
+  }
+  ~PhaseScope() {
+    if (b) cudaEventRecord(b, s);
+  }
+};
+
 size_t count_elems(const ace_detector* h) { return (static_cast<size_t>(1) << h->K) * static_cast<size_t>(h->L); }
 
 void free_all(ace_detector* h) {
+  for (auto& m : h->marks) {
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+  }
+  for (auto e : h->pool) cudaEventDestroy(e);
+  h->marks.clear();
+  h->pool.clear();
   cudaFree(h->W);
   cudaFree(h->Wt);
   cudaFree(h->cB);
@@ -222,6 +268,7 @@ size_t id_bytes(ace_handle h) { return h->K <= 16 ? 2 : 4; }
 
 int run_hash(ace_handle h, const ace::HashArgs& a, cudaStream_t s) {
   h->last_precision = ACE_PROJ_FP32;
+  PhaseScope ps(h, ACE_PHASE_HASH, s);
   cudaError_t e = ace::launch_hash_simt(a, s);
   if (e != cudaSuccess) return cuda_fail(e, "hash kernel launch");
   return ACE_OK;
@@ -246,9 +293,16 @@ int score_common(ace_handle h, const void* X, long long n, int dtype, double alp
   ace::HashArgs a = hash_args(h, X, n, dtype, ace::kStoreIds | (insert ? ace::kInsert : 0));
   if ((rc = run_hash(h, a, s))) return rc;
   if (insert) h->n_ins += static_cast<uint64_t>(n);
-  cudaError_t e = ace::launch_score_gather(h->ids, h->K <= 16, n, n, h->K, h->L, h->counts, sum_out, h->st, s);
+  cudaError_t e;
+  {
+    PhaseScope ps(h, ACE_PHASE_SCORE, s);
+    e = ace::launch_score_gather(h->ids, h->K <= 16, n, n, h->K, h->L, h->counts, sum_out, h->st, s);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "score kernel launch");
-  e = ace::launch_flags(sum_out, (scores || flags) ? n : 0, h->L, alpha, h->st, scores, flags, s);
+  {
+    PhaseScope ps(h, ACE_PHASE_FLAGS, s);
+    e = ace::launch_flags(sum_out, (scores || flags) ? n : 0, h->L, alpha, h->st, scores, flags, s);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "flags kernel launch");
   return ACE_OK;
 }
@@ -369,7 +423,11 @@ int ace_stats(ace_handle h, void* stream, ace_stats_t* out) {
   if (!h || !out) return fail(ACE_ERR_ARG, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   ACE_CUDA(cudaMemsetAsync(h->st->Q, 0, sizeof(h->st->Q), s));
-  cudaError_t e = ace::launch_sum_squares(h->counts, static_cast<long long>(count_elems(h)), h->st, s);
+  cudaError_t e;
+  {
+    PhaseScope ps(h, ACE_PHASE_OTHER, s);
+    e = ace::launch_sum_squares(h->counts, static_cast<long long>(count_elems(h)), h->st, s);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "sum of squares launch");
   ace::DevStats st;
   ACE_CUDA(cudaMemcpyAsync(&st, h->st, sizeof st, cudaMemcpyDeviceToHost, s));
@@ -423,6 +481,32 @@ int ace_get_shape(ace_handle h, int* d, int* K, int* L) {
   if (K) *K = h->K;
   if (L) *L = h->L;
   return ACE_OK;
+}
+
+int ace_profile_enable(ace_handle h, int enable) {
+  if (!h) return fail(ACE_ERR_ARG, "handle is NULL");
+  h->prof = enable != 0;
+  return ACE_OK;
+}
+
+int ace_profile_read(ace_handle h, ace_profile_t* out) {
+  if (!h || !out) return fail(ACE_ERR_ARG, "NULL argument");
+  std::memset(out, 0, sizeof *out);
+  for (int p = 0; p < ACE_NPHASE; ++p) out->launches[p] = h->launches[p];
+  int rc = ACE_OK;
+  for (auto& m : h->marks) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(m.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, m.a, m.b);
+    if (e != cudaSuccess && rc == ACE_OK) rc = cuda_fail(e, "profile event");
+    out->ms[m.phase] += ms;
+    out->timed[m.phase] += 1;
+    h->pool.push_back(m.a);
+    h->pool.push_back(m.b);
+  }
+  h->marks.clear();
+  for (int p = 0; p < ACE_NPHASE; ++p) h->launches[p] = 0;
+  return rc;
 }
 
 const char* ace_last_error(void) { return g_err.c_str(); }
