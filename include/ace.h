@@ -183,6 +183,30 @@ typedef struct {
 int ace_profile_enable(ace_handle h, int enable);
 int ace_profile_read(ace_handle h, ace_profile_t* out);
 
+/*
+ * ace_insert_score_noalloc — ace_insert_score for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is an engineering entry point.  Some callers
+ * cannot call cudaMalloc: a process whose device memory is entirely reserved by another
+ * allocator (a framework's caching pool), or a latency-bound loop that must never block
+ * (cudaFree synchronises the whole device, and ace_insert_score may grow its scratch).
+ * This variant allocates nothing.  Its scratch (the cached bucket ids, and the per-point
+ * sums when sums_dev is NULL) lives in one static device array of
+ * ACE_NOALLOC_SCRATCH_BYTES (32 MiB) inside the library, which every GPU that loads the
+ * library holds until the process exits.
+ *   - A batch must fit: n*L*(2 if K <= 16 else 4) bytes of ids, rounded up to 256, plus
+ *     4*n bytes when sums_dev is NULL, must not exceed ACE_NOALLOC_SCRATCH_BYTES; larger
+ *     batches fail with ACE_ERR_ARG and change nothing.
+ *   - The first call on each device looks up the array's device address (with that device
+ *     current); make that first call before any stream capture begins.
+ *   - Every call, on every handle of the process, shares the one array, and a call
+ *     overwrites what the previous call left there.  Calls whose kernels overlap on the GPU
+ *     (different streams, or different handles without ordering) race on it: order them.
+ * Outputs, semantics and the other errors are those of ace_insert_score.
+ */
+#define ACE_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int ace_insert_score_noalloc(ace_handle h, const void* X_dev, int64_t n, int dtype, double alpha,
+                             double* scores_dev, uint32_t* sums_dev, uint8_t* flags_dev, void* stream);
+
 /* Library version string. */
 const char* ace_version(void);
 

@@ -24,8 +24,9 @@ EXPORTS = [
     "ace_create", "ace_create_with_projection", "ace_destroy", "ace_reset", "ace_set_precision",
     "ace_insert", "ace_score", "ace_insert_score", "ace_insert_score_host", "ace_hash", "ace_stats",
     "ace_get_counts", "ace_get_projection", "ace_get_shape", "ace_last_error", "ace_version",
-    "ace_profile_enable", "ace_profile_read",
+    "ace_profile_enable", "ace_profile_read", "ace_insert_score_noalloc",
 ]
+NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 PHASES = ("hash", "score", "flags", "other")
 
 
@@ -76,6 +77,7 @@ def load_library(path: str = LIB_PATH):
             "ace_score": ([H, P, i64, i32, f64, P, P, P, P], i32),
             "ace_insert_score": ([H, P, i64, i32, f64, P, P, P, P], i32),
             "ace_insert_score_host": ([H, P, i64, i32, f64, P, P, P, P], i32),
+            "ace_insert_score_noalloc": ([H, P, i64, i32, f64, P, P, P, P], i32),
             "ace_hash": ([H, P, i64, i32, P, P], i32),
             "ace_stats": ([H, P, ctypes.POINTER(ace_stats_t)], i32),
             "ace_get_counts": ([H, P, P], i32),
@@ -199,6 +201,14 @@ class Detector:
         sc, su, fl = self._outs(X.shape[0], scores, sums, flags, X.device)
         _check(load_library().ace_insert_score(self._h, _ptr(X), X.shape[0], _x_dtype(X), float(alpha), _ptr(sc),
                                                _ptr(su), _ptr(fl), _stream_ptr(stream)))
+        return sc, su, fl
+
+    def insert_score_noalloc(self, X, alpha: float = 1.0, scores=True, sums=True, flags=True, stream=None):
+        """ace_insert_score through the allocation-free entry point (static library scratch)."""
+        self._xcheck(X)
+        sc, su, fl = self._outs(X.shape[0], scores, sums, flags, X.device)
+        _check(load_library().ace_insert_score_noalloc(self._h, _ptr(X), X.shape[0], _x_dtype(X), float(alpha),
+                                                       _ptr(sc), _ptr(su), _ptr(fl), _stream_ptr(stream)))
         return sc, su, fl
 
     def insert_score_host(self, X: np.ndarray, alpha: float = 1.0, scores=None, sums=None, flags=None,

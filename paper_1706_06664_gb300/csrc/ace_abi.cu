@@ -514,3 +514,80 @@ const char* ace_last_error(void) { return g_err.c_str(); }
 const char* ace_version(void) { return "ace-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free variant of ace_insert_score (for callers that cannot call cudaMalloc).
+//
+// The scratch is a file-scope device array.  Host code may not use the array's name as a
+// device address (on the host it is only a stand-in), so its real address is looked up
+// once per device with cudaGetSymbolAddress while that device is current, and that
+// pointer is what the kernels receive.
+// ---------------------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[ACE_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch on `device` (looked up on first use, with that device
+// current; the previously current device is restored).
+int noalloc_scratch(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices) return fail(ACE_ERR_ARG, "device %d out of range", device);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    int cur = -1;
+    ACE_CUDA(cudaGetDevice(&cur));
+    if (cur != device) ACE_CUDA(cudaSetDevice(device));
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (cur != device) cudaSetDevice(cur);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+    if (!p) return fail(ACE_ERR_CUDA, "scratch has no device address");
+    g_noalloc_ptr[device] = p;
+  }
+  *out = g_noalloc_ptr[device];
+  return ACE_OK;
+}
+
+}  // namespace
+
+extern "C" int ace_insert_score_noalloc(ace_handle h, const void* X_dev, int64_t n, int dtype, double alpha,
+                                        double* scores_dev, uint32_t* sums_dev, uint8_t* flags_dev, void* stream) {
+  int rc = check_x(h, X_dev, n, dtype);
+  if (rc) return rc;
+  if (!std::isfinite(alpha)) return fail(ACE_ERR_ARG, "alpha must be finite");
+  if (h->n_ins + static_cast<uint64_t>(n) > 0xFFFFFFFFull)
+    return fail(ACE_ERR_OVERFLOW, "inserting %lld points would allow a count above 2^32-1", static_cast<long long>(n));
+  const size_t ids_bytes = (static_cast<size_t>(n) * h->L * id_bytes(h) + 255) & ~static_cast<size_t>(255);
+  const size_t need = ids_bytes + (sums_dev ? 0 : static_cast<size_t>(n) * sizeof(uint32_t));
+  if (need > ACE_NOALLOC_SCRATCH_BYTES)
+    return fail(ACE_ERR_ARG,
+                "batch of %lld points needs %zu bytes of scratch; the static scratch holds %u bytes "
+                "(split the batch)",
+                static_cast<long long>(n), need, static_cast<unsigned>(ACE_NOALLOC_SCRATCH_BYTES));
+  if (n == 0) return ACE_OK;
+  void* base = nullptr;
+  if ((rc = noalloc_scratch(h->device, &base))) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void* ids = base;
+  uint32_t* sum_out = sums_dev ? sums_dev : reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(base) + ids_bytes);
+  ace::HashArgs a = hash_args(h, X_dev, n, dtype, ace::kStoreIds | ace::kInsert);
+  a.ids = ids;
+  a.ld = n;
+  h->last_precision = ACE_PROJ_FP32;
+  h->launches[ACE_PHASE_HASH] += 1;
+  cudaError_t e = ace::launch_hash_simt(a, s);
+  if (e != cudaSuccess) return cuda_fail(e, "hash kernel launch");
+  h->n_ins += static_cast<uint64_t>(n);
+  h->launches[ACE_PHASE_SCORE] += 1;
+  e = ace::launch_score_gather(ids, h->K <= 16, n, n, h->K, h->L, h->counts, sum_out, h->st, s);
+  if (e != cudaSuccess) return cuda_fail(e, "score kernel launch");
+  h->launches[ACE_PHASE_FLAGS] += 1;
+  e = ace::launch_flags(sum_out, (scores_dev || flags_dev) ? n : 0, h->L, alpha, h->st, scores_dev, flags_dev, s);
+  if (e != cudaSuccess) return cuda_fail(e, "flags kernel launch");
+  return ACE_OK;
+}
