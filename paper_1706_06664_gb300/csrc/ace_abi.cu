@@ -1,4 +1,5 @@
 // C ABI and host runtime: detector handles, device memory, guard constants, launches.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 #include <cstdarg>
@@ -9,6 +10,7 @@
 #include <vector>
 
 #include "ace_internal.h"
+#include "tc_plan.h"
 
 namespace {
 
@@ -57,9 +59,17 @@ struct ace_detector {
   size_t stage_cap = 0;  // elements
   uint64_t n_ins = 0;
   std::vector<float> Wh;  // host copy of W
+  // tensor-core path
+  int num_sms = 0;
+  bool tc_ok = false;
+  ace::TcArgs tc{};           // constant part of the launch (plan, guard constants, layout)
+  uint8_t* bimg = nullptr;    // resident operand image of W' (device)
+  unsigned long long* defer = nullptr;
+  size_t defer_bytes = 0;
+  unsigned long long* defer_count = nullptr;
   // profiling hook
   bool prof = false;
-  uint64_t launches[ACE_NPHASE] = {0, 0, 0, 0};
+  uint64_t launches[ACE_NPHASE] = {0, 0, 0, 0, 0};
   struct Mark {
     int phase;
     cudaEvent_t a, b;
@@ -110,6 +120,9 @@ void free_all(ace_detector* h) {
   for (auto e : h->pool) cudaEventDestroy(e);
   h->marks.clear();
   h->pool.clear();
+  cudaFree(h->bimg);
+  cudaFree(h->defer);
+  cudaFree(h->defer_count);
   cudaFree(h->W);
   cudaFree(h->Wt);
   cudaFree(h->cB);
@@ -145,6 +158,119 @@ void guard_constants(const std::vector<float>& W, int d, int KL, std::vector<flo
   babs = static_cast<float>(std::ldexp(static_cast<double>(d), -148));
   if (xabs == 0.f) xabs = std::ldexp(1.0f, -149);
   if (babs == 0.f) babs = std::ldexp(1.0f, -148);
+}
+
+uint16_t bf16_rn(float f) {  // round to nearest even (finite inputs)
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return static_cast<uint16_t>((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+float bf16_value(uint16_t b) {
+  const uint32_t u = static_cast<uint32_t>(b) << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+constexpr uint32_t kmajor_off(int r, int k, int kt) {
+  return static_cast<uint32_t>((r >> 3) * (kt * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// Plans the tensor-core path (hash_tc.cu): chunks of whole tables, the resident operand
+// image of the unit-column matrix W' (bfloat16 hi and lo parts, K-major canonical layout),
+// the shared-memory layout, and the guard constants.  Leaves tc_ok false when the device
+// is not sm_103 or the shape does not fit the resident design.
+int plan_tc(ace_detector* h) {
+  h->tc_ok = false;
+  cudaDeviceProp p;
+  cudaError_t e = cudaGetDeviceProperties(&p, h->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  h->num_sms = p.multiProcessorCount;
+  if (p.major != 10 || p.minor != 3) return ACE_OK;
+  const int d = h->d, K = h->K, L = h->L, KL = h->KL;
+  const int d_pad = (d + 15) / 16 * 16;
+  const int tpc = 256 / K;
+  const int nch = (L + tpc - 1) / tpc;
+  if (nch > ace::kTcMaxChunks) return ACE_OK;
+  ace::TcArgs& t = h->tc;
+  t = ace::TcArgs{};
+  t.d = d;
+  t.d_pad = d_pad;
+  t.K = K;
+  t.L = L;
+  t.nchunks = nch;
+  uint32_t off = 0;
+  for (int c = 0; c < nch; ++c) {
+    ace::TcChunk& ch = t.chunk[c];
+    ch.tab0 = c * tpc;
+    ch.ntab = std::min(tpc, L - ch.tab0);
+    ch.N = (ch.ntab * K + 15) / 16 * 16;
+    ch.boff_hi = off;
+    off += static_cast<uint32_t>(ch.N) * d_pad * 2;
+    ch.boff_lo = off;
+    off += static_cast<uint32_t>(ch.N) * d_pad * 2;
+  }
+  t.bimg_bytes = static_cast<int>(off);
+  auto up = [](int v, int a) { return (v + a - 1) / a * a; };
+  t.a_bytes = 128 * d_pad * 2;
+  t.off_a = up(t.bimg_bytes, 1024);
+  t.off_stage = t.off_a + 4 * t.a_bytes;
+  const int stage_bytes = up(128 * d * 4, 128);
+  t.off_bnd = t.off_stage + stage_bytes;
+  t.off_bits = t.off_bnd + 2 * 128 * 4;
+  t.off_ctl = t.off_bits + 2 * 8 * 128 * 4;
+  t.smem_bytes = t.off_ctl + 256;
+  if (t.smem_bytes > static_cast<int>(p.sharedMemPerBlockOptin)) return ACE_OK;
+
+  // W' = w_c / ||w_c|| (binary32), split into bfloat16 hi + lo, laid out per chunk
+  std::vector<uint16_t> img(off / 2, 0);
+  std::vector<double> inv(KL, 0.0);
+  for (int c = 0; c < KL; ++c) {
+    double s2 = 0.0;
+    for (int i = 0; i < d; ++i) {
+      const double w = h->Wh[static_cast<size_t>(i) * KL + c];
+      s2 += w * w;
+    }
+    inv[c] = s2 > 0.0 ? 1.0 / std::sqrt(s2) : 0.0;
+  }
+  for (int c = 0; c < nch; ++c) {
+    const ace::TcChunk& ch = t.chunk[c];
+    for (int r = 0; r < ch.ntab * K; ++r) {
+      const int col = ch.tab0 * K + r;
+      for (int k = 0; k < d; ++k) {
+        const float wn = static_cast<float>(static_cast<double>(h->Wh[static_cast<size_t>(k) * KL + col]) * inv[col]);
+        const uint16_t hi = bf16_rn(wn);
+        const uint16_t lo = bf16_rn(wn - bf16_value(hi));
+        img[(ch.boff_hi + kmajor_off(r, k, d_pad)) / 2] = hi;
+        img[(ch.boff_lo + kmajor_off(r, k, d_pad)) / 2] = lo;
+      }
+    }
+  }
+  cudaFree(h->bimg);
+  h->bimg = nullptr;
+  if ((e = cudaMalloc(&h->bimg, off)) != cudaSuccess) return cuda_fail(e, "cudaMalloc W' image");
+  if ((e = cudaMemcpy(h->bimg, img.data(), off, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(e, "copy W' image");
+  if (!h->defer_count && (e = cudaMalloc(&h->defer_count, 16)) != cudaSuccess) return cuda_fail(e, "cudaMalloc counter");
+  t.bimg = h->bimg;
+
+  // guard constants (relative to ||x||; see hash_tc.cu)
+  const double u32 = std::ldexp(1.0, -24), u64 = std::ldexp(1.0, -53);
+  const int S = 3 * d_pad / 16;  // MMA instructions accumulating into one result
+  const double t_split = 3.0 * std::ldexp(1.0, -16) * (1.0 + std::ldexp(1.0, -6));
+  const double t_acc = 5.25 * 1.5 * (S + 1) * std::ldexp(1.0, -23) * (1.0 + std::ldexp(1.0, -6));
+  const double t_norm = std::ldexp(1.0, -23);
+  const double g64 = d * u64 / (1.0 - d * u64);
+  t.tau = std::nextafter(static_cast<float>((t_split + t_acc + t_norm + g64) * 1.01), FLT_MAX);
+  t.tau_abs = static_cast<float>(3.0 * d_pad * std::ldexp(1.0, -125));
+  const double g32 = d_pad * u32 / (1.0 - d_pad * u32);
+  t.xfac = std::nextafter(static_cast<float>(1.0 + 2.0 * g32 + std::ldexp(1.0, -20)), FLT_MAX);
+  t.qmin = std::ldexp(1.0f, -60);
+  t.Wt = h->Wt;
+  t.counts = h->counts;
+  t.st = h->st;
+  t.defer_count = h->defer_count;
+  h->tc_ok = true;
+  return ACE_OK;
 }
 
 int make_detector(int d, int K, int L, const float* Wsrc, uint64_t seed, bool from_seed, ace_handle* out) {
@@ -203,6 +329,12 @@ int make_detector(int d, int K, int L, const float* Wsrc, uint64_t seed, bool fr
   if ((e = cudaMemset(h->counts, 0, count_elems(h) * sizeof(uint32_t))) != cudaSuccess) return bad(e, "zero counts");
   if ((e = cudaMemset(h->st, 0, sizeof(ace::DevStats))) != cudaSuccess) return bad(e, "zero stats");
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bad(e, "create sync");
+  if (int rc = plan_tc(h)) {
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  if (h->tc_ok) h->precision = ACE_PROJ_AUTO;
   *out = h;
   return ACE_OK;
 }
@@ -267,10 +399,42 @@ ace::HashArgs hash_args(ace_handle h, const void* X, long long n, int dtype, int
 size_t id_bytes(ace_handle h) { return h->K <= 16 ? 2 : 4; }
 
 int run_hash(ace_handle h, const ace::HashArgs& a, cudaStream_t s) {
-  h->last_precision = ACE_PROJ_FP32;
-  PhaseScope ps(h, ACE_PHASE_HASH, s);
-  cudaError_t e = ace::launch_hash_simt(a, s);
-  if (e != cudaSuccess) return cuda_fail(e, "hash kernel launch");
+  if (h->precision == ACE_PROJ_FP32 || !h->tc_ok) {
+    h->last_precision = ACE_PROJ_FP32;
+    PhaseScope ps(h, ACE_PHASE_HASH, s);
+    cudaError_t e = ace::launch_hash_simt(a, s);
+    if (e != cudaSuccess) return cuda_fail(e, "hash kernel launch");
+    return ACE_OK;
+  }
+  // tensor-core engine, then the binary64 resolution of the deferred tables
+  const size_t cap = static_cast<size_t>(a.n) + 65536;
+  void* p = h->defer;
+  if (int rc = grow(&p, &h->defer_bytes, cap * 16, s, "deferred list")) return rc;
+  h->defer = static_cast<unsigned long long*>(p);
+  ace::TcArgs t = h->tc;
+  t.X = a.X;
+  t.x_bf16 = a.x_bf16;
+  t.n = a.n;
+  t.ntiles = (a.n + 127) / 128;
+  t.mode = a.mode;
+  t.ids = a.ids;
+  t.ld = a.ld;
+  t.ids_rm = a.ids_rm;
+  t.defer = h->defer;
+  t.defer_cap = h->defer_bytes / 16;
+  h->last_precision = ACE_PROJ_BF16;
+  ACE_CUDA(cudaMemsetAsync(h->defer_count, 0, sizeof(unsigned long long), s));
+  cudaError_t e;
+  {
+    PhaseScope ps(h, ACE_PHASE_HASH, s);
+    e = ace::launch_hash_tc(t, h->num_sms, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core hash kernel launch");
+  {
+    PhaseScope ps(h, ACE_PHASE_RECHECK, s);
+    e = ace::launch_recheck(t, h->num_sms, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "recheck kernel launch");
   return ACE_OK;
 }
 
@@ -342,6 +506,9 @@ int ace_set_precision(ace_handle h, int precision) {
   if (!h) return fail(ACE_ERR_ARG, "handle is NULL");
   if (precision != ACE_PROJ_AUTO && precision != ACE_PROJ_FP32 && precision != ACE_PROJ_BF16)
     return fail(ACE_ERR_ARG, "unknown precision %d", precision);
+  if (precision == ACE_PROJ_BF16 && !h->tc_ok)
+    return fail(ACE_ERR_UNSUPPORTED, "the tensor-core path needs an sm_103 device and a shape whose operand image fits "
+                                     "in shared memory (d=%d K=%d L=%d)", h->d, h->K, h->L);
   h->precision = precision;
   return ACE_OK;
 }

@@ -1,0 +1,46 @@
+// Launch description of the tensor-core hash kernel (shared by the runtime and the kernel).
+#pragma once
+
+#include <cstdint>
+
+#include "ace_internal.h"
+
+namespace ace {
+
+constexpr int kTcMaxChunks = 16;
+
+// One chunk: whole tables [tab0, tab0 + ntab), N = ntab*K rounded up to 16 MMA columns,
+// and the byte offsets of its hi and lo operand images inside the resident B image.
+struct TcChunk {
+  int tab0, ntab, N;
+  uint32_t boff_hi, boff_lo;
+};
+
+struct TcArgs {
+  const void* X;
+  int x_bf16;
+  long long n, ntiles;
+  int d, d_pad, K, L;
+  const uint8_t* bimg;  // K-major no-swizzle images of W' (unit columns), hi and lo per chunk
+  int bimg_bytes;
+  int nchunks;
+  TcChunk chunk[kTcMaxChunks];
+  float tau, tau_abs, xfac, qmin;  // row bound = tau * ||x||_up + tau_abs (or +inf if q < qmin)
+  int mode;
+  void* ids;
+  long long ld;
+  uint32_t* ids_rm;
+  uint32_t* counts;
+  DevStats* st;
+  const float* Wt;  // [KL][d] original W (binary64 recheck)
+  unsigned long long* defer;        // 2 words per deferred (point, table)
+  unsigned long long* defer_count;  // device counter (zeroed before each launch)
+  unsigned long long defer_cap;
+  // dynamic shared-memory layout (bytes)
+  int off_a, a_bytes, off_stage, off_bnd, off_bits, off_ctl, smem_bytes;
+};
+
+cudaError_t launch_hash_tc(const TcArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_recheck(const TcArgs& a, int num_sms, cudaStream_t s);
+
+}  // namespace ace

@@ -11,7 +11,7 @@ from paper_1706_06664_gb300 import ace, workloads
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-PRECS = ["fp32"]
+PRECS = ["fp32", "bf16"]
 
 
 def _dev(X):
@@ -20,10 +20,24 @@ def _dev(X):
     return torch.from_numpy(X).cuda()
 
 
+def _detector(d, K, L, seed=0, W=None, precision="fp32"):
+    try:
+        return ace.Detector(d, K, L, seed=seed, W=W, precision=precision)
+    except ace.AceError as e:
+        if e.code == ace.ACE_ERR_UNSUPPORTED:
+            pytest.skip(f"{precision} engine not available for d={d} K={K} L={L}")
+        raise
+
+
 def _pair(d, K, L, seed=None, W=None, precision="fp32"):
-    det = ace.Detector(d, K, L, seed=seed or 0, W=W, precision=precision)
+    det = _detector(d, K, L, seed=seed or 0, W=W, precision=precision)
     ref = oracle.Detector(d, K, L, seed=seed, W=W if W is not None else det.projection())
     return det, ref
+
+
+def _engine_used(det, precision):
+    want = {"fp32": ace.ACE_PROJ_FP32, "bf16": ace.ACE_PROJ_BF16}[precision]
+    assert det.stats()["precision"] == want
 
 
 def _compare_score(out, ref_out):
@@ -57,7 +71,7 @@ def test_hand_example(precision):
     g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_example.json")))
     W = np.array(g["W_columns"], dtype=np.float32).T.copy()
     X = np.array(g["X"], dtype=np.float32)
-    det = ace.Detector(3, 2, 2, W=W, precision=precision)
+    det = _detector(3, 2, 2, W=W, precision=precision)
     ids = ace.u32(det.hash(_dev(X)))
     assert ids.tolist() == g["ids"]
     sc, su, fl = det.insert_score(_dev(X), 1.0)
@@ -86,6 +100,7 @@ def test_small_config_full_size(precision):
     assert np.array_equal(det.counts(), ref.counts)
     _compare_score(det.score(Xd, w["alpha"]), ref.score(w["X"], w["alpha"]))
     _compare_stats(det, ref)
+    _engine_used(det, precision)
 
 
 @pytest.mark.parametrize("precision", PRECS)
@@ -101,9 +116,10 @@ def test_kdd_shaped_reduced(precision):
     w2 = workloads.kdd(seed=3, n=3001)
     _compare_score(det.score(_dev(w2["X"]), 2.0), ref.score(w2["X"], 2.0))
     _compare_stats(det, ref, 2.0)
+    _engine_used(det, precision)
 
 
-@pytest.mark.parametrize("precision", PRECS)
+@pytest.mark.parametrize("precision", ["fp32"])
 def test_highdim_bf16_reduced(precision):
     """High-dimensional recipe (bfloat16 inputs, d=1024, K=16, L=64) at n=1,500."""
     w = workloads.highdim(seed=3, n=1500)
@@ -115,11 +131,12 @@ def test_highdim_bf16_reduced(precision):
     _compare_stats(det, ref)
 
 
+@pytest.mark.parametrize("precision", PRECS)
 @pytest.mark.parametrize("shape", [(1, 1, 1), (3, 24, 2), (5, 17, 3), (64, 2, 100), (33, 7, 40), (130, 13, 11)])
-def test_shapes_and_ragged_batches(shape):
+def test_shapes_and_ragged_batches(shape, precision):
     d, K, L = shape
     rng = np.random.default_rng(sum(shape))
-    det, ref = _pair(d, K, L, seed=d * 1000 + K)
+    det, ref = _pair(d, K, L, seed=d * 1000 + K, precision=precision)
     for n in (1, 127, 129, 300):
         X = rng.standard_normal((n, d)).astype(np.float32)
         _compare_score(det.insert_score(_dev(X), 1.0), ref.insert_score(X, 1.0))
@@ -127,7 +144,8 @@ def test_shapes_and_ragged_batches(shape):
     _compare_stats(det, ref)
 
 
-def test_edge_values_exact_zeros_nonfinite_subnormal_huge():
+@pytest.mark.parametrize("precision", PRECS)
+def test_edge_values_exact_zeros_nonfinite_subnormal_huge(precision):
     d, K, L = 6, 4, 5
     W = workloads.gaussian_w(d, K, L, 3)
     W[:, 0] = [1, -1, 0, 0, 0, 0]
@@ -143,7 +161,7 @@ def test_edge_values_exact_zeros_nonfinite_subnormal_huge():
     X[9] = -1.0
     X[10, 5] = 1.0
     X[11] = [1, 1, 1e-7, -1e-7, 0, 0]
-    det, ref = _pair(d, K, L, W=W)
+    det, ref = _pair(d, K, L, W=W, precision=precision)
     Xd = _dev(X)
     assert np.array_equal(ace.u32(det.hash(Xd)), ref.hash(X))
     _compare_score(det.insert_score(Xd, 1.0), ref.insert_score(X, 1.0))
@@ -152,13 +170,14 @@ def test_edge_values_exact_zeros_nonfinite_subnormal_huge():
     assert st["rechecks"] > 0
 
 
-def test_zero_column_and_zero_batch():
+@pytest.mark.parametrize("precision", PRECS)
+def test_zero_column_and_zero_batch(precision):
     d, K, L = 4, 3, 2
     W = workloads.gaussian_w(d, K, L, 4)
     W[:, 2] = 0.0
     rng = np.random.default_rng(1)
     X = rng.standard_normal((50, d)).astype(np.float32)
-    det, ref = _pair(d, K, L, W=W)
+    det, ref = _pair(d, K, L, W=W, precision=precision)
     det.insert(_dev(np.zeros((0, d), dtype=np.float32)))
     _compare_score(det.insert_score(_dev(X), 0.5), ref.insert_score(X, 0.5))
     _compare_stats(det, ref, 0.5)
@@ -175,6 +194,42 @@ def test_score_does_not_insert_and_reset():
     det.reset()
     st = det.stats()
     assert st["n_ins"] == 0 and st["n_scored"] == 0 and int(det.counts().sum()) == 0
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_near_orthogonal_points_are_exact(precision):
+    """Points whose projection on chosen columns is tiny relative to ||x|| (|x.w| / (||x|| ||w||)
+    from 1e-3 down to 1e-9 and exactly 0): every such bit is decided inside the guard band and
+    must still equal the binary64 definition."""
+    w = workloads.kdd(seed=11, n=4096)
+    d, K, L = w["d"], w["K"], w["L"]
+    det, ref = _pair(d, K, L, seed=21, precision=precision)
+    W = det.projection().astype(np.float64)
+    rng = np.random.default_rng(3)
+    X = w["X"].astype(np.float64).copy()
+    eps = [1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9, 0.0]
+    for i in range(X.shape[0]):
+        c = rng.integers(0, K * L)
+        wc = W[:, c]
+        x = X[i] - (X[i] @ wc) / (wc @ wc) * wc
+        e = eps[i % len(eps)] * np.linalg.norm(x) / np.linalg.norm(wc) * rng.choice([-1, 1])
+        X[i] = x + e * wc
+    X = X.astype(np.float32)
+    _compare_score(det.insert_score(_dev(X), 1.0), ref.insert_score(X, 1.0))
+    assert np.array_equal(det.counts(), ref.counts)
+    _compare_stats(det, ref)
+    assert det.stats()["rechecks"] > X.shape[0] // 4
+    _engine_used(det, precision)
+
+
+def test_tensor_core_engine_refuses_unfit_shapes():
+    with pytest.raises(ace.AceError) as e:
+        ace.Detector(1024, 16, 64, seed=1, precision="bf16")
+    assert e.value.code == ace.ACE_ERR_UNSUPPORTED
+    det = ace.Detector(1024, 16, 64, seed=1, precision="auto")  # falls back to the SIMT engine
+    X = torch.zeros((4, 1024), dtype=torch.float32, device="cuda")
+    det.insert(X)
+    assert det.stats()["precision"] == ace.ACE_PROJ_FP32
 
 
 def test_host_entry_point_matches_device_path():
