@@ -175,7 +175,7 @@ const char* ace_last_error(void);
  * every kernel the library launched on this handle since creation or the last read.
  */
 enum { ACE_PHASE_HASH = 0, ACE_PHASE_SCORE = 1, ACE_PHASE_FLAGS = 2, ACE_PHASE_OTHER = 3, ACE_PHASE_RECHECK = 4,
-       ACE_NPHASE = 5 };
+       ACE_PHASE_INSERT = 5, ACE_NPHASE = 6 };
 typedef struct {
   uint64_t launches[ACE_NPHASE]; /* kernels launched per phase                           */
   double ms[ACE_NPHASE];         /* summed event time per phase (enabled periods only)   */

@@ -27,7 +27,7 @@ EXPORTS = [
     "ace_profile_enable", "ace_profile_read", "ace_insert_score_noalloc",
 ]
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
-PHASES = ("hash", "score", "flags", "other", "recheck")
+PHASES = ("hash", "score", "flags", "other", "recheck", "insert")
 
 
 class AceError(RuntimeError):
@@ -49,7 +49,7 @@ class ace_stats_t(ctypes.Structure):
 
 
 class ace_profile_t(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_uint64 * 5), ("ms", ctypes.c_double * 5), ("timed", ctypes.c_uint64 * 5)]
+    _fields_ = [("launches", ctypes.c_uint64 * 6), ("ms", ctypes.c_double * 6), ("timed", ctypes.c_uint64 * 6)]
 
 
 _lib = None

@@ -66,10 +66,10 @@ struct ace_detector {
   uint8_t* bimg = nullptr;    // resident operand image of W' (device)
   unsigned long long* defer = nullptr;
   size_t defer_bytes = 0;
-  unsigned long long* defer_count = nullptr;
+  unsigned int* defer_counts = nullptr;  // one per CTA of the tensor-core kernel
   // profiling hook
   bool prof = false;
-  uint64_t launches[ACE_NPHASE] = {0, 0, 0, 0, 0};
+  uint64_t launches[ACE_NPHASE] = {0, 0, 0, 0, 0, 0};
   struct Mark {
     int phase;
     cudaEvent_t a, b;
@@ -122,7 +122,7 @@ void free_all(ace_detector* h) {
   h->pool.clear();
   cudaFree(h->bimg);
   cudaFree(h->defer);
-  cudaFree(h->defer_count);
+  cudaFree(h->defer_counts);
   cudaFree(h->W);
   cudaFree(h->Wt);
   cudaFree(h->cB);
@@ -187,8 +187,9 @@ int plan_tc(ace_detector* h) {
   h->num_sms = p.multiProcessorCount;
   if (p.major != 10 || p.minor != 3) return ACE_OK;
   const int d = h->d, K = h->K, L = h->L, KL = h->KL;
+  if (d > ace::kMaxD) return ACE_OK;
   const int d_pad = (d + 15) / 16 * 16;
-  const int tpc = 256 / K;
+  const int tpc = std::min(256 / K, 32);  // at most 32 tables per chunk (32-bit table masks)
   const int nch = (L + tpc - 1) / tpc;
   if (nch > ace::kTcMaxChunks) return ACE_OK;
   ace::TcArgs& t = h->tc;
@@ -214,10 +215,9 @@ int plan_tc(ace_detector* h) {
   t.a_bytes = 128 * d_pad * 2;
   t.off_a = up(t.bimg_bytes, 1024);
   t.off_stage = t.off_a + 4 * t.a_bytes;
-  const int stage_bytes = up(128 * d * 4, 128);
-  t.off_bnd = t.off_stage + stage_bytes;
+  t.off_bnd = t.off_stage + up(128 * d * 4, 128);
   t.off_bits = t.off_bnd + 2 * 128 * 4;
-  t.off_ctl = t.off_bits + 2 * 8 * 128 * 4;
+  t.off_ctl = t.off_bits;
   t.smem_bytes = t.off_ctl + 256;
   if (t.smem_bytes > static_cast<int>(p.sharedMemPerBlockOptin)) return ACE_OK;
 
@@ -250,7 +250,9 @@ int plan_tc(ace_detector* h) {
   if ((e = cudaMalloc(&h->bimg, off)) != cudaSuccess) return cuda_fail(e, "cudaMalloc W' image");
   if ((e = cudaMemcpy(h->bimg, img.data(), off, cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_fail(e, "copy W' image");
-  if (!h->defer_count && (e = cudaMalloc(&h->defer_count, 16)) != cudaSuccess) return cuda_fail(e, "cudaMalloc counter");
+  if (!h->defer_counts &&
+      (e = cudaMalloc(&h->defer_counts, sizeof(unsigned int) * static_cast<size_t>(h->num_sms))) != cudaSuccess)
+    return cuda_fail(e, "cudaMalloc deferred counters");
   t.bimg = h->bimg;
 
   // guard constants (relative to ||x||; see hash_tc.cu)
@@ -266,9 +268,14 @@ int plan_tc(ace_detector* h) {
   t.xfac = std::nextafter(static_cast<float>(1.0 + 2.0 * g32 + std::ldexp(1.0, -20)), FLT_MAX);
   t.qmin = std::ldexp(1.0f, -60);
   t.Wt = h->Wt;
+  t.W = h->W;
+  t.cB32 = h->cB;
+  t.xfac32 = h->xfac;
+  t.xabs32 = h->xabs;
+  t.babs32 = h->babs;
   t.counts = h->counts;
   t.st = h->st;
-  t.defer_count = h->defer_count;
+  t.defer_counts = h->defer_counts;
   h->tc_ok = true;
   return ACE_OK;
 }
@@ -406,24 +413,32 @@ int run_hash(ace_handle h, const ace::HashArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return cuda_fail(e, "hash kernel launch");
     return ACE_OK;
   }
-  // tensor-core engine, then the binary64 resolution of the deferred tables
+  // tensor-core engine (ids only), the binary64 resolution of the deferred tables, then the
+  // count increments from the stored ids
+  const bool insert = (a.mode & ace::kInsert) != 0;
+  void* ids = a.ids;
+  if (insert && !ids) {
+    if (int rc = grow(&h->ids, &h->ids_cap, static_cast<size_t>(a.n) * h->L * id_bytes(h), s, "ids scratch"))
+      return rc;
+    ids = h->ids;
+  }
   const size_t cap = static_cast<size_t>(a.n) + 65536;
   void* p = h->defer;
-  if (int rc = grow(&p, &h->defer_bytes, cap * 16, s, "deferred list")) return rc;
+  if (int rc = grow(&p, &h->defer_bytes, cap * 8, s, "deferred list")) return rc;
   h->defer = static_cast<unsigned long long*>(p);
   ace::TcArgs t = h->tc;
   t.X = a.X;
   t.x_bf16 = a.x_bf16;
   t.n = a.n;
   t.ntiles = (a.n + 127) / 128;
-  t.mode = a.mode;
-  t.ids = a.ids;
+  const long long grid = std::min(static_cast<long long>(h->num_sms), t.ntiles);
+  t.mode = (a.mode & ~ace::kInsert) | (insert ? ace::kStoreIds : 0);
+  t.ids = ids;
   t.ld = a.ld;
   t.ids_rm = a.ids_rm;
   t.defer = h->defer;
-  t.defer_cap = h->defer_bytes / 16;
+  t.seg_cap = h->defer_bytes / 8 / static_cast<size_t>(grid);
   h->last_precision = ACE_PROJ_BF16;
-  ACE_CUDA(cudaMemsetAsync(h->defer_count, 0, sizeof(unsigned long long), s));
   cudaError_t e;
   {
     PhaseScope ps(h, ACE_PHASE_HASH, s);
@@ -435,6 +450,11 @@ int run_hash(ace_handle h, const ace::HashArgs& a, cudaStream_t s) {
     e = ace::launch_recheck(t, h->num_sms, s);
   }
   if (e != cudaSuccess) return cuda_fail(e, "recheck kernel launch");
+  if (insert) {
+    PhaseScope ps(h, ACE_PHASE_INSERT, s);
+    e = ace::launch_insert_from_ids(ids, h->K <= 16, a.ld, a.n, h->K, h->L, h->counts, h->num_sms, s);
+    if (e != cudaSuccess) return cuda_fail(e, "insert kernel launch");
+  }
   return ACE_OK;
 }
 

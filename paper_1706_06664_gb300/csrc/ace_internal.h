@@ -5,7 +5,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
-#include "../../include/ace.h"
+#include "ace.h"
 
 namespace ace {
 
@@ -55,6 +55,8 @@ cudaError_t launch_score_gather(const void* ids, int ids16, long long ld, long l
                                 const uint32_t* counts, uint32_t* sums, DevStats* st, cudaStream_t s);
 cudaError_t launch_flags(const uint32_t* sums, long long n, int L, double alpha, DevStats* st,
                          double* scores, uint8_t* flags, cudaStream_t s);
+cudaError_t launch_insert_from_ids(const void* ids, int ids16, long long ld, long long n, int K, int L,
+                                   uint32_t* counts, int num_sms, cudaStream_t s);
 cudaError_t launch_sum_squares(const uint32_t* counts, long long total, DevStats* st, cudaStream_t s);
 
 // Host-side generator of the projection matrix (SplitMix64 counter mode + Box-Muller).

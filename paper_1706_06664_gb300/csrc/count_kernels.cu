@@ -168,7 +168,85 @@ __global__ void __launch_bounds__(256) sum_squares_kernel(const uint32_t* __rest
   }
 }
 
+// Counting phase (Algorithm 1; §3.2) from cached table-major ids.  CTA (j, part, range)
+// counts the ids of table j among points [range] whose bucket lies in bucket part `part`,
+// in a shared-memory histogram (at most 16,384 bins = 64 KB), then adds the non-zero bins to
+// A_j with atomicAdd.  Counts are exact integers, so the order of the additions is irrelevant.
+template <typename IdT>
+__global__ void __launch_bounds__(512) insert_hist_kernel(const IdT* __restrict__ ids, long long ld, long long n,
+                                                          int K, int nparts, int nranges,
+                                                          uint32_t* __restrict__ counts) {
+  extern __shared__ uint32_t hist[];
+  const int bins = (1 << K) / nparts;
+  const int j = blockIdx.x / (nparts * nranges);
+  const int part = (blockIdx.x / nranges) % nparts;
+  const int rr = blockIdx.x % nranges;
+  const long long per = (n + nranges - 1) / nranges;
+  const long long i0 = rr * per;
+  const long long i1 = min(n, i0 + per);
+  const uint32_t lo = static_cast<uint32_t>(part) * static_cast<uint32_t>(bins);
+  for (int b = threadIdx.x; b < bins; b += blockDim.x) hist[b] = 0u;
+  __syncthreads();
+  const IdT* col = ids + static_cast<size_t>(j) * ld;
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const uint32_t rel = static_cast<uint32_t>(col[i]) - lo;
+    if (rel < static_cast<uint32_t>(bins)) atomicAdd(&hist[rel], 1u);
+  }
+  __syncthreads();
+  uint32_t* dst = counts + (static_cast<size_t>(j) << K) + lo;
+  for (int b = threadIdx.x; b < bins; b += blockDim.x) {
+    const uint32_t v = hist[b];
+    if (v) atomicAdd(dst + b, v);
+  }
+}
+
+// Same counting for wide tables (K > 16): warp-merged global atomics.
+template <typename IdT>
+__global__ void __launch_bounds__(256) insert_direct_kernel(const IdT* __restrict__ ids, long long ld, long long n,
+                                                            int K, int L, uint32_t* __restrict__ counts) {
+  const long long total = n * L;
+  for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int j = static_cast<int>(e / n);
+    const long long i = e - static_cast<long long>(j) * n;
+    atomicAdd(counts + (static_cast<size_t>(j) << K) + ids[static_cast<size_t>(j) * ld + i], 1u);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_insert_from_ids(const void* ids, int ids16, long long ld, long long n, int K, int L,
+                                   uint32_t* counts, int num_sms, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (K <= 16) {
+    const int nparts = K <= 14 ? 1 : (1 << (K - 14));
+    const int bins = (1 << K) / nparts;
+    const long long want = 2LL * num_sms;
+    int nranges = static_cast<int>((want + static_cast<long long>(L) * nparts - 1) / (static_cast<long long>(L) * nparts));
+    nranges = max(1, min(nranges, static_cast<int>((n + 4095) / 4096)));
+    const long long blocks = static_cast<long long>(L) * nparts * nranges;
+    const size_t smem = static_cast<size_t>(bins) * sizeof(uint32_t);
+    cudaError_t e;
+    if (ids16) {
+      e = cudaFuncSetAttribute(insert_hist_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+      if (e != cudaSuccess) return e;
+      insert_hist_kernel<uint16_t><<<static_cast<unsigned>(blocks), 512, smem, s>>>(
+          static_cast<const uint16_t*>(ids), ld, n, K, nparts, nranges, counts);
+    } else {
+      e = cudaFuncSetAttribute(insert_hist_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+      if (e != cudaSuccess) return e;
+      insert_hist_kernel<uint32_t><<<static_cast<unsigned>(blocks), 512, smem, s>>>(
+          static_cast<const uint32_t*>(ids), ld, n, K, nparts, nranges, counts);
+    }
+    return cudaGetLastError();
+  }
+  const unsigned blocks = static_cast<unsigned>(num_sms * 8);
+  if (ids16)
+    insert_direct_kernel<uint16_t><<<blocks, 256, 0, s>>>(static_cast<const uint16_t*>(ids), ld, n, K, L, counts);
+  else
+    insert_direct_kernel<uint32_t><<<blocks, 256, 0, s>>>(static_cast<const uint32_t*>(ids), ld, n, K, L, counts);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_score_gather(const void* ids, int ids16, long long ld, long long n, int K, int L,
                                 const uint32_t* counts, uint32_t* sums, DevStats* st, cudaStream_t s) {

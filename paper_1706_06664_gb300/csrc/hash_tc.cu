@@ -16,29 +16,36 @@
 //     margin is applied);
 //   - normalisation: w' is w_c / ||w_c|| rounded to binary32 elementwise (2^-24);
 //   - the binary64 reference itself (gamma64_d).
-// A point whose |projection| is inside the bound on some column of a table is appended to a
-// deferred list; recheck_kernel recomputes those bits in binary64 (index order) and inserts
-// the final ids, so every id equals the binary64 definition.
+// A (point, table) pair with a projection inside the bound on some column is appended to a
+// deferred list; recheck_kernel recomputes that table's K bits exactly (binary32 with the
+// SIMT bound, binary64 inside it) and stores the final id, so every id equals the binary64
+// definition.
 //
 // Roles (one CTA per SM, persistent over 128-point tiles):
 //   warp 0       TMEM allocation, B image load (resident W'), MMA issue (one lane)
-//   warps 1-4    converters: X tile (bulk copy into staging, or plain loads for the tail)
-//                -> bf16 hi/lo operand images + per-row bound
-//   warps 5-8    epilogue: tcgen05.ld, guard classification, bit packing, id store,
-//                warp-merged count increments, deferral of ambiguous tables
+//   warps 1-4    converters: X tile bulk-copied into a staging buffer (TMA engine), one
+//                row per thread -> bf16 hi/lo operand images + per-row bound
+//   warps 5-12   epilogue, two groups alternating TMEM buffers: tcgen05.ld, guard
+//                classification, streaming bit packing, id store, deferral of ambiguous
+//                tables to this CTA's segment of the deferred list
+// The count increments (Algorithm 1 counting phase) run afterwards in insert_hist_kernel,
+// from the stored ids, with per-table shared-memory histograms.
 #include "guard.cuh"
 #include "tc_ptx.cuh"
 #include "tc_plan.h"
+
+#include <type_traits>
 
 namespace ace {
 namespace {
 
 using namespace tc;
 
-constexpr int kThreads = 288;
-constexpr int kConv0 = 32;    // first converter thread
-constexpr int kEpi0 = 160;    // first epilogue thread
+constexpr int kThreads = 416;  // 13 warps: MMA, 4 converters, 2 x 4 epilogue
+constexpr int kConv0 = 32;     // first converter thread
+constexpr int kEpi0 = 160;     // first epilogue thread
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
+constexpr int kMaxSeg = 1024;                    // per-CTA deferred segments (grid <= this)
 
 struct Smem {
   uint64_t st_full;
@@ -49,6 +56,7 @@ struct Smem {
   uint64_t t_full[2], t_empty[2];
   uint32_t taddr;
   int abort;
+  unsigned int ndef;  // entries in this CTA's deferred segment
 };
 
 __device__ __forceinline__ void set_abort(Smem* S, DevStats* st) {
@@ -88,25 +96,54 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-template <bool BF16, typename IdT>
+// The exact bucket id of table j for point i, for the rare path where a CTA's deferred list
+// is full: each of the K projections in binary32 with the SIMT engine's bound, binary64
+// (the definition) when inside it.
+template <bool BF16>
+__device__ __noinline__ uint32_t exact_table_id(const void* X, long long i, int d, int K, int j, const float* Wt,
+                                                const float* cB32, float xfac32, float xabs32, float babs32,
+                                                DevStats* st) {
+  float q = 0.f;
+  for (int t = 0; t < d; ++t) {
+    const float x = load_x<BF16>(X, i * d + t);
+    q = fmaf(x, x, q);
+  }
+  const float xu = norm_upper(q, xfac32, xabs32);
+  uint32_t id = 0u;
+  for (int k = 0; k < K; ++k) {
+    const int col = j * K + k;
+    const float* wc = Wt + static_cast<size_t>(col) * d;
+    float s32 = 0.f;
+    for (int t = 0; t < d; ++t) s32 = fmaf(load_x<BF16>(X, i * d + t), __ldg(wc + t), s32);
+    bool bit;
+    if (fabsf(s32) > fmaf(__ldg(cB32 + col), xu, babs32)) bit = s32 > 0.f;
+    else bit = exact_bit<BF16>(X, i, d, Wt, col);
+    id |= (bit ? 1u : 0u) << k;
+  }
+  atomicAdd(&st->rechecks, static_cast<unsigned long long>(K));
+  return id;
+}
+
+// KC > 0: the kernel is specialised for K = KC (the table offsets inside a chunk are then
+// compile-time constants and the pack is a fully unrolled, branch-free sequence); KC = 0
+// handles any K with a streaming extractor.
+template <bool BF16, typename IdT, int KC>
 __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_constant__ TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* Bimg = smem;
+  uint8_t* stage = smem + a.off_stage;
   // A stage s: hi image at off_a + 2 s a_bytes, lo image right after it
   auto a_hi = [&](int st) { return smem + a.off_a + 2 * st * a.a_bytes; };
   auto a_lo = [&](int st) { return smem + a.off_a + (2 * st + 1) * a.a_bytes; };
-  uint8_t* stage = smem + a.off_stage;
   float* bnd = reinterpret_cast<float*>(smem + a.off_bnd);          // [2][128]
-  uint32_t* wbits = reinterpret_cast<uint32_t*>(smem + a.off_bits);  // [8][128]
-  uint32_t* wamb = wbits + 8 * 128;                                  // [8][128]
   Smem* S = reinterpret_cast<Smem*>(smem + a.off_ctl);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long ntiles = a.ntiles;
-  const int esz = BF16 ? 2 : 4;
 
   if (tid == 0) {
     S->abort = 0;
+    S->ndef = 0;
     mbar_init(&S->st_full, 1);
     mbar_init(&S->b_full, 1);
     mbar_init(&S->drain, 1);
@@ -114,12 +151,20 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
       mbar_init(&S->a_full[s], 128);
       mbar_init(&S->a_empty[s], 1);
       mbar_init(&S->bnd_full[s], 128);
-      mbar_init(&S->bnd_empty[s], 128);
+      mbar_init(&S->bnd_empty[s], 256);
       mbar_init(&S->t_full[s], 1);
       mbar_init(&S->t_empty[s], 128);
     }
     mbar_fence_init();
   }
+  // zero both A stages once: the padding columns k >= d are never written again
+  for (int i = tid; i < a.a_bytes; i += kThreads) {
+    a_hi(0)[i] = 0;
+    a_lo(0)[i] = 0;
+    a_hi(1)[i] = 0;
+    a_lo(1)[i] = 0;
+  }
+  fence_proxy_async();
   if (warp == 0) {
     tmem_alloc(&S->taddr, 512);
     tmem_relinquish();
@@ -175,8 +220,8 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
         if (!ok) break;
         mma_commit(&S->a_empty[s]);
       }
-      // drain: wait until every MMA this thread issued has completed
-      // (bounded by time only: TMEM must not be released under a running MMA)
+      // drain: every MMA this thread issued has completed before TMEM is released
+      // (bounded by time only)
       const int never = 0;
       mma_commit(&S->drain);
       if (!mbar_wait(&S->drain, 0, &never, kWaitCycles)) set_abort(S, a.st);
@@ -184,18 +229,30 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
     __syncwarp();
   } else if (warp >= 1 && warp <= 4) {
     // ------------------------------------------------------------------ converters
-    const int r = tid - kConv0;  // row of the tile
-    const bool aligned = (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0;
-    const uint32_t tile_bytes = static_cast<uint32_t>(128) * a.d * esz;
-    auto full_tile = [&](long long m) { return aligned && (m + 1) * 128 <= a.n; };
-    int staged = 0;        // staging-buffer phases consumed
-    bool pending = false;  // (thread r == 0) a bulk copy into the staging buffer is in flight
+    // Tiles arrive in a staging buffer by bulk copy (the TMA engine); thread r converts row r
+    // of the tile into its bfloat16 hi/lo operand rows (16-byte stores) and derives the row's
+    // bound.  The tail tile (and an unaligned X) is read with plain loads instead.
+    const int r = tid - kConv0;
+    const int d = a.d, d_pad = a.d_pad;
+    const long long n = a.n;
+    const void* const X = a.X;
+    const float tau = a.tau, tau_abs = a.tau_abs, xfac = a.xfac, qmin = a.qmin;
+    DevStats* const st = a.st;
+    const bool aligned = (reinterpret_cast<uintptr_t>(X) & 15u) == 0;
+    const uint32_t tile_bytes = static_cast<uint32_t>(128) * d * (BF16 ? 2 : 4);
+    auto full_tile = [&](long long m) { return aligned && (m + 1) * 128 <= n; };
+    auto issue_copy = [&](long long m) {
+      mbar_expect_tx(&S->st_full, tile_bytes);
+      bulk_g2s(stage, static_cast<const uint8_t*>(X) + static_cast<size_t>(m) * tile_bytes, tile_bytes, &S->st_full);
+    };
+    int staged = 0;        // staging phases consumed
+    bool pending = false;  // (r == 0) a copy is in flight
     if (r == 0 && blockIdx.x < ntiles && full_tile(blockIdx.x)) {
       pending = true;
-      mbar_expect_tx(&S->st_full, tile_bytes);
-      bulk_g2s(stage, static_cast<const uint8_t*>(a.X) + static_cast<size_t>(blockIdx.x) * tile_bytes, tile_bytes,
-               &S->st_full);
+      issue_copy(blockIdx.x);
     }
+    const int rot = (d & 1) ? 0 : r;  // even d: rotate the read order across rows (banks)
+    const int ngrp = d_pad / 8;
     int tl = 0;
     for (long long m = blockIdx.x; m < ntiles; m += gridDim.x, ++tl) {
       const int s = tl & 1;
@@ -203,8 +260,8 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
       bool ok = S->abort == 0;
       if (ok && full) {
         if (mbar_wait(&S->st_full, staged & 1, &S->abort, kWaitCycles)) {
-          if (r == 0) pending = false;
           ++staged;
+          if (r == 0) pending = false;
         } else {
           ok = false;
           set_abort(S, a.st);
@@ -220,10 +277,8 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
       // every converter reaches the barrier; stopping is decided for all of them at once
       if (conv_bar_or(!ok)) break;
       const long long i = m * 128 + r;
-      const bool valid = i < a.n;
+      const bool valid = i < n;
       float q = 0.f;
-      const int ngrp = a.d_pad / 8;
-      const int rot = (a.d & 1) ? 0 : r;  // rotate the read order when d is even (bank spread)
       for (int gi = 0; gi < ngrp; ++gi) {
         const int g = (gi + rot) % ngrp;
         float v[8];
@@ -231,10 +286,10 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
         for (int e = 0; e < 8; ++e) {
           const int k = g * 8 + e;
           float x = 0.f;
-          if (valid && k < a.d) {
-            if (full) x = BF16 ? __uint_as_float(static_cast<unsigned>(reinterpret_cast<const unsigned short*>(stage)[r * a.d + k]) << 16)
-                               : reinterpret_cast<const float*>(stage)[r * a.d + k];
-            else x = xval<BF16>(a.X, i * a.d + k);
+          if (valid && k < d) {
+            if (full) x = BF16 ? __uint_as_float(static_cast<unsigned>(reinterpret_cast<const unsigned short*>(stage)[r * d + k]) << 16)
+                               : reinterpret_cast<const float*>(stage)[r * d + k];
+            else x = xval<BF16>(X, i * d + k);
           }
           v[e] = x;
           q = fmaf(x, x, q);
@@ -247,41 +302,55 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
           hi[e] = pack_bf16x2(h0, h1);
           lo[e] = pack_bf16x2(v[2 * e] - h0, v[2 * e + 1] - h1);
         }
-        const uint32_t off = kmajor_offset(r, g * 8, a.d_pad);
+        const uint32_t off = kmajor_offset(r, g * 8, d_pad);
         *reinterpret_cast<uint4*>(a_hi(s) + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
         *reinterpret_cast<uint4*>(a_lo(s) + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
       }
-      // per-row bound: tau * ||x||_up + tau_abs; +inf forces a binary64 recheck of every column
+      // row bound: tau * ||x||_up + tau_abs; +inf makes every column of the row a recheck
       float B;
-      if (!isfinite(q) || q < a.qmin) B = __int_as_float(0x7f800000);
-      else B = fmaf(a.tau, sqrtf(q * a.xfac) * 1.00000095367431640625f, a.tau_abs);
+      if (!isfinite(q) || q < qmin) B = __int_as_float(0x7f800000);
+      else B = fmaf(tau, sqrtf(q * xfac) * 1.00000095367431640625f, tau_abs);
       bnd[s * 128 + r] = B;
-      if (valid && !isfinite(q)) atomicAdd(&a.st->nonfinite, 1ull);
+      if (valid && !isfinite(q)) atomicAdd(&st->nonfinite, 1ull);
       fence_proxy_async();
       mbar_arrive(&S->a_full[s]);
       mbar_arrive(&S->bnd_full[s]);
-      conv_bar_or(false);  // every converter has finished reading the staging buffer
+      conv_bar_or(false);  // every converter is done with the staging buffer
       const long long mn = m + gridDim.x;
       if (r == 0 && mn < ntiles && full_tile(mn)) {
         pending = true;
-        mbar_expect_tx(&S->st_full, tile_bytes);
-        bulk_g2s(stage, static_cast<const uint8_t*>(a.X) + static_cast<size_t>(mn) * tile_bytes, tile_bytes,
-                 &S->st_full);
+        issue_copy(mn);
       }
     }
-    // leave no bulk copy in flight: wait (bounded, ignoring the abort flag) for an issued
-    // copy that was never consumed
+    // leave no bulk copy in flight (bounded wait that ignores the abort flag)
     if (r == 0 && pending) {
       const int never = 0;
       mbar_wait(&S->st_full, staged & 1, &never, kWaitCycles);
     }
   } else {
     // ------------------------------------------------------------------ epilogue
+    // Two groups of four warps; group wg takes the work items whose TMEM buffer is wg.
+    // Every parameter is copied into registers first: the loop stores to global memory, and
+    // a field re-read from the parameter block after each store would cost a load each time.
+    const int et = tid - kEpi0;
+    const int wg = et >> 7;
     const int q4 = warp & 3;
     const int r = q4 * 32 + lane;  // TMEM lane = tile row
-    const int et = tid - kEpi0;    // 0..127, for the bits scratch
-    (void)et;
-    const unsigned lanemask_lt = (1u << lane) - 1u;
+    const int K = KC > 0 ? KC : a.K;
+    const int L = a.L, mode = a.mode, nch = a.nchunks, d = a.d;
+    const bool st_tm = (mode & kStoreIds) != 0, st_rm = (mode & kStoreIdsRowMajor) != 0;
+    const int tpc = min(256 / K, 32);  // tables per chunk (the host plans chunks the same way)
+    const long long n = a.n, ld = a.ld;
+    IdT* const ids = reinterpret_cast<IdT*>(a.ids);
+    uint32_t* const ids_rm = a.ids_rm;
+    const unsigned long long seg_cap = a.seg_cap;
+    const void* const X = a.X;
+    const float* const Wt = a.Wt;
+    const float* const cB32 = a.cB32;
+    const float xfac32 = a.xfac32, xabs32 = a.xabs32, babs32 = a.babs32;
+    DevStats* const st = a.st;
+    const uint32_t kmask = (1u << K) - 1u;
+    unsigned long long* seg = a.defer + seg_cap * blockIdx.x;
     long long item = 0;
     int tl = 0;
     bool ok = true;
@@ -290,101 +359,137 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
       ok = mbar_wait(&S->bnd_full[s], (tl >> 1) & 1, &S->abort, kWaitCycles);
       if (!__all_sync(0xFFFFFFFFu, ok)) {
         ok = false;
-        set_abort(S, a.st);
+        set_abort(S, st);
         break;
       }
       const float B = bnd[s * 128 + r];
       mbar_arrive(&S->bnd_empty[s]);
       const long long i = m * 128 + r;
-      const bool valid = i < a.n;
-      for (int c = 0; c < a.nchunks; ++c, ++item) {
+      const bool valid = i < n;
+      for (int c = 0; c < nch; ++c, ++item) {
         const int b = static_cast<int>(item & 1);
+        if (b != wg) continue;
         ok = mbar_wait(&S->t_full[b], (item >> 1) & 1, &S->abort, kWaitCycles);
         if (!__all_sync(0xFFFFFFFFu, ok)) {
           ok = false;
-          set_abort(S, a.st);
+          set_abort(S, st);
           break;
         }
         tc_fence_after();
-        const TcChunk& ch = a.chunk[c];
-        const int ncols = ch.ntab * a.K;
+        const int tab0 = c * tpc;
+        const int ntab = min(tpc, L - tab0);
+        const int ncols = ntab * K;
         const int ng = (ncols + 31) >> 5;
         const uint32_t tbase = tmem + (static_cast<uint32_t>(q4 * 32) << 16) + static_cast<uint32_t>(b * 256);
-#pragma unroll 1
-        for (int g = 0; g < ng; ++g) {
-          uint32_t v[32];
-          tmem_ld32(tbase + 32u * g, v);
-          tmem_ld_wait();
-          const int left = ncols - 32 * g;
-          const uint32_t vmask = left >= 32 ? 0xFFFFFFFFu : ((1u << left) - 1u);
-          uint32_t neg = 0;
-          bool any = false;
+        // Classify the chunk's columns.  bw[g] bit k = [column 32g+k > 0].  A table with any
+        // column inside the bound (|projection| <= B, compared on bit patterns: both are
+        // non-negative floats; Bi = all ones for a row whose bound is +inf) is deferred whole
+        // to the recheck kernel.  The next 32 columns are loaded from TMEM while the current
+        // ones are classified; signs are packed by four independent funnel-shift chains.
+        const uint32_t Bi = isinf(B) ? 0xFFFFFFFFu : __float_as_uint(B);
+        uint32_t bw[8];
+        uint32_t va[32], vb[32];
+        uint32_t defmask = 0u;  // bit t: table t of the chunk has a column inside the bound
+        constexpr int TPC = KC > 0 ? 256 / KC : 1;
+        uint32_t tmin[TPC];
 #pragma unroll
-          for (int k = 0; k < 32; ++k) {
-            neg |= (v[k] >> 31) << k;
-            any |= !(fabsf(__uint_as_float(v[k])) > B);
-          }
-          uint32_t am = 0;
-          if (any) {
+        for (int t = 0; t < TPC; ++t) tmin[t] = 0xFFFFFFFFu;
+        uint32_t aw[8];
+        tmem_ld32(tbase, va);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) am |= (!(fabsf(__uint_as_float(v[k])) > B) ? 1u : 0u) << k;
-            am &= vmask;
-          }
-          wbits[g * 128 + r] = ~neg;
-          wamb[g * 128 + r] = am;
-        }
-        tc_fence_before();
-        mbar_arrive(&S->t_empty[b]);
-        // pack, resolve, store, insert
-        for (int t = 0; t < ch.ntab; ++t) {
-          const int cb = t * a.K;
-          const int w0 = cb >> 5, sh = cb & 31;
-          unsigned long long bv = wbits[w0 * 128 + r], av = wamb[w0 * 128 + r];
-          if (w0 + 1 < ng) {
-            bv |= static_cast<unsigned long long>(wbits[(w0 + 1) * 128 + r]) << 32;
-            av |= static_cast<unsigned long long>(wamb[(w0 + 1) * 128 + r]) << 32;
-          }
-          const uint32_t kmask = (1u << a.K) - 1u;
-          uint32_t id = static_cast<uint32_t>(bv >> sh) & kmask;
-          const uint32_t amb = static_cast<uint32_t>(av >> sh) & kmask;
-          const int j = ch.tab0 + t;
-          bool def = valid && amb != 0;
-          const uint32_t dm = __ballot_sync(0xFFFFFFFFu, def);
-          if (dm) {
-            const int leader = __ffs(dm) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(a.defer_count, static_cast<unsigned long long>(__popc(dm)));
-            base = __shfl_sync(0xFFFFFFFFu, base, leader);
-            if (def) {
-              const unsigned long long idx = base + __popc(dm & lanemask_lt);
-              if (idx < a.defer_cap) {
-                a.defer[2 * idx] = static_cast<unsigned long long>(i);
-                a.defer[2 * idx + 1] = static_cast<unsigned long long>(id) | (static_cast<unsigned long long>(amb) << 24) |
-                                       (static_cast<unsigned long long>(j) << 48);
-              } else {
-                // list full: resolve here (slow, still exact)
-                uint32_t m2 = amb;
-                while (m2) {
-                  const int k = __ffs(m2) - 1;
-                  m2 &= m2 - 1u;
-                  if (exact_bit<BF16>(a.X, i, a.d, a.Wt, j * a.K + k)) id |= 1u << k;
-                  else id &= ~(1u << k);
-                }
-                atomicAdd(&a.st->rechecks, static_cast<unsigned long long>(__popc(amb)));
-                def = false;
+        for (int g = 0; g < 8; ++g) {
+          bw[g] = 0u;
+          aw[g] = 0u;
+          if (g < ng) {
+            uint32_t(&v)[32] = (g & 1) ? vb : va;
+            uint32_t(&nx)[32] = (g & 1) ? va : vb;
+            tmem_ld_wait(v);
+            if (g + 1 < ng) tmem_ld32(tbase + 32u * (g + 1), nx);
+            uint32_t c0 = 0u, c1 = 0u, c2 = 0u, c3 = 0u;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              c0 = __funnelshift_l(v[k], c0, 1);
+              c1 = __funnelshift_l(v[8 + k], c1, 1);
+              c2 = __funnelshift_l(v[16 + k], c2, 1);
+              c3 = __funnelshift_l(v[24 + k], c3, 1);
+            }
+            // column k's sign sits at bit 31 - k of the concatenation
+            bw[g] = ~__brev((c0 << 24) | (c1 << 16) | (c2 << 8) | c3);
+            if constexpr (KC > 0) {
+#pragma unroll
+              for (int k = 0; k < 32; ++k) {
+                const int t = (32 * g + k) / KC;  // compile-time
+                if (t < TPC) tmin[t] = min(tmin[t], v[k] & 0x7FFFFFFFu);
+              }
+            } else {
+              bool any = false;
+#pragma unroll
+              for (int k = 0; k < 32; ++k) any |= (v[k] & 0x7FFFFFFFu) <= Bi;
+              if (any) {
+                uint32_t am = 0u;
+#pragma unroll
+                for (int k = 0; k < 32; ++k) am |= ((v[k] & 0x7FFFFFFFu) <= Bi ? 1u : 0u) << k;
+                aw[g] = am;
               }
             }
           }
-          const bool fin = valid && !def;
-          if (fin) {
-            if (a.mode & kStoreIds) reinterpret_cast<IdT*>(a.ids)[static_cast<size_t>(j) * a.ld + i] = static_cast<IdT>(id);
-            if (a.mode & kStoreIdsRowMajor) a.ids_rm[i * a.L + j] = id;
+        }
+        tc_fence_before();
+        mbar_arrive(&S->t_empty[b]);
+        auto store = [&](uint32_t id, int j) {
+          if (st_tm) ids[static_cast<size_t>(j) * ld + i] = static_cast<IdT>(id);
+          if (st_rm) ids_rm[i * L + j] = id;
+        };
+        if constexpr (KC > 0) {
+          constexpr uint32_t KM = (1u << KC) - 1u;
+#pragma unroll
+          for (int t = 0; t < TPC; ++t)
+            if (t < ntab && tmin[t] <= Bi) defmask |= 1u << t;
+          if (!valid) defmask = 0u;
+          // table t is bits [t KC, t KC + KC) of the chunk: compile-time word and shift
+#pragma unroll
+          for (int t = 0; t < TPC; ++t) {
+            const int cb = t * KC, wi = cb >> 5, sh = cb & 31;
+            uint32_t id = bw[wi] >> sh;
+            if (sh + KC > 32) id |= bw[wi + 1] << (32 - sh);
+            if (valid && t < ntab && !((defmask >> t) & 1u)) store(id & KM, tab0 + t);
           }
-          if (a.mode & kInsert) {
-            const uint32_t key = fin ? id : 0xFFFFFFFFu;
-            const uint32_t grp = __match_any_sync(0xFFFFFFFFu, key);
-            if (fin && lane == __ffs(grp) - 1)
-              atomicAdd(a.counts + (static_cast<size_t>(j) << a.K) + id, static_cast<uint32_t>(__popc(grp)));
+        } else {
+          // any K: streaming extraction, table t is bits [tK, tK + K) of the chunk
+          unsigned long long accb = 0ull, acca = 0ull;
+          int nacc = 0, t = 0;
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            if (g < ng) {
+              accb |= static_cast<unsigned long long>(bw[g]) << nacc;
+              acca |= static_cast<unsigned long long>(aw[g]) << nacc;
+              nacc += 32;
+              while (nacc >= K && t < ntab) {
+                const uint32_t id = static_cast<uint32_t>(accb) & kmask;
+                const uint32_t amb = static_cast<uint32_t>(acca) & kmask;
+                accb >>= K;
+                acca >>= K;
+                nacc -= K;
+                if (amb != 0u) defmask |= 1u << t;
+                else if (valid) store(id, tab0 + t);
+                ++t;
+              }
+            }
+          }
+          if (!valid) defmask = 0u;
+        }
+        // append the deferred (point, table) pairs to this CTA's segment (one shared-memory
+        // atomic per row that has any); beyond the segment's capacity, resolve them here
+        if (__any_sync(0xFFFFFFFFu, defmask != 0u) && defmask != 0u) {
+          unsigned int idx = atomicAdd(&S->ndef, static_cast<unsigned int>(__popc(defmask)));
+          uint32_t dm = defmask;
+          while (dm) {
+            const int t = __ffs(dm) - 1;
+            dm &= dm - 1u;
+            const int j = tab0 + t;
+            if (idx < seg_cap) seg[idx] = (static_cast<unsigned long long>(i) << 24) | static_cast<unsigned long long>(j);
+            else store(exact_table_id<BF16>(X, i, d, K, j, Wt, cB32, xfac32, xabs32, babs32, st), j);
+            ++idx;
           }
         }
       }
@@ -393,40 +498,104 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
 
   tc_fence_before();
   __syncthreads();
+  if (tid == 0) a.defer_counts[blockIdx.x] = static_cast<unsigned int>(min(static_cast<unsigned long long>(S->ndef), a.seg_cap));
   if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tmem, 512);
   }
 }
 
-// Resolves the deferred (point, table) pairs: binary64 bits (index order), final id, store,
-// insert.
+// Resolves the deferred (point, table) pairs: one warp per pair, lane k recomputes column
+// j K + k as a binary32 FMA chain in index order and decides its bit with the SIMT engine's
+// rigorous bound (|s32 - s| <= gamma_d sum|x_i w_i| + d 2^-150, folded into cB32[c] ||x||_up +
+// babs32); a bit still inside that bound is evaluated in binary64, index order (the
+// definition).  The id is the ballot of the lanes' bits.  One block per CTA segment.
 template <bool BF16, typename IdT>
-__global__ void __launch_bounds__(256) recheck_kernel(const __grid_constant__ TcArgs a) {
-  const unsigned long long cnt = min(*a.defer_count, a.defer_cap);
-  unsigned long long nre = 0;
-  for (unsigned long long e = static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < cnt;
-       e += static_cast<unsigned long long>(gridDim.x) * blockDim.x) {
-    const long long i = static_cast<long long>(a.defer[2 * e]);
-    const unsigned long long w = a.defer[2 * e + 1];
-    uint32_t id = static_cast<uint32_t>(w & 0xFFFFFFull);
-    const uint32_t amb = static_cast<uint32_t>((w >> 24) & 0xFFFFFFull);
-    const int j = static_cast<int>(w >> 48);
-    uint32_t m = amb;
-    while (m) {
-      const int k = __ffs(m) - 1;
-      m &= m - 1u;
-      if (exact_bit<BF16>(a.X, i, a.d, a.Wt, j * a.K + k)) id |= 1u << k;
-      else id &= ~(1u << k);
+__global__ void __launch_bounds__(256) recheck_kernel(const __grid_constant__ TcArgs a, int nseg) {
+  // Entries live in nseg per-CTA segments; a prefix sum of their counts maps a global entry
+  // index to (segment, offset).  Each half warp takes one entry (K <= 16; else a whole warp):
+  // lane k recomputes column j K + k.
+  __shared__ unsigned long long pref[kMaxSeg + 1];
+  const int d = a.d, K = a.K, L = a.L, mode = a.mode;
+  const long long ld = a.ld;
+  const void* const X = a.X;
+  const float* const Wt = a.Wt;
+  const float* const W = a.W;
+  const int KL = K * L;
+  const float* const cB32 = a.cB32;
+  const float xfac32 = a.xfac32, xabs32 = a.xabs32, babs32 = a.babs32;
+  IdT* const ids = reinterpret_cast<IdT*>(a.ids);
+  uint32_t* const ids_rm = a.ids_rm;
+  const uint32_t kmask = (1u << K) - 1u;
+  if (threadIdx.x == 0) {
+    unsigned long long acc = 0;
+    pref[0] = 0;
+    for (int g = 0; g < nseg; ++g) {
+      acc += a.defer_counts[g];
+      pref[g + 1] = acc;
     }
-    nre += __popc(amb);
-    if (a.mode & kStoreIds) reinterpret_cast<IdT*>(a.ids)[static_cast<size_t>(j) * a.ld + i] = static_cast<IdT>(id);
-    if (a.mode & kStoreIdsRowMajor) a.ids_rm[i * a.L + j] = id;
-    if (a.mode & kInsert) atomicAdd(a.counts + (static_cast<size_t>(j) << a.K) + id, 1u);
   }
+  __syncthreads();
+  const unsigned long long total = pref[nseg];
+  const int lane = threadIdx.x & 31;
+  const int width = K <= 16 ? 16 : 32;  // lanes per entry
+  const int sub = lane / width, sl = lane % width;
+  const unsigned long long per_warp = 32 / width;
+  const unsigned long long nwarps = static_cast<unsigned long long>(gridDim.x) * (blockDim.x >> 5);
+  const unsigned long long gw = static_cast<unsigned long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  unsigned long long nre = 0;
+  for (unsigned long long base = gw * per_warp; base < total; base += nwarps * per_warp) {
+    const unsigned long long e = base + sub;
+    const bool has = e < total;
+    long long i = 0;
+    int j = 0;
+    if (has) {
+      int lo = 0, hi = nseg;  // segment g with pref[g] <= e < pref[g + 1]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pref[mid] <= e) lo = mid;
+        else hi = mid;
+      }
+      const unsigned long long w = a.defer[a.seg_cap * lo + (e - pref[lo])];
+      i = static_cast<long long>(w >> 24);
+      j = static_cast<int>(w & 0xFFFFFFull);
+    }
+    // coordinates: lane sl holds x[sl + width m], m < 64 / width
+    float xs[4];
+    float q = 0.f;
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) nre += __shfl_down_sync(0xFFFFFFFFu, nre, off);
-  if ((threadIdx.x & 31) == 0 && nre) atomicAdd(&a.st->rechecks, nre);
+    for (int m = 0; m < 4; ++m) {
+      const int t = sl + width * m;
+      xs[m] = (has && m * width < 64 && t < d) ? load_x<BF16>(X, i * d + t) : 0.f;
+      q = fmaf(xs[m], xs[m], q);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+      if (off < width) q += __shfl_xor_sync(0xFFFFFFFFu, q, off);
+    const float xu = norm_upper(q, xfac32, xabs32);
+    const int col = j * K + (sl < K ? sl : 0);
+    float s32 = 0.f;
+#pragma unroll 8
+    for (int t = 0; t < d; ++t) {
+      const int m = t / width;  // the same in every lane
+      const float src = m == 0 ? xs[0] : (m == 1 ? xs[1] : (m == 2 ? xs[2] : xs[3]));
+      const float x = __shfl_sync(0xFFFFFFFFu, src, t % width + sub * width);
+      s32 = fmaf(x, __ldg(W + static_cast<size_t>(t) * KL + col), s32);
+    }
+    bool bit = false;
+    if (has && sl < K) {
+      if (fabsf(s32) > fmaf(__ldg(cB32 + col), xu, babs32)) bit = s32 > 0.f;
+      else bit = exact_bit<BF16>(X, i, d, Wt, col);
+    }
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, bit);
+    const uint32_t id = (bal >> (sub * width)) & kmask;
+    if (has && sl == 0) {
+      if (mode & kStoreIds) ids[static_cast<size_t>(j) * ld + i] = static_cast<IdT>(id);
+      if (mode & kStoreIdsRowMajor) ids_rm[i * L + j] = id;
+      nre += static_cast<unsigned long long>(K);
+    }
+  }
+  if (nre) atomicAdd(&a.st->rechecks, nre);
 }
 
 }  // namespace
@@ -434,27 +603,39 @@ __global__ void __launch_bounds__(256) recheck_kernel(const __grid_constant__ Tc
 cudaError_t launch_hash_tc(const TcArgs& a, int num_sms, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
   const long long grid = min(static_cast<long long>(num_sms), a.ntiles);
-  const bool id16 = a.K <= 16;
   auto go = [&](auto kern) -> cudaError_t {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes);
     if (e != cudaSuccess) return e;
     kern<<<static_cast<unsigned>(grid), kThreads, a.smem_bytes, s>>>(a);
     return cudaGetLastError();
   };
-  if (a.x_bf16) return id16 ? go(hash_tc_kernel<true, uint16_t>) : go(hash_tc_kernel<true, uint32_t>);
-  return id16 ? go(hash_tc_kernel<false, uint16_t>) : go(hash_tc_kernel<false, uint32_t>);
+  auto pick = [&](auto bf16_tag) -> cudaError_t {
+    constexpr bool B = decltype(bf16_tag)::value;
+    if (a.K > 16) return go(hash_tc_kernel<B, uint32_t, 0>);
+    switch (a.K) {
+      case 10: return go(hash_tc_kernel<B, uint16_t, 10>);
+      case 12: return go(hash_tc_kernel<B, uint16_t, 12>);
+      case 15: return go(hash_tc_kernel<B, uint16_t, 15>);
+      case 16: return go(hash_tc_kernel<B, uint16_t, 16>);
+      default: return go(hash_tc_kernel<B, uint16_t, 0>);
+    }
+  };
+  if (a.x_bf16) return pick(std::true_type{});
+  return pick(std::false_type{});
 }
 
 cudaError_t launch_recheck(const TcArgs& a, int num_sms, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  const unsigned grid = static_cast<unsigned>(num_sms * 4);
+  const int nseg = static_cast<int>(min(static_cast<long long>(num_sms), a.ntiles));  // one segment per CTA
+  if (nseg > kMaxSeg) return cudaErrorInvalidValue;
+  const unsigned grid = static_cast<unsigned>(num_sms * 16);
   const bool id16 = a.K <= 16;
   if (a.x_bf16) {
-    if (id16) recheck_kernel<true, uint16_t><<<grid, 256, 0, s>>>(a);
-    else recheck_kernel<true, uint32_t><<<grid, 256, 0, s>>>(a);
+    if (id16) recheck_kernel<true, uint16_t><<<grid, 256, 0, s>>>(a, nseg);
+    else recheck_kernel<true, uint32_t><<<grid, 256, 0, s>>>(a, nseg);
   } else {
-    if (id16) recheck_kernel<false, uint16_t><<<grid, 256, 0, s>>>(a);
-    else recheck_kernel<false, uint32_t><<<grid, 256, 0, s>>>(a);
+    if (id16) recheck_kernel<false, uint16_t><<<grid, 256, 0, s>>>(a, nseg);
+    else recheck_kernel<false, uint32_t><<<grid, 256, 0, s>>>(a, nseg);
   }
   return cudaGetLastError();
 }

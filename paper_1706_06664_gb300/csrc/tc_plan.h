@@ -8,6 +8,7 @@
 namespace ace {
 
 constexpr int kTcMaxChunks = 16;
+constexpr int kMaxD = 64;  // largest d of the resident design (staging and recheck registers)
 
 // One chunk: whole tables [tab0, tab0 + ntab), N = ntab*K rounded up to 16 MMA columns,
 // and the byte offsets of its hi and lo operand images inside the resident B image.
@@ -32,10 +33,13 @@ struct TcArgs {
   uint32_t* ids_rm;
   uint32_t* counts;
   DevStats* st;
-  const float* Wt;  // [KL][d] original W (binary64 recheck)
-  unsigned long long* defer;        // 2 words per deferred (point, table)
-  unsigned long long* defer_count;  // device counter (zeroed before each launch)
-  unsigned long long defer_cap;
+  const float* Wt;  // [KL][d] original W, columns contiguous (binary64 recheck)
+  const float* W;   // [d][KL] original W, rows contiguous (binary32 recheck)
+  const float* cB32;                // SIMT-engine guard coefficients per column
+  float xfac32, xabs32, babs32;     // SIMT-engine norm inflation and absolute allowances
+  unsigned long long* defer;         // (point << 24 | table) per deferred pair; one segment per CTA
+  unsigned int* defer_counts;        // entries per segment, written by each CTA at exit
+  unsigned long long seg_cap;        // entries per segment
   // dynamic shared-memory layout (bytes)
   int off_a, a_bytes, off_stage, off_bnd, off_bits, off_ctl, smem_bytes;
 };
