@@ -39,6 +39,8 @@ WORKLOAD = "kdd-shaped n=500000 d=41 K=15 L=50 alpha=1 (23-cluster mixture, 1% u
 N_POINTS, D, KH, LT, ALPHA = 500_000, 41, 15, 50, 1.0
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 x max SM clock
 
+REF_BUDGET_S = 90.0  # timed CPU work of one --impl reference run
+
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -179,7 +181,12 @@ def run_reference(args):
         return 0  # the CPU oracle runs on rank 0 only
     import oracle
     X = _batches(0, N_POINTS)[0]
-    sample = args.ref_sample
+    # Size each step so the timed steps take about REF_BUDGET_S in all, whatever --steps is.
+    probe = 2000
+    t0 = time.perf_counter()
+    oracle.Detector(D, KH, LT, seed=7).insert_score(X[:probe], ALPHA)
+    per_pt = (time.perf_counter() - t0) / probe
+    sample = int(max(1000, min(args.ref_sample, REF_BUDGET_S / max(1, args.steps) / max(per_pt, 1e-9))))
     for _ in range(args.warmup):
         oracle.Detector(D, KH, LT, seed=7).insert_score(X[:max(1, sample // 10)], ALPHA)
     times = []
@@ -335,8 +342,8 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16"])
     ap.add_argument("--n", type=int, default=N_POINTS, help="points per batch (profiling runs only)")

@@ -267,6 +267,13 @@ int plan_tc(ace_detector* h) {
   const double g32 = d_pad * u32 / (1.0 - d_pad * u32);
   t.xfac = std::nextafter(static_cast<float>(1.0 + 2.0 * g32 + std::ldexp(1.0, -20)), FLT_MAX);
   t.qmin = std::ldexp(1.0f, -60);
+  // Dot2 filter: (gamma_d^2 + gamma64_d) (1 + u) sum|x_i w_i|, with sum|x_i w_i| <=
+  // a / ((1 - u)(1 - gamma_d)) for the binary32 sum a of the rounded |products|; underflow
+  // (each product error and each sum below 2^-126 off by at most 2^-150) in dot2abs.
+  const double g32d = d * u32 / (1.0 - d * u32);
+  t.dot2c = std::nextafter(static_cast<float>((g32d * g32d + g64) * (1.0 + u32) / ((1.0 - u32) * (1.0 - g32d)) * 1.01),
+                           FLT_MAX);
+  t.dot2abs = static_cast<float>(4.0 * d * std::ldexp(1.0, -149));
   t.Wt = h->Wt;
   t.W = h->W;
   t.cB32 = h->cB;

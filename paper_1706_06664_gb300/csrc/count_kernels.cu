@@ -168,30 +168,56 @@ __global__ void __launch_bounds__(256) sum_squares_kernel(const uint32_t* __rest
   }
 }
 
-// Counting phase (Algorithm 1; §3.2) from cached table-major ids.  CTA (j, part, range)
-// counts the ids of table j among points [range] whose bucket lies in bucket part `part`,
-// in a shared-memory histogram (at most 16,384 bins = 64 KB), then adds the non-zero bins to
-// A_j with atomicAdd.  Counts are exact integers, so the order of the additions is irrelevant.
+constexpr size_t kHistBytes = 128 * 1024;  // shared-memory histogram of one insert block
+
+// Counting phase (Algorithm 1; §3.2) from cached table-major ids: A_j[id] += 1 for every
+// point.  Block (j, part, range) owns table j, bucket slice `part` (all 2^K buckets when they
+// fit in kHistBytes) and one range of points; it counts into a shared-memory histogram, then
+// adds the non-zero bins to A_j with one global atomic each.  The ids are read with 16-byte
+// loads over the aligned middle of the range.  Counts are exact integers, so the order of
+// the additions is irrelevant.
 template <typename IdT>
-__global__ void __launch_bounds__(512) insert_hist_kernel(const IdT* __restrict__ ids, long long ld, long long n,
-                                                          int K, int nparts, int nranges,
-                                                          uint32_t* __restrict__ counts) {
+__global__ void __launch_bounds__(1024) insert_hist_kernel(const IdT* __restrict__ ids, long long ld, long long n,
+                                                           int K, int nparts, int nranges,
+                                                           uint32_t* __restrict__ counts) {
   extern __shared__ uint32_t hist[];
   const int bins = (1 << K) / nparts;
   const int j = blockIdx.x / (nparts * nranges);
   const int part = (blockIdx.x / nranges) % nparts;
   const int rr = blockIdx.x % nranges;
-  const long long per = (n + nranges - 1) / nranges;
-  const long long i0 = rr * per;
+  const long long per = ((n + nranges - 1) / nranges + 7) & ~7LL;
+  const long long i0 = min(n, rr * per);
   const long long i1 = min(n, i0 + per);
   const uint32_t lo = static_cast<uint32_t>(part) * static_cast<uint32_t>(bins);
   for (int b = threadIdx.x; b < bins; b += blockDim.x) hist[b] = 0u;
   __syncthreads();
   const IdT* col = ids + static_cast<size_t>(j) * ld;
-  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    const uint32_t rel = static_cast<uint32_t>(col[i]) - lo;
+  auto add = [&](uint32_t id) {
+    const uint32_t rel = id - lo;
     if (rel < static_cast<uint32_t>(bins)) atomicAdd(&hist[rel], 1u);
+  };
+  constexpr int V = 16 / sizeof(IdT);  // ids per 16-byte load
+  const long long mis =
+      static_cast<long long>((16 - (reinterpret_cast<uintptr_t>(col + i0) & 15)) & 15) / static_cast<long long>(sizeof(IdT));
+  const long long h1 = min(i1, i0 + mis);  // first 16-byte-aligned id of the range
+  const long long nvec = (i1 - h1) / V;
+  const long long t0 = h1 + nvec * V;  // scalar tail [t0, i1)
+  for (long long i = i0 + threadIdx.x; i < h1; i += blockDim.x) add(col[i]);
+  const uint4* vp = reinterpret_cast<const uint4*>(col + h1);
+  for (long long v = threadIdx.x; v < nvec; v += blockDim.x) {
+    const uint4 u = vp[v];
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if constexpr (sizeof(IdT) == 2) {
+        add(w[k] & 0xFFFFu);
+        add(w[k] >> 16);
+      } else {
+        add(w[k]);
+      }
+    }
   }
+  for (long long i = t0 + threadIdx.x; i < i1; i += blockDim.x) add(col[i]);
   __syncthreads();
   uint32_t* dst = counts + (static_cast<size_t>(j) << K) + lo;
   for (int b = threadIdx.x; b < bins; b += blockDim.x) {
@@ -219,26 +245,27 @@ cudaError_t launch_insert_from_ids(const void* ids, int ids16, long long ld, lon
                                    uint32_t* counts, int num_sms, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   if (K <= 16) {
-    const int nparts = K <= 14 ? 1 : (1 << (K - 14));
+    // the fewest bucket slices whose histogram fits in kHistBytes of shared memory
+    int nparts = 1;
+    while ((static_cast<size_t>(1) << K) / nparts * sizeof(uint32_t) > kHistBytes) nparts *= 2;
     const int bins = (1 << K) / nparts;
-    const long long want = 2LL * num_sms;
-    int nranges = static_cast<int>((want + static_cast<long long>(L) * nparts - 1) / (static_cast<long long>(L) * nparts));
-    nranges = max(1, min(nranges, static_cast<int>((n + 4095) / 4096)));
-    const long long blocks = static_cast<long long>(L) * nparts * nranges;
     const size_t smem = static_cast<size_t>(bins) * sizeof(uint32_t);
-    cudaError_t e;
-    if (ids16) {
-      e = cudaFuncSetAttribute(insert_hist_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    auto go = [&](auto kern, const auto* typed) -> cudaError_t {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
       if (e != cudaSuccess) return e;
-      insert_hist_kernel<uint16_t><<<static_cast<unsigned>(blocks), 512, smem, s>>>(
-          static_cast<const uint16_t*>(ids), ld, n, K, nparts, nranges, counts);
-    } else {
-      e = cudaFuncSetAttribute(insert_hist_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+      int per_sm = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 1024, smem);
       if (e != cudaSuccess) return e;
-      insert_hist_kernel<uint32_t><<<static_cast<unsigned>(blocks), 512, smem, s>>>(
-          static_cast<const uint32_t*>(ids), ld, n, K, nparts, nranges, counts);
-    }
-    return cudaGetLastError();
+      // one wave: split each (table, slice) into point ranges until the SMs are covered
+      const long long units = static_cast<long long>(L) * nparts;
+      const long long want = static_cast<long long>(num_sms) * max(1, per_sm);
+      const long long nranges = max(1LL, min(want / units, (n + 4095) / 4096));
+      kern<<<static_cast<unsigned>(units * nranges), 1024, smem, s>>>(typed, ld, n, K, nparts,
+                                                                       static_cast<int>(nranges), counts);
+      return cudaGetLastError();
+    };
+    if (ids16) return go(insert_hist_kernel<uint16_t>, static_cast<const uint16_t*>(ids));
+    return go(insert_hist_kernel<uint32_t>, static_cast<const uint32_t*>(ids));
   }
   const unsigned blocks = static_cast<unsigned>(num_sms * 8);
   if (ids16)

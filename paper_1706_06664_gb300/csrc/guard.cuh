@@ -1,4 +1,5 @@
-// Device helpers shared by the hash kernels: input loads and the exact binary64 recheck.
+// Device helpers shared by the hash kernels: input loads, the Dot2 filter and the exact
+// binary64 recheck.
 //
 // The SRP bit of Eq. 1 is defined here as [s > 0] with s the binary64 sum, in index order,
 // of the products (double)x_i * (double)w_i.  A binary32 x binary32 (or bfloat16 x binary32)
@@ -30,6 +31,40 @@ __device__ __noinline__ bool exact_bit(const void* X, long long i, int d, const 
   for (int k = 0; k < d; ++k)
     s = fma(static_cast<double>(load_x<BF16>(X, base + k)), static_cast<double>(__ldg(w + k)), s);
   return s > 0.0;
+}
+
+// Sign of the exact dot product x.w by Dot2 (Ogita, Rump & Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26(6), 2005): binary32 error-free transformations
+// (TwoProduct by FMA, Knuth's TwoSum) carry the sum in about twice the working precision, and
+// without underflow the result satisfies |res - x.w| <= u |x.w| + gamma_d^2 sum|x_i w_i|.
+// When |res| exceeds gamma_d^2 sum|x_i w_i| plus the binary64 sum's own error gamma64_d
+// sum|x_i w_i|, the exact value and the binary64 definition both have the sign of res and are
+// non-zero.  c2 covers those terms together with the rounding of the computed sum of |x_i w_i|;
+// cabs covers underflow.  Returns +1 or -1 when decided, 0 when only binary64 can tell
+// (exact ties, NaN, overflow).  Every operation is an explicitly rounded intrinsic, so no
+// contraction into an FMA can break the transformations.  w is read with stride ws.
+template <bool BF16>
+__device__ __noinline__ int dot2_sign(const void* X, long long i, int d, const float* w, long long ws, float c2,
+                                      float cabs) {
+  const long long base = i * static_cast<long long>(d);
+  float p = 0.f, e = 0.f, a = 0.f;
+#pragma unroll 4
+  for (int k = 0; k < d; ++k) {
+    const float x = load_x<BF16>(X, base + k);
+    const float y = __ldg(w + k * ws);
+    const float h = __fmul_rn(x, y);
+    const float r = __fmaf_rn(x, y, -h);  // h + r = x y exactly (TwoProduct)
+    const float p1 = __fadd_rn(p, h);
+    const float z = __fsub_rn(p1, p);
+    const float q = __fadd_rn(__fsub_rn(p, __fsub_rn(p1, z)), __fsub_rn(h, z));  // p1 + q = p + h (TwoSum)
+    p = p1;
+    e = __fadd_rn(e, __fadd_rn(q, r));
+    a = __fadd_rn(a, fabsf(h));
+  }
+  const float res = __fadd_rn(p, e);
+  const float T = __fmaf_ru(c2, a, cabs);
+  if (fabsf(res) > T) return res > 0.f ? 1 : -1;  // false for NaN, and for any res when T = inf
+  return 0;
 }
 
 // K (<= 24) consecutive bits starting at bit `cb` of a row of 32-bit words.

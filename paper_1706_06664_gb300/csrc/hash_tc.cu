@@ -383,7 +383,8 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
         const uint32_t tbase = tmem + (static_cast<uint32_t>(q4 * 32) << 16) + static_cast<uint32_t>(b * 256);
         // Classify the chunk's columns.  bw[g] bit k = [column 32g+k > 0].  A table with any
         // column inside the bound (|projection| <= B, compared on bit patterns: both are
-        // non-negative floats; Bi = all ones for a row whose bound is +inf) is deferred whole
+        // non-negative floats; Bi = all ones for a row whose bound is +inf, so that row is
+        // deferred whatever the minimum, NaN included) is deferred whole
         // to the recheck kernel.  The next 32 columns are loaded from TMEM while the current
         // ones are classified; signs are packed by four independent funnel-shift chains.
         const uint32_t Bi = isinf(B) ? 0xFFFFFFFFu : __float_as_uint(B);
@@ -391,9 +392,7 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
         uint32_t va[32], vb[32];
         uint32_t defmask = 0u;  // bit t: table t of the chunk has a column inside the bound
         constexpr int TPC = KC > 0 ? 256 / KC : 1;
-        uint32_t tmin[TPC];
-#pragma unroll
-        for (int t = 0; t < TPC; ++t) tmin[t] = 0xFFFFFFFFu;
+        float tmin[TPC];  // per table: smallest |projection| (a min with |.| operands)
         uint32_t aw[8];
         tmem_ld32(tbase, va);
 #pragma unroll
@@ -418,8 +417,11 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
             if constexpr (KC > 0) {
 #pragma unroll
               for (int k = 0; k < 32; ++k) {
-                const int t = (32 * g + k) / KC;  // compile-time
-                if (t < TPC) tmin[t] = min(tmin[t], v[k] & 0x7FFFFFFFu);
+                const int col = 32 * g + k, t = col / KC;  // compile-time
+                if (t < TPC) {
+                  const float av = fabsf(__uint_as_float(v[k]));
+                  tmin[t] = col % KC == 0 ? av : fminf(tmin[t], av);
+                }
               }
             } else {
               bool any = false;
@@ -444,7 +446,7 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
           constexpr uint32_t KM = (1u << KC) - 1u;
 #pragma unroll
           for (int t = 0; t < TPC; ++t)
-            if (t < ntab && tmin[t] <= Bi) defmask |= 1u << t;
+            if (t < ntab && __float_as_uint(tmin[t]) <= Bi) defmask |= 1u << t;
           if (!valid) defmask = 0u;
           // table t is bits [t KC, t KC + KC) of the chunk: compile-time word and shift
 #pragma unroll
@@ -505,17 +507,20 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
   }
 }
 
-// Resolves the deferred (point, table) pairs: one warp per pair, lane k recomputes column
-// j K + k as a binary32 FMA chain in index order and decides its bit with the SIMT engine's
-// rigorous bound (|s32 - s| <= gamma_d sum|x_i w_i| + d 2^-150, folded into cB32[c] ||x||_up +
-// babs32); a bit still inside that bound is evaluated in binary64, index order (the
-// definition).  The id is the ballot of the lanes' bits.  One block per CTA segment.
+// Resolves the deferred (point, table) pairs: lane k of an entry's lane group recomputes
+// column j K + k as a binary32 FMA chain in index order and decides its bit with the SIMT
+// engine's rigorous bound (|s32 - s| <= gamma_d sum|x_i w_i| + d 2^-150, folded into
+// cB32[c] ||x||_up + babs32); a bit inside that bound goes to the Dot2 filter, and only what
+// Dot2 cannot decide is evaluated in binary64, index order (the definition).  GB300 issues
+// binary64 FMAs at a small fraction of the binary32 rate, so the filter keeps that path to
+// exact ties.  The id is the ballot of the lanes' bits.
 template <bool BF16, typename IdT>
 __global__ void __launch_bounds__(256) recheck_kernel(const __grid_constant__ TcArgs a, int nseg) {
   // Entries live in nseg per-CTA segments; a prefix sum of their counts maps a global entry
   // index to (segment, offset).  Each half warp takes one entry (K <= 16; else a whole warp):
   // lane k recomputes column j K + k.
   __shared__ unsigned long long pref[kMaxSeg + 1];
+  __shared__ float xsm[8][2][kMaxD];  // per warp, per half-warp entry
   const int d = a.d, K = a.K, L = a.L, mode = a.mode;
   const long long ld = a.ld;
   const void* const X = a.X;
@@ -524,25 +529,40 @@ __global__ void __launch_bounds__(256) recheck_kernel(const __grid_constant__ Tc
   const int KL = K * L;
   const float* const cB32 = a.cB32;
   const float xfac32 = a.xfac32, xabs32 = a.xabs32, babs32 = a.babs32;
+  const float dot2c = a.dot2c, dot2abs = a.dot2abs;
   IdT* const ids = reinterpret_cast<IdT*>(a.ids);
   uint32_t* const ids_rm = a.ids_rm;
   const uint32_t kmask = (1u << K) - 1u;
-  if (threadIdx.x == 0) {
-    unsigned long long acc = 0;
-    pref[0] = 0;
-    for (int g = 0; g < nseg; ++g) {
-      acc += a.defer_counts[g];
-      pref[g + 1] = acc;
+  // prefix sums of the segment counts: parallel loads, then one warp scans lane-sized runs
+  const int lane = threadIdx.x & 31;
+  for (int g = threadIdx.x; g < nseg; g += blockDim.x) pref[g + 1] = a.defer_counts[g];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int per = (nseg + 31) / 32;
+    const int g0 = min(nseg, lane * per), g1 = min(nseg, g0 + per);
+    unsigned long long own = 0;
+    for (int g = g0; g < g1; ++g) own += pref[g + 1];
+    unsigned long long incl = own;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned long long v = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+      if (lane >= off) incl += v;
     }
+    unsigned long long run = incl - own;
+    for (int g = g0; g < g1; ++g) {
+      run += pref[g + 1];
+      pref[g + 1] = run;
+    }
+    if (lane == 0) pref[0] = 0;
   }
   __syncthreads();
   const unsigned long long total = pref[nseg];
-  const int lane = threadIdx.x & 31;
   const int width = K <= 16 ? 16 : 32;  // lanes per entry
   const int sub = lane / width, sl = lane % width;
   const unsigned long long per_warp = 32 / width;
   const unsigned long long nwarps = static_cast<unsigned long long>(gridDim.x) * (blockDim.x >> 5);
   const unsigned long long gw = static_cast<unsigned long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  float* const xe = xsm[threadIdx.x >> 5][sub];  // this entry's x, read as a shared-memory broadcast
   unsigned long long nre = 0;
   for (unsigned long long base = gw * per_warp; base < total; base += nwarps * per_warp) {
     const unsigned long long e = base + sub;
@@ -560,32 +580,36 @@ __global__ void __launch_bounds__(256) recheck_kernel(const __grid_constant__ Tc
       i = static_cast<long long>(w >> 24);
       j = static_cast<int>(w & 0xFFFFFFull);
     }
-    // coordinates: lane sl holds x[sl + width m], m < 64 / width
-    float xs[4];
+    // stage x (lane sl holds coordinates sl + width m) and its squared norm
     float q = 0.f;
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
+    for (int m = 0; m < kMaxD / 16; ++m) {
       const int t = sl + width * m;
-      xs[m] = (has && m * width < 64 && t < d) ? load_x<BF16>(X, i * d + t) : 0.f;
-      q = fmaf(xs[m], xs[m], q);
+      if (t < kMaxD) {
+        const float x = (has && t < d) ? load_x<BF16>(X, i * d + t) : 0.f;
+        xe[t] = x;
+        q = fmaf(x, x, q);
+      }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
       if (off < width) q += __shfl_xor_sync(0xFFFFFFFFu, q, off);
+    __syncwarp();
     const float xu = norm_upper(q, xfac32, xabs32);
     const int col = j * K + (sl < K ? sl : 0);
+    // binary32 FMA chain in index order: x from shared memory, W row by row (L1-resident)
+    const float* wp = W + col;
     float s32 = 0.f;
 #pragma unroll 8
-    for (int t = 0; t < d; ++t) {
-      const int m = t / width;  // the same in every lane
-      const float src = m == 0 ? xs[0] : (m == 1 ? xs[1] : (m == 2 ? xs[2] : xs[3]));
-      const float x = __shfl_sync(0xFFFFFFFFu, src, t % width + sub * width);
-      s32 = fmaf(x, __ldg(W + static_cast<size_t>(t) * KL + col), s32);
-    }
+    for (int t = 0; t < d; ++t, wp += KL) s32 = fmaf(xe[t], __ldg(wp), s32);
     bool bit = false;
     if (has && sl < K) {
-      if (fabsf(s32) > fmaf(__ldg(cB32 + col), xu, babs32)) bit = s32 > 0.f;
-      else bit = exact_bit<BF16>(X, i, d, Wt, col);
+      if (fabsf(s32) > fmaf(__ldg(cB32 + col), xu, babs32)) {
+        bit = s32 > 0.f;
+      } else {
+        const int sg = dot2_sign<BF16>(X, i, d, W + col, KL, dot2c, dot2abs);
+        bit = sg != 0 ? sg > 0 : exact_bit<BF16>(X, i, d, Wt, col);
+      }
     }
     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, bit);
     const uint32_t id = (bal >> (sub * width)) & kmask;
@@ -594,6 +618,7 @@ __global__ void __launch_bounds__(256) recheck_kernel(const __grid_constant__ Tc
       if (mode & kStoreIdsRowMajor) ids_rm[i * L + j] = id;
       nre += static_cast<unsigned long long>(K);
     }
+    __syncwarp();  // xe is rewritten by the next entry
   }
   if (nre) atomicAdd(&a.st->rechecks, nre);
 }
@@ -628,16 +653,17 @@ cudaError_t launch_recheck(const TcArgs& a, int num_sms, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
   const int nseg = static_cast<int>(min(static_cast<long long>(num_sms), a.ntiles));  // one segment per CTA
   if (nseg > kMaxSeg) return cudaErrorInvalidValue;
-  const unsigned grid = static_cast<unsigned>(num_sms * 16);
+  // one wave: as many 256-thread blocks per SM as its registers and threads allow
+  auto go = [&](auto kern) -> cudaError_t {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+    if (e != cudaSuccess) return e;
+    kern<<<static_cast<unsigned>(num_sms * max(1, per_sm)), 256, 0, s>>>(a, nseg);
+    return cudaGetLastError();
+  };
   const bool id16 = a.K <= 16;
-  if (a.x_bf16) {
-    if (id16) recheck_kernel<true, uint16_t><<<grid, 256, 0, s>>>(a, nseg);
-    else recheck_kernel<true, uint32_t><<<grid, 256, 0, s>>>(a, nseg);
-  } else {
-    if (id16) recheck_kernel<false, uint16_t><<<grid, 256, 0, s>>>(a, nseg);
-    else recheck_kernel<false, uint32_t><<<grid, 256, 0, s>>>(a, nseg);
-  }
-  return cudaGetLastError();
+  if (a.x_bf16) return id16 ? go(recheck_kernel<true, uint16_t>) : go(recheck_kernel<true, uint32_t>);
+  return id16 ? go(recheck_kernel<false, uint16_t>) : go(recheck_kernel<false, uint32_t>);
 }
 
 }  // namespace ace

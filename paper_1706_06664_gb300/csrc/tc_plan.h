@@ -37,6 +37,7 @@ struct TcArgs {
   const float* W;   // [d][KL] original W, rows contiguous (binary32 recheck)
   const float* cB32;                // SIMT-engine guard coefficients per column
   float xfac32, xabs32, babs32;     // SIMT-engine norm inflation and absolute allowances
+  float dot2c, dot2abs;             // Dot2 filter: bound = dot2c * sum|x_i w_i|^ + dot2abs
   unsigned long long* defer;         // (point << 24 | table) per deferred pair; one segment per CTA
   unsigned int* defer_counts;        // entries per segment, written by each CTA at exit
   unsigned long long seg_cap;        // entries per segment
