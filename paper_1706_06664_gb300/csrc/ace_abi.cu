@@ -58,6 +58,7 @@ struct ace_detector {
   uint8_t* flstage = nullptr;
   size_t stage_cap = 0;  // elements
   uint64_t n_ins = 0;
+  ace::DivConst div{};    // constants of the score division by L
   std::vector<float> Wh;  // host copy of W
   // tensor-core path
   int num_sms = 0;
@@ -299,6 +300,7 @@ int make_detector(int d, int K, int L, const float* Wsrc, uint64_t seed, bool fr
   h->K = K;
   h->L = L;
   h->KL = K * L;
+  h->div = ace::make_div_const(static_cast<uint32_t>(L));
   cudaError_t e = cudaGetDevice(&h->device);
   if (e != cudaSuccess) {
     delete h;
@@ -487,12 +489,12 @@ int score_common(ace_handle h, const void* X, long long n, int dtype, double alp
   cudaError_t e;
   {
     PhaseScope ps(h, ACE_PHASE_SCORE, s);
-    e = ace::launch_score_gather(h->ids, h->K <= 16, n, n, h->K, h->L, h->counts, sum_out, h->st, s);
+    e = ace::launch_score_gather(h->ids, h->K <= 16, n, n, h->K, h->L, alpha, h->counts, sum_out, h->st, s);
   }
   if (e != cudaSuccess) return cuda_fail(e, "score kernel launch");
   {
     PhaseScope ps(h, ACE_PHASE_FLAGS, s);
-    e = ace::launch_flags(sum_out, (scores || flags) ? n : 0, h->L, alpha, h->st, scores, flags, s);
+    e = ace::launch_flags(sum_out, n, h->div, h->st, scores, flags, s);
   }
   if (e != cudaSuccess) return cuda_fail(e, "flags kernel launch");
   return ACE_OK;
@@ -778,10 +780,10 @@ extern "C" int ace_insert_score_noalloc(ace_handle h, const void* X_dev, int64_t
   if (e != cudaSuccess) return cuda_fail(e, "hash kernel launch");
   h->n_ins += static_cast<uint64_t>(n);
   h->launches[ACE_PHASE_SCORE] += 1;
-  e = ace::launch_score_gather(ids, h->K <= 16, n, n, h->K, h->L, h->counts, sum_out, h->st, s);
+  e = ace::launch_score_gather(ids, h->K <= 16, n, n, h->K, h->L, alpha, h->counts, sum_out, h->st, s);
   if (e != cudaSuccess) return cuda_fail(e, "score kernel launch");
   h->launches[ACE_PHASE_FLAGS] += 1;
-  e = ace::launch_flags(sum_out, (scores_dev || flags_dev) ? n : 0, h->L, alpha, h->st, scores_dev, flags_dev, s);
+  e = ace::launch_flags(sum_out, n, h->div, h->st, scores_dev, flags_dev, s);
   if (e != cudaSuccess) return cuda_fail(e, "flags kernel launch");
   return ACE_OK;
 }

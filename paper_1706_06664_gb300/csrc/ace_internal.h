@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 
 #include "ace.h"
+#include "exact_div.h"
 
 namespace ace {
 
@@ -19,7 +20,7 @@ struct DevStats {
   unsigned long long rechecks;   // binary64 recomputations
   unsigned long long nonfinite;  // points with a non-finite squared norm
   unsigned int status;           // ACE_STATUS_* bits
-  unsigned int pad;
+  unsigned int done;             // blocks of the running score kernel that have folded (reset by its last)
   double mu, sigma, threshold;
 };
 
@@ -51,9 +52,9 @@ struct HashArgs {
 
 // Kernels launched from the runtime (each returns the launch error).
 cudaError_t launch_hash_simt(const HashArgs& a, cudaStream_t s);
-cudaError_t launch_score_gather(const void* ids, int ids16, long long ld, long long n, int K, int L,
+cudaError_t launch_score_gather(const void* ids, int ids16, long long ld, long long n, int K, int L, double alpha,
                                 const uint32_t* counts, uint32_t* sums, DevStats* st, cudaStream_t s);
-cudaError_t launch_flags(const uint32_t* sums, long long n, int L, double alpha, DevStats* st,
+cudaError_t launch_flags(const uint32_t* sums, long long n, const DivConst& div, const DevStats* st,
                          double* scores, uint8_t* flags, cudaStream_t s);
 cudaError_t launch_insert_from_ids(const void* ids, int ids16, long long ld, long long n, int K, int L,
                                    uint32_t* counts, int num_sms, cudaStream_t s);

@@ -1,10 +1,11 @@
 // Query phase and score statistics.
 //
 //   score_gather  Algorithm 1 query phase (§3.2): c_i = sum_j A_j[H_j(q_i)] from the cached
-//                 table-major ids; folds N += n, S1 += sum c, S2 += sum c^2 (exact 128-bit).
-//   flags         §5.3 threshold: mu = S1/(N L), sigma = sqrt(N S2 - S1^2)/(N L),
-//                 t = mu - alpha*sigma, score = c/L, flag = score < t.  Every binary64 step
-//                 is an explicit correctly rounded intrinsic, so no contraction can change it.
+//                 table-major ids; folds N += n, S1 += sum c, S2 += sum c^2 (exact 128-bit);
+//                 its last block derives the §5.3 threshold once: mu = S1/(N L),
+//                 sigma = sqrt(N S2 - S1^2)/(N L), t = mu - alpha*sigma.  Every binary64 step is
+//                 an explicit correctly rounded intrinsic, so no contraction can change it.
+//   flags         score = c/L (correctly rounded, integer arithmetic) and flag = score < t.
 //   sum_squares   Q = sum over all counters of A^2 (the closed form of Eq. 11 summed over
 //                 the inserts: mu_ins = Q / (n_ins L)).
 #include "ace_internal.h"
@@ -63,9 +64,50 @@ __device__ void block_fold(unsigned long long s1, unsigned long long s2lo, unsig
   }
 }
 
+// Correctly rounded (nearest-even) conversion of a 128-bit unsigned integer to binary64.
+__device__ double u128_to_f64(unsigned long long lo, unsigned long long hi) {
+  if (hi == 0) return __ull2double_rn(lo);
+  const int s = __clzll(static_cast<long long>(hi));
+  unsigned long long top = s == 0 ? hi : ((hi << s) | (lo >> (64 - s)));
+  const unsigned long long rest = lo << s;
+  top |= rest != 0 ? 1ull : 0ull;  // sticky bit, below the rounding position of a 64-bit value
+  const double scale = __longlong_as_double(static_cast<long long>(1023 + 64 - s) << 52);
+  return __dmul_rn(__ull2double_rn(top), scale);
+}
+
+// mu, sigma and t from the folded N, S1, S2 (called once, by the last block to fold).
+__device__ void finish_stats(DevStats* st, int L, double alpha) {
+  volatile DevStats* v = st;
+  const unsigned long long N = v->n_scored;
+  const unsigned long long s1lo = v->S1[0], s1hi = v->S1[1], s2lo = v->S2[0], s2hi = v->S2[1];
+  // N * S2 as 128 bits, with overflow detection
+  const unsigned long long plo = N * s2lo;
+  const unsigned long long pmid = __umul64hi(N, s2lo);
+  const unsigned long long hlo = N * s2hi;
+  const bool ovf = __umul64hi(N, s2hi) != 0 || pmid + hlo < pmid || s1hi != 0 || N == 0;
+  const unsigned long long phi = pmid + hlo;
+  // S1^2 (S1 < 2^64 whenever N*S2 < 2^128, by Cauchy-Schwarz)
+  const unsigned long long qlo = s1lo * s1lo, qhi = __umul64hi(s1lo, s1lo);
+  const unsigned long long vlo = plo - qlo;
+  const unsigned long long vhi = phi - qhi - (plo < qlo ? 1ull : 0ull);
+  double mu, sigma, t;
+  if (ovf) {
+    if (N != 0) atomicOr(&st->status, static_cast<unsigned>(ACE_STATUS_SUM_OVERFLOW));
+    mu = sigma = t = __longlong_as_double(0x7ff8000000000000LL);
+  } else {
+    const double NL = __dmul_rn(__ull2double_rn(N), static_cast<double>(L));
+    mu = __ddiv_rn(u128_to_f64(s1lo, s1hi), NL);
+    sigma = __ddiv_rn(__dsqrt_rn(u128_to_f64(vlo, vhi)), NL);
+    t = __dsub_rn(mu, __dmul_rn(alpha, sigma));
+  }
+  st->mu = mu;
+  st->sigma = sigma;
+  st->threshold = t;
+}
+
 template <typename IdT>
 __global__ void __launch_bounds__(256) score_gather_kernel(const IdT* __restrict__ ids, long long ld, long long n, int K,
-                                                           int L, const uint32_t* __restrict__ counts,
+                                                           int L, double alpha, const uint32_t* __restrict__ counts,
                                                            uint32_t* __restrict__ sums, DevStats* st) {
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   unsigned long long c = 0;
@@ -80,62 +122,32 @@ __global__ void __launch_bounds__(256) score_gather_kernel(const IdT* __restrict
     sums[i] = static_cast<uint32_t>(c);
   }
   block_fold(c, c * c, __umul64hi(c, c), st->S1, st->S2);
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&st->n_scored, static_cast<unsigned long long>(n));
-}
-
-// Correctly rounded (nearest-even) conversion of a 128-bit unsigned integer to binary64.
-__device__ double u128_to_f64(unsigned long long lo, unsigned long long hi) {
-  if (hi == 0) return __ull2double_rn(lo);
-  const int s = __clzll(static_cast<long long>(hi));
-  unsigned long long top = s == 0 ? hi : ((hi << s) | (lo >> (64 - s)));
-  const unsigned long long rest = lo << s;
-  top |= rest != 0 ? 1ull : 0ull;  // sticky bit, below the rounding position of a 64-bit value
-  const double scale = __longlong_as_double(static_cast<long long>(1023 + 64 - s) << 52);
-  return __dmul_rn(__ull2double_rn(top), scale);
-}
-
-__global__ void __launch_bounds__(256) flags_kernel(const uint32_t* __restrict__ sums, long long n, int L, double alpha,
-                                                    DevStats* st, double* __restrict__ scores,
-                                                    uint8_t* __restrict__ flags) {
-  __shared__ double t_sh;
   if (threadIdx.x == 0) {
-    const unsigned long long N = st->n_scored;
-    const unsigned long long s1lo = st->S1[0], s1hi = st->S1[1], s2lo = st->S2[0], s2hi = st->S2[1];
-    // N * S2 as 128 bits, with overflow detection
-    const unsigned long long plo = N * s2lo;
-    const unsigned long long pmid = __umul64hi(N, s2lo);
-    const unsigned long long hlo = N * s2hi;
-    const bool ovf = __umul64hi(N, s2hi) != 0 || pmid + hlo < pmid || s1hi != 0 || N == 0;
-    const unsigned long long phi = pmid + hlo;
-    // S1^2 (S1 < 2^64 whenever N*S2 < 2^128, by Cauchy-Schwarz)
-    const unsigned long long qlo = s1lo * s1lo, qhi = __umul64hi(s1lo, s1lo);
-    const unsigned long long vlo = plo - qlo;
-    const unsigned long long vhi = phi - qhi - (plo < qlo ? 1ull : 0ull);
-    double mu, sigma, t;
-    if (ovf) {
-      if (N != 0) atomicOr(&st->status, static_cast<unsigned>(ACE_STATUS_SUM_OVERFLOW));
-      mu = sigma = t = __longlong_as_double(0x7ff8000000000000LL);
-    } else {
-      const double NL = __dmul_rn(__ull2double_rn(N), static_cast<double>(L));
-      mu = __ddiv_rn(u128_to_f64(s1lo, s1hi), NL);
-      sigma = __ddiv_rn(__dsqrt_rn(u128_to_f64(vlo, vhi)), NL);
-      t = __dsub_rn(mu, __dmul_rn(alpha, sigma));
-    }
-    t_sh = t;
-    if (blockIdx.x == 0) {
-      st->mu = mu;
-      st->sigma = sigma;
-      st->threshold = t;
+    if (blockIdx.x == 0) atomicAdd(&st->n_scored, static_cast<unsigned long long>(n));
+    // the last block to fold (after every other block's sums are visible) derives mu, sigma, t
+    __threadfence();
+    const unsigned int ticket = atomicAdd(&st->done, 1u);
+    if (ticket == gridDim.x - 1) {
+      __threadfence();
+      finish_stats(st, L, alpha);
+      st->done = 0u;
     }
   }
-  __syncthreads();
-  const double t = t_sh;
-  const double Ld = static_cast<double>(L);
+}
+
+// score = RN(c / L) by integer arithmetic; flag = score < t, compared on bit patterns (scores
+// are non-negative, so their order is that of their bits; a threshold that is not positive,
+// NaN included, flags nothing).
+__global__ void __launch_bounds__(256) flags_kernel(const uint32_t* __restrict__ sums, long long n, DivConst div,
+                                                    const DevStats* __restrict__ st, double* __restrict__ scores,
+                                                    uint8_t* __restrict__ flags) {
+  const long long tb = __double_as_longlong(st->threshold);
+  const bool tpos = tb > 0 && tb <= 0x7ff0000000000000LL;
   for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const double sc = __ddiv_rn(__uint2double_rn(sums[i]), Ld);
-    if (scores) scores[i] = sc;
-    if (flags) flags[i] = sc < t ? 1 : 0;
+    const unsigned long long sb = rn_quotient_bits(sums[i], div);
+    if (scores) scores[i] = __longlong_as_double(static_cast<long long>(sb));
+    if (flags) flags[i] = (tpos && static_cast<long long>(sb) < tb) ? 1 : 0;
   }
 }
 
@@ -275,26 +287,26 @@ cudaError_t launch_insert_from_ids(const void* ids, int ids16, long long ld, lon
   return cudaGetLastError();
 }
 
-cudaError_t launch_score_gather(const void* ids, int ids16, long long ld, long long n, int K, int L,
+cudaError_t launch_score_gather(const void* ids, int ids16, long long ld, long long n, int K, int L, double alpha,
                                 const uint32_t* counts, uint32_t* sums, DevStats* st, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const long long blocks = (n + 255) / 256;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   if (ids16)
     score_gather_kernel<uint16_t><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
-        static_cast<const uint16_t*>(ids), ld, n, K, L, counts, sums, st);
+        static_cast<const uint16_t*>(ids), ld, n, K, L, alpha, counts, sums, st);
   else
     score_gather_kernel<uint32_t><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
-        static_cast<const uint32_t*>(ids), ld, n, K, L, counts, sums, st);
+        static_cast<const uint32_t*>(ids), ld, n, K, L, alpha, counts, sums, st);
   return cudaGetLastError();
 }
 
-cudaError_t launch_flags(const uint32_t* sums, long long n, int L, double alpha, DevStats* st, double* scores,
+cudaError_t launch_flags(const uint32_t* sums, long long n, const DivConst& div, const DevStats* st, double* scores,
                          uint8_t* flags, cudaStream_t s) {
+  if (n <= 0 || (!scores && !flags)) return cudaSuccess;
   long long blocks = (n + 255) / 256;
-  if (blocks < 1) blocks = 1;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  flags_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(sums, n, L, alpha, st, scores, flags);
+  flags_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(sums, n, div, st, scores, flags);
   return cudaGetLastError();
 }
 
