@@ -190,7 +190,7 @@ int plan_tc(ace_detector* h) {
   const int d = h->d, K = h->K, L = h->L, KL = h->KL;
   if (d > ace::kMaxD) return ACE_OK;
   const int d_pad = (d + 15) / 16 * 16;
-  const int tpc = std::min(256 / K, 32);  // at most 32 tables per chunk (32-bit table masks)
+  const int tpc = std::min(ace::kTcBufCols / K, 32);  // N <= kTcBufCols per chunk, at most 32 tables (32-bit masks)
   const int nch = (L + tpc - 1) / tpc;
   if (nch > ace::kTcMaxChunks) return ACE_OK;
   ace::TcArgs& t = h->tc;

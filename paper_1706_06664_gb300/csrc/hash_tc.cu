@@ -41,7 +41,9 @@ namespace {
 
 using namespace tc;
 
-constexpr int kThreads = 416;  // 13 warps: MMA, 4 converters, 2 x 4 epilogue
+constexpr int kBufs = kTcBufs;        // TMEM accumulator buffers, one epilogue group each
+constexpr int kBufCols = kTcBufCols;  // largest chunk N
+constexpr int kThreads = 32 * (5 + 4 * kBufs);  // MMA, 4 converters, kBufs x 4 epilogue warps
 constexpr int kConv0 = 32;     // first converter thread
 constexpr int kEpi0 = 160;     // first epilogue thread
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
@@ -53,7 +55,7 @@ struct Smem {
   uint64_t drain;
   uint64_t a_full[2], a_empty[2];
   uint64_t bnd_full[2], bnd_empty[2];
-  uint64_t t_full[2], t_empty[2];
+  uint64_t t_full[kBufs], t_empty[kBufs];
   uint32_t taddr;
   int abort;
   unsigned int ndef;  // entries in this CTA's deferred segment
@@ -151,9 +153,11 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
       mbar_init(&S->a_full[s], 128);
       mbar_init(&S->a_empty[s], 1);
       mbar_init(&S->bnd_full[s], 128);
-      mbar_init(&S->bnd_empty[s], 256);
-      mbar_init(&S->t_full[s], 1);
-      mbar_init(&S->t_empty[s], 128);
+      mbar_init(&S->bnd_empty[s], 128 * kBufs);
+    }
+    for (int b = 0; b < kBufs; ++b) {
+      mbar_init(&S->t_full[b], 1);
+      mbar_init(&S->t_empty[b], 128);
     }
     mbar_fence_init();
   }
@@ -194,8 +198,8 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
         tc_fence_after();
         const uint32_t ahi = smem_u32(a_hi(s)), alo = smem_u32(a_lo(s));
         for (int c = 0; c < a.nchunks; ++c, ++item) {
-          const int b = static_cast<int>(item & 1);
-          if (item >= 2 && !mbar_wait(&S->t_empty[b], ((item >> 1) + 1) & 1, &S->abort, kWaitCycles)) {
+          const int b = static_cast<int>(item % kBufs);
+          if (item >= kBufs && !mbar_wait(&S->t_empty[b], ((item / kBufs) + 1) & 1, &S->abort, kWaitCycles)) {
             ok = false;
             set_abort(S, a.st);
             break;
@@ -204,7 +208,7 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
           const TcChunk& ch = a.chunk[c];
           const uint32_t idesc = idesc_bf16(128, ch.N);
           const uint32_t bhi = smem_u32(Bimg) + ch.boff_hi, blo = smem_u32(Bimg) + ch.boff_lo;
-          const uint32_t dt = tmem + static_cast<uint32_t>(b * 256);
+          const uint32_t dt = tmem + static_cast<uint32_t>(b * kBufCols);
           uint32_t acc = 0;
           // x_hi . w_hi, x_hi . w_lo, x_lo . w_hi
           for (int p = 0; p < 3; ++p) {
@@ -251,12 +255,34 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
       pending = true;
       issue_copy(blockIdx.x);
     }
-    const int rot = (d & 1) ? 0 : r;  // even d: rotate the read order across rows (banks)
+    // Odd d: rows of the staging buffer sit d words apart, an odd stride, so thread r reading
+    // its own row is free of bank conflicts; the whole row is read into registers first (the
+    // compiler cannot move a later load of the staging buffer above an earlier store to the A
+    // stage, so reading while converting would serialise the groups), and the next tile's
+    // copy is issued as soon as every converter has read the buffer, overlapping the
+    // conversion.  Even d: the group order is rotated across rows (banks) and the buffer is
+    // read group by group while converting.
+    const bool odd = (d & 1) != 0;
     const int ngrp = d_pad / 8;
+    const int rot = odd ? 0 : r % ngrp;
+    const float* const stagef = reinterpret_cast<const float*>(stage);
+    const unsigned short* const stageh = reinterpret_cast<const unsigned short*>(stage);
+    auto staged_x = [&](int k) {
+      return BF16 ? __uint_as_float(static_cast<unsigned>(stageh[r * d + k]) << 16) : stagef[r * d + k];
+    };
+    // hi = bf16(v), lo = bf16(v - hi) for a pair, as two packed bfloat16x2 words
+    auto split2 = [](float v0, float v1, uint32_t& hi, uint32_t& lo) {
+      hi = pack_bf16x2(v0, v1);
+      const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xFFFF0000u);
+      lo = pack_bf16x2(v0 - h0, v1 - h1);
+    };
     int tl = 0;
     for (long long m = blockIdx.x; m < ntiles; m += gridDim.x, ++tl) {
       const int s = tl & 1;
       const bool full = full_tile(m);
+      const long long i = m * 128 + r;
+      const bool valid = i < n;
+      const long long mn = m + gridDim.x;
       bool ok = S->abort == 0;
       if (ok && full) {
         if (mbar_wait(&S->st_full, staged & 1, &S->abort, kWaitCycles)) {
@@ -265,6 +291,28 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
         } else {
           ok = false;
           set_abort(S, a.st);
+        }
+      }
+      float xr[kMaxD];
+      if (odd) {
+        if (conv_bar_or(!ok)) break;
+#pragma unroll
+        for (int k = 0; k < kMaxD; ++k) xr[k] = 0.f;
+        if (valid) {
+          if (full) {
+#pragma unroll
+            for (int k = 0; k < kMaxD; ++k)
+              if (k < d) xr[k] = staged_x(k);
+          } else {
+#pragma unroll
+            for (int k = 0; k < kMaxD; ++k)
+              if (k < d) xr[k] = xval<BF16>(X, i * d + k);
+          }
+        }
+        conv_bar_or(false);  // every converter has read the staging buffer
+        if (r == 0 && mn < ntiles && full_tile(mn)) {
+          pending = true;
+          issue_copy(mn);
         }
       }
       if (ok && tl >= 2) {
@@ -276,35 +324,41 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
       }
       // every converter reaches the barrier; stopping is decided for all of them at once
       if (conv_bar_or(!ok)) break;
-      const long long i = m * 128 + r;
-      const bool valid = i < n;
       float q = 0.f;
-      for (int gi = 0; gi < ngrp; ++gi) {
-        const int g = (gi + rot) % ngrp;
-        float v[8];
+      if (odd) {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int k = g * 8 + e;
-          float x = 0.f;
-          if (valid && k < d) {
-            if (full) x = BF16 ? __uint_as_float(static_cast<unsigned>(reinterpret_cast<const unsigned short*>(stage)[r * d + k]) << 16)
-                               : reinterpret_cast<const float*>(stage)[r * d + k];
-            else x = xval<BF16>(X, i * d + k);
+        for (int k = 0; k < kMaxD; ++k) q = fmaf(xr[k], xr[k], q);
+#pragma unroll
+        for (int g = 0; g < kMaxD / 8; ++g) {
+          if (g < ngrp) {
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) split2(xr[8 * g + 2 * e], xr[8 * g + 2 * e + 1], hi[e], lo[e]);
+            const uint32_t off = kmajor_offset(r, g * 8, d_pad);
+            *reinterpret_cast<uint4*>(a_hi(s) + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(a_lo(s) + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
           }
-          v[e] = x;
-          q = fmaf(x, x, q);
         }
-        uint32_t hi[4], lo[4];
+      } else {
+        for (int gi = 0; gi < ngrp; ++gi) {
+          int g = gi + rot;
+          if (g >= ngrp) g -= ngrp;
+          float v[8];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float h0 = __bfloat162float(__float2bfloat16_rn(v[2 * e]));
-          const float h1 = __bfloat162float(__float2bfloat16_rn(v[2 * e + 1]));
-          hi[e] = pack_bf16x2(h0, h1);
-          lo[e] = pack_bf16x2(v[2 * e] - h0, v[2 * e + 1] - h1);
+          for (int e = 0; e < 8; ++e) {
+            const int k = g * 8 + e;
+            float x = 0.f;
+            if (valid && k < d) x = full ? staged_x(k) : xval<BF16>(X, i * d + k);
+            v[e] = x;
+            q = fmaf(x, x, q);
+          }
+          uint32_t hi[4], lo[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) split2(v[2 * e], v[2 * e + 1], hi[e], lo[e]);
+          const uint32_t off = kmajor_offset(r, g * 8, d_pad);
+          *reinterpret_cast<uint4*>(a_hi(s) + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<uint4*>(a_lo(s) + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
-        const uint32_t off = kmajor_offset(r, g * 8, d_pad);
-        *reinterpret_cast<uint4*>(a_hi(s) + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(a_lo(s) + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
       }
       // row bound: tau * ||x||_up + tau_abs; +inf makes every column of the row a recheck
       float B;
@@ -315,11 +369,12 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
       fence_proxy_async();
       mbar_arrive(&S->a_full[s]);
       mbar_arrive(&S->bnd_full[s]);
-      conv_bar_or(false);  // every converter is done with the staging buffer
-      const long long mn = m + gridDim.x;
-      if (r == 0 && mn < ntiles && full_tile(mn)) {
-        pending = true;
-        issue_copy(mn);
+      if (!odd) {
+        conv_bar_or(false);  // every converter is done with the staging buffer
+        if (r == 0 && mn < ntiles && full_tile(mn)) {
+          pending = true;
+          issue_copy(mn);
+        }
       }
     }
     // leave no bulk copy in flight (bounded wait that ignores the abort flag)
@@ -339,7 +394,7 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
     const int K = KC > 0 ? KC : a.K;
     const int L = a.L, mode = a.mode, nch = a.nchunks, d = a.d;
     const bool st_tm = (mode & kStoreIds) != 0, st_rm = (mode & kStoreIdsRowMajor) != 0;
-    const int tpc = min(256 / K, 32);  // tables per chunk (the host plans chunks the same way)
+    const int tpc = min(kBufCols / K, 32);  // tables per chunk (the host plans chunks the same way)
     const long long n = a.n, ld = a.ld;
     IdT* const ids = reinterpret_cast<IdT*>(a.ids);
     uint32_t* const ids_rm = a.ids_rm;
@@ -367,9 +422,9 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
       const long long i = m * 128 + r;
       const bool valid = i < n;
       for (int c = 0; c < nch; ++c, ++item) {
-        const int b = static_cast<int>(item & 1);
+        const int b = static_cast<int>(item % kBufs);
         if (b != wg) continue;
-        ok = mbar_wait(&S->t_full[b], (item >> 1) & 1, &S->abort, kWaitCycles);
+        ok = mbar_wait(&S->t_full[b], (item / kBufs) & 1, &S->abort, kWaitCycles);
         if (!__all_sync(0xFFFFFFFFu, ok)) {
           ok = false;
           set_abort(S, st);
@@ -380,23 +435,24 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
         const int ntab = min(tpc, L - tab0);
         const int ncols = ntab * K;
         const int ng = (ncols + 31) >> 5;
-        const uint32_t tbase = tmem + (static_cast<uint32_t>(q4 * 32) << 16) + static_cast<uint32_t>(b * 256);
+        const uint32_t tbase = tmem + (static_cast<uint32_t>(q4 * 32) << 16) + static_cast<uint32_t>(b * kBufCols);
         // Classify the chunk's columns.  bw[g] bit k = [column 32g+k > 0].  A table with any
         // column inside the bound (|projection| <= B, compared on bit patterns: both are
         // non-negative floats; Bi = all ones for a row whose bound is +inf, so that row is
-        // deferred whatever the minimum, NaN included) is deferred whole
-        // to the recheck kernel.  The next 32 columns are loaded from TMEM while the current
-        // ones are classified; signs are packed by four independent funnel-shift chains.
+        // deferred whatever the minimum, NaN included) is deferred whole to the recheck
+        // kernel.  The next 32 columns are loaded from TMEM while the current ones are
+        // classified; signs are packed by four independent funnel-shift chains.
         const uint32_t Bi = isinf(B) ? 0xFFFFFFFFu : __float_as_uint(B);
-        uint32_t bw[8];
+        constexpr int NG = kBufCols / 32;  // 32-column groups of a buffer
+        uint32_t bw[NG];
         uint32_t va[32], vb[32];
         uint32_t defmask = 0u;  // bit t: table t of the chunk has a column inside the bound
-        constexpr int TPC = KC > 0 ? 256 / KC : 1;
+        constexpr int TPC = KC > 0 ? kBufCols / KC : 1;
         float tmin[TPC];  // per table: smallest |projection| (a min with |.| operands)
-        uint32_t aw[8];
+        uint32_t aw[NG];
         tmem_ld32(tbase, va);
 #pragma unroll
-        for (int g = 0; g < 8; ++g) {
+        for (int g = 0; g < NG; ++g) {
           bw[g] = 0u;
           aw[g] = 0u;
           if (g < ng) {
@@ -448,20 +504,31 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
           for (int t = 0; t < TPC; ++t)
             if (t < ntab && __float_as_uint(tmin[t]) <= Bi) defmask |= 1u << t;
           if (!valid) defmask = 0u;
-          // table t is bits [t KC, t KC + KC) of the chunk: compile-time word and shift
+          // table t is bits [t KC, t KC + KC) of the chunk: compile-time word and shift.  Every
+          // table's id is stored, deferred ones too: the recheck kernel, which runs after this
+          // one, overwrites those.  One pointer steps through the tables (no per-table multiply).
+          if (valid) {
+            IdT* pt = ids + static_cast<size_t>(tab0) * ld + i;
+            uint32_t* pr = ids_rm + i * L + tab0;
 #pragma unroll
-          for (int t = 0; t < TPC; ++t) {
-            const int cb = t * KC, wi = cb >> 5, sh = cb & 31;
-            uint32_t id = bw[wi] >> sh;
-            if (sh + KC > 32) id |= bw[wi + 1] << (32 - sh);
-            if (valid && t < ntab && !((defmask >> t) & 1u)) store(id & KM, tab0 + t);
+            for (int t = 0; t < TPC; ++t) {
+              if (t < ntab) {
+                const int cb = t * KC, wi = cb >> 5, sh = cb & 31;
+                uint32_t id = bw[wi] >> sh;
+                if (sh + KC > 32) id |= bw[wi + 1] << (32 - sh);
+                id &= KM;
+                if (st_tm) *pt = static_cast<IdT>(id);
+                if (st_rm) pr[t] = id;
+                pt += ld;
+              }
+            }
           }
         } else {
           // any K: streaming extraction, table t is bits [tK, tK + K) of the chunk
           unsigned long long accb = 0ull, acca = 0ull;
           int nacc = 0, t = 0;
 #pragma unroll
-          for (int g = 0; g < 8; ++g) {
+          for (int g = 0; g < NG; ++g) {
             if (g < ng) {
               accb |= static_cast<unsigned long long>(bw[g]) << nacc;
               acca |= static_cast<unsigned long long>(aw[g]) << nacc;

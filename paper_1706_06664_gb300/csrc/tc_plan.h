@@ -8,6 +8,8 @@
 namespace ace {
 
 constexpr int kTcMaxChunks = 16;
+constexpr int kTcBufs = 2;       // TMEM accumulator buffers (and epilogue warp groups)
+constexpr int kTcBufCols = 256;  // columns of one buffer: a chunk has N <= kTcBufCols
 constexpr int kMaxD = 64;  // largest d of the resident design (staging and recheck registers)
 
 // One chunk: whole tables [tab0, tab0 + ntab), N = ntab*K rounded up to 16 MMA columns,
