@@ -68,6 +68,7 @@ struct ace_detector {
   unsigned long long* defer = nullptr;
   size_t defer_bytes = 0;
   unsigned int* defer_counts = nullptr;  // one per CTA of the tensor-core kernel
+  float* wpad = nullptr;                 // [KL][dp] W, columns contiguous, zero-padded (recheck)
   // profiling hook
   bool prof = false;
   uint64_t launches[ACE_NPHASE] = {0, 0, 0, 0, 0, 0};
@@ -124,6 +125,7 @@ void free_all(ace_detector* h) {
   cudaFree(h->bimg);
   cudaFree(h->defer);
   cudaFree(h->defer_counts);
+  cudaFree(h->wpad);
   cudaFree(h->W);
   cudaFree(h->Wt);
   cudaFree(h->cB);
@@ -277,6 +279,19 @@ int plan_tc(ace_detector* h) {
   t.dot2abs = static_cast<float>(4.0 * d * std::ldexp(1.0, -149));
   t.Wt = h->Wt;
   t.W = h->W;
+  // W with contiguous, zero-padded columns for the recheck's 16-byte loads
+  t.dp = (d + 3) / 4 * 4;
+  {
+    std::vector<float> wp(static_cast<size_t>(KL) * t.dp, 0.f);
+    for (int c = 0; c < KL; ++c)
+      for (int i = 0; i < d; ++i) wp[static_cast<size_t>(c) * t.dp + i] = h->Wh[static_cast<size_t>(i) * KL + c];
+    cudaFree(h->wpad);
+    h->wpad = nullptr;
+    if ((e = cudaMalloc(&h->wpad, wp.size() * sizeof(float))) != cudaSuccess) return cuda_fail(e, "cudaMalloc padded W");
+    if ((e = cudaMemcpy(h->wpad, wp.data(), wp.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cuda_fail(e, "copy padded W");
+  }
+  t.Wp = h->wpad;
   t.cB32 = h->cB;
   t.xfac32 = h->xfac;
   t.xabs32 = h->xabs;

@@ -583,79 +583,68 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
 // exact ties.  The id is the ballot of the lanes' bits.
 template <bool BF16, typename IdT>
 __global__ void __launch_bounds__(256) recheck_kernel(const __grid_constant__ TcArgs a, int nseg) {
-  // Entries live in nseg per-CTA segments; a prefix sum of their counts maps a global entry
-  // index to (segment, offset).  Each half warp takes one entry (K <= 16; else a whole warp):
-  // lane k recomputes column j K + k.
-  __shared__ unsigned long long pref[kMaxSeg + 1];
-  __shared__ float xsm[8][2][kMaxD];  // per warp, per half-warp entry
-  const int d = a.d, K = a.K, L = a.L, mode = a.mode;
+  // Entries live in nseg per-CTA segments of the deferred list; warp gw works on segment
+  // gw % nseg with the other warps of that segment.  Each half warp takes one entry (K <= 16;
+  // else a whole warp): lane k recomputes column j K + k.
+  __shared__ __align__(16) float xsm[8][2][kMaxD];  // per warp, per half-warp entry
+  const int d = a.d, K = a.K, L = a.L, mode = a.mode, dp = a.dp;
   const long long ld = a.ld;
   const void* const X = a.X;
   const float* const Wt = a.Wt;
-  const float* const W = a.W;
-  const int KL = K * L;
+  const float* const Wp = a.Wp;
   const float* const cB32 = a.cB32;
   const float xfac32 = a.xfac32, xabs32 = a.xabs32, babs32 = a.babs32;
   const float dot2c = a.dot2c, dot2abs = a.dot2abs;
   IdT* const ids = reinterpret_cast<IdT*>(a.ids);
   uint32_t* const ids_rm = a.ids_rm;
   const uint32_t kmask = (1u << K) - 1u;
-  // prefix sums of the segment counts: parallel loads, then one warp scans lane-sized runs
   const int lane = threadIdx.x & 31;
-  for (int g = threadIdx.x; g < nseg; g += blockDim.x) pref[g + 1] = a.defer_counts[g];
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int per = (nseg + 31) / 32;
-    const int g0 = min(nseg, lane * per), g1 = min(nseg, g0 + per);
-    unsigned long long own = 0;
-    for (int g = g0; g < g1; ++g) own += pref[g + 1];
-    unsigned long long incl = own;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const unsigned long long v = __shfl_up_sync(0xFFFFFFFFu, incl, off);
-      if (lane >= off) incl += v;
-    }
-    unsigned long long run = incl - own;
-    for (int g = g0; g < g1; ++g) {
-      run += pref[g + 1];
-      pref[g + 1] = run;
-    }
-    if (lane == 0) pref[0] = 0;
-  }
-  __syncthreads();
-  const unsigned long long total = pref[nseg];
   const int width = K <= 16 ? 16 : 32;  // lanes per entry
   const int sub = lane / width, sl = lane % width;
-  const unsigned long long per_warp = 32 / width;
-  const unsigned long long nwarps = static_cast<unsigned long long>(gridDim.x) * (blockDim.x >> 5);
-  const unsigned long long gw = static_cast<unsigned long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const unsigned per_warp = 32 / width;
+  const unsigned nwarps = gridDim.x * (blockDim.x >> 5);
+  const unsigned gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (gw >= nwarps - nwarps % static_cast<unsigned>(nseg) && nwarps >= static_cast<unsigned>(nseg)) return;
+  const int seg = static_cast<int>(gw % static_cast<unsigned>(nseg));
+  const unsigned lw = gw / static_cast<unsigned>(nseg);             // this warp's rank in the segment
+  const unsigned nw = max(1u, nwarps / static_cast<unsigned>(nseg));  // warps per segment
+  const unsigned long long cnt = a.defer_counts[seg];
+  const unsigned long long* const list = a.defer + a.seg_cap * static_cast<unsigned long long>(seg);
   float* const xe = xsm[threadIdx.x >> 5][sub];  // this entry's x, read as a shared-memory broadcast
-  unsigned long long nre = 0;
-  for (unsigned long long base = gw * per_warp; base < total; base += nwarps * per_warp) {
-    const unsigned long long e = base + sub;
-    const bool has = e < total;
-    long long i = 0;
-    int j = 0;
-    if (has) {
-      int lo = 0, hi = nseg;  // segment g with pref[g] <= e < pref[g + 1]
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (pref[mid] <= e) lo = mid;
-        else hi = mid;
-      }
-      const unsigned long long w = a.defer[a.seg_cap * lo + (e - pref[lo])];
-      i = static_cast<long long>(w >> 24);
-      j = static_cast<int>(w & 0xFFFFFFull);
+  const unsigned long long stride = static_cast<unsigned long long>(nw) * per_warp;
+  auto word_at = [&](unsigned long long e) -> unsigned long long { return e < cnt ? list[e] : 0ull; };
+  // lane sl's coordinates sl + width m of point i
+  auto load_row = [&](bool has, long long i, float (&xv)[4]) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int t = sl + width * m;
+      xv[m] = (has && t < d && t < kMaxD) ? load_x<BF16>(X, i * d + t) : 0.f;
     }
-    // stage x (lane sl holds coordinates sl + width m) and its squared norm
+  };
+  // Software pipeline over this warp's rounds: while round r is computed, the x row of round
+  // r + 1 and the entry word of round r + 2 are in flight (each depends on the one before).
+  const unsigned long long e0 = static_cast<unsigned long long>(lw) * per_warp + sub;
+  unsigned long long w_cur = word_at(e0);
+  float xv[4];
+  load_row(e0 < cnt, static_cast<long long>(w_cur >> 24), xv);
+  unsigned long long w_nxt = word_at(e0 + stride);
+  unsigned long long nre = 0;
+  for (unsigned long long base = static_cast<unsigned long long>(lw) * per_warp; base < cnt; base += stride) {
+    const unsigned long long e = base + sub;
+    const bool has = e < cnt;
+    const long long i = static_cast<long long>(w_cur >> 24);
+    const int j = static_cast<int>(w_cur & 0xFFFFFFull);
+    float xn[4];
+    load_row(e + stride < cnt, static_cast<long long>(w_nxt >> 24), xn);
+    const unsigned long long w_nn = word_at(e + 2 * stride);
+    // stage x (zero beyond d) and its squared norm
     float q = 0.f;
 #pragma unroll
-    for (int m = 0; m < kMaxD / 16; ++m) {
+    for (int m = 0; m < 4; ++m) {
       const int t = sl + width * m;
       if (t < kMaxD) {
-        const float x = (has && t < d) ? load_x<BF16>(X, i * d + t) : 0.f;
-        xe[t] = x;
-        q = fmaf(x, x, q);
+        xe[t] = xv[m];
+        q = fmaf(xv[m], xv[m], q);
       }
     }
 #pragma unroll
@@ -664,17 +653,26 @@ __global__ void __launch_bounds__(256) recheck_kernel(const __grid_constant__ Tc
     __syncwarp();
     const float xu = norm_upper(q, xfac32, xabs32);
     const int col = j * K + (sl < K ? sl : 0);
-    // binary32 FMA chain in index order: x from shared memory, W row by row (L1-resident)
-    const float* wp = W + col;
+    // binary32 FMA chain in index order (the zero padding adds exact zeros): x from shared
+    // memory and the column of W with 16-byte loads
+    const float4* wq = reinterpret_cast<const float4*>(Wp + static_cast<size_t>(col) * dp);
+    const float4* xq = reinterpret_cast<const float4*>(xe);
     float s32 = 0.f;
-#pragma unroll 8
-    for (int t = 0; t < d; ++t, wp += KL) s32 = fmaf(xe[t], __ldg(wp), s32);
+#pragma unroll 4
+    for (int t4 = 0; t4 < dp / 4; ++t4) {
+      const float4 w = __ldg(wq + t4);
+      const float4 x = xq[t4];
+      s32 = fmaf(x.x, w.x, s32);
+      s32 = fmaf(x.y, w.y, s32);
+      s32 = fmaf(x.z, w.z, s32);
+      s32 = fmaf(x.w, w.w, s32);
+    }
     bool bit = false;
     if (has && sl < K) {
       if (fabsf(s32) > fmaf(__ldg(cB32 + col), xu, babs32)) {
         bit = s32 > 0.f;
       } else {
-        const int sg = dot2_sign<BF16>(X, i, d, W + col, KL, dot2c, dot2abs);
+        const int sg = dot2_sign<BF16>(X, i, d, Wp + static_cast<size_t>(col) * dp, 1, dot2c, dot2abs);
         bit = sg != 0 ? sg > 0 : exact_bit<BF16>(X, i, d, Wt, col);
       }
     }
@@ -686,6 +684,10 @@ __global__ void __launch_bounds__(256) recheck_kernel(const __grid_constant__ Tc
       nre += static_cast<unsigned long long>(K);
     }
     __syncwarp();  // xe is rewritten by the next entry
+    w_cur = w_nxt;
+    w_nxt = w_nn;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) xv[m] = xn[m];
   }
   if (nre) atomicAdd(&a.st->rechecks, nre);
 }
@@ -722,10 +724,16 @@ cudaError_t launch_recheck(const TcArgs& a, int num_sms, cudaStream_t s) {
   if (nseg > kMaxSeg) return cudaErrorInvalidValue;
   // one wave: as many 256-thread blocks per SM as its registers and threads allow
   auto go = [&](auto kern) -> cudaError_t {
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+    // a small shared-memory carveout leaves most of the SM's L1 to cache W (d x KL binary32,
+    // read row by row for every entry)
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 25);
     if (e != cudaSuccess) return e;
-    kern<<<static_cast<unsigned>(num_sms * max(1, per_sm)), 256, 0, s>>>(a, nseg);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = static_cast<unsigned>(num_sms * max(1, per_sm));
+    if (grid * 8u < static_cast<unsigned>(nseg)) return cudaErrorInvalidConfiguration;  // a warp per segment at least
+    kern<<<grid, 256, 0, s>>>(a, nseg);
     return cudaGetLastError();
   };
   const bool id16 = a.K <= 16;

@@ -36,7 +36,9 @@ struct TcArgs {
   uint32_t* counts;
   DevStats* st;
   const float* Wt;  // [KL][d] original W, columns contiguous (binary64 recheck)
-  const float* W;   // [d][KL] original W, rows contiguous (binary32 recheck)
+  const float* W;   // [d][KL] original W, rows contiguous
+  const float* Wp;  // [KL][dp] original W, columns contiguous and zero-padded to dp = d rounded up to 4
+  int dp;
   const float* cB32;                // SIMT-engine guard coefficients per column
   float xfac32, xabs32, babs32;     // SIMT-engine norm inflation and absolute allowances
   float dot2c, dot2abs;             // Dot2 filter: bound = dot2c * sum|x_i w_i|^ + dot2abs
