@@ -55,22 +55,29 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "src": "fallback"}
 
 
-def _src_sha(kernel_file: str) -> str:
+# sources that determine each timed kernel's code (its traffic figure is void once one changes)
+KERNEL_SOURCES = {
+    "hash_tc": ("hash_tc.cu", "tc_ptx.cuh", "tc_plan.h", "guard.cuh", "ace_internal.h", "exact_div.h"),
+    "hash_simt": ("hash_simt.cu", "guard.cuh", "ace_internal.h", "exact_div.h"),
+}
+
+
+def _src_sha(kernel_key: str) -> str:
     h = hashlib.sha256()
-    for f in (kernel_file, "guard.cuh", "ace_internal.h"):
+    for f in KERNEL_SOURCES[kernel_key]:
         with open(os.path.join(ROOT, "paper_1706_06664_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel_key: str, kernel_file: str, units: int):
+def _traffic(kernel_key: str, units: int):
     """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
     try:
         with open(TRAFFIC_PATH) as f:
             t = json.load(f)[kernel_key]
     except Exception:
         return None
-    if t.get("src_sha") != _src_sha(kernel_file):
+    if t.get("src_sha") != _src_sha(kernel_key):
         return None
     return t["bytes_per_point"] * units
 
@@ -298,14 +305,14 @@ def run_ours(args):
     if top == "hash":
         t = per_launch_ms["hash"] / 1e3
         if precision == ace.ACE_PROJ_BF16:
-            kfile, kkey = "hash_tc.cu", "hash_tc"
+            kkey = "hash_tc"
             roof = {"bound": "tensor", "achieved": flops / t / 1e12, "peak": peaks["bf16_tflops"],
                     "unit": "TFLOP/s", "peak_src": f"bf16 burst, {peaks['src']}"}
         else:
-            kfile, kkey = "hash_simt.cu", "hash_simt"
+            kkey = "hash_simt"
             roof = {"bound": "alu", "achieved": flops / t / 1e12, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "peak_src": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"}
-        roof["traffic"] = _traffic(kkey, kfile, n)
+        roof["traffic"] = _traffic(kkey, n)
         roof["kernel"] = kkey
     else:
         t = per_launch_ms[top] / 1e3
