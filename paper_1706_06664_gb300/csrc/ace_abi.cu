@@ -57,6 +57,9 @@ struct ace_detector {
   double* scstage = nullptr;
   uint8_t* flstage = nullptr;
   size_t stage_cap = 0;  // elements
+  // host-buffer entry: copy stream and per-chunk events (created on first use)
+  cudaStream_t cstream = nullptr;
+  cudaEvent_t cev[17] = {};
   uint64_t n_ins = 0;
   ace::DivConst div{};    // constants of the score division by L
   std::vector<float> Wh;  // host copy of W
@@ -133,6 +136,9 @@ void free_all(ace_detector* h) {
   cudaFree(h->st);
   cudaFree(h->ids);
   cudaFree(h->sums);
+  for (auto& e : h->cev)
+    if (e) cudaEventDestroy(e);
+  if (h->cstream) cudaStreamDestroy(h->cstream);
   cudaFree(h->xstage);
   cudaFree(h->scstage);
   cudaFree(h->flstage);
@@ -429,7 +435,10 @@ ace::HashArgs hash_args(ace_handle h, const void* X, long long n, int dtype, int
 
 size_t id_bytes(ace_handle h) { return h->K <= 16 ? 2 : 4; }
 
-int run_hash(ace_handle h, const ace::HashArgs& a, cudaStream_t s) {
+// Hashes a.n points into the ids scratch (a.ids, leading dimension a.ld).  With kInsert the
+// counts are incremented too: fused in the SIMT engine; on the tensor-core path by a pass over
+// the stored ids, which `tc_insert` = false leaves to the caller (chunked hashing of one batch).
+int run_hash(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_insert = true) {
   if (h->precision == ACE_PROJ_FP32 || !h->tc_ok) {
     h->last_precision = ACE_PROJ_FP32;
     PhaseScope ps(h, ACE_PHASE_HASH, s);
@@ -474,11 +483,28 @@ int run_hash(ace_handle h, const ace::HashArgs& a, cudaStream_t s) {
     e = ace::launch_recheck(t, h->num_sms, s);
   }
   if (e != cudaSuccess) return cuda_fail(e, "recheck kernel launch");
-  if (insert) {
+  if (insert && tc_insert) {
     PhaseScope ps(h, ACE_PHASE_INSERT, s);
     e = ace::launch_insert_from_ids(ids, h->K <= 16, a.ld, a.n, h->K, h->L, h->counts, h->num_sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "insert kernel launch");
   }
+  return ACE_OK;
+}
+
+// Query phase and §5.3 rule over the n ids already in the scratch.
+int score_tail(ace_handle h, long long n, double alpha, double* scores, uint32_t* sum_out, uint8_t* flags,
+               cudaStream_t s) {
+  cudaError_t e;
+  {
+    PhaseScope ps(h, ACE_PHASE_SCORE, s);
+    e = ace::launch_score_gather(h->ids, h->K <= 16, n, n, h->K, h->L, alpha, h->counts, sum_out, h->st, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "score kernel launch");
+  {
+    PhaseScope ps(h, ACE_PHASE_FLAGS, s);
+    e = ace::launch_flags(sum_out, n, h->div, h->st, scores, flags, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "flags kernel launch");
   return ACE_OK;
 }
 
@@ -501,18 +527,7 @@ int score_common(ace_handle h, const void* X, long long n, int dtype, double alp
   ace::HashArgs a = hash_args(h, X, n, dtype, ace::kStoreIds | (insert ? ace::kInsert : 0));
   if ((rc = run_hash(h, a, s))) return rc;
   if (insert) h->n_ins += static_cast<uint64_t>(n);
-  cudaError_t e;
-  {
-    PhaseScope ps(h, ACE_PHASE_SCORE, s);
-    e = ace::launch_score_gather(h->ids, h->K <= 16, n, n, h->K, h->L, alpha, h->counts, sum_out, h->st, s);
-  }
-  if (e != cudaSuccess) return cuda_fail(e, "score kernel launch");
-  {
-    PhaseScope ps(h, ACE_PHASE_FLAGS, s);
-    e = ace::launch_flags(sum_out, n, h->div, h->st, scores, flags, s);
-  }
-  if (e != cudaSuccess) return cuda_fail(e, "flags kernel launch");
-  return ACE_OK;
+  return score_tail(h, n, alpha, scores, sum_out, flags, s);
 }
 
 using u128 = unsigned __int128;
@@ -586,9 +601,13 @@ int ace_insert_score_host(ace_handle h, const void* X_host, int64_t n, int dtype
                           uint32_t* sums_host, uint8_t* flags_host, void* stream) {
   int rc = check_x(h, X_host, n, dtype);
   if (rc) return rc;
+  if (!std::isfinite(alpha)) return fail(ACE_ERR_ARG, "alpha must be finite");
+  if (h->n_ins + static_cast<uint64_t>(n) > 0xFFFFFFFFull)
+    return fail(ACE_ERR_OVERFLOW, "inserting %lld points would allow a count above 2^32-1", static_cast<long long>(n));
   if (n == 0) return ACE_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const size_t xbytes = static_cast<size_t>(n) * h->d * (dtype == ACE_F32 ? 4 : 2);
+  const size_t row = static_cast<size_t>(h->d) * (dtype == ACE_F32 ? 4 : 2);
+  const size_t xbytes = static_cast<size_t>(n) * row;
   if ((rc = grow(&h->xstage, &h->xstage_cap, xbytes, s, "X staging"))) return rc;
   if (static_cast<size_t>(n) > h->stage_cap) {
     ACE_CUDA(cudaStreamSynchronize(s));
@@ -609,10 +628,50 @@ int ace_insert_score_host(ace_handle h, const void* X_host, int64_t n, int dtype
   void* p = h->sums;
   if ((rc = grow(&p, &h->sums_cap, static_cast<size_t>(n) * sizeof(uint32_t), s, "sums scratch"))) return rc;
   h->sums = static_cast<uint32_t*>(p);
-  ACE_CUDA(cudaMemcpyAsync(h->xstage, X_host, xbytes, cudaMemcpyHostToDevice, s));
-  rc = score_common(h, h->xstage, n, dtype, alpha, scores_host ? h->scstage : nullptr, h->sums,
-                    flags_host ? h->flstage : nullptr, s, true);
-  if (rc) return rc;
+  if ((rc = grow(&h->ids, &h->ids_cap, static_cast<size_t>(n) * h->L * id_bytes(h), s, "ids scratch"))) return rc;
+  if (!h->cstream) ACE_CUDA(cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking));
+  for (auto& ev : h->cev)
+    if (!ev) ACE_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+
+  // X goes up in chunks on the copy stream; each chunk is hashed on `s` as soon as it has
+  // landed, so the copy of chunk c + 1 overlaps the hashing of chunk c.  Hashing is per point,
+  // so the ids of the whole batch are the same as from one launch; the count increments
+  // (tensor-core path), the query phase and the flags then run once over the batch.
+  constexpr long long kMinChunk = 32768;
+  const int kMaxChunks = static_cast<int>(sizeof(h->cev) / sizeof(h->cev[0])) - 1;
+  long long chunk = std::max<long long>(kMinChunk, (static_cast<long long>(n) + 7) / 8);
+  chunk = (chunk + 127) / 128 * 128;
+  const int nch = static_cast<int>(std::min<long long>((n + chunk - 1) / chunk, kMaxChunks));
+  chunk = (n + nch - 1) / nch;
+  chunk = (chunk + 127) / 128 * 128;
+  ACE_CUDA(cudaEventRecord(h->cev[kMaxChunks], s));  // earlier work on s is done with the staging
+  ACE_CUDA(cudaStreamWaitEvent(h->cstream, h->cev[kMaxChunks], 0));
+  for (int c = 0; c < nch; ++c) {
+    const long long c0 = c * chunk, nc = std::min<long long>(chunk, n - c0);
+    if (nc <= 0) break;
+    ACE_CUDA(cudaMemcpyAsync(static_cast<char*>(h->xstage) + c0 * row, static_cast<const char*>(X_host) + c0 * row,
+                             static_cast<size_t>(nc) * row, cudaMemcpyHostToDevice, h->cstream));
+    ACE_CUDA(cudaEventRecord(h->cev[c], h->cstream));
+  }
+  const bool simt = h->precision == ACE_PROJ_FP32 || !h->tc_ok;
+  for (int c = 0; c < nch; ++c) {
+    const long long c0 = c * chunk, nc = std::min<long long>(chunk, n - c0);
+    if (nc <= 0) break;
+    ACE_CUDA(cudaStreamWaitEvent(s, h->cev[c], 0));
+    ace::HashArgs a = hash_args(h, static_cast<const char*>(h->xstage) + c0 * row, nc, dtype,
+                                ace::kStoreIds | (simt ? ace::kInsert : 0));
+    a.ids = static_cast<char*>(h->ids) + static_cast<size_t>(c0) * id_bytes(h);
+    a.ld = n;
+    if ((rc = run_hash(h, a, s, false))) return rc;
+  }
+  if (!simt) {
+    PhaseScope ps(h, ACE_PHASE_INSERT, s);
+    cudaError_t e = ace::launch_insert_from_ids(h->ids, h->K <= 16, n, n, h->K, h->L, h->counts, h->num_sms, s);
+    if (e != cudaSuccess) return cuda_fail(e, "insert kernel launch");
+  }
+  h->n_ins += static_cast<uint64_t>(n);
+  if ((rc = score_tail(h, n, alpha, scores_host ? h->scstage : nullptr, h->sums, flags_host ? h->flstage : nullptr, s)))
+    return rc;
   if (scores_host) ACE_CUDA(cudaMemcpyAsync(scores_host, h->scstage, n * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (sums_host) ACE_CUDA(cudaMemcpyAsync(sums_host, h->sums, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   if (flags_host) ACE_CUDA(cudaMemcpyAsync(flags_host, h->flstage, n, cudaMemcpyDeviceToHost, s));

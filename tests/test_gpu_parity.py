@@ -245,6 +245,26 @@ def test_host_entry_point_matches_device_path():
     _compare_stats(a, ref)
 
 
+@pytest.mark.parametrize("precision", PRECS)
+def test_host_entry_point_chunked(precision):
+    """A batch large enough for the host entry point to copy and hash it in eight chunks
+    (ragged last chunk), twice in a row: every output equals the oracle's."""
+    w = workloads.kdd(seed=9, n=262147)
+    a, ref = _pair(w["d"], w["K"], w["L"], seed=4, precision=precision)
+    n = w["X"].shape[0]
+    for rep in range(2):
+        X = w["X"] if rep == 0 else np.ascontiguousarray(w["X"][::-1])
+        sc = np.empty(n, dtype=np.float64)
+        su = np.empty(n, dtype=np.uint32)
+        fl = np.empty(n, dtype=np.uint8)
+        a.insert_score_host(X, 1.0, sc, su, fl)
+        rs, ru, rf = ref.insert_score(X, 1.0)
+        assert np.array_equal(su, ru) and np.array_equal(sc, rs) and np.array_equal(fl, rf)
+    _engine_used(a, precision)
+    _compare_stats(a, ref)
+    assert np.array_equal(a.counts(), ref.counts)
+
+
 def test_kdd_full_size_sampled():
     """KDD-shaped recipe at its full size (n=500,000), in the bench's launch configuration:
     ids of a sample of points against the oracle, plus invariants that hold at any size."""
