@@ -146,6 +146,26 @@ int ace_insert_score_host(ace_handle h, const void* X_host, int64_t n, int dtype
                           void* stream);
 
 /*
+ * ace_insert_score_host_async — ace_insert_score_host without the wait: enqueues the copy
+ * of X_host (in chunks, each hashed as soon as it has arrived), the insert, the query phase
+ * and the copies of the outputs back to the host buffers on `stream`, and returns.  Batches
+ * are processed in call order with the same results as synchronous calls.  Until
+ * ace_host_wait returns, X_host must not change and the outputs are not valid.  At most two
+ * batches are in flight per detector (a third call first waits for the oldest); the copy of
+ * one batch overlaps the computation of the previous one.  A call on a different stream
+ * first waits for the batches in flight.  Device-path calls (ace_insert, ace_score, ...) on
+ * another stream must not overlap batches in flight.  Outputs may be NULL.  Error codes as
+ * ace_insert_score_host; an error reported here leaves earlier batches enqueued.
+ */
+int ace_insert_score_host_async(ace_handle h, const void* X_host, int64_t n, int dtype, double alpha,
+                                double* scores_host, uint32_t* sums_host, uint8_t* flags_host,
+                                void* stream);
+
+/* Blocks until every batch enqueued by ace_insert_score_host_async has completed; returns
+ * ACE_ERR_CUDA if one of them failed on the device. */
+int ace_host_wait(ace_handle h);
+
+/*
  * ace_hash — Eq. 1 + Eq. 2 only: ids_dev[i*L + j] = H_j(x_i) (uint32, n x L).  No state
  * changes except the recheck counter.
  */

@@ -22,7 +22,8 @@ PRECISIONS = {"auto": ACE_PROJ_AUTO, "fp32": ACE_PROJ_FP32, "bf16": ACE_PROJ_BF1
 # Every symbol include/ace.h declares (checked by the tests).
 EXPORTS = [
     "ace_create", "ace_create_with_projection", "ace_destroy", "ace_reset", "ace_set_precision",
-    "ace_insert", "ace_score", "ace_insert_score", "ace_insert_score_host", "ace_hash", "ace_stats",
+    "ace_insert", "ace_score", "ace_insert_score", "ace_insert_score_host",
+    "ace_insert_score_host_async", "ace_host_wait", "ace_hash", "ace_stats",
     "ace_get_counts", "ace_get_projection", "ace_get_shape", "ace_last_error", "ace_version",
     "ace_profile_enable", "ace_profile_read", "ace_insert_score_noalloc",
 ]
@@ -77,6 +78,8 @@ def load_library(path: str = LIB_PATH):
             "ace_score": ([H, P, i64, i32, f64, P, P, P, P], i32),
             "ace_insert_score": ([H, P, i64, i32, f64, P, P, P, P], i32),
             "ace_insert_score_host": ([H, P, i64, i32, f64, P, P, P, P], i32),
+            "ace_insert_score_host_async": ([H, P, i64, i32, f64, P, P, P, P], i32),
+            "ace_host_wait": ([H], i32),
             "ace_insert_score_noalloc": ([H, P, i64, i32, f64, P, P, P, P], i32),
             "ace_hash": ([H, P, i64, i32, P, P], i32),
             "ace_stats": ([H, P, ctypes.POINTER(ace_stats_t)], i32),
@@ -225,6 +228,27 @@ class Detector:
         _check(load_library().ace_insert_score_host(self._h, ctypes.c_void_p(X.ctypes.data), n, dt, float(alpha),
                                                     p(scores), p(sums), p(flags), _stream_ptr(stream)))
         return scores, sums, flags
+
+    def insert_score_host_async(self, X: np.ndarray, alpha: float = 1.0, scores=None, sums=None, flags=None,
+                                stream=None):
+        """Enqueues one host-buffer batch and returns; X must stay unchanged and the outputs
+        are valid only after host_wait()."""
+        n = X.shape[0]
+        dt = ACE_F32 if X.dtype == np.float32 else ACE_BF16
+        if X.dtype not in (np.float32, np.uint16):
+            raise TypeError("X must be float32 or uint16 bfloat16 bits")
+
+        def p(a):
+            return ctypes.c_void_p(a.ctypes.data) if a is not None else ctypes.c_void_p(0)
+
+        _check(load_library().ace_insert_score_host_async(self._h, ctypes.c_void_p(X.ctypes.data), n, dt,
+                                                          float(alpha), p(scores), p(sums), p(flags),
+                                                          _stream_ptr(stream)))
+        return scores, sums, flags
+
+    def host_wait(self):
+        """Waits for every batch enqueued by insert_score_host_async."""
+        _check(load_library().ace_host_wait(self._h))
 
     def hash(self, X, stream=None):
         """n x L bucket ids (int32 tensor holding uint32 values)."""

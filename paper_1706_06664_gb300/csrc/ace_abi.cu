@@ -51,15 +51,22 @@ struct ace_detector {
   void* ids = nullptr;
   size_t ids_cap = 0;  // bytes
   uint32_t* sums = nullptr;
-  size_t sums_cap = 0;  // elements
-  void* xstage = nullptr;
-  size_t xstage_cap = 0;  // bytes
+  size_t sums_cap = 0;  // bytes
+  // host-buffer entry: two X staging slots, so the copy of one batch overlaps the work of the
+  // previous one; each with its per-chunk copy events and a "batch done" event on the stream
+  struct HostSlot {
+    void* x = nullptr;
+    size_t cap = 0;  // bytes
+    cudaEvent_t done = nullptr;
+    cudaEvent_t chunk[16] = {};
+    bool busy = false;
+  } hs[2];
+  int hs_next = 0;
+  cudaStream_t hs_stream = nullptr;  // stream of the batches in flight
   double* scstage = nullptr;
   uint8_t* flstage = nullptr;
   size_t stage_cap = 0;  // elements
-  // host-buffer entry: copy stream and per-chunk events (created on first use)
-  cudaStream_t cstream = nullptr;
-  cudaEvent_t cev[17] = {};
+  cudaStream_t cstream = nullptr;  // copy stream of the host-buffer entry (created on first use)
   uint64_t n_ins = 0;
   ace::DivConst div{};    // constants of the score division by L
   std::vector<float> Wh;  // host copy of W
@@ -136,10 +143,13 @@ void free_all(ace_detector* h) {
   cudaFree(h->st);
   cudaFree(h->ids);
   cudaFree(h->sums);
-  for (auto& e : h->cev)
-    if (e) cudaEventDestroy(e);
+  for (auto& sl : h->hs) {
+    for (auto& e : sl.chunk)
+      if (e) cudaEventDestroy(e);
+    if (sl.done) cudaEventDestroy(sl.done);
+    cudaFree(sl.x);
+  }
   if (h->cstream) cudaStreamDestroy(h->cstream);
-  cudaFree(h->xstage);
   cudaFree(h->scstage);
   cudaFree(h->flstage);
 }
@@ -597,8 +607,20 @@ int ace_insert_score(ace_handle h, const void* X_dev, int64_t n, int dtype, doub
                       true);
 }
 
-int ace_insert_score_host(ace_handle h, const void* X_host, int64_t n, int dtype, double alpha, double* scores_host,
-                          uint32_t* sums_host, uint8_t* flags_host, void* stream) {
+int ace_host_wait(ace_handle h) {
+  if (!h) return fail(ACE_ERR_ARG, "handle is NULL");
+  int rc = ACE_OK;
+  for (auto& sl : h->hs) {
+    if (!sl.busy) continue;
+    cudaError_t e = cudaEventSynchronize(sl.done);
+    sl.busy = false;
+    if (e != cudaSuccess && rc == ACE_OK) rc = cuda_fail(e, "host batch");
+  }
+  return rc;
+}
+
+int ace_insert_score_host_async(ace_handle h, const void* X_host, int64_t n, int dtype, double alpha,
+                                double* scores_host, uint32_t* sums_host, uint8_t* flags_host, void* stream) {
   int rc = check_x(h, X_host, n, dtype);
   if (rc) return rc;
   if (!std::isfinite(alpha)) return fail(ACE_ERR_ARG, "alpha must be finite");
@@ -606,10 +628,36 @@ int ace_insert_score_host(ace_handle h, const void* X_host, int64_t n, int dtype
     return fail(ACE_ERR_OVERFLOW, "inserting %lld points would allow a count above 2^32-1", static_cast<long long>(n));
   if (n == 0) return ACE_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // batches in flight share the ids scratch and rely on the order of one stream
+  if (s != h->hs_stream) {
+    if ((rc = ace_host_wait(h))) return rc;
+    h->hs_stream = s;
+  }
+  ace_detector::HostSlot& sl = h->hs[h->hs_next];
+  if (sl.busy) {  // at most two batches in flight
+    cudaError_t e = cudaEventSynchronize(sl.done);
+    sl.busy = false;
+    if (e != cudaSuccess) return cuda_fail(e, "host batch");
+  }
   const size_t row = static_cast<size_t>(h->d) * (dtype == ACE_F32 ? 4 : 2);
   const size_t xbytes = static_cast<size_t>(n) * row;
-  if ((rc = grow(&h->xstage, &h->xstage_cap, xbytes, s, "X staging"))) return rc;
+  const size_t need_ids = static_cast<size_t>(n) * h->L * id_bytes(h);
+  // The slot's own staging buffer is idle here; sums and ids are used on `s` only (grow
+  // synchronises it); the output staging is replaced below only once nothing is in flight.
+  if (xbytes > sl.cap) {
+    cudaFree(sl.x);
+    sl.x = nullptr;
+    sl.cap = 0;
+    const size_t cap = xbytes + xbytes / 2;
+    cudaError_t e = cudaMalloc(&sl.x, cap);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ACE_ERR_OOM, "X staging: %s", cudaGetErrorString(e));
+    }
+    sl.cap = cap;
+  }
   if (static_cast<size_t>(n) > h->stage_cap) {
+    if ((rc = ace_host_wait(h))) return rc;
     ACE_CUDA(cudaStreamSynchronize(s));
     cudaFree(h->scstage);
     cudaFree(h->flstage);
@@ -628,37 +676,38 @@ int ace_insert_score_host(ace_handle h, const void* X_host, int64_t n, int dtype
   void* p = h->sums;
   if ((rc = grow(&p, &h->sums_cap, static_cast<size_t>(n) * sizeof(uint32_t), s, "sums scratch"))) return rc;
   h->sums = static_cast<uint32_t*>(p);
-  if ((rc = grow(&h->ids, &h->ids_cap, static_cast<size_t>(n) * h->L * id_bytes(h), s, "ids scratch"))) return rc;
+  if ((rc = grow(&h->ids, &h->ids_cap, need_ids, s, "ids scratch"))) return rc;
   if (!h->cstream) ACE_CUDA(cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking));
-  for (auto& ev : h->cev)
+  if (!sl.done) ACE_CUDA(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
+  for (auto& ev : sl.chunk)
     if (!ev) ACE_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
 
-  // X goes up in chunks on the copy stream; each chunk is hashed on `s` as soon as it has
-  // landed, so the copy of chunk c + 1 overlaps the hashing of chunk c.  Hashing is per point,
-  // so the ids of the whole batch are the same as from one launch; the count increments
-  // (tensor-core path), the query phase and the flags then run once over the batch.
+  // X goes up in chunks on the copy stream (after the slot's previous batch is done with its
+  // staging buffer); each chunk is hashed on `s` as soon as it has landed, so the copy of
+  // chunk c + 1 — and of the next batch — overlaps the hashing of chunk c.  Hashing is per
+  // point, so the ids of the whole batch are the same as from one launch; the count
+  // increments (tensor-core path), the query phase and the flags then run once over the batch.
   constexpr long long kMinChunk = 32768;
-  const int kMaxChunks = static_cast<int>(sizeof(h->cev) / sizeof(h->cev[0])) - 1;
+  const int kMaxChunks = static_cast<int>(sizeof(sl.chunk) / sizeof(sl.chunk[0]));
   long long chunk = std::max<long long>(kMinChunk, (static_cast<long long>(n) + 7) / 8);
   chunk = (chunk + 127) / 128 * 128;
   const int nch = static_cast<int>(std::min<long long>((n + chunk - 1) / chunk, kMaxChunks));
   chunk = (n + nch - 1) / nch;
   chunk = (chunk + 127) / 128 * 128;
-  ACE_CUDA(cudaEventRecord(h->cev[kMaxChunks], s));  // earlier work on s is done with the staging
-  ACE_CUDA(cudaStreamWaitEvent(h->cstream, h->cev[kMaxChunks], 0));
+  ACE_CUDA(cudaStreamWaitEvent(h->cstream, sl.done, 0));
   for (int c = 0; c < nch; ++c) {
     const long long c0 = c * chunk, nc = std::min<long long>(chunk, n - c0);
     if (nc <= 0) break;
-    ACE_CUDA(cudaMemcpyAsync(static_cast<char*>(h->xstage) + c0 * row, static_cast<const char*>(X_host) + c0 * row,
+    ACE_CUDA(cudaMemcpyAsync(static_cast<char*>(sl.x) + c0 * row, static_cast<const char*>(X_host) + c0 * row,
                              static_cast<size_t>(nc) * row, cudaMemcpyHostToDevice, h->cstream));
-    ACE_CUDA(cudaEventRecord(h->cev[c], h->cstream));
+    ACE_CUDA(cudaEventRecord(sl.chunk[c], h->cstream));
   }
   const bool simt = h->precision == ACE_PROJ_FP32 || !h->tc_ok;
   for (int c = 0; c < nch; ++c) {
     const long long c0 = c * chunk, nc = std::min<long long>(chunk, n - c0);
     if (nc <= 0) break;
-    ACE_CUDA(cudaStreamWaitEvent(s, h->cev[c], 0));
-    ace::HashArgs a = hash_args(h, static_cast<const char*>(h->xstage) + c0 * row, nc, dtype,
+    ACE_CUDA(cudaStreamWaitEvent(s, sl.chunk[c], 0));
+    ace::HashArgs a = hash_args(h, static_cast<const char*>(sl.x) + c0 * row, nc, dtype,
                                 ace::kStoreIds | (simt ? ace::kInsert : 0));
     a.ids = static_cast<char*>(h->ids) + static_cast<size_t>(c0) * id_bytes(h);
     a.ld = n;
@@ -675,8 +724,17 @@ int ace_insert_score_host(ace_handle h, const void* X_host, int64_t n, int dtype
   if (scores_host) ACE_CUDA(cudaMemcpyAsync(scores_host, h->scstage, n * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (sums_host) ACE_CUDA(cudaMemcpyAsync(sums_host, h->sums, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   if (flags_host) ACE_CUDA(cudaMemcpyAsync(flags_host, h->flstage, n, cudaMemcpyDeviceToHost, s));
-  ACE_CUDA(cudaStreamSynchronize(s));
+  ACE_CUDA(cudaEventRecord(sl.done, s));
+  sl.busy = true;
+  h->hs_next ^= 1;
   return ACE_OK;
+}
+
+int ace_insert_score_host(ace_handle h, const void* X_host, int64_t n, int dtype, double alpha, double* scores_host,
+                          uint32_t* sums_host, uint8_t* flags_host, void* stream) {
+  int rc = ace_insert_score_host_async(h, X_host, n, dtype, alpha, scores_host, sums_host, flags_host, stream);
+  if (rc) return rc;
+  return ace_host_wait(h);
 }
 
 int ace_hash(ace_handle h, const void* X_dev, int64_t n, int dtype, uint32_t* ids_dev, void* stream) {

@@ -265,6 +265,30 @@ def test_host_entry_point_chunked(precision):
     assert np.array_equal(a.counts(), ref.counts)
 
 
+@pytest.mark.parametrize("precision", PRECS)
+def test_host_async_batches_in_order(precision):
+    """Three batches enqueued back to back (two staging slots alternate, buffers grow between
+    batches of different sizes), then one wait: each batch's outputs equal the oracle's run
+    of the same batches in the same order."""
+    w = workloads.kdd(seed=10, n=200000)
+    a, ref = _pair(w["d"], w["K"], w["L"], seed=6, precision=precision)
+    parts = [w["X"][:70000], w["X"][70000:190001], w["X"][190001:]]
+    outs = []
+    for X in parts:
+        n = X.shape[0]
+        o = (torch.empty(n, dtype=torch.float64).pin_memory().numpy(),
+             torch.empty(n, dtype=torch.int32).pin_memory().numpy().view(np.uint32),
+             torch.empty(n, dtype=torch.uint8).pin_memory().numpy())
+        a.insert_score_host_async(X, 1.0, *o)
+        outs.append(o)
+    a.host_wait()
+    for X, (sc, su, fl) in zip(parts, outs):
+        rs, ru, rf = ref.insert_score(X, 1.0)
+        assert np.array_equal(su, ru) and np.array_equal(sc, rs) and np.array_equal(fl, rf)
+    _engine_used(a, precision)
+    _compare_stats(a, ref)
+
+
 def test_kdd_full_size_sampled():
     """KDD-shaped recipe at its full size (n=500,000), in the bench's launch configuration:
     ids of a sample of points against the oracle, plus invariants that hold at any size."""
