@@ -276,9 +276,14 @@ int plan_tc(ace_detector* h) {
 
   // guard constants (relative to ||x||; see hash_tc.cu)
   const double u32 = std::ldexp(1.0, -24), u64 = std::ldexp(1.0, -53);
-  const int S = 3 * d_pad / 16;  // MMA instructions accumulating into one result
+  // MMA instructions accumulating into one result: the two small products first (each
+  // addend at most 2^-8 (1 + 2^-8)^2 |x_i w'_i|, so each instruction's addends sum to at most
+  // about 2^-7 sum|x_i w'_i|; 2^-6 is used), then x_hi . w'_hi (addends at most about
+  // sum|x_i w'_i|)
+  const int S_small = 2 * d_pad / 16, S_big = d_pad / 16;
   const double t_split = 3.0 * std::ldexp(1.0, -16) * (1.0 + std::ldexp(1.0, -6));
-  const double t_acc = 5.25 * 1.5 * (S + 1) * std::ldexp(1.0, -23) * (1.0 + std::ldexp(1.0, -6));
+  const double t_acc = 5.25 * 1.5 * ((S_big + 1) + S_small * std::ldexp(1.0, -6)) * std::ldexp(1.0, -23) *
+                       (1.0 + std::ldexp(1.0, -6));
   const double t_norm = std::ldexp(1.0, -23);
   const double g64 = d * u64 / (1.0 - d * u64);
   t.tau = std::nextafter(static_cast<float>((t_split + t_acc + t_norm + g64) * 1.01), FLT_MAX);
