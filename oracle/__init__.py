@@ -62,6 +62,10 @@ def _load():
         lib.oracle_project.argtypes = [P, i32, i64, i32, P, i32, P]
         lib.oracle_insert.argtypes = [P, i64, i32, i32, P]
         lib.oracle_insert.restype = i32
+        lib.oracle_delete.argtypes = [P, i64, i32, i32, P]
+        lib.oracle_delete.restype = i32
+        lib.oracle_mu_decremental.argtypes = [P, i64, i32, i32, P, i64, f64, P]
+        lib.oracle_mu_decremental.restype = f64
         lib.oracle_sum_squares.argtypes = [P, i32, i32, P]
         lib.oracle_mu_incremental.argtypes = [P, i64, i32, i32, P, i64, f64, P]
         lib.oracle_mu_incremental.restype = f64
@@ -139,6 +143,24 @@ def insert_ids(ids: np.ndarray, counts: np.ndarray, K: int) -> None:
         raise OverflowError("a count would pass 2^32-1")
 
 
+def delete_ids(ids: np.ndarray, counts: np.ndarray, K: int) -> None:
+    """§3.4.1 deletion: counts[j][ids[i, j]] -= 1; raises (counts unchanged) if a count
+    would go below zero."""
+    n, L = ids.shape
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    if _load().oracle_delete(_ptr(ids), n, K, L, _ptr(counts)) != 0:
+        raise ValueError("deleting points that were not inserted (a count would go below zero)")
+
+
+def mu_decremental(ids: np.ndarray, counts: np.ndarray, K: int, n_before: int, mu_before: float):
+    """Eq. 12 point by point (pre-decrement counts); updates counts; returns (mu, trace)."""
+    n, L = ids.shape
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    trace = np.empty(n, dtype=np.float64)
+    mu = _load().oracle_mu_decremental(_ptr(ids), n, K, L, _ptr(counts), n_before, mu_before, _ptr(trace))
+    return mu, trace
+
+
 def sum_squares(counts: np.ndarray, K: int, L: int) -> int:
     q = np.zeros(2, dtype=np.uint64)
     _load().oracle_sum_squares(_ptr(counts), K, L, _ptr(q))
@@ -184,6 +206,15 @@ class Detector:
         ids = self.hash(X)
         insert_ids(ids, self.counts, self.K)
         self.n_ins += ids.shape[0]
+        return ids
+
+    def delete(self, X):
+        """Removes the batch's points from the arrays (§3.4.1); all or nothing."""
+        ids = self.hash(X)
+        if ids.shape[0] > self.n_ins:
+            raise ValueError("deleting more points than were inserted")
+        delete_ids(ids, self.counts, self.K)
+        self.n_ins -= ids.shape[0]
         return ids
 
     def _score_ids(self, ids, alpha):

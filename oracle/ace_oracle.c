@@ -18,6 +18,8 @@
  *                                (K bits concatenated into the meta-hash H_j), §3.2.
  *   oracle_insert                Algorithm 1 pre-processing phase; §3.2 "Counting Phase".
  *   oracle_mu_incremental        Eq. 11 (mean update on insertion, §3.4.1), point by point.
+ *   oracle_delete                §3.4.1 deletion: A_j[H_j(x)] -= 1 for every point of a batch.
+ *   oracle_mu_decremental        Eq. 12 (mean update on deletion, §3.4.1), point by point.
  *   oracle_gather / oracle_score Algorithm 1 query phase; §3.2 "Real-time (query) Phase":
  *                                S^(q) = (1/L) sum_j A_j[H_j(q)].
  *   oracle_stats_*               §5.3 threshold rule: report a point whose score is below
@@ -31,7 +33,10 @@
  *     (double)x_i * (double)w_i of the stored inputs.
  *   - counts are uint32 (the paper's 16-bit shorts are a memory choice, §3.4); a count
  *     that would pass 2^32-1 is an overflow error, never a wrap.
- *   - Eq. 11 is applied with the counts read BEFORE the point's own increment.
+ *   - Eq. 11 is applied with the counts read BEFORE the point's own increment, and Eq. 12
+ *     with the counts read BEFORE the point's own decrement.
+ *   - deleting a batch that would take a count below zero (a point that was never inserted)
+ *     is an error that leaves the arrays unchanged.
  *   - sigma is the population standard deviation of every score returned for the
  *     detector so far, the current batch included; the flag is score < mu - alpha*sigma.
  */
@@ -154,6 +159,51 @@ int oracle_insert(const uint32_t* ids, int64_t n, int K, int L, uint32_t* counts
   memcpy(counts, scratch, sizeof(uint32_t) * B * (size_t)L);
   free(scratch);
   return 0;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Deletion (§3.4.1): A_j[H_j(x)] -= 1 for every point.  Returns 0, or 1 if a count     */
+/* would go below zero (the arrays are then left as they were).                        */
+/* ---------------------------------------------------------------------------------- */
+int oracle_delete(const uint32_t* ids, int64_t n, int K, int L, uint32_t* counts) {
+  const size_t B = (size_t)1 << K;
+  uint32_t* scratch = (uint32_t*)malloc(sizeof(uint32_t) * B * (size_t)L);
+  memcpy(scratch, counts, sizeof(uint32_t) * B * (size_t)L);
+  for (int64_t i = 0; i < n; ++i)
+    for (int j = 0; j < L; ++j) {
+      uint32_t* a = &scratch[(size_t)j * B + ids[(size_t)i * L + j]];
+      if (*a == 0u) { free(scratch); return 1; }
+      *a -= 1u;
+    }
+  memcpy(counts, scratch, sizeof(uint32_t) * B * (size_t)L);
+  free(scratch);
+  return 0;
+}
+
+/*
+ * Eq. 12, applied literally point by point: before x's decrements,
+ *   mu' = ( n*mu - sum_j (2*A_j[H_j(x)] - 1)/L ) / (n-1),
+ * with A_j read before x's own decrement.  counts is updated as it goes (the caller makes
+ * sure every count stays >= 0).  mu_trace[i] receives mu after point i (0 once the last
+ * point is gone).  Returns the final mu.
+ */
+double oracle_mu_decremental(const uint32_t* ids, int64_t n, int K, int L, uint32_t* counts,
+                             int64_t n_before, double mu_before, double* mu_trace) {
+  const size_t B = (size_t)1 << K;
+  double mu = mu_before;
+  int64_t m = n_before;
+  for (int64_t i = 0; i < n; ++i) {
+    double decre = 0.0;
+    for (int j = 0; j < L; ++j) {
+      uint32_t* a = &counts[(size_t)j * B + ids[(size_t)i * L + j]];
+      decre += (2.0 * (double)(*a) - 1.0) / (double)L;
+      *a -= 1u;
+    }
+    mu = m > 1 ? ((double)m * mu - decre) / (double)(m - 1) : 0.0;
+    m -= 1;
+    if (mu_trace) mu_trace[i] = mu;
+  }
+  return mu;
 }
 
 /* Q = sum_j sum_b A_j[b]^2 as two 64-bit halves (lo, hi). */

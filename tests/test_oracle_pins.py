@@ -204,6 +204,65 @@ def test_counts_match_bincount_and_sum_to_n():
         assert int(det.counts[j].sum()) == 3777
 
 
+def test_hand_example_delete_eq12():
+    """Deletion (§3.4.1) on the worked example: counts, Q, mu_ins, and Eq. 12 point by point,
+    all against the values worked out by hand."""
+    g, W, X = _hand()
+    gd = _load("hand_example_delete.json")
+    det = oracle.Detector(g["d"], g["K"], g["L"], W=W)
+    det.insert(X)
+    counts = det.counts.copy()
+    ids = oracle.hash_ids(X[gd["delete_order"]], W, g["K"], g["L"])
+    mu, trace = oracle.mu_decremental(ids, counts, g["K"], n_before=4, mu_before=g["mu"])
+    assert trace.tolist() == gd["mu_decremental_trace"]
+    for step, i in enumerate(gd["delete_order"]):
+        det.delete(X[i:i + 1])
+        assert det.counts.tolist() == gd["counts_after"][step]
+        st = det.stats()
+        assert st["Q"] == gd["Q_after"][step]
+        assert st["mu_ins"] == gd["mu_ins_after"][step]
+        assert st["n_ins"] == 3 - step
+    assert counts.tolist() == gd["counts_after"][-1]
+
+
+def test_delete_rejects_points_not_inserted():
+    g, W, X = _hand()
+    gd = _load("hand_example_delete.json")
+    det = oracle.Detector(g["d"], g["K"], g["L"], W=W)
+    det.insert(X)
+    before = det.counts.copy()
+    x = np.array([gd["not_inserted_point"]], dtype=np.float32)
+    assert oracle.hash_ids(x, W, g["K"], g["L"]).tolist() == [gd["not_inserted_ids"]]
+    with pytest.raises(ValueError):
+        det.delete(np.concatenate([X[:1], x]))  # a valid point first: nothing may change
+    assert np.array_equal(det.counts, before) and det.n_ins == 4
+
+
+def test_delete_inverts_insert_and_eq12_matches_closed_form():
+    """Inserting A then B and deleting B leaves exactly the arrays of A alone; Eq. 12 point
+    by point agrees with Q/(nL) at every stage of the deletion."""
+    w = workloads.small(seed=11, n=3000)
+    A, Bset = w["X"][:1800], w["X"][1800:]
+    det = oracle.Detector(w["d"], w["K"], w["L"], seed=3)
+    only_a = oracle.Detector(w["d"], w["K"], w["L"], seed=3)
+    det.insert(A)
+    only_a.insert(A)
+    det.insert(Bset)
+    mu_full = det.stats()["mu_ins"]
+    counts = det.counts.copy()
+    ids_b = det.hash(Bset)
+    mu_dec, trace = oracle.mu_decremental(ids_b, counts, w["K"], n_before=3000, mu_before=mu_full)
+    det.delete(Bset)
+    assert np.array_equal(det.counts, only_a.counts) and np.array_equal(counts, det.counts)
+    assert det.stats()["Q"] == only_a.stats()["Q"]
+    assert mu_dec == pytest.approx(only_a.stats()["mu_ins"], rel=1e-12)
+    # a midpoint of the deletion: the first 600 of B removed
+    mid = oracle.Detector(w["d"], w["K"], w["L"], seed=3)
+    mid.insert(A)
+    mid.insert(Bset[600:])
+    assert trace[599] == pytest.approx(mid.stats()["mu_ins"], rel=1e-12)
+
+
 def test_mu_identity_three_ways():
     """Eq. 11 point by point == Q/(nL) == mean score of the inserted set at final counts."""
     w = workloads.small(seed=4, n=2000)
