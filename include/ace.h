@@ -146,6 +146,17 @@ int ace_insert_score_host(ace_handle h, const void* X_host, int64_t n, int dtype
                           void* stream);
 
 /*
+ * ace_delete — §3.4.1 deletion: removes the points of X_dev (n x d, device, as ace_insert)
+ * from the count arrays, A_j[H_j(x)] -= 1 for every point, so that mu_ins follows Eq. 12
+ * (ace_stats reports it as Q / (n_ins L), Q = sum of count^2, which Eq. 12 keeps in closed
+ * form).  All or nothing: if some bucket would go below zero (a point of the batch was never
+ * inserted), or n exceeds the points inserted, nothing changes and ACE_ERR_ARG is returned.
+ * The statistics of returned scores (N, S1, S2, mu, sigma) are not changed.  Synchronises
+ * `stream` once (to read the check).
+ */
+int ace_delete(ace_handle h, const void* X_dev, int64_t n, int dtype, void* stream);
+
+/*
  * ace_insert_score_host_async — ace_insert_score_host without the wait: enqueues the copy
  * of X_host (in chunks, each hashed as soon as it has arrived), the insert, the query phase
  * and the copies of the outputs back to the host buffers on `stream`, and returns.  Batches

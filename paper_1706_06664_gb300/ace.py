@@ -23,7 +23,7 @@ PRECISIONS = {"auto": ACE_PROJ_AUTO, "fp32": ACE_PROJ_FP32, "bf16": ACE_PROJ_BF1
 EXPORTS = [
     "ace_create", "ace_create_with_projection", "ace_destroy", "ace_reset", "ace_set_precision",
     "ace_insert", "ace_score", "ace_insert_score", "ace_insert_score_host",
-    "ace_insert_score_host_async", "ace_host_wait", "ace_hash", "ace_stats",
+    "ace_insert_score_host_async", "ace_host_wait", "ace_delete", "ace_hash", "ace_stats",
     "ace_get_counts", "ace_get_projection", "ace_get_shape", "ace_last_error", "ace_version",
     "ace_profile_enable", "ace_profile_read", "ace_insert_score_noalloc",
 ]
@@ -80,6 +80,7 @@ def load_library(path: str = LIB_PATH):
             "ace_insert_score_host": ([H, P, i64, i32, f64, P, P, P, P], i32),
             "ace_insert_score_host_async": ([H, P, i64, i32, f64, P, P, P, P], i32),
             "ace_host_wait": ([H], i32),
+            "ace_delete": ([H, P, i64, i32, P], i32),
             "ace_insert_score_noalloc": ([H, P, i64, i32, f64, P, P, P, P], i32),
             "ace_hash": ([H, P, i64, i32, P, P], i32),
             "ace_stats": ([H, P, ctypes.POINTER(ace_stats_t)], i32),
@@ -180,6 +181,11 @@ class Detector:
     def insert(self, X, stream=None):
         self._xcheck(X)
         _check(load_library().ace_insert(self._h, _ptr(X), X.shape[0], _x_dtype(X), _stream_ptr(stream)))
+
+    def delete(self, X, stream=None):
+        """§3.4.1 deletion of the batch's points (all or nothing; synchronises the stream)."""
+        self._xcheck(X)
+        _check(load_library().ace_delete(self._h, _ptr(X), X.shape[0], _x_dtype(X), _stream_ptr(stream)))
 
     def _outs(self, n, scores, sums, flags, device):
         torch = _torch()

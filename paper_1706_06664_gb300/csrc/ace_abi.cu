@@ -79,6 +79,8 @@ struct ace_detector {
   size_t defer_bytes = 0;
   unsigned int* defer_counts = nullptr;  // one per CTA of the tensor-core kernel
   float* wpad = nullptr;                 // [KL][dp] W, columns contiguous, zero-padded (recheck)
+  uint32_t* hist = nullptr;              // [L][2^K] histogram of a batch being deleted
+  unsigned int* dflag = nullptr;         // deletion check flag
   // profiling hook
   bool prof = false;
   uint64_t launches[ACE_NPHASE] = {0, 0, 0, 0, 0, 0};
@@ -136,6 +138,8 @@ void free_all(ace_detector* h) {
   cudaFree(h->defer);
   cudaFree(h->defer_counts);
   cudaFree(h->wpad);
+  cudaFree(h->hist);
+  cudaFree(h->dflag);
   cudaFree(h->W);
   cudaFree(h->Wt);
   cudaFree(h->cB);
@@ -740,6 +744,53 @@ int ace_insert_score_host(ace_handle h, const void* X_host, int64_t n, int dtype
   int rc = ace_insert_score_host_async(h, X_host, n, dtype, alpha, scores_host, sums_host, flags_host, stream);
   if (rc) return rc;
   return ace_host_wait(h);
+}
+
+int ace_delete(ace_handle h, const void* X_dev, int64_t n, int dtype, void* stream) {
+  int rc = check_x(h, X_dev, n, dtype);
+  if (rc) return rc;
+  if (n == 0) return ACE_OK;
+  if (static_cast<uint64_t>(n) > h->n_ins)
+    return fail(ACE_ERR_ARG, "deleting %lld points from a detector holding %llu", static_cast<long long>(n),
+                static_cast<unsigned long long>(h->n_ins));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((rc = grow(&h->ids, &h->ids_cap, static_cast<size_t>(n) * h->L * id_bytes(h), s, "ids scratch"))) return rc;
+  const long long total = static_cast<long long>(count_elems(h));
+  if (!h->hist) {
+    cudaError_t e = cudaMalloc(&h->hist, static_cast<size_t>(total) * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&h->dflag, sizeof(unsigned int));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ACE_ERR_OOM, "deletion scratch: %s", cudaGetErrorString(e));
+    }
+  }
+  // the batch's ids (no count change), then its histogram into the scratch
+  ace::HashArgs a = hash_args(h, X_dev, n, dtype, ace::kStoreIds);
+  if ((rc = run_hash(h, a, s))) return rc;
+  ACE_CUDA(cudaMemsetAsync(h->hist, 0, static_cast<size_t>(total) * sizeof(uint32_t), s));
+  ACE_CUDA(cudaMemsetAsync(h->dflag, 0, sizeof(unsigned int), s));
+  cudaError_t e;
+  {
+    PhaseScope ps(h, ACE_PHASE_INSERT, s);
+    e = ace::launch_insert_from_ids(h->ids, h->K <= 16, n, n, h->K, h->L, h->hist, h->num_sms, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "deletion histogram launch");
+  {
+    PhaseScope ps(h, ACE_PHASE_OTHER, s);
+    e = ace::launch_delete_check(h->hist, h->counts, total, h->dflag, h->num_sms, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "deletion check launch");
+  unsigned int bad = 0;
+  ACE_CUDA(cudaMemcpyAsync(&bad, h->dflag, sizeof bad, cudaMemcpyDeviceToHost, s));
+  ACE_CUDA(cudaStreamSynchronize(s));
+  if (bad) return fail(ACE_ERR_ARG, "deleting points that were not inserted (a count would go below zero)");
+  {
+    PhaseScope ps(h, ACE_PHASE_OTHER, s);
+    e = ace::launch_delete_apply(h->hist, h->counts, total, h->num_sms, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "deletion launch");
+  h->n_ins -= static_cast<uint64_t>(n);
+  return ACE_OK;
 }
 
 int ace_hash(ace_handle h, const void* X_dev, int64_t n, int dtype, uint32_t* ids_dev, void* stream) {

@@ -59,6 +59,9 @@ cudaError_t launch_flags(const uint32_t* sums, long long n, const DivConst& div,
 cudaError_t launch_insert_from_ids(const void* ids, int ids16, long long ld, long long n, int K, int L,
                                    uint32_t* counts, int num_sms, cudaStream_t s);
 cudaError_t launch_sum_squares(const uint32_t* counts, long long total, DevStats* st, cudaStream_t s);
+cudaError_t launch_delete_check(const uint32_t* hist, const uint32_t* counts, long long total, unsigned int* flag,
+                                int num_sms, cudaStream_t s);
+cudaError_t launch_delete_apply(const uint32_t* hist, uint32_t* counts, long long total, int num_sms, cudaStream_t s);
 
 // Host-side generator of the projection matrix (SplitMix64 counter mode + Box-Muller).
 void generate_projection(int d, int K, int L, uint64_t seed, float* W);

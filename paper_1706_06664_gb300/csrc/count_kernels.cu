@@ -8,6 +8,8 @@
 //   flags         score = c/L (correctly rounded, integer arithmetic) and flag = score < t.
 //   sum_squares   Q = sum over all counters of A^2 (the closed form of Eq. 11 summed over
 //                 the inserts: mu_ins = Q / (n_ins L)).
+#include <algorithm>
+
 #include "ace_internal.h"
 
 namespace ace {
@@ -251,7 +253,39 @@ __global__ void __launch_bounds__(256) insert_direct_kernel(const IdT* __restric
   }
 }
 
+// Deletion (§3.4.1), checked before it is applied: a bucket whose count is below the batch's
+// histogram means a point of the batch was never inserted.
+__global__ void __launch_bounds__(256) delete_check_kernel(const uint32_t* __restrict__ hist,
+                                                           const uint32_t* __restrict__ counts, long long total,
+                                                           unsigned int* __restrict__ flag) {
+  bool bad = false;
+  for (long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
+       t += static_cast<long long>(gridDim.x) * blockDim.x)
+    bad |= hist[t] > counts[t];
+  if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
+__global__ void __launch_bounds__(256) delete_apply_kernel(const uint32_t* __restrict__ hist, uint32_t* __restrict__ counts,
+                                                           long long total) {
+  for (long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
+       t += static_cast<long long>(gridDim.x) * blockDim.x)
+    counts[t] -= hist[t];
+}
+
 }  // namespace
+
+cudaError_t launch_delete_check(const uint32_t* hist, const uint32_t* counts, long long total, unsigned int* flag,
+                                int num_sms, cudaStream_t s) {
+  const long long blocks = std::min<long long>((total + 255) / 256, static_cast<long long>(num_sms) * 8);
+  delete_check_kernel<<<static_cast<unsigned>(std::max<long long>(1, blocks)), 256, 0, s>>>(hist, counts, total, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_delete_apply(const uint32_t* hist, uint32_t* counts, long long total, int num_sms, cudaStream_t s) {
+  const long long blocks = std::min<long long>((total + 255) / 256, static_cast<long long>(num_sms) * 8);
+  delete_apply_kernel<<<static_cast<unsigned>(std::max<long long>(1, blocks)), 256, 0, s>>>(hist, counts, total);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_insert_from_ids(const void* ids, int ids16, long long ld, long long n, int K, int L,
                                    uint32_t* counts, int num_sms, cudaStream_t s) {

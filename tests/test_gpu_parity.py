@@ -324,3 +324,53 @@ def test_kdd_full_size_sampled():
     assert np.array_equal(ref_su, ace.u32(su))
     assert np.array_equal(sc.cpu().numpy(), ref_sc) and np.array_equal(fl.cpu().numpy(), ref_fl)
     assert st["mu"] == ref.stats()["mu"] and st["sigma"] == ref.stats()["sigma"]
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_delete_matches_oracle(precision):
+    """§3.4.1 deletion on the device: insert A and B, delete B, then score C — counts,
+    statistics and scores equal the oracle's, and the arrays equal those of A alone."""
+    w = workloads.kdd(seed=12, n=60000)
+    A, Bset, C = w["X"][:30000], w["X"][30000:52000], w["X"][52000:]
+    a, ref = _pair(w["d"], w["K"], w["L"], seed=7, precision=precision)
+    a.insert(_dev(A))
+    ref.insert(A)
+    a.insert(_dev(Bset))
+    ref.insert(Bset)
+    a.delete(_dev(Bset))
+    ref.delete(Bset)
+    assert np.array_equal(a.counts(), ref.counts)
+    only_a = oracle.Detector(w["d"], w["K"], w["L"], W=a.projection())
+    only_a.insert(A)
+    assert np.array_equal(a.counts(), only_a.counts)
+    sc, su, fl = a.score(_dev(C), 1.0)
+    rs, ru, rf = ref.score(C, 1.0)
+    torch.cuda.synchronize()
+    assert np.array_equal(ace.u32(su), ru) and np.array_equal(sc.cpu().numpy(), rs)
+    assert np.array_equal(fl.cpu().numpy(), rf)
+    _engine_used(a, precision)
+    _compare_stats(a, ref)
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_delete_hand_example_and_rejection(precision):
+    import json, os
+    gd_path = os.path.join(os.path.dirname(__file__), "golden")
+    g = json.load(open(os.path.join(gd_path, "hand_example.json")))
+    gd = json.load(open(os.path.join(gd_path, "hand_example_delete.json")))
+    W = np.array(g["W_columns"], dtype=np.float32).T.copy()
+    X = np.array(g["X"], dtype=np.float32)
+    det = _detector(3, 2, 2, W=W, precision=precision)
+    det.insert(_dev(X))
+    bad = np.array([X[0], gd["not_inserted_point"]], dtype=np.float32)
+    with pytest.raises(ace.AceError) as e:
+        det.delete(_dev(bad))
+    assert e.value.code == ace.ACE_ERR_ARG
+    assert det.counts().tolist() == g["counts"] and det.stats()["n_ins"] == 4
+    for step, i in enumerate(gd["delete_order"]):
+        det.delete(_dev(X[i:i + 1]))
+        st = det.stats()
+        assert det.counts().tolist() == gd["counts_after"][step]
+        assert st["Q"] == gd["Q_after"][step] and st["mu_ins"] == gd["mu_ins_after"][step]
+    with pytest.raises(ace.AceError):
+        det.delete(_dev(X))  # four points from a detector that holds two
