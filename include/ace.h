@@ -156,6 +156,35 @@ int ace_insert_score_host(ace_handle h, const void* X_host, int64_t n, int dtype
  */
 int ace_delete(ace_handle h, const void* X_dev, int64_t n, int dtype, void* stream);
 
+/* Operations of a host-buffer request (ace_server_submit). */
+enum { ACE_OP_INSERT = 0, ACE_OP_SCORE = 1, ACE_OP_INSERT_SCORE = 2 };
+
+/*
+ * Request server: continuous batching of host-buffer requests over several detectors (the
+ * paper states the method for one dataset; serving many detectors is this library's).
+ * ace_server_create takes n_dets detector handles (the server owns their use until it is
+ * destroyed: make no other call on them meanwhile) and a device-memory budget for the staged
+ * bytes of requests in flight (a request larger than the budget still runs, alone).
+ * ace_server_submit queues one request — op ACE_OP_INSERT (Algorithm 1 counting phase),
+ * ACE_OP_SCORE (query phase and §5.3 rule) or ACE_OP_INSERT_SCORE — on detector `det` with
+ * X_host (n x d, pinned for asynchrony) and optional output buffers (ignored for inserts),
+ * and returns a ticket at once; X_host and the outputs must stay valid until the ticket is
+ * waited for.  A scheduler thread admits queued requests as slots (two per detector) and
+ * memory free up; each detector's requests run in submission order on its own stream, so
+ * every result is the same as in a run of that detector's requests alone, while different
+ * detectors overlap on the device.  ace_server_wait blocks until the ticket's request has
+ * completed and returns its latency from submission to completion in seconds (or its error
+ * code); each ticket is waited for once.  ace_server_drain waits for everything submitted;
+ * ace_server_destroy drains, stops the scheduler and releases the server (not the detectors).
+ */
+typedef struct ace_server_s* ace_server;
+int ace_server_create(const ace_handle* dets, int n_dets, size_t mem_budget_bytes, ace_server* out);
+int ace_server_submit(ace_server s, int det, int op, const void* X_host, int64_t n, int dtype, double alpha,
+                      double* scores_host, uint32_t* sums_host, uint8_t* flags_host, uint64_t* ticket);
+int ace_server_wait(ace_server s, uint64_t ticket, double* latency_s);
+int ace_server_drain(ace_server s);
+int ace_server_destroy(ace_server s);
+
 /*
  * ace_insert_score_host_async — ace_insert_score_host without the wait: enqueues the copy
  * of X_host (in chunks, each hashed as soon as it has arrived), the insert, the query phase

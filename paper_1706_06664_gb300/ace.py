@@ -23,7 +23,8 @@ PRECISIONS = {"auto": ACE_PROJ_AUTO, "fp32": ACE_PROJ_FP32, "bf16": ACE_PROJ_BF1
 EXPORTS = [
     "ace_create", "ace_create_with_projection", "ace_destroy", "ace_reset", "ace_set_precision",
     "ace_insert", "ace_score", "ace_insert_score", "ace_insert_score_host",
-    "ace_insert_score_host_async", "ace_host_wait", "ace_delete", "ace_hash", "ace_stats",
+    "ace_insert_score_host_async", "ace_host_wait", "ace_delete", "ace_hash",
+    "ace_server_create", "ace_server_submit", "ace_server_wait", "ace_server_drain", "ace_server_destroy", "ace_stats",
     "ace_get_counts", "ace_get_projection", "ace_get_shape", "ace_last_error", "ace_version",
     "ace_profile_enable", "ace_profile_read", "ace_insert_score_noalloc",
 ]
@@ -81,6 +82,11 @@ def load_library(path: str = LIB_PATH):
             "ace_insert_score_host_async": ([H, P, i64, i32, f64, P, P, P, P], i32),
             "ace_host_wait": ([H], i32),
             "ace_delete": ([H, P, i64, i32, P], i32),
+            "ace_server_create": ([P, i32, ctypes.c_size_t, P], i32),
+            "ace_server_submit": ([P, i32, i32, P, i64, i32, f64, P, P, P, P], i32),
+            "ace_server_wait": ([P, ctypes.c_uint64, P], i32),
+            "ace_server_drain": ([P], i32),
+            "ace_server_destroy": ([P], i32),
             "ace_insert_score_noalloc": ([H, P, i64, i32, f64, P, P, P, P], i32),
             "ace_hash": ([H, P, i64, i32, P, P], i32),
             "ace_stats": ([H, P, ctypes.POINTER(ace_stats_t)], i32),
@@ -294,6 +300,60 @@ class Detector:
         out = np.empty((self.d, self.K * self.L), dtype=np.float32)
         _check(load_library().ace_get_projection(self._h, ctypes.c_void_p(out.ctypes.data)))
         return out
+
+
+OP_INSERT, OP_SCORE, OP_INSERT_SCORE = 0, 1, 2
+
+
+class Server:
+    """Continuous batching of host-buffer requests over several detectors (ace_server_*).
+    Keeps every request's arrays alive until its ticket has been waited for."""
+
+    def __init__(self, detectors, mem_budget_bytes: int = 1 << 30):
+        self._dets = list(detectors)
+        arr = (ctypes.c_void_p * len(self._dets))(*[d._h for d in self._dets])
+        h = ctypes.c_void_p()
+        _check(load_library().ace_server_create(arr, len(self._dets), int(mem_budget_bytes), ctypes.byref(h)))
+        self._h = h
+        self._live = {}
+
+    def submit(self, det: int, op: int, X: np.ndarray, alpha: float = 1.0, scores=None, sums=None, flags=None) -> int:
+        if X.dtype not in (np.float32, np.uint16):
+            raise TypeError("X must be float32 or uint16 bfloat16 bits")
+        dt = ACE_F32 if X.dtype == np.float32 else ACE_BF16
+
+        def p(a):
+            return ctypes.c_void_p(a.ctypes.data) if a is not None else ctypes.c_void_p(0)
+
+        t = ctypes.c_uint64()
+        _check(load_library().ace_server_submit(self._h, int(det), int(op), ctypes.c_void_p(X.ctypes.data), X.shape[0],
+                                                dt, float(alpha), p(scores), p(sums), p(flags), ctypes.byref(t)))
+        self._live[t.value] = (X, scores, sums, flags)
+        return t.value
+
+    def wait(self, ticket: int) -> float:
+        """Blocks until the request has completed; returns its latency in seconds."""
+        lat = ctypes.c_double()
+        try:
+            _check(load_library().ace_server_wait(self._h, ctypes.c_uint64(ticket), ctypes.byref(lat)))
+        finally:
+            self._live.pop(ticket, None)
+        return lat.value
+
+    def drain(self):
+        _check(load_library().ace_server_drain(self._h))
+
+    def close(self):
+        if self._h:
+            load_library().ace_server_destroy(self._h)
+            self._h = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def u32(t) -> np.ndarray:

@@ -1,6 +1,12 @@
 // C ABI and host runtime: detector handles, device memory, guard constants, launches.
 #include <algorithm>
 #include <cfloat>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -628,12 +634,16 @@ int ace_host_wait(ace_handle h) {
   return rc;
 }
 
-int ace_insert_score_host_async(ace_handle h, const void* X_host, int64_t n, int dtype, double alpha,
-                                double* scores_host, uint32_t* sums_host, uint8_t* flags_host, void* stream) {
+// One host-buffer batch on `stream`: op ACE_OP_INSERT, ACE_OP_SCORE or ACE_OP_INSERT_SCORE.
+static int enqueue_host_batch(ace_handle h, int op, const void* X_host, int64_t n, int dtype, double alpha,
+                              double* scores_host, uint32_t* sums_host, uint8_t* flags_host, void* stream) {
+  if (op != ACE_OP_INSERT && op != ACE_OP_SCORE && op != ACE_OP_INSERT_SCORE)
+    return fail(ACE_ERR_ARG, "unknown operation %d", op);
+  const bool do_insert = op != ACE_OP_SCORE, do_score = op != ACE_OP_INSERT;
   int rc = check_x(h, X_host, n, dtype);
   if (rc) return rc;
   if (!std::isfinite(alpha)) return fail(ACE_ERR_ARG, "alpha must be finite");
-  if (h->n_ins + static_cast<uint64_t>(n) > 0xFFFFFFFFull)
+  if (do_insert && h->n_ins + static_cast<uint64_t>(n) > 0xFFFFFFFFull)
     return fail(ACE_ERR_OVERFLOW, "inserting %lld points would allow a count above 2^32-1", static_cast<long long>(n));
   if (n == 0) return ACE_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -665,7 +675,7 @@ int ace_insert_score_host_async(ace_handle h, const void* X_host, int64_t n, int
     }
     sl.cap = cap;
   }
-  if (static_cast<size_t>(n) > h->stage_cap) {
+  if (do_score && static_cast<size_t>(n) > h->stage_cap) {
     if ((rc = ace_host_wait(h))) return rc;
     ACE_CUDA(cudaStreamSynchronize(s));
     cudaFree(h->scstage);
@@ -682,9 +692,11 @@ int ace_insert_score_host_async(ace_handle h, const void* X_host, int64_t n, int
     }
     h->stage_cap = cap;
   }
-  void* p = h->sums;
-  if ((rc = grow(&p, &h->sums_cap, static_cast<size_t>(n) * sizeof(uint32_t), s, "sums scratch"))) return rc;
-  h->sums = static_cast<uint32_t*>(p);
+  if (do_score) {
+    void* p = h->sums;
+    if ((rc = grow(&p, &h->sums_cap, static_cast<size_t>(n) * sizeof(uint32_t), s, "sums scratch"))) return rc;
+    h->sums = static_cast<uint32_t*>(p);
+  }
   if ((rc = grow(&h->ids, &h->ids_cap, need_ids, s, "ids scratch"))) return rc;
   if (!h->cstream) ACE_CUDA(cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking));
   if (!sl.done) ACE_CUDA(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
@@ -717,26 +729,35 @@ int ace_insert_score_host_async(ace_handle h, const void* X_host, int64_t n, int
     if (nc <= 0) break;
     ACE_CUDA(cudaStreamWaitEvent(s, sl.chunk[c], 0));
     ace::HashArgs a = hash_args(h, static_cast<const char*>(sl.x) + c0 * row, nc, dtype,
-                                ace::kStoreIds | (simt ? ace::kInsert : 0));
+                                ace::kStoreIds | (simt && do_insert ? ace::kInsert : 0));
     a.ids = static_cast<char*>(h->ids) + static_cast<size_t>(c0) * id_bytes(h);
     a.ld = n;
     if ((rc = run_hash(h, a, s, false))) return rc;
   }
-  if (!simt) {
+  if (do_insert && !simt) {
     PhaseScope ps(h, ACE_PHASE_INSERT, s);
     cudaError_t e = ace::launch_insert_from_ids(h->ids, h->K <= 16, n, n, h->K, h->L, h->counts, h->num_sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "insert kernel launch");
   }
-  h->n_ins += static_cast<uint64_t>(n);
-  if ((rc = score_tail(h, n, alpha, scores_host ? h->scstage : nullptr, h->sums, flags_host ? h->flstage : nullptr, s)))
-    return rc;
-  if (scores_host) ACE_CUDA(cudaMemcpyAsync(scores_host, h->scstage, n * sizeof(double), cudaMemcpyDeviceToHost, s));
-  if (sums_host) ACE_CUDA(cudaMemcpyAsync(sums_host, h->sums, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-  if (flags_host) ACE_CUDA(cudaMemcpyAsync(flags_host, h->flstage, n, cudaMemcpyDeviceToHost, s));
+  if (do_insert) h->n_ins += static_cast<uint64_t>(n);
+  if (do_score) {
+    if ((rc = score_tail(h, n, alpha, scores_host ? h->scstage : nullptr, h->sums, flags_host ? h->flstage : nullptr,
+                         s)))
+      return rc;
+    if (scores_host) ACE_CUDA(cudaMemcpyAsync(scores_host, h->scstage, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (sums_host) ACE_CUDA(cudaMemcpyAsync(sums_host, h->sums, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    if (flags_host) ACE_CUDA(cudaMemcpyAsync(flags_host, h->flstage, n, cudaMemcpyDeviceToHost, s));
+  }
   ACE_CUDA(cudaEventRecord(sl.done, s));
   sl.busy = true;
   h->hs_next ^= 1;
   return ACE_OK;
+}
+
+int ace_insert_score_host_async(ace_handle h, const void* X_host, int64_t n, int dtype, double alpha,
+                                double* scores_host, uint32_t* sums_host, uint8_t* flags_host, void* stream) {
+  return enqueue_host_batch(h, ACE_OP_INSERT_SCORE, X_host, n, dtype, alpha, scores_host, sums_host, flags_host,
+                            stream);
 }
 
 int ace_insert_score_host(ace_handle h, const void* X_host, int64_t n, int dtype, double alpha, double* scores_host,
@@ -744,6 +765,207 @@ int ace_insert_score_host(ace_handle h, const void* X_host, int64_t n, int dtype
   int rc = ace_insert_score_host_async(h, X_host, n, dtype, alpha, scores_host, sums_host, flags_host, stream);
   if (rc) return rc;
   return ace_host_wait(h);
+}
+
+// ---------------------------------------------------------------------------------------
+// Request server (continuous batching over several detectors).  Requests are kept in
+// submission order; a scheduler thread admits the first admissible one whenever a slot or
+// memory frees up: at most two per detector are in flight (its two staging slots), their
+// staged bytes stay within the budget, and a detector whose oldest waiting request cannot
+// start yet keeps its later requests waiting too, so each detector sees its requests in
+// submission order — its results are the same alone and in any mix.  Each detector runs on
+// its own stream, so different detectors' work overlaps on the device; completion is
+// stamped by a host callback on that stream.
+// ---------------------------------------------------------------------------------------
+}  // extern "C"
+
+struct ace_server_s {
+  struct Req {
+    uint64_t id = 0;
+    int det = 0, op = 0, dtype = 0;
+    const void* X = nullptr;
+    int64_t n = 0;
+    double alpha = 1.0;
+    double* scores = nullptr;
+    uint32_t* sums = nullptr;
+    uint8_t* flags = nullptr;
+    size_t bytes = 0;
+    std::chrono::steady_clock::time_point t_sub, t_done;
+    int rc = ACE_OK;
+    bool done = false;
+    ace_server_s* srv = nullptr;
+  };
+  std::vector<ace_handle> dets;
+  std::vector<cudaStream_t> streams;
+  std::vector<int> inflight;
+  size_t budget = 0, bytes_inflight = 0;
+  std::deque<Req*> pending;
+  std::unordered_map<uint64_t, Req*> reqs;
+  uint64_t next_id = 1;
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::thread worker;
+  bool stop = false;
+
+  static void CUDART_CB on_done(void* p) {
+    Req* r = static_cast<Req*>(p);
+    ace_server_s* s = r->srv;
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->t_done = std::chrono::steady_clock::now();
+    r->done = true;
+    s->inflight[r->det] -= 1;
+    s->bytes_inflight -= r->bytes;
+    s->cv.notify_all();
+  }
+
+  // The first admissible waiting request (caller holds mu), or nullptr.
+  Req* pick() {
+    std::vector<char> held(dets.size(), 0);
+    for (auto it = pending.begin(); it != pending.end(); ++it) {
+      Req* r = *it;
+      if (held[r->det]) continue;
+      const bool slot = inflight[r->det] < 2;
+      const bool mem = bytes_inflight == 0 || bytes_inflight + r->bytes <= budget;
+      if (slot && mem) {
+        pending.erase(it);
+        return r;
+      }
+      held[r->det] = 1;  // keep this detector's later requests behind this one
+    }
+    return nullptr;
+  }
+
+  void run() {
+    cudaSetDevice(device);
+    std::unique_lock<std::mutex> lk(mu);
+    for (;;) {
+      Req* r = nullptr;
+      cv.wait(lk, [&] { return (r = pick()) != nullptr || (stop && pending.empty()); });
+      if (!r) break;
+      inflight[r->det] += 1;
+      bytes_inflight += r->bytes;
+      lk.unlock();
+      int rc = enqueue_host_batch(dets[r->det], r->op, r->X, r->n, r->dtype, r->alpha, r->scores, r->sums, r->flags,
+                                  streams[r->det]);
+      if (rc == ACE_OK && cudaLaunchHostFunc(streams[r->det], on_done, r) != cudaSuccess) rc = ACE_ERR_CUDA;
+      lk.lock();
+      if (rc != ACE_OK) {
+        r->rc = rc;
+        r->t_done = std::chrono::steady_clock::now();
+        r->done = true;
+        inflight[r->det] -= 1;
+        bytes_inflight -= r->bytes;
+        cv.notify_all();
+      }
+    }
+  }
+};
+
+extern "C" {
+
+int ace_server_create(const ace_handle* dets, int n_dets, size_t mem_budget_bytes, ace_server* out) {
+  if (!out || !dets || n_dets < 1) return fail(ACE_ERR_ARG, "invalid server arguments");
+  *out = nullptr;
+  for (int i = 0; i < n_dets; ++i)
+    if (!dets[i]) return fail(ACE_ERR_ARG, "detector %d is NULL", i);
+  ace_server_s* s = new (std::nothrow) ace_server_s();
+  if (!s) return fail(ACE_ERR_OOM, "host allocation failed");
+  s->dets.assign(dets, dets + n_dets);
+  s->inflight.assign(n_dets, 0);
+  s->budget = mem_budget_bytes;
+  cudaGetDevice(&s->device);
+  s->streams.assign(n_dets, nullptr);
+  for (int i = 0; i < n_dets; ++i) {
+    cudaError_t e = cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      for (auto st : s->streams)
+        if (st) cudaStreamDestroy(st);
+      delete s;
+      return cuda_fail(e, "server stream");
+    }
+  }
+  s->worker = std::thread([s] { s->run(); });
+  *out = s;
+  return ACE_OK;
+}
+
+int ace_server_submit(ace_server s, int det, int op, const void* X_host, int64_t n, int dtype, double alpha,
+                      double* scores_host, uint32_t* sums_host, uint8_t* flags_host, uint64_t* ticket) {
+  if (!s || !ticket) return fail(ACE_ERR_ARG, "NULL argument");
+  if (det < 0 || det >= static_cast<int>(s->dets.size())) return fail(ACE_ERR_ARG, "detector index %d out of range", det);
+  if (op != ACE_OP_INSERT && op != ACE_OP_SCORE && op != ACE_OP_INSERT_SCORE)
+    return fail(ACE_ERR_ARG, "unknown operation %d", op);
+  if (int rc = check_x(s->dets[det], X_host, n, dtype)) return rc;
+  auto* r = new (std::nothrow) ace_server_s::Req();
+  if (!r) return fail(ACE_ERR_OOM, "host allocation failed");
+  r->det = det;
+  r->op = op;
+  r->dtype = dtype;
+  r->X = X_host;
+  r->n = n;
+  r->alpha = alpha;
+  r->scores = scores_host;
+  r->sums = sums_host;
+  r->flags = flags_host;
+  r->srv = s;
+  const size_t row = static_cast<size_t>(s->dets[det]->d) * (dtype == ACE_F32 ? 4 : 2);
+  r->bytes = static_cast<size_t>(n) * (row + static_cast<size_t>(s->dets[det]->L) * 4 + 13);
+  r->t_sub = std::chrono::steady_clock::now();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->id = s->next_id++;
+    s->reqs[r->id] = r;
+    s->pending.push_back(r);
+  }
+  s->cv.notify_all();
+  *ticket = r->id;
+  return ACE_OK;
+}
+
+int ace_server_wait(ace_server s, uint64_t ticket, double* latency_s) {
+  if (!s) return fail(ACE_ERR_ARG, "server is NULL");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return fail(ACE_ERR_ARG, "unknown ticket %llu", static_cast<unsigned long long>(ticket));
+  ace_server_s::Req* r = it->second;
+  s->cv.wait(lk, [&] { return r->done; });
+  if (latency_s) latency_s[0] = std::chrono::duration<double>(r->t_done - r->t_sub).count();
+  const int rc = r->rc;
+  s->reqs.erase(it);
+  delete r;
+  if (rc != ACE_OK) return fail(rc, "request %llu failed", static_cast<unsigned long long>(ticket));
+  return ACE_OK;
+}
+
+int ace_server_drain(ace_server s) {
+  if (!s) return fail(ACE_ERR_ARG, "server is NULL");
+  std::unique_lock<std::mutex> lk(s->mu);
+  s->cv.wait(lk, [&] {
+    if (!s->pending.empty()) return false;
+    for (int v : s->inflight)
+      if (v) return false;
+    return true;
+  });
+  return ACE_OK;
+}
+
+int ace_server_destroy(ace_server s) {
+  if (!s) return ACE_OK;
+  ace_server_drain(s);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  for (auto st : s->streams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  for (auto& kv : s->reqs) delete kv.second;
+  delete s;
+  return ACE_OK;
 }
 
 int ace_delete(ace_handle h, const void* X_dev, int64_t n, int dtype, void* stream) {

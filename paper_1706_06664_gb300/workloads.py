@@ -24,6 +24,12 @@ Recipes (sizes are the defaults; tests pass smaller n):
 * ``batched``  — many independent detectors: d log-uniform in [16,512], n log-uniform in
                  [100,100000], 8 clusters N(m_c, I) with m_c ~ N(0,4I), 1% anomalies shifted
                  by +4 in 3 dimensions; K=12, L=32.
+* ``stream_chunk`` — a drifting stream for serving: d=128 binary32, 16 means that move
+                 linearly from m0_c to m1_c (both ~ N(0,4I)) over the stream's length, points
+                 N(m_c(t), I); 0.1% anomalies in bursts of 100 consecutive points, shifted by
+                 +6 in 3 seed-chosen dimensions.  Chunks are drawn from (seed, start), so any
+                 window of the stream can be generated on its own.  K=15, L=50, 64 detectors;
+                 request sizes log-uniform in [1, 8192] (``request_sizes``).
 """
 from __future__ import annotations
 
@@ -31,8 +37,8 @@ import math
 
 import numpy as np
 
-__all__ = ["small", "kdd", "highdim", "batched_specs", "batched_points", "to_bf16_bits",
-           "bf16_bits_to_f32", "gaussian_w"]
+__all__ = ["small", "kdd", "highdim", "batched_specs", "batched_points", "stream_chunk", "request_sizes",
+           "to_bf16_bits", "bf16_bits_to_f32", "gaussian_w"]
 
 
 def _rng(seed: int, stream: int = 0) -> np.random.Generator:
@@ -133,3 +139,27 @@ def batched_points(d: int, n: int, seed: int, clusters: int = 8):
     dims = rng.choice(d, size=min(3, d), replace=False)
     X[np.ix_(idx, dims)] += 4.0
     return np.ascontiguousarray(X, dtype=np.float32)
+
+
+def stream_chunk(seed: int, start: int, n: int, total: int = 100_000_000, d: int = 128, means: int = 16):
+    """Points [start, start + n) of the drifting stream (see the module notes)."""
+    base = _rng(seed, 0)
+    m0 = base.normal(0.0, 2.0, size=(means, d))
+    m1 = base.normal(0.0, 2.0, size=(means, d))
+    dims = base.choice(d, size=3, replace=False)
+    r = _rng(seed, 1 + int(start))
+    pos = np.arange(start, start + n, dtype=np.float64)
+    t = (pos / float(total))[:, None]
+    c = r.integers(0, means, size=n)
+    X = (1.0 - t) * m0[c] + t * m1[c] + r.normal(size=(n, d))
+    # one burst of 100 anomalous points in every 100,000 (0.1%), at a seed-chosen offset
+    off = int(base.integers(0, 100_000 - 100))
+    burst = ((pos.astype(np.int64) % 100_000) >= off) & ((pos.astype(np.int64) % 100_000) < off + 100)
+    X[np.ix_(burst, dims)] += 6.0
+    return np.ascontiguousarray(X, dtype=np.float32)
+
+
+def request_sizes(seed: int, count: int, lo: int = 1, hi: int = 8192) -> np.ndarray:
+    """Request sizes log-uniform in [lo, hi]."""
+    r = _rng(seed, 7)
+    return np.exp(r.uniform(math.log(lo), math.log(hi), size=count)).round().astype(np.int64).clip(lo, hi)
