@@ -244,6 +244,71 @@ def _e2e(args, det, host_batches, stream, dist, dev, n, ws):
             "d2h_bytes_per_step": int(o_sc.nbytes + o_su.nbytes + o_fl.nbytes)}
 
 
+def serving(seed: int = 31, pool_points: int = 1 << 20, n_det: int = 64, n_req: int = 3000) -> dict:
+    """Streaming-serving shape: 64 detectors (d=128, K=15, L=50), request sizes log-uniform
+    in [1, 8192], inserts and scores 50/50 on random detectors, points from a window of the
+    drifting stream.  Capacity from a closed-loop burst; then Poisson arrivals at 0.5x and
+    0.8x that rate; latency = submission to completion (outputs in host memory)."""
+    import torch
+    from paper_1706_06664_gb300 import ace, workloads
+    d, K, L = 128, 15, 50
+    dets = [ace.Detector(d, K, L, seed=1000 + i) for i in range(n_det)]
+    pool = torch.from_numpy(workloads.stream_chunk(seed, 0, pool_points, total=100_000_000, d=d)).pin_memory().numpy()
+    rng = np.random.default_rng(seed)
+    srv = ace.Server(dets, mem_budget_bytes=1 << 30)
+
+    def workload(count, salt):
+        sizes = workloads.request_sizes(seed + salt, count)
+        offs = np.concatenate([[0], np.cumsum(sizes)[:-1]]) % (pool_points - 8192)
+        ops = rng.integers(0, 2, size=count)  # 0 insert, 1 score
+        dsel = rng.integers(0, n_det, size=count)
+        out = torch.empty(int(sizes.sum()) * 13 + 64 * (count + 1), dtype=torch.uint8).pin_memory().numpy()
+        return sizes, offs, ops, dsel, out
+
+    def submit_all(sizes, offs, ops, dsel, out, arrivals=None):
+        tickets, pos = [], 0
+        t0 = time.perf_counter()
+        for k in range(len(sizes)):
+            if arrivals is not None:
+                while time.perf_counter() - t0 < arrivals[k]:
+                    pass
+            n = int(sizes[k])
+            X = pool[offs[k]:offs[k] + n]
+            if ops[k] == 0:
+                tickets.append(srv.submit(int(dsel[k]), ace.OP_INSERT, X))
+            else:
+                sc = out[pos:pos + 8 * n].view(np.float64)
+                su = out[pos + 8 * n:pos + 12 * n].view(np.uint32)
+                fl = out[pos + 12 * n:pos + 13 * n]
+                pos = (pos + 13 * n + 63) // 64 * 64
+                tickets.append(srv.submit(int(dsel[k]), ace.OP_SCORE, X, 1.0, sc, su, fl))
+        lat = np.array([srv.wait(t) for t in tickets])
+        return lat, time.perf_counter() - t0
+
+    # every detector starts with 8192 inserted points
+    for i in range(n_det):
+        srv.wait(srv.submit(i, ace.OP_INSERT, pool[i * 8192:(i + 1) * 8192]))
+    w = workload(n_req, 1)
+    submit_all(*w)  # warm-up (buffers grow to their final sizes)
+    w = workload(n_req, 2)
+    lat, el = submit_all(*w)
+    cap_req, cap_pts = n_req / el, float(w[0].sum()) / el
+    res = {"workload": f"drifting stream d={d} K={K} L={L}, {n_det} detectors, requests log-uniform 1-8192, "
+                       f"50/50 insert/score, {n_req} requests per run",
+           "capacity": {"points_per_s": cap_pts, "requests_per_s": cap_req,
+                        "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3)}}
+    for f in (0.5, 0.8):
+        w = workload(n_req, 3 + int(f * 10))
+        arrivals = np.cumsum(rng.exponential(1.0 / (f * cap_req), size=n_req))
+        lat, el = submit_all(*w, arrivals=arrivals)
+        res[f"load_{f}"] = {"points_per_s": float(w[0].sum()) / el, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                            "p99_ms": float(np.percentile(lat, 99) * 1e3)}
+    srv.close()
+    for dd in dets:
+        dd.close()
+    return res
+
+
 def run_ours(args):
     import torch
     from paper_1706_06664_gb300 import ace
@@ -341,6 +406,8 @@ def run_ours(args):
     }
     if rank == 0 and args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(host_batches[0], seed)
+    if rank == 0 and ws == 1 and args.serving:
+        line["serving"] = serving()
     if rank == 0:
         print(json.dumps(line), flush=True)
     det.close()
@@ -361,6 +428,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=100_000, help="points per reference step")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-serving", dest="serving", action="store_false")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":
