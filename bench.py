@@ -309,6 +309,47 @@ def serving(seed: int = 31, pool_points: int = 1 << 20, n_det: int = 64, n_req: 
     return res
 
 
+def batched(n_det: int = 2048, seed: int = 4) -> dict:
+    """Batched-detectors shape: 2048 detectors, d log-uniform in [16, 512], n log-uniform in
+    [100, 100000], K=12, L=32, Gaussian-mixture points (8 clusters N(m_c, I), m_c ~ N(0, 4I),
+    1% shifted by +4 in 3 dimensions) drawn on the device from a seeded generator.  One
+    ace_batch_insert_score call against the same work as one ace_insert_score per detector."""
+    import torch
+    from paper_1706_06664_gb300 import ace, workloads
+    specs = workloads.batched_specs(seed=seed, n_det=n_det)
+    K, L = 12, 32
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    Xs = []
+    for (d, n, sd) in specs:
+        means = 2.0 * torch.randn(8, d, device="cuda", generator=g)
+        which = torch.randint(0, 8, (n,), device="cuda", generator=g)
+        X = means[which] + torch.randn(n, d, device="cuda", generator=g)
+        k = max(1, n // 100)
+        X[torch.randint(0, n, (k,), device="cuda", generator=g)[:, None],
+          torch.randint(0, d, (min(3, d),), device="cuda", generator=g)[None, :]] += 4.0
+        Xs.append(X.contiguous())
+    points = int(sum(n for _, n, _ in specs))
+    dets = [ace.Detector(d, K, L, seed=sd, precision="fp32") for (d, _, sd) in specs]
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ace.batch_insert_score(dets, Xs)  # warm-up: scratch grows to size
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    ace.batch_insert_score(dets, Xs)
+    ev[1].record(stream)
+    for det, X in zip(dets, Xs):
+        det.insert_score(X, ALPHA)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    t_b, t_l = ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3
+    for det in dets:
+        det.close()
+    return {"workload": f"{n_det} detectors, d log-uniform 16-512, n log-uniform 100-100000, K={K} L={L}, "
+                        f"{points} points, binary32 engine",
+            "points_per_s": points / t_b, "ms": t_b * 1e3,
+            "one_call_per_detector_points_per_s": points / t_l, "one_call_per_detector_ms": t_l * 1e3}
+
+
 def run_ours(args):
     import torch
     from paper_1706_06664_gb300 import ace
@@ -408,6 +449,8 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline(host_batches[0], seed)
     if rank == 0 and ws == 1 and args.serving:
         line["serving"] = serving()
+    if rank == 0 and ws == 1 and args.batched:
+        line["batched"] = batched()
     if rank == 0:
         print(json.dumps(line), flush=True)
     det.close()
@@ -429,6 +472,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-serving", dest="serving", action="store_false")
+    ap.add_argument("--no-batched", dest="batched", action="store_false")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

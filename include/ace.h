@@ -156,6 +156,21 @@ int ace_insert_score_host(ace_handle h, const void* X_host, int64_t n, int dtype
  */
 int ace_delete(ace_handle h, const void* X_dev, int64_t n, int dtype, void* stream);
 
+/*
+ * ace_batch_insert_score — ace_insert_score on `count` distinct detectors at once, each with
+ * its own X_dev[g] (n[g] x d_g, device; one dtype for the whole batch) and optional outputs
+ * (scores_dev, sums_dev, flags_dev: arrays of `count` device pointers, or NULL; an entry may
+ * be NULL).  Every detector's results are exactly those of its own ace_insert_score call
+ * (Algorithm 1 counting and query phases, §5.3 rule on its own statistics); the work of all
+ * detectors runs as one launch per phase (hash + insert, query, flags) on the binary32 engine,
+ * so many small detectors fill the GPU together.  The K of all detectors is <= 16, or > 16
+ * for all.  All or nothing on argument errors; asynchronous on `stream`.  (The paper states
+ * the method for one dataset; running many detectors together is this library's.)
+ */
+int ace_batch_insert_score(const ace_handle* dets, int count, const void* const* X_dev, const int64_t* n, int dtype,
+                           double alpha, double* const* scores_dev, uint32_t* const* sums_dev,
+                           uint8_t* const* flags_dev, void* stream);
+
 /* Operations of a host-buffer request (ace_server_submit). */
 enum { ACE_OP_INSERT = 0, ACE_OP_SCORE = 1, ACE_OP_INSERT_SCORE = 2 };
 

@@ -24,7 +24,7 @@ EXPORTS = [
     "ace_create", "ace_create_with_projection", "ace_destroy", "ace_reset", "ace_set_precision",
     "ace_insert", "ace_score", "ace_insert_score", "ace_insert_score_host",
     "ace_insert_score_host_async", "ace_host_wait", "ace_delete", "ace_hash",
-    "ace_server_create", "ace_server_submit", "ace_server_wait", "ace_server_drain", "ace_server_destroy", "ace_stats",
+    "ace_batch_insert_score", "ace_server_create", "ace_server_submit", "ace_server_wait", "ace_server_drain", "ace_server_destroy", "ace_stats",
     "ace_get_counts", "ace_get_projection", "ace_get_shape", "ace_last_error", "ace_version",
     "ace_profile_enable", "ace_profile_read", "ace_insert_score_noalloc",
 ]
@@ -82,6 +82,7 @@ def load_library(path: str = LIB_PATH):
             "ace_insert_score_host_async": ([H, P, i64, i32, f64, P, P, P, P], i32),
             "ace_host_wait": ([H], i32),
             "ace_delete": ([H, P, i64, i32, P], i32),
+            "ace_batch_insert_score": ([P, i32, P, P, i32, f64, P, P, P, P], i32),
             "ace_server_create": ([P, i32, ctypes.c_size_t, P], i32),
             "ace_server_submit": ([P, i32, i32, P, i64, i32, f64, P, P, P, P], i32),
             "ace_server_wait": ([P, ctypes.c_uint64, P], i32),
@@ -300,6 +301,31 @@ class Detector:
         out = np.empty((self.d, self.K * self.L), dtype=np.float32)
         _check(load_library().ace_get_projection(self._h, ctypes.c_void_p(out.ctypes.data)))
         return out
+
+
+def batch_insert_score(detectors, Xs, alpha: float = 1.0, stream=None):
+    """ace_batch_insert_score: insert_score on many detectors in one set of launches.
+    Xs are device tensors (one per detector, same dtype).  Returns lists of (scores, sums,
+    flags) device tensors."""
+    torch = _torch()
+    cnt = len(detectors)
+    if cnt != len(Xs) or cnt == 0:
+        raise ValueError("one X per detector")
+    for d, X in zip(detectors, Xs):
+        d._xcheck(X)
+    dt = _x_dtype(Xs[0])
+    dev = Xs[0].device
+    sc = [torch.empty(X.shape[0], dtype=torch.float64, device=dev) for X in Xs]
+    su = [torch.empty(X.shape[0], dtype=torch.int32, device=dev) for X in Xs]
+    fl = [torch.empty(X.shape[0], dtype=torch.uint8, device=dev) for X in Xs]
+    V = ctypes.c_void_p * cnt
+    hs = V(*[d._h for d in detectors])
+    xs = V(*[X.data_ptr() for X in Xs])
+    ns = (ctypes.c_int64 * cnt)(*[X.shape[0] for X in Xs])
+    _check(load_library().ace_batch_insert_score(hs, cnt, xs, ns, dt, float(alpha), V(*[t.data_ptr() for t in sc]),
+                                                 V(*[t.data_ptr() for t in su]), V(*[t.data_ptr() for t in fl]),
+                                                 _stream_ptr(stream)))
+    return sc, su, fl
 
 
 OP_INSERT, OP_SCORE, OP_INSERT_SCORE = 0, 1, 2

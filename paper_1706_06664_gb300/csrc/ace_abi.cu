@@ -1015,6 +1015,76 @@ int ace_delete(ace_handle h, const void* X_dev, int64_t n, int dtype, void* stre
   return ACE_OK;
 }
 
+int ace_batch_insert_score(const ace_handle* dets, int count, const void* const* X_dev, const int64_t* n, int dtype,
+                           double alpha, double* const* scores_dev, uint32_t* const* sums_dev,
+                           uint8_t* const* flags_dev, void* stream) {
+  if (!dets || !X_dev || !n || count < 1) return fail(ACE_ERR_ARG, "invalid batch arguments");
+  if (!std::isfinite(alpha)) return fail(ACE_ERR_ARG, "alpha must be finite");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool id16 = dets[0] && dets[0]->K <= 16;
+  std::vector<ace_handle> seen(dets, dets + count);
+  std::sort(seen.begin(), seen.end());
+  if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+    return fail(ACE_ERR_ARG, "a detector appears twice in one batch");
+  for (int g = 0; g < count; ++g) {
+    ace_handle h = dets[g];
+    if (int rc = check_x(h, X_dev[g], n[g], dtype)) return rc;
+    if ((h->K <= 16) != id16) return fail(ACE_ERR_ARG, "a batch mixes K <= 16 and K > 16");
+    if (h->n_ins + static_cast<uint64_t>(n[g]) > 0xFFFFFFFFull)
+      return fail(ACE_ERR_OVERFLOW, "detector %d: inserting %lld points would allow a count above 2^32-1", g,
+                  static_cast<long long>(n[g]));
+  }
+  // per detector: scratch, hash arguments (SIMT engine, ids stored and counts incremented)
+  // and its query job; then the block prefixes of the three batched launches
+  std::vector<ace::HashArgs> ha(count);
+  std::vector<ace::ScoreJob> sj(count);
+  std::vector<long long> hstart(count + 1, 0), sstart(count + 1, 0);
+  for (int g = 0; g < count; ++g) {
+    ace_handle h = dets[g];
+    const long long ng = n[g];
+    uint32_t* sum_out = sums_dev ? sums_dev[g] : nullptr;
+    if (ng > 0) {
+      if (int rc = grow(&h->ids, &h->ids_cap, static_cast<size_t>(ng) * h->L * id_bytes(h), s, "ids scratch")) return rc;
+      if (!sum_out) {
+        void* p = h->sums;
+        if (int rc = grow(&p, &h->sums_cap, static_cast<size_t>(ng) * sizeof(uint32_t), s, "sums scratch")) return rc;
+        h->sums = static_cast<uint32_t*>(p);
+        sum_out = h->sums;
+      }
+    }
+    ha[g] = hash_args(h, X_dev[g], ng, dtype, ace::kStoreIds | ace::kInsert);
+    sj[g] = ace::ScoreJob{h->ids, ng, ng, h->K, h->L, alpha, h->counts, sum_out, h->st, h->div,
+                          scores_dev ? scores_dev[g] : nullptr, flags_dev ? flags_dev[g] : nullptr};
+    hstart[g + 1] = hstart[g] + ace::hash_simt_blocks(ha[g]);
+    sstart[g + 1] = sstart[g] + (ng + 255) / 256;
+  }
+  const size_t b_ha = sizeof(ace::HashArgs) * count, b_sj = sizeof(ace::ScoreJob) * count;
+  const size_t b_st = sizeof(long long) * (count + 1);
+  std::vector<unsigned char> host(b_ha + b_sj + 2 * b_st);
+  std::memcpy(host.data(), ha.data(), b_ha);
+  std::memcpy(host.data() + b_ha, sj.data(), b_sj);
+  std::memcpy(host.data() + b_ha + b_sj, hstart.data(), b_st);
+  std::memcpy(host.data() + b_ha + b_sj + b_st, sstart.data(), b_st);
+  unsigned char* dev = nullptr;
+  ACE_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&dev), host.size(), s));
+  cudaError_t e = cudaMemcpyAsync(dev, host.data(), host.size(), cudaMemcpyHostToDevice, s);
+  const auto* d_ha = reinterpret_cast<const ace::HashArgs*>(dev);
+  const auto* d_sj = reinterpret_cast<const ace::ScoreJob*>(dev + b_ha);
+  const auto* d_hs = reinterpret_cast<const long long*>(dev + b_ha + b_sj);
+  const auto* d_ss = reinterpret_cast<const long long*>(dev + b_ha + b_sj + b_st);
+  const int sms = dets[0]->num_sms > 0 ? dets[0]->num_sms : 152;
+  if (e == cudaSuccess) e = ace::launch_hash_simt_batched(d_ha, d_hs, count, dtype == ACE_BF16, id16, sms, s);
+  if (e == cudaSuccess) e = ace::launch_score_batched(d_sj, d_ss, count, id16, sms, s);
+  if (e == cudaSuccess) e = ace::launch_flags_batched(d_sj, d_ss, count, sms, s);
+  cudaFreeAsync(dev, s);
+  if (e != cudaSuccess) return cuda_fail(e, "batched launch");
+  for (int g = 0; g < count; ++g) {
+    dets[g]->n_ins += static_cast<uint64_t>(n[g]);
+    dets[g]->last_precision = ACE_PROJ_FP32;
+  }
+  return ACE_OK;
+}
+
 int ace_hash(ace_handle h, const void* X_dev, int64_t n, int dtype, uint32_t* ids_dev, void* stream) {
   int rc = check_x(h, X_dev, n, dtype);
   if (rc) return rc;

@@ -50,6 +50,20 @@ struct HashArgs {
   DevStats* st;
 };
 
+// One detector's share of a batched query phase and flags pass.
+struct ScoreJob {
+  const void* ids;  // table-major ids [L][ld]
+  long long ld, n;
+  int K, L;
+  double alpha;
+  const uint32_t* counts;
+  uint32_t* sums;
+  DevStats* st;
+  DivConst div;
+  double* scores;   // may be null
+  uint8_t* flags;   // may be null
+};
+
 // Kernels launched from the runtime (each returns the launch error).
 cudaError_t launch_hash_simt(const HashArgs& a, cudaStream_t s);
 cudaError_t launch_score_gather(const void* ids, int ids16, long long ld, long long n, int K, int L, double alpha,
@@ -59,6 +73,13 @@ cudaError_t launch_flags(const uint32_t* sums, long long n, const DivConst& div,
 cudaError_t launch_insert_from_ids(const void* ids, int ids16, long long ld, long long n, int K, int L,
                                    uint32_t* counts, int num_sms, cudaStream_t s);
 cudaError_t launch_sum_squares(const uint32_t* counts, long long total, DevStats* st, cudaStream_t s);
+long long hash_simt_blocks(const HashArgs& a);
+cudaError_t launch_hash_simt_batched(const HashArgs* args_dev, const long long* start_dev, int ndet, bool bf16,
+                                     bool id16, int num_sms, cudaStream_t s);
+cudaError_t launch_score_batched(const ScoreJob* jobs_dev, const long long* start_dev, int ndet, bool id16, int num_sms,
+                                 cudaStream_t s);
+cudaError_t launch_flags_batched(const ScoreJob* jobs_dev, const long long* start_dev, int ndet, int num_sms,
+                                 cudaStream_t s);
 cudaError_t launch_delete_check(const uint32_t* hist, const uint32_t* counts, long long total, unsigned int* flag,
                                 int num_sms, cudaStream_t s);
 cudaError_t launch_delete_apply(const uint32_t* hist, uint32_t* counts, long long total, int num_sms, cudaStream_t s);

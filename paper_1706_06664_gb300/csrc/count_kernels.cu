@@ -107,11 +107,13 @@ __device__ void finish_stats(DevStats* st, int L, double alpha) {
   st->threshold = t;
 }
 
+// Block `blk` of `nblocks` of one detector's query phase.
 template <typename IdT>
-__global__ void __launch_bounds__(256) score_gather_kernel(const IdT* __restrict__ ids, long long ld, long long n, int K,
-                                                           int L, double alpha, const uint32_t* __restrict__ counts,
-                                                           uint32_t* __restrict__ sums, DevStats* st) {
-  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void score_block(const IdT* __restrict__ ids, long long ld, long long n, int K, int L,
+                                            double alpha, const uint32_t* __restrict__ counts,
+                                            uint32_t* __restrict__ sums, DevStats* st, long long blk,
+                                            long long nblocks) {
+  const long long i = blk * blockDim.x + threadIdx.x;
   unsigned long long c = 0;
   if (i < n) {
     const IdT* col = ids + i;
@@ -125,15 +127,63 @@ __global__ void __launch_bounds__(256) score_gather_kernel(const IdT* __restrict
   }
   block_fold(c, c * c, __umul64hi(c, c), st->S1, st->S2);
   if (threadIdx.x == 0) {
-    if (blockIdx.x == 0) atomicAdd(&st->n_scored, static_cast<unsigned long long>(n));
+    if (blk == 0) atomicAdd(&st->n_scored, static_cast<unsigned long long>(n));
     // the last block to fold (after every other block's sums are visible) derives mu, sigma, t
     __threadfence();
     const unsigned int ticket = atomicAdd(&st->done, 1u);
-    if (ticket == gridDim.x - 1) {
+    if (ticket == nblocks - 1) {
       __threadfence();
       finish_stats(st, L, alpha);
       st->done = 0u;
     }
+  }
+}
+
+template <typename IdT>
+__global__ void __launch_bounds__(256) score_gather_kernel(const IdT* __restrict__ ids, long long ld, long long n, int K,
+                                                           int L, double alpha, const uint32_t* __restrict__ counts,
+                                                           uint32_t* __restrict__ sums, DevStats* st) {
+  score_block<IdT>(ids, ld, n, K, L, alpha, counts, sums, st, blockIdx.x, gridDim.x);
+}
+
+__device__ __forceinline__ int job_of(const long long* __restrict__ start, int ndet, long long b) {
+  int lo = 0, hi = ndet;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (start[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Many detectors' query phases in one launch (blocks of detector g: [start[g], start[g+1])).
+template <typename IdT>
+__global__ void __launch_bounds__(256) score_batched_kernel(const ScoreJob* __restrict__ jobs,
+                                                            const long long* __restrict__ start, int ndet) {
+  const long long total = start[ndet];
+  for (long long b = blockIdx.x; b < total; b += gridDim.x) {
+    const int g = job_of(start, ndet, b);
+    const ScoreJob& j = jobs[g];
+    score_block<IdT>(static_cast<const IdT*>(j.ids), j.ld, j.n, j.K, j.L, j.alpha, j.counts, j.sums, j.st,
+                     b - start[g], start[g + 1] - start[g]);
+    __syncthreads();  // block_fold's shared memory is reused by the next block
+  }
+}
+
+// Many detectors' flags in one launch (same block layout as score_batched_kernel).
+__global__ void __launch_bounds__(256) flags_batched_kernel(const ScoreJob* __restrict__ jobs,
+                                                            const long long* __restrict__ start, int ndet) {
+  const long long total = start[ndet];
+  for (long long b = blockIdx.x; b < total; b += gridDim.x) {
+    const int g = job_of(start, ndet, b);
+    const ScoreJob& j = jobs[g];
+    const long long i = (b - start[g]) * blockDim.x + threadIdx.x;
+    if (i >= j.n) continue;
+    const long long tb = __double_as_longlong(j.st->threshold);
+    const bool tpos = tb > 0 && tb <= 0x7ff0000000000000LL;
+    const unsigned long long sb = rn_quotient_bits(j.sums[i], j.div);
+    if (j.scores) j.scores[i] = __longlong_as_double(static_cast<long long>(sb));
+    if (j.flags) j.flags[i] = (tpos && static_cast<long long>(sb) < tb) ? 1 : 0;
   }
 }
 
@@ -273,6 +323,20 @@ __global__ void __launch_bounds__(256) delete_apply_kernel(const uint32_t* __res
 }
 
 }  // namespace
+
+cudaError_t launch_score_batched(const ScoreJob* jobs_dev, const long long* start_dev, int ndet, bool id16, int num_sms,
+                                 cudaStream_t s) {
+  const unsigned grid = static_cast<unsigned>(num_sms * 8);
+  if (id16) score_batched_kernel<uint16_t><<<grid, 256, 0, s>>>(jobs_dev, start_dev, ndet);
+  else score_batched_kernel<uint32_t><<<grid, 256, 0, s>>>(jobs_dev, start_dev, ndet);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flags_batched(const ScoreJob* jobs_dev, const long long* start_dev, int ndet, int num_sms,
+                                 cudaStream_t s) {
+  flags_batched_kernel<<<static_cast<unsigned>(num_sms * 8), 256, 0, s>>>(jobs_dev, start_dev, ndet);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_delete_check(const uint32_t* hist, const uint32_t* counts, long long total, unsigned int* flag,
                                 int num_sms, cudaStream_t s) {

@@ -22,16 +22,17 @@ constexpr int BN = 128;  // columns per CTA (at most)
 constexpr int DK = 32;   // d per staged chunk
 constexpr int NT = 256;  // threads: 16 column groups x 16 point groups, 8 x 8 outputs each
 
+// Block `blk` of one detector's hash: tile blk / ntb of 128 points, table block blk % ntb.
 template <bool BF16, typename IdT>
-__global__ void __launch_bounds__(NT, 2) hash_simt_kernel(HashArgs a, int tpb, int ntb) {
+__device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int ntb, long long blk) {
   __shared__ float Xs[BM][DK + 1];
   __shared__ __align__(16) float Ws[DK][BN];
   __shared__ uint32_t bits[BM][BN / 32];
   __shared__ uint32_t amb[BM][BN / 32];
   __shared__ float xn[BM];
 
-  const long long tile = blockIdx.x / ntb;
-  const int tb = blockIdx.x % ntb;
+  const long long tile = blk / ntb;
+  const int tb = static_cast<int>(blk % ntb);
   const int j0 = tb * tpb;
   const int ntab = min(tpb, a.L - j0);
   const int c0 = j0 * a.K;
@@ -162,7 +163,53 @@ __global__ void __launch_bounds__(NT, 2) hash_simt_kernel(HashArgs a, int tpb, i
   }
 }
 
+template <bool BF16, typename IdT>
+__global__ void __launch_bounds__(NT, 2) hash_simt_kernel(HashArgs a, int tpb, int ntb) {
+  hash_simt_block<BF16, IdT>(a, tpb, ntb, blockIdx.x);
+}
+
+// Many detectors in one launch: block index b of the whole batch belongs to detector g with
+// start[g] <= b < start[g + 1]; each detector's blocks run exactly as in its own launch.
+template <bool BF16, typename IdT>
+__global__ void __launch_bounds__(NT, 2) hash_simt_batched_kernel(const HashArgs* __restrict__ args,
+                                                                  const long long* __restrict__ start, int ndet) {
+  const long long total = start[ndet];
+  for (long long b = blockIdx.x; b < total; b += gridDim.x) {
+    int lo = 0, hi = ndet;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (start[mid] <= b) lo = mid;
+      else hi = mid;
+    }
+    const HashArgs a = args[lo];
+    const int tpb = BN / a.K;
+    const int ntb = (a.L + tpb - 1) / tpb;
+    hash_simt_block<BF16, IdT>(a, tpb, ntb, b - start[lo]);
+    __syncthreads();  // shared memory is reused by the next block
+  }
+}
+
 }  // namespace
+
+long long hash_simt_blocks(const HashArgs& a) {
+  if (a.n <= 0) return 0;
+  const int tpb = BN / a.K;
+  const int ntb = (a.L + tpb - 1) / tpb;
+  return (a.n + BM - 1) / BM * ntb;
+}
+
+cudaError_t launch_hash_simt_batched(const HashArgs* args_dev, const long long* start_dev, int ndet, bool bf16,
+                                     bool id16, int num_sms, cudaStream_t s) {
+  const unsigned grid = static_cast<unsigned>(num_sms * 2);  // two blocks per SM (registers)
+  if (bf16) {
+    if (id16) hash_simt_batched_kernel<true, uint16_t><<<grid, NT, 0, s>>>(args_dev, start_dev, ndet);
+    else hash_simt_batched_kernel<true, uint32_t><<<grid, NT, 0, s>>>(args_dev, start_dev, ndet);
+  } else {
+    if (id16) hash_simt_batched_kernel<false, uint16_t><<<grid, NT, 0, s>>>(args_dev, start_dev, ndet);
+    else hash_simt_batched_kernel<false, uint32_t><<<grid, NT, 0, s>>>(args_dev, start_dev, ndet);
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_hash_simt(const HashArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
