@@ -309,6 +309,38 @@ def serving(seed: int = 31, pool_points: int = 1 << 20, n_det: int = 64, n_req: 
     return res
 
 
+def projection_errors() -> dict:
+    """Per config and engine: max and mean of |estimate - binary64| / (||x|| ||w_c||) over a
+    sample (estimates from ace_project, binary64 from the oracle), and rechecks per point of an
+    insert_score of the same sample."""
+    import torch
+    import oracle
+    from paper_1706_06664_gb300 import ace, workloads
+    cases = [("small", workloads.small(seed=1, n=4000), ("fp32", "bf16")),
+             ("kdd-shaped", workloads.kdd(seed=2, n=20000), ("fp32", "bf16")),
+             ("high-dimensional (d=1024, bf16 input)", workloads.highdim(seed=3, n=1000), ("fp32",))]
+    out = {}
+    for name, w, precs in cases:
+        X = w["X"]
+        Xd = torch.from_numpy(X.view(np.int16) if X.dtype == np.uint16 else X).cuda()
+        Xf = workloads.bf16_bits_to_f32(X) if X.dtype == np.uint16 else X
+        res = {}
+        for prec in precs:
+            det = ace.Detector(w["d"], w["K"], w["L"], seed=5, precision=prec)
+            est = det.project(Xd).cpu().numpy().astype(np.float64)
+            W = det.projection()
+            s64 = oracle.project(X, W)
+            rel = np.abs(est - s64) / (np.linalg.norm(Xf.astype(np.float64), axis=1)[:, None] *
+                                       np.linalg.norm(W.astype(np.float64), axis=0)[None, :])
+            det.insert_score(Xd, ALPHA)
+            torch.cuda.synchronize()
+            res[prec] = {"max": float(rel.max()), "mean": float(rel.mean()),
+                         "rechecks_per_point": det.stats()["rechecks"] / X.shape[0]}
+            det.close()
+        out[f"{name}: n={X.shape[0]} d={w['d']} K={w['K']} L={w['L']}"] = res
+    return out
+
+
 def batched(n_det: int = 2048, seed: int = 4) -> dict:
     """Batched-detectors shape: 2048 detectors, d log-uniform in [16, 512], n log-uniform in
     [100, 100000], K=12, L=32, Gaussian-mixture points (8 clusters N(m_c, I), m_c ~ N(0, 4I),
@@ -451,6 +483,8 @@ def run_ours(args):
         line["serving"] = serving()
     if rank == 0 and ws == 1 and args.batched:
         line["batched"] = batched()
+    if rank == 0 and ws == 1 and args.proj_error:
+        line["projection_error"] = projection_errors()
     if rank == 0:
         print(json.dumps(line), flush=True)
     det.close()
@@ -473,6 +507,7 @@ def main():
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-serving", dest="serving", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--no-projection-error", dest="proj_error", action="store_false")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

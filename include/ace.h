@@ -227,6 +227,15 @@ int ace_host_wait(ace_handle h);
 int ace_hash(ace_handle h, const void* X_dev, int64_t n, int dtype, uint32_t* ids_dev,
              void* stream);
 
+/*
+ * ace_project — measurement of the engines' error: proj_dev[i*KL + c] = the active engine's
+ * binary32 estimate of x_i.w_c (Eq. 1 before the sign): the SIMT engine's FMA chain, or the
+ * tensor-core engine's accumulator of x.(w_c/||w_c||) multiplied by ||w_c|| (one more binary32
+ * rounding).  proj_dev is n x KL float, device, caller-owned.  No state changes (no ids, no
+ * counts, no counters).  Asynchronous on `stream`.
+ */
+int ace_project(ace_handle h, const void* X_dev, int64_t n, int dtype, float* proj_dev, void* stream);
+
 /* Synchronises `stream`, then fills *out (Q is computed from the arrays here). */
 int ace_stats(ace_handle h, void* stream, ace_stats_t* out);
 

@@ -23,7 +23,7 @@ PRECISIONS = {"auto": ACE_PROJ_AUTO, "fp32": ACE_PROJ_FP32, "bf16": ACE_PROJ_BF1
 EXPORTS = [
     "ace_create", "ace_create_with_projection", "ace_destroy", "ace_reset", "ace_set_precision",
     "ace_insert", "ace_score", "ace_insert_score", "ace_insert_score_host",
-    "ace_insert_score_host_async", "ace_host_wait", "ace_delete", "ace_hash",
+    "ace_insert_score_host_async", "ace_host_wait", "ace_delete", "ace_project", "ace_hash",
     "ace_batch_insert_score", "ace_server_create", "ace_server_submit", "ace_server_wait", "ace_server_drain", "ace_server_destroy", "ace_stats",
     "ace_get_counts", "ace_get_projection", "ace_get_shape", "ace_last_error", "ace_version",
     "ace_profile_enable", "ace_profile_read", "ace_insert_score_noalloc",
@@ -82,6 +82,7 @@ def load_library(path: str = LIB_PATH):
             "ace_insert_score_host_async": ([H, P, i64, i32, f64, P, P, P, P], i32),
             "ace_host_wait": ([H], i32),
             "ace_delete": ([H, P, i64, i32, P], i32),
+            "ace_project": ([H, P, i64, i32, P, P], i32),
             "ace_batch_insert_score": ([P, i32, P, P, i32, f64, P, P, P, P], i32),
             "ace_server_create": ([P, i32, ctypes.c_size_t, P], i32),
             "ace_server_submit": ([P, i32, i32, P, i64, i32, f64, P, P, P, P], i32),
@@ -188,6 +189,14 @@ class Detector:
     def insert(self, X, stream=None):
         self._xcheck(X)
         _check(load_library().ace_insert(self._h, _ptr(X), X.shape[0], _x_dtype(X), _stream_ptr(stream)))
+
+    def project(self, X, stream=None):
+        """The active engine's binary32 projection estimates, n x KL (a measurement hook)."""
+        self._xcheck(X)
+        torch = _torch()
+        out = torch.empty((X.shape[0], self.K * self.L), dtype=torch.float32, device=X.device)
+        _check(load_library().ace_project(self._h, _ptr(X), X.shape[0], _x_dtype(X), _ptr(out), _stream_ptr(stream)))
+        return out
 
     def delete(self, X, stream=None):
         """§3.4.1 deletion of the batch's points (all or nothing; synchronises the stream)."""

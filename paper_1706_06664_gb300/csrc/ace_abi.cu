@@ -85,6 +85,7 @@ struct ace_detector {
   size_t defer_bytes = 0;
   unsigned int* defer_counts = nullptr;  // one per CTA of the tensor-core kernel
   float* wpad = nullptr;                 // [KL][dp] W, columns contiguous, zero-padded (recheck)
+  float* wnorm = nullptr;                // [KL] ||w_c|| in binary32 (ace_project, tensor-core engine)
   uint32_t* hist = nullptr;              // [L][2^K] histogram of a batch being deleted
   unsigned int* dflag = nullptr;         // deletion check flag
   // profiling hook
@@ -144,6 +145,7 @@ void free_all(ace_detector* h) {
   cudaFree(h->defer);
   cudaFree(h->defer_counts);
   cudaFree(h->wpad);
+  cudaFree(h->wnorm);
   cudaFree(h->hist);
   cudaFree(h->dflag);
   cudaFree(h->W);
@@ -323,6 +325,16 @@ int plan_tc(ace_detector* h) {
       return cuda_fail(e, "copy padded W");
   }
   t.Wp = h->wpad;
+  {
+    std::vector<float> wn(KL);
+    for (int c = 0; c < KL; ++c) wn[c] = inv[c] > 0.0 ? static_cast<float>(1.0 / inv[c]) : 0.f;
+    cudaFree(h->wnorm);
+    h->wnorm = nullptr;
+    if ((e = cudaMalloc(&h->wnorm, KL * sizeof(float))) != cudaSuccess) return cuda_fail(e, "cudaMalloc column norms");
+    if ((e = cudaMemcpy(h->wnorm, wn.data(), KL * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cuda_fail(e, "copy column norms");
+  }
+  t.wnorm = h->wnorm;
   t.cB32 = h->cB;
   t.xfac32 = h->xfac;
   t.xabs32 = h->xabs;
@@ -1082,6 +1094,40 @@ int ace_batch_insert_score(const ace_handle* dets, int count, const void* const*
     dets[g]->n_ins += static_cast<uint64_t>(n[g]);
     dets[g]->last_precision = ACE_PROJ_FP32;
   }
+  return ACE_OK;
+}
+
+int ace_project(ace_handle h, const void* X_dev, int64_t n, int dtype, float* proj_dev, void* stream) {
+  int rc = check_x(h, X_dev, n, dtype);
+  if (rc) return rc;
+  if (n > 0 && !proj_dev) return fail(ACE_ERR_ARG, "proj_dev is NULL");
+  if (n == 0) return ACE_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ace::HashArgs a = hash_args(h, X_dev, n, dtype, ace::kStoreProj);
+  a.proj = proj_dev;
+  cudaError_t e;
+  if (h->precision == ACE_PROJ_FP32 || !h->tc_ok) {
+    e = ace::launch_hash_simt(a, s);
+  } else {
+    const size_t cap = static_cast<size_t>(n) + 65536;
+    void* p = h->defer;
+    if ((rc = grow(&p, &h->defer_bytes, cap * 8, s, "deferred list"))) return rc;
+    h->defer = static_cast<unsigned long long*>(p);
+    ace::TcArgs t = h->tc;
+    t.X = X_dev;
+    t.x_bf16 = dtype == ACE_BF16;
+    t.n = n;
+    t.ntiles = (n + 127) / 128;
+    const long long grid = std::min(static_cast<long long>(h->num_sms), t.ntiles);
+    t.mode = ace::kStoreProj;
+    t.ids = nullptr;
+    t.ids_rm = nullptr;
+    t.proj = proj_dev;
+    t.defer = h->defer;
+    t.seg_cap = h->defer_bytes / 8 / static_cast<size_t>(grid);
+    e = ace::launch_hash_tc(t, h->num_sms, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "projection launch");
   return ACE_OK;
 }
 

@@ -27,7 +27,8 @@ struct DevStats {
 enum HashMode : int {
   kStoreIds = 1,      // write ids to the table-major scratch [L][ld]
   kInsert = 2,        // increment the count arrays
-  kStoreIdsRowMajor = 4  // write uint32 ids point-major [n][L] (ace_hash)
+  kStoreIdsRowMajor = 4,  // write uint32 ids point-major [n][L] (ace_hash)
+  kStoreProj = 8          // write the engine's binary32 projection estimates [n][KL] (ace_project)
 };
 
 // Everything a hash kernel needs.  Columns c = j*K + k; W is d x KL row-major.
@@ -48,6 +49,7 @@ struct HashArgs {
   uint32_t* ids_rm;     // [n][L] uint32 (kStoreIdsRowMajor)
   uint32_t* counts;     // [L][2^K]
   DevStats* st;
+  float* proj;          // [n][KL] (kStoreProj)
 };
 
 // One detector's share of a batched query phase and flags pass.

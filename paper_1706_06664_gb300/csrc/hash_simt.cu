@@ -89,11 +89,26 @@ __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int 
   // ---- guard classification ------------------------------------------------------------
   if (threadIdx.x < BM) {
     xn[threadIdx.x] = norm_upper(q, a.xfac, a.xabs);
-    if (!isfinite(q) && tb == 0 && static_cast<int>(threadIdx.x) < npt) atomicAdd(&a.st->nonfinite, 1ull);
+    if (!isfinite(q) && tb == 0 && static_cast<int>(threadIdx.x) < npt && !(a.mode & kStoreProj))
+      atomicAdd(&a.st->nonfinite, 1ull);
   }
   for (int e = threadIdx.x; e < BM * (BN / 32); e += NT) {
     (&bits[0][0])[e] = 0u;
     (&amb[0][0])[e] = 0u;
+  }
+  if (a.mode & kStoreProj) {  // measurement path: the binary32 estimates themselves
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int p = (r < 4) ? ty * 4 + r : 64 + ty * 4 + (r - 4);
+      if (p < npt) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int col = (c >> 2) * 64 + tx * 4 + (c & 3);
+          if (col < ncol) a.proj[(i0 + p) * a.KL + c0 + col] = acc[r][c];
+        }
+      }
+    }
+    return;  // nothing else in this mode (the whole block takes this branch)
   }
   float cb[8];
 #pragma unroll

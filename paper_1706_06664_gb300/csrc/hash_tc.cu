@@ -130,7 +130,7 @@ __device__ __noinline__ uint32_t exact_table_id(const void* X, long long i, int 
 // KC > 0: the kernel is specialised for K = KC (the table offsets inside a chunk are then
 // compile-time constants and the pack is a fully unrolled, branch-free sequence); KC = 0
 // handles any K with a streaming extractor.
-template <bool BF16, typename IdT, int KC>
+template <bool BF16, typename IdT, int KC, bool PROJ = false>
 __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_constant__ TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* Bimg = smem;
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
       if (!isfinite(q) || q < qmin) B = __int_as_float(0x7f800000);
       else B = fmaf(tau, sqrtf(q * xfac) * 1.00000095367431640625f, tau_abs);
       bnd[s * 128 + r] = B;
-      if (valid && !isfinite(q)) atomicAdd(&st->nonfinite, 1ull);
+      if (valid && !isfinite(q) && !(a.mode & kStoreProj)) atomicAdd(&st->nonfinite, 1ull);
       fence_proxy_async();
       mbar_arrive(&S->a_full[s]);
       mbar_arrive(&S->bnd_full[s]);
@@ -483,6 +483,17 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
                 }
               }
             } else {
+              if constexpr (PROJ) {  // measurement path: the accumulators, scaled back by ||w_c||
+                if (valid) {
+#pragma unroll
+                  for (int k = 0; k < 32; ++k) {
+                    const int col = 32 * g + k;
+                    if (col < ncols)
+                      a.proj[i * static_cast<long long>(K * L) + tab0 * K + col] =
+                          __uint_as_float(v[k]) * a.wnorm[tab0 * K + col];
+                  }
+                }
+              }
               bool any = false;
 #pragma unroll
               for (int k = 0; k < 32; ++k) any |= (v[k] & 0x7FFFFFFFu) <= Bi;
@@ -590,6 +601,7 @@ cudaError_t launch_hash_tc(const TcArgs& a, int num_sms, cudaStream_t s) {
   };
   auto pick = [&](auto bf16_tag) -> cudaError_t {
     constexpr bool B = decltype(bf16_tag)::value;
+    if (a.mode & kStoreProj) return a.K > 16 ? go(hash_tc_kernel<B, uint32_t, 0, true>) : go(hash_tc_kernel<B, uint16_t, 0, true>);
     if (a.K > 16) return go(hash_tc_kernel<B, uint32_t, 0>);
     switch (a.K) {
       case 10: return go(hash_tc_kernel<B, uint16_t, 10>);

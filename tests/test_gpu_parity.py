@@ -374,3 +374,31 @@ def test_delete_hand_example_and_rejection(precision):
         assert st["Q"] == gd["Q_after"][step] and st["mu_ins"] == gd["mu_ins_after"][step]
     with pytest.raises(ace.AceError):
         det.delete(_dev(X))  # four points from a detector that holds two
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_projection_error_within_guard_bound(precision):
+    """ace_project: each engine's binary32 estimate of x.w_c lies within the bound its guard
+    relies on (binary32 chain: (gamma_d + gamma64_d) ||x|| ||w_c||; tensor cores: the band tau
+    of the BF16 split, the probed accumulation model and the binary64 sum), against the
+    oracle's binary64 projection; and the call changes no state."""
+    for w in (workloads.small(seed=3, n=3000), workloads.kdd(seed=4, n=4000)):
+        det = _detector(w["d"], w["K"], w["L"], seed=9, precision=precision)
+        X = w["X"]
+        est = det.project(_dev(X)).cpu().numpy().astype(np.float64)
+        torch.cuda.synchronize()
+        W = det.projection()
+        s64 = oracle.project(X, W)
+        xn = np.linalg.norm(X.astype(np.float64), axis=1)[:, None]
+        wn = np.linalg.norm(W.astype(np.float64), axis=0)[None, :]
+        rel = np.abs(est - s64) / (xn * wn)
+        d = w["d"]
+        u32, u64 = 2.0**-24, 2.0**-53
+        if precision == "fp32":
+            bound = (d * u32 / (1 - d * u32) + d * u64 / (1 - d * u64)) * 1.02
+        else:
+            d_pad = (d + 15) // 16 * 16
+            tau_acc = 5.25 * 1.5 * ((d_pad // 16 + 1) + 2 * d_pad // 16 * 2.0**-6) * 2.0**-23 * (1 + 2.0**-6)
+            bound = (3 * 2.0**-16 * (1 + 2.0**-6) + tau_acc * (1 + 2.0**-6) + 2.0**-23 + d * u64) * 1.01 + 2.0**-23
+        assert rel.max() <= bound, (precision, rel.max(), bound)
+        assert det.stats()["n_ins"] == 0 and det.stats()["rechecks"] == 0 and not det.counts().any()
