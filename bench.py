@@ -193,7 +193,7 @@ def run_reference(args):
     t0 = time.perf_counter()
     oracle.Detector(D, KH, LT, seed=7).insert_score(X[:probe], ALPHA)
     per_pt = (time.perf_counter() - t0) / probe
-    sample = int(max(1000, min(args.ref_sample, REF_BUDGET_S / max(1, args.steps) / max(per_pt, 1e-9))))
+    sample = int(max(1000, min(args.ref_sample, args.ref_budget / max(1, args.steps) / max(per_pt, 1e-9))))
     for _ in range(args.warmup):
         oracle.Detector(D, KH, LT, seed=7).insert_score(X[:max(1, sample // 10)], ALPHA)
     times = []
@@ -503,6 +503,7 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16"])
     ap.add_argument("--n", type=int, default=N_POINTS, help="points per batch (profiling runs only)")
     ap.add_argument("--ref-sample", type=int, default=100_000, help="points per reference step")
+    ap.add_argument("--ref-budget", type=float, default=REF_BUDGET_S, help="seconds of timed reference work")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-serving", dest="serving", action="store_false")
