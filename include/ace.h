@@ -85,6 +85,8 @@ typedef struct {
   uint64_t nonfinite_points;/* points with a NaN/Inf coordinate or an overflowing norm   */
   uint32_t status;          /* ACE_STATUS_* bits                                         */
   int32_t precision;        /* ACE_PROJ_* path used by the last hash                     */
+  uint64_t deferred;        /* (point, table) pairs the tensor-core engine left to exact */
+                            /* resolution (inside its error bound); 0 on the SIMT engine */
 } ace_stats_t;
 
 /*

@@ -46,7 +46,7 @@ class ace_stats_t(ctypes.Structure):
         ("S2_lo", ctypes.c_uint64), ("S2_hi", ctypes.c_uint64),
         ("mu_ins", ctypes.c_double), ("mu", ctypes.c_double), ("sigma", ctypes.c_double),
         ("rechecks", ctypes.c_uint64), ("nonfinite_points", ctypes.c_uint64),
-        ("status", ctypes.c_uint32), ("precision", ctypes.c_int32),
+        ("status", ctypes.c_uint32), ("precision", ctypes.c_int32), ("deferred", ctypes.c_uint64),
     ]
 
 
@@ -289,6 +289,7 @@ class Detector:
             "Q": st.Q_lo | (st.Q_hi << 64), "S1": st.S1_lo | (st.S1_hi << 64), "S2": st.S2_lo | (st.S2_hi << 64),
             "mu_ins": st.mu_ins, "mu": st.mu, "sigma": st.sigma, "rechecks": st.rechecks,
             "nonfinite_points": st.nonfinite_points, "status": st.status, "precision": st.precision,
+            "deferred": st.deferred,
         }
 
     def counts(self, stream=None) -> np.ndarray:

@@ -88,6 +88,10 @@ struct ace_detector {
   float* wnorm = nullptr;                // [KL] ||w_c|| in binary32 (ace_project, tensor-core engine)
   uint32_t* hist = nullptr;              // [L][2^K] histogram of a batch being deleted
   unsigned int* dflag = nullptr;         // deletion check flag
+  // insert path of the tensor-core engine: the deferred tables are resolved (and counted) on
+  // rstream while the insert pass runs on the caller's stream
+  cudaStream_t rstream = nullptr;
+  cudaEvent_t ev_hashed = nullptr, ev_resolved = nullptr;
   // profiling hook
   bool prof = false;
   uint64_t launches[ACE_NPHASE] = {0, 0, 0, 0, 0, 0};
@@ -134,6 +138,9 @@ struct PhaseScope {
 size_t count_elems(const ace_detector* h) { return (static_cast<size_t>(1) << h->K) * static_cast<size_t>(h->L); }
 
 void free_all(ace_detector* h) {
+  if (h->ev_hashed) cudaEventDestroy(h->ev_hashed);
+  if (h->ev_resolved) cudaEventDestroy(h->ev_resolved);
+  if (h->rstream) cudaStreamDestroy(h->rstream);
   for (auto& m : h->marks) {
     cudaEventDestroy(m.a);
     cudaEventDestroy(m.b);
@@ -310,6 +317,20 @@ int plan_tc(ace_detector* h) {
   t.dot2c = std::nextafter(static_cast<float>((g32d * g32d + g64) * (1.0 + u32) / ((1.0 - u32) * (1.0 - g32d)) * 1.01),
                            FLT_MAX);
   t.dot2abs = static_cast<float>(4.0 * d * std::ldexp(1.0, -149));
+  // Running error bound of the recheck's binary32 FMA chain over dp steps (zero padding
+  // included): each step s^_k = RN(s^_(k-1) + x_k w_k) is off by at most u |s^_k| / (1 - u)
+  // plus 2^-150 below 2^-126, so |s^ - s| <= u / (1 - u) sum_k |s^_k| + dp 2^-150 / (1 - u);
+  // the binary32 sum R^ of the |s^_k| has sum_k |s^_k| <= R^ / (1 - gamma_dp).  The binary64
+  // definition's own error, gamma64_d sum|x_i w_i| <= gamma64_d ||x|| ||w_c||, is a multiple of
+  // the a priori coefficient cB32[c] = 1.02 (gamma_d + gamma64_d) ||w_c||^.
+  {
+    const int dp = (d + 3) / 4 * 4;
+    const double g32p = dp * u32 / (1.0 - dp * u32);
+    const double g32a = d * u32 / (1.0 - d * u32);
+    t.runc = std::nextafter(static_cast<float>(u32 / ((1.0 - u32) * (1.0 - g32p)) * 1.01), FLT_MAX);
+    t.run64 = std::nextafter(static_cast<float>(g64 / (1.02 * (g32a + g64)) * 1.01), FLT_MAX);
+    t.runabs = static_cast<float>(std::ldexp(static_cast<double>(dp), -149));
+  }
   t.Wt = h->Wt;
   t.W = h->W;
   // W with contiguous, zero-padded columns for the recheck's 16-byte loads
@@ -408,7 +429,12 @@ int make_detector(int d, int K, int L, const float* Wsrc, uint64_t seed, bool fr
     delete h;
     return rc;
   }
-  if (h->tc_ok) h->precision = ACE_PROJ_AUTO;
+  if (h->tc_ok) {
+    if ((e = cudaStreamCreateWithFlags(&h->rstream, cudaStreamNonBlocking)) != cudaSuccess) return bad(e, "recheck stream");
+    if ((e = cudaEventCreateWithFlags(&h->ev_hashed, cudaEventDisableTiming)) != cudaSuccess) return bad(e, "event");
+    if ((e = cudaEventCreateWithFlags(&h->ev_resolved, cudaEventDisableTiming)) != cudaSuccess) return bad(e, "event");
+    h->precision = ACE_PROJ_AUTO;
+  }
   *out = h;
   return ACE_OK;
 }
@@ -484,8 +510,11 @@ int run_hash(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_inser
     return ACE_OK;
   }
   // tensor-core engine (ids only), the binary64 resolution of the deferred tables, then the
-  // count increments from the stored ids
+  // count increments from the stored ids.  With 16-bit ids and K <= 15 the deferred tables are
+  // tagged (kTagDeferred): their resolution, which counts them too, runs on rstream while the
+  // insert pass counts the rest; the caller's stream joins it before anything reads the ids.
   const bool insert = (a.mode & ace::kInsert) != 0;
+  const bool overlap = insert && tc_insert && h->K <= 15 && !a.ids_rm && h->rstream;
   void* ids = a.ids;
   if (insert && !ids) {
     if (int rc = grow(&h->ids, &h->ids_cap, static_cast<size_t>(a.n) * h->L * id_bytes(h), s, "ids scratch"))
@@ -502,7 +531,7 @@ int run_hash(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_inser
   t.n = a.n;
   t.ntiles = (a.n + 127) / 128;
   const long long grid = std::min(static_cast<long long>(h->num_sms), t.ntiles);
-  t.mode = (a.mode & ~ace::kInsert) | (insert ? ace::kStoreIds : 0);
+  t.mode = (a.mode & ~ace::kInsert) | (insert ? ace::kStoreIds : 0) | (overlap ? ace::kTagDeferred : 0);
   t.ids = ids;
   t.ld = a.ld;
   t.ids_rm = a.ids_rm;
@@ -515,6 +544,23 @@ int run_hash(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_inser
     e = ace::launch_hash_tc(t, h->num_sms, s);
   }
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core hash kernel launch");
+  if (overlap) {
+    ACE_CUDA(cudaEventRecord(h->ev_hashed, s));
+    {
+      PhaseScope ps(h, ACE_PHASE_INSERT, s);  // launched first: its blocks need the most shared memory
+      e = ace::launch_insert_from_ids(ids, 1, a.ld, a.n, h->K, h->L, h->counts, h->num_sms, s);
+      if (e != cudaSuccess) return cuda_fail(e, "insert kernel launch");
+    }
+    ACE_CUDA(cudaStreamWaitEvent(h->rstream, h->ev_hashed, 0));
+    {
+      PhaseScope ps(h, ACE_PHASE_RECHECK, h->rstream);
+      e = ace::launch_recheck(t, h->num_sms, h->rstream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "recheck kernel launch");
+    ACE_CUDA(cudaEventRecord(h->ev_resolved, h->rstream));
+    ACE_CUDA(cudaStreamWaitEvent(s, h->ev_resolved, 0));
+    return ACE_OK;
+  }
   {
     PhaseScope ps(h, ACE_PHASE_RECHECK, s);
     e = ace::launch_recheck(t, h->num_sms, s);
@@ -1178,6 +1224,7 @@ int ace_stats(ace_handle h, void* stream, ace_stats_t* out) {
   }
   out->rechecks = st.rechecks;
   out->nonfinite_points = st.nonfinite;
+  out->deferred = st.deferred;
   out->status = st.status;
   out->precision = h->last_precision;
   return ACE_OK;

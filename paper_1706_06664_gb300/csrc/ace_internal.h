@@ -19,6 +19,7 @@ struct DevStats {
   unsigned long long Q[2];       // scratch for ace_stats: sum of count^2
   unsigned long long rechecks;   // binary64 recomputations
   unsigned long long nonfinite;  // points with a non-finite squared norm
+  unsigned long long deferred;   // (point, table) pairs the tensor-core engine deferred
   unsigned int status;           // ACE_STATUS_* bits
   unsigned int done;             // blocks of the running score kernel that have folded (reset by its last)
   double mu, sigma, threshold;
@@ -28,7 +29,12 @@ enum HashMode : int {
   kStoreIds = 1,      // write ids to the table-major scratch [L][ld]
   kInsert = 2,        // increment the count arrays
   kStoreIdsRowMajor = 4,  // write uint32 ids point-major [n][L] (ace_hash)
-  kStoreProj = 8          // write the engine's binary32 projection estimates [n][KL] (ace_project)
+  kStoreProj = 8,         // write the engine's binary32 projection estimates [n][KL] (ace_project)
+  // Tensor-core engine, 16-bit ids, K <= 15: a deferred table's id is stored with bit 15 set
+  // (a value no count range holds, so the insert pass skips it), and the recheck kernel stores
+  // the resolved id, still tagged, and increments its count itself.  The insert pass can then
+  // run while the deferred tables are resolved; the score gather masks the tag off.
+  kTagDeferred = 16
 };
 
 // Everything a hash kernel needs.  Columns c = j*K + k; W is d x KL row-major.

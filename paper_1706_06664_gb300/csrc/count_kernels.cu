@@ -117,9 +117,10 @@ __device__ __forceinline__ void score_block(const IdT* __restrict__ ids, long lo
   unsigned long long c = 0;
   if (i < n) {
     const IdT* col = ids + i;
+    const uint32_t kmask = (1u << K) - 1u;  // drops the deferred-table tag (16-bit ids, K <= 15)
 #pragma unroll 10
     for (int j = 0; j < L; ++j) {
-      const uint32_t id = col[static_cast<size_t>(j) * ld];
+      const uint32_t id = col[static_cast<size_t>(j) * ld] & kmask;
       c += __ldg(counts + (static_cast<size_t>(j) << K) + id);
     }
     if (c > 0xFFFFFFFFull) atomicOr(&st->status, static_cast<unsigned>(ACE_STATUS_SUM_OVERFLOW));

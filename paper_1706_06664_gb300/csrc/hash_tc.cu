@@ -397,6 +397,7 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
     const int K = KC > 0 ? KC : a.K;
     const int L = a.L, mode = a.mode, nch = a.nchunks, d = a.d;
     const bool st_tm = (mode & kStoreIds) != 0, st_rm = (mode & kStoreIdsRowMajor) != 0;
+    const uint32_t tag = (mode & kTagDeferred) ? 0x8000u : 0u;  // 16-bit ids only
     const int tpc = min(kBufCols / K, 32);  // tables per chunk (the host plans chunks the same way)
     const long long n = a.n, ld = a.ld;
     IdT* const ids = reinterpret_cast<IdT*>(a.ids);
@@ -443,26 +444,32 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
         // column inside the bound (|projection| <= B, compared on bit patterns: both are
         // non-negative floats; Bi = all ones for a row whose bound is +inf, so that row is
         // deferred whatever the minimum, NaN included) is deferred whole to the recheck
-        // kernel.  The next 32 columns are loaded from TMEM while the current ones are
-        // classified; signs are packed by four independent funnel-shift chains.
+        // kernel.  Columns come from TMEM 64 at a time, each load waited for at once: fewer,
+        // larger loads measured faster than double-buffered 32-column loads, and overlapping
+        // the loads with the classification (or handing the buffer back before the last
+        // columns are classified) measured no faster.  Signs are packed by four independent
+        // funnel-shift chains.
         const uint32_t Bi = isinf(B) ? 0xFFFFFFFFu : __float_as_uint(B);
         constexpr int NG = kBufCols / 32;  // 32-column groups of a buffer
         uint32_t bw[NG];
-        uint32_t va[32], vb[32];
         uint32_t defmask = 0u;  // bit t: table t of the chunk has a column inside the bound
         constexpr int TPC = KC > 0 ? kBufCols / KC : 1;
         float tmin[TPC];  // per table: smallest |projection| (a min with |.| operands)
         uint32_t aw[NG];
-        tmem_ld32(tbase, va);
+        uint32_t v64[64];
+        // Pairs of groups: a pair past the chunk's last column is skipped, and a pair's second
+        // group past it is classified too (those bits and minima are never read).
 #pragma unroll
-        for (int g = 0; g < NG; ++g) {
-          bw[g] = 0u;
-          aw[g] = 0u;
-          if (g < ng) {
-            uint32_t(&v)[32] = (g & 1) ? vb : va;
-            uint32_t(&nx)[32] = (g & 1) ? va : vb;
-            tmem_ld_wait(v);
-            if (g + 1 < ng) tmem_ld32(tbase + 32u * (g + 1), nx);
+        for (int h = 0; h < NG / 2; ++h) {
+          bw[2 * h] = bw[2 * h + 1] = 0u;
+          aw[2 * h] = aw[2 * h + 1] = 0u;
+          if (2 * h >= ng) continue;
+          tmem_ld64(tbase + 64u * h, v64);
+          tmem_ld_wait(v64);
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int g = 2 * h + q;
+            const uint32_t* v = v64 + 32 * q;
             uint32_t c0 = 0u, c1 = 0u, c2 = 0u, c3 = 0u;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
@@ -562,7 +569,9 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
           if (!valid) defmask = 0u;
         }
         // append the deferred (point, table) pairs to this CTA's segment (one shared-memory
-        // atomic per row that has any); beyond the segment's capacity, resolve them here
+        // atomic per row that has any) and, with kTagDeferred, replace their stored ids by the
+        // tag; beyond the segment's capacity, resolve them here (untagged: counted by the insert
+        // pass)
         if (__any_sync(0xFFFFFFFFu, defmask != 0u) && defmask != 0u) {
           unsigned int idx = atomicAdd(&S->ndef, static_cast<unsigned int>(__popc(defmask)));
           uint32_t dm = defmask;
@@ -570,8 +579,10 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
             const int t = __ffs(dm) - 1;
             dm &= dm - 1u;
             const int j = tab0 + t;
-            if (idx < seg_cap) seg[idx] = (static_cast<unsigned long long>(i) << 24) | static_cast<unsigned long long>(j);
-            else store(exact_table_id<BF16>(X, i, d, K, j, Wt, cB32, xfac32, xabs32, babs32, st), j);
+            if (idx < seg_cap) {
+              seg[idx] = (static_cast<unsigned long long>(i) << 24) | static_cast<unsigned long long>(j);
+              if (tag) ids[static_cast<size_t>(j) * ld + i] = static_cast<IdT>(tag);
+            } else store(exact_table_id<BF16>(X, i, d, K, j, Wt, cB32, xfac32, xabs32, babs32, st), j);
             ++idx;
           }
         }
@@ -581,7 +592,10 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(const __grid_const
 
   tc_fence_before();
   __syncthreads();
-  if (tid == 0) a.defer_counts[blockIdx.x] = static_cast<unsigned int>(min(static_cast<unsigned long long>(S->ndef), a.seg_cap));
+  if (tid == 0) {
+    a.defer_counts[blockIdx.x] = static_cast<unsigned int>(min(static_cast<unsigned long long>(S->ndef), a.seg_cap));
+    if (S->ndef) atomicAdd(&a.st->deferred, static_cast<unsigned long long>(S->ndef));
+  }
   if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tmem, 512);

@@ -8,12 +8,15 @@ namespace ace {
 namespace {
 
 // Resolves the deferred (point, table) pairs: lane k of an entry's lane group recomputes
-// column j K + k as a binary32 FMA chain in index order and decides its bit with the SIMT
-// engine's rigorous bound (|s32 - s| <= gamma_d sum|x_i w_i| + d 2^-150, folded into
-// cB32[c] ||x||_up + babs32); a bit inside that bound goes to the Dot2 filter, and only what
-// Dot2 cannot decide is evaluated in binary64, index order (the definition).  GB300 issues
-// binary64 FMAs at a small fraction of the binary32 rate, so the filter keeps that path to
-// exact ties.  The id is the ballot of the lanes' bits.
+// column j K + k as a binary32 FMA chain in index order and decides its bit with the smaller
+// of two rigorous bounds on its distance from the binary64 definition: the SIMT engine's a
+// priori bound (gamma_d sum|x_i w_i| + d 2^-150, folded into cB32[c] ||x||_up + babs32) and the
+// chain's running error bound (u / (1 - u) times the sum of the partial sums' magnitudes,
+// accumulated alongside, plus the binary64 sum's own error), which is several times tighter
+// where the sum crosses zero -- exactly the deferred columns.  A bit inside both goes to the
+// Dot2 filter, and only what Dot2 cannot decide is evaluated in binary64, index order (the
+// definition).  GB300 issues binary64 FMAs at a small fraction of the binary32 rate, so the
+// filters keep that path to exact ties.  The id is the ballot of the lanes' bits.
 template <bool BF16, typename IdT>
 __global__ void __launch_bounds__(256) recheck_kernel(const __grid_constant__ TcArgs a, int nseg) {
   // Entries live in nseg per-CTA segments of the deferred list; warp gw works on segment
@@ -28,6 +31,7 @@ __global__ void __launch_bounds__(256) recheck_kernel(const __grid_constant__ Tc
   const float* const cB32 = a.cB32;
   const float xfac32 = a.xfac32, xabs32 = a.xabs32, babs32 = a.babs32;
   const float dot2c = a.dot2c, dot2abs = a.dot2abs;
+  const float runc = a.runc, run64 = a.run64, runabs = a.runabs;
   IdT* const ids = reinterpret_cast<IdT*>(a.ids);
   uint32_t* const ids_rm = a.ids_rm;
   const uint32_t kmask = (1u << K) - 1u;
@@ -90,19 +94,25 @@ __global__ void __launch_bounds__(256) recheck_kernel(const __grid_constant__ Tc
     // memory and the column of W with 16-byte loads
     const float4* wq = reinterpret_cast<const float4*>(Wp + static_cast<size_t>(col) * dp);
     const float4* xq = reinterpret_cast<const float4*>(xe);
-    float s32 = 0.f;
+    float s32 = 0.f, run = 0.f;  // run: binary32 sum of |partial sums|
 #pragma unroll 4
     for (int t4 = 0; t4 < dp / 4; ++t4) {
       const float4 w = __ldg(wq + t4);
       const float4 x = xq[t4];
       s32 = fmaf(x.x, w.x, s32);
+      run = __fadd_rn(run, fabsf(s32));
       s32 = fmaf(x.y, w.y, s32);
+      run = __fadd_rn(run, fabsf(s32));
       s32 = fmaf(x.z, w.z, s32);
+      run = __fadd_rn(run, fabsf(s32));
       s32 = fmaf(x.w, w.w, s32);
+      run = __fadd_rn(run, fabsf(s32));
     }
     bool bit = false;
     if (has && sl < K) {
-      if (fabsf(s32) > fmaf(__ldg(cB32 + col), xu, babs32)) {
+      const float cb = __ldg(cB32 + col);
+      const float brun = __fmaf_ru(runc, run, __fmaf_ru(__fmul_ru(run64, cb), xu, runabs));
+      if (fabsf(s32) > fminf(fmaf(cb, xu, babs32), brun)) {
         bit = s32 > 0.f;
       } else {
         const int sg = dot2_sign<BF16>(X, i, d, Wp + static_cast<size_t>(col) * dp, 1, dot2c, dot2abs);
@@ -112,7 +122,12 @@ __global__ void __launch_bounds__(256) recheck_kernel(const __grid_constant__ Tc
     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, bit);
     const uint32_t id = (bal >> (sub * width)) & kmask;
     if (has && sl == 0) {
-      if (mode & kStoreIds) ids[static_cast<size_t>(j) * ld + i] = static_cast<IdT>(id);
+      if (mode & kTagDeferred) {  // the insert pass skips this table: count it here
+        ids[static_cast<size_t>(j) * ld + i] = static_cast<IdT>(id | 0x8000u);
+        atomicAdd(a.counts + (static_cast<size_t>(j) << K) + id, 1u);
+      } else if (mode & kStoreIds) {
+        ids[static_cast<size_t>(j) * ld + i] = static_cast<IdT>(id);
+      }
       if (mode & kStoreIdsRowMajor) ids_rm[i * L + j] = id;
       nre += static_cast<unsigned long long>(K);
     }

@@ -42,6 +42,7 @@ struct TcArgs {
   const float* cB32;                // SIMT-engine guard coefficients per column
   float xfac32, xabs32, babs32;     // SIMT-engine norm inflation and absolute allowances
   float dot2c, dot2abs;             // Dot2 filter: bound = dot2c * sum|x_i w_i|^ + dot2abs
+  float runc, run64, runabs;        // recheck running bound: runc * R^ + run64 * cB32[c] * ||x||^ + runabs
   float* proj;                      // [n][KL] estimates x.w_c (measurement path, kStoreProj)
   const float* wnorm;               // [KL] ||w_c|| (binary32), to scale x.w'_c back to x.w_c
   unsigned long long* defer;         // (point << 24 | table) per deferred pair; one segment per CTA
