@@ -183,6 +183,87 @@ def cpu_baseline(X: np.ndarray, detector_seed: int, budget_s: float = 12.0) -> d
                       f"({dt:.1f} s, binary64 C oracle, OpenMP over points)"}
 
 
+def _config_cases():
+    """C1, C2 at full size and C3's shape at n = 100,000 (its generator costs about a second per
+    10,000 rows on the host; the d = 1024 projection is compute-bound, so the rate per point
+    does not depend on n at this size)."""
+    from paper_1706_06664_gb300 import workloads
+    return [("small", workloads.small(seed=1)), ("kdd-shaped", workloads.kdd(seed=2)),
+            ("high-dimensional (n=100,000 of 1,000,000)", workloads.highdim(seed=3, n=100_000))]
+
+
+def oracle_per_config(cases, budget_s: float = 1.5) -> dict:
+    """The CPU oracle's insert+score rate per config, on all host cores and on one core:
+    insert_score on a fresh detector over a prefix of the config's batch sized to about
+    budget_s seconds (a 200-point probe sets the size)."""
+    import oracle
+    out = {}
+    all_cores = oracle.num_threads()
+    try:
+        for name, w in cases:
+            X = w["X"]
+            res = {}
+            for cores in (all_cores, 1):
+                oracle.set_num_threads(cores)
+                probe = min(200, X.shape[0])
+                t0 = time.perf_counter()
+                oracle.Detector(w["d"], w["K"], w["L"], seed=11).insert_score(X[:probe], ALPHA)
+                per_pt = (time.perf_counter() - t0) / probe
+                m = int(min(X.shape[0], max(probe, budget_s / max(per_pt, 1e-9))))
+                ref = oracle.Detector(w["d"], w["K"], w["L"], seed=11)
+                t0 = time.perf_counter()
+                ref.insert_score(X[:m], ALPHA)
+                dt = time.perf_counter() - t0
+                res[f"{cores}_cores"] = {"points_per_s": m / dt, "sample_points": m}
+            out[name] = res
+    finally:
+        oracle.set_num_threads(all_cores)
+    return out
+
+
+def per_config(cases) -> dict:
+    """insert+score points/s per config on each engine it runs on, against the plain binary32
+    (FP32) engine: CUDA events on the launching stream around each call, median of 10 calls
+    after 3 warm-up calls on one detector per engine, the batch resident in HBM.  The batched
+    (C4) and streaming (C5) configs have sections of their own."""
+    import torch
+    from paper_1706_06664_gb300 import ace
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, w in cases:
+        X = w["X"]
+        Xd = torch.from_numpy(X.view(np.int16) if X.dtype == np.uint16 else X).cuda()
+        n = X.shape[0]
+        flop = 2.0 * n * w["d"] * w["K"] * w["L"]
+        res = {"n": n, "d": w["d"], "K": w["K"], "L": w["L"]}
+        for prec, want in (("fp32", ace.ACE_PROJ_FP32), ("bf16", ace.ACE_PROJ_BF16)):
+            try:
+                det = ace.Detector(w["d"], w["K"], w["L"], seed=11, precision=prec)
+            except ace.AceError as e:
+                if e.code == ace.ACE_ERR_UNSUPPORTED:
+                    res[prec] = "engine not available for this shape"
+                    continue
+                raise
+            times = []
+            for r in range(13):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                det.insert_score(Xd, ALPHA, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if r >= 3:
+                    times.append(e0.elapsed_time(e1) / 1e3)
+            assert det.stats()["precision"] == want
+            det.close()
+            t = statistics.median(times)
+            res[prec] = {"points_per_s": n / t, "ms": t * 1e3, "projection_tflops": flop / t / 1e12}
+        if isinstance(res.get("bf16"), dict):
+            res["bf16_vs_fp32"] = res["bf16"]["points_per_s"] / res["fp32"]["points_per_s"]
+        out[name] = res
+        del Xd
+    return out
+
+
 def run_reference(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return 0  # the CPU oracle runs on rank 0 only
@@ -492,8 +573,13 @@ def run_ours(args):
         "gpu_launches": int(sum(v["launches"] for v in prof.values())),
         "clocks": ck,
     }
+    cases = _config_cases() if rank == 0 and ws == 1 and (args.per_config or args.cpu_baseline) else None
+    if rank == 0 and ws == 1 and args.per_config:
+        line["per_config"] = per_config(cases)
     if rank == 0 and args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(host_batches[0], seed)
+        if cases is not None:
+            line["cpu_baseline"]["per_config"] = oracle_per_config(cases)
     if rank == 0 and ws == 1 and args.serving:
         line["serving"] = serving_isolated()
     if rank == 0 and ws == 1 and args.batched:
@@ -524,6 +610,7 @@ def main():
     ap.add_argument("--no-serving", dest="serving", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-projection-error", dest="proj_error", action="store_false")
+    ap.add_argument("--no-per-config", dest="per_config", action="store_false")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -52,6 +52,7 @@ struct ace_detector {
   float* Wt = nullptr;      // [KL][d]
   float* cB = nullptr;      // [KL]
   float xfac = 1.f, xabs = 0.f, babs = 0.f;
+  float dot2c = 0.f, dot2abs = 0.f;  // Dot2 filter constants for this d
   uint32_t* counts = nullptr;  // [L][2^K]
   ace::DevStats* st = nullptr;
   void* ids = nullptr;
@@ -176,7 +177,7 @@ void free_all(ace_detector* h) {
 // Guard constants of the binary32 paths (see hash_simt.cu): both gammas, ||w_c|| rounded
 // up, and a 2% margin that covers the few binary32 roundings of the bound itself.
 void guard_constants(const std::vector<float>& W, int d, int KL, std::vector<float>& cB, float& xfac, float& xabs,
-                     float& babs) {
+                     float& babs, float& dot2c, float& dot2abs) {
   const double u32 = std::ldexp(1.0, -24), u64 = std::ldexp(1.0, -53);
   const double g32 = d * u32 / (1.0 - d * u32);
   const double g64 = d * u64 / (1.0 - d * u64);
@@ -196,6 +197,12 @@ void guard_constants(const std::vector<float>& W, int d, int KL, std::vector<flo
   babs = static_cast<float>(std::ldexp(static_cast<double>(d), -148));
   if (xabs == 0.f) xabs = std::ldexp(1.0f, -149);
   if (babs == 0.f) babs = std::ldexp(1.0f, -148);
+  // Dot2 filter: (gamma_d^2 + gamma64_d) (1 + u) sum|x_i w_i|, with sum|x_i w_i| <=
+  // a / ((1 - u)(1 - gamma_d)) for the binary32 sum a of the rounded |products|; underflow
+  // (each product error and each sum below 2^-126 off by at most 2^-150) in dot2abs.
+  dot2c = std::nextafter(static_cast<float>((g32 * g32 + g64) * (1.0 + u32) / ((1.0 - u32) * (1.0 - g32)) * 1.01),
+                         FLT_MAX);
+  dot2abs = static_cast<float>(4.0 * d * std::ldexp(1.0, -149));
 }
 
 uint16_t bf16_rn(float f) {  // round to nearest even (finite inputs)
@@ -310,13 +317,8 @@ int plan_tc(ace_detector* h) {
   const double g32 = d_pad * u32 / (1.0 - d_pad * u32);
   t.xfac = std::nextafter(static_cast<float>(1.0 + 2.0 * g32 + std::ldexp(1.0, -20)), FLT_MAX);
   t.qmin = std::ldexp(1.0f, -60);
-  // Dot2 filter: (gamma_d^2 + gamma64_d) (1 + u) sum|x_i w_i|, with sum|x_i w_i| <=
-  // a / ((1 - u)(1 - gamma_d)) for the binary32 sum a of the rounded |products|; underflow
-  // (each product error and each sum below 2^-126 off by at most 2^-150) in dot2abs.
-  const double g32d = d * u32 / (1.0 - d * u32);
-  t.dot2c = std::nextafter(static_cast<float>((g32d * g32d + g64) * (1.0 + u32) / ((1.0 - u32) * (1.0 - g32d)) * 1.01),
-                           FLT_MAX);
-  t.dot2abs = static_cast<float>(4.0 * d * std::ldexp(1.0, -149));
+  t.dot2c = h->dot2c;  // the Dot2 filter's constants depend on d only (guard_constants)
+  t.dot2abs = h->dot2abs;
   // Running error bound of the recheck's binary32 FMA chain over dp steps (zero padding
   // included): each step s^_k = RN(s^_(k-1) + x_k w_k) is off by at most u |s^_k| / (1 - u)
   // plus 2^-150 below 2^-126, so |s^ - s| <= u / (1 - u) sum_k |s^_k| + dp 2^-150 / (1 - u);
@@ -402,7 +404,7 @@ int make_detector(int d, int K, int L, const float* Wsrc, uint64_t seed, bool fr
   std::vector<float> Wt(dkl), cB;
   for (int i = 0; i < d; ++i)
     for (int c = 0; c < h->KL; ++c) Wt[static_cast<size_t>(c) * d + i] = h->Wh[static_cast<size_t>(i) * h->KL + c];
-  guard_constants(h->Wh, d, h->KL, cB, h->xfac, h->xabs, h->babs);
+  guard_constants(h->Wh, d, h->KL, cB, h->xfac, h->xabs, h->babs, h->dot2c, h->dot2abs);
 
   auto bad = [&](cudaError_t err, const char* what) {
     free_all(h);
@@ -487,6 +489,8 @@ ace::HashArgs hash_args(ace_handle h, const void* X, long long n, int dtype, int
   a.xfac = h->xfac;
   a.xabs = h->xabs;
   a.babs = h->babs;
+  a.dot2c = h->dot2c;
+  a.dot2abs = h->dot2abs;
   a.mode = mode;
   a.ids = h->ids;
   a.ld = n;

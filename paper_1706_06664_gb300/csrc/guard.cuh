@@ -28,7 +28,8 @@ __device__ __noinline__ bool exact_bit(const void* X, long long i, int d, const 
   const long long base = i * static_cast<long long>(d);
   const float* w = Wt + static_cast<size_t>(col) * static_cast<size_t>(d);
   double s = 0.0;
-  for (int k = 0; k < d; ++k)
+#pragma unroll 8
+  for (int k = 0; k < d; ++k)  // unrolled so that the loads run ahead; the order of the sum is kept
     s = fma(static_cast<double>(load_x<BF16>(X, base + k)), static_cast<double>(__ldg(w + k)), s);
   return s > 0.0;
 }

@@ -11,7 +11,10 @@
 // and the binary64 reference satisfies |s64 - s| <= gamma64_d sum_i |x_i w_i|.  With
 // sum |x_i w_i| <= ||x|| ||w_c||, the host folds both gammas, ||w_c|| and a 2% margin into
 // cB[c]; when |s32| > cB[c] * ||x||_up + babs the sign of s32 is the sign of s64 (and s64
-// is non-zero); otherwise the bit is recomputed exactly in binary64.
+// is non-zero); otherwise the Dot2 filter (guard.cuh) decides the bit, and the binary64
+// definition only what Dot2 cannot (exact ties, NaN, overflow).  At d = 1024 about 1.6
+// columns per point land inside the binary32 bound; a binary64 chain of 1024 dependent FMAs
+// per such column cost four times the projection itself on GB300.
 #include "guard.cuh"
 
 namespace ace {
@@ -159,7 +162,9 @@ __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int 
       while (m) {
         const int k = __ffs(m) - 1;
         m &= m - 1u;
-        if (exact_bit<BF16>(a.X, i, a.d, a.Wt, c0 + cbit + k)) id |= 1u << k;
+        const int col = c0 + cbit + k;
+        const int sg = dot2_sign<BF16>(a.X, i, a.d, a.Wt + static_cast<size_t>(col) * a.d, 1, a.dot2c, a.dot2abs);
+        if (sg != 0 ? sg > 0 : exact_bit<BF16>(a.X, i, a.d, a.Wt, col)) id |= 1u << k;
         ++nre;
       }
       atomicAdd(&a.st->rechecks, nre);
