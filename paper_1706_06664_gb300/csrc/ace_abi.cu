@@ -53,6 +53,7 @@ struct ace_detector {
   float* cB = nullptr;      // [KL]
   float xfac = 1.f, xabs = 0.f, babs = 0.f;
   float dot2c = 0.f, dot2abs = 0.f;  // Dot2 filter constants for this d
+  float runc = 0.f, run64 = 0.f, runabs = 0.f;  // the SIMT engine's warp recheck (running bound)
   uint32_t* counts = nullptr;  // [L][2^K]
   ace::DevStats* st = nullptr;
   void* ids = nullptr;
@@ -177,7 +178,7 @@ void free_all(ace_detector* h) {
 // Guard constants of the binary32 paths (see hash_simt.cu): both gammas, ||w_c|| rounded
 // up, and a 2% margin that covers the few binary32 roundings of the bound itself.
 void guard_constants(const std::vector<float>& W, int d, int KL, std::vector<float>& cB, float& xfac, float& xabs,
-                     float& babs, float& dot2c, float& dot2abs) {
+                     float& babs, float& dot2c, float& dot2abs, float& runc, float& run64, float& runabs) {
   const double u32 = std::ldexp(1.0, -24), u64 = std::ldexp(1.0, -53);
   const double g32 = d * u32 / (1.0 - d * u32);
   const double g64 = d * u64 / (1.0 - d * u64);
@@ -203,6 +204,15 @@ void guard_constants(const std::vector<float>& W, int d, int KL, std::vector<flo
   dot2c = std::nextafter(static_cast<float>((g32 * g32 + g64) * (1.0 + u32) / ((1.0 - u32) * (1.0 - g32)) * 1.01),
                          FLT_MAX);
   dot2abs = static_cast<float>(4.0 * d * std::ldexp(1.0, -149));
+  // Running error bound of the SIMT engine's warp recheck: d FMAs spread over 32 lane chains
+  // and 31 additions joining them, each rounding step r^ = RN(r) off by at most u |r^| / (1 - u)
+  // plus 2^-150 below 2^-126; the binary32 tree sum R^ of the d + 31 terms |r^| has
+  // sum |r^| <= R^ / (1 - gamma_(d+64)) (generous: no term passes through more additions).  The
+  // binary64 definition's own error, gamma64_d ||x|| ||w_c||, is a multiple of cB[c].
+  const double gr = (d + 64) * u32 / (1.0 - (d + 64) * u32);
+  runc = std::nextafter(static_cast<float>(u32 / ((1.0 - u32) * (1.0 - gr)) * 1.01), FLT_MAX);
+  run64 = std::nextafter(static_cast<float>(g64 / (1.02 * (g32 + g64)) * 1.01), FLT_MAX);
+  runabs = static_cast<float>(std::ldexp(static_cast<double>(d + 31), -149));
 }
 
 uint16_t bf16_rn(float f) {  // round to nearest even (finite inputs)
@@ -404,7 +414,8 @@ int make_detector(int d, int K, int L, const float* Wsrc, uint64_t seed, bool fr
   std::vector<float> Wt(dkl), cB;
   for (int i = 0; i < d; ++i)
     for (int c = 0; c < h->KL; ++c) Wt[static_cast<size_t>(c) * d + i] = h->Wh[static_cast<size_t>(i) * h->KL + c];
-  guard_constants(h->Wh, d, h->KL, cB, h->xfac, h->xabs, h->babs, h->dot2c, h->dot2abs);
+  guard_constants(h->Wh, d, h->KL, cB, h->xfac, h->xabs, h->babs, h->dot2c, h->dot2abs, h->runc, h->run64,
+                  h->runabs);
 
   auto bad = [&](cudaError_t err, const char* what) {
     free_all(h);
@@ -491,6 +502,9 @@ ace::HashArgs hash_args(ace_handle h, const void* X, long long n, int dtype, int
   a.babs = h->babs;
   a.dot2c = h->dot2c;
   a.dot2abs = h->dot2abs;
+  a.runc = h->runc;
+  a.run64 = h->run64;
+  a.runabs = h->runabs;
   a.mode = mode;
   a.ids = h->ids;
   a.ld = n;

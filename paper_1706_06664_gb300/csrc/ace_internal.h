@@ -50,6 +50,7 @@ struct HashArgs {
   float xabs;           // squared-norm underflow allowance
   float babs;           // absolute allowance in the projection bound
   float dot2c, dot2abs; // Dot2 filter (before binary64): bound = dot2c * sum|x_i w_i|^ + dot2abs
+  float runc, run64, runabs;  // warp recheck: bound = runc * R^ + run64 * cB[c] * ||x||^ + runabs
   int mode;             // HashMode bits
   void* ids;            // scratch ids (uint16 when K <= 16, else uint32), [L][ld]
   long long ld;         // leading dimension of the scratch ids (>= n)

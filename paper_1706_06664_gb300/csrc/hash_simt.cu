@@ -146,9 +146,61 @@ __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int 
   }
   __syncthreads();
 
+  // ---- warp recheck of the columns inside the bound ----------------------------------------
+  // Each non-zero word of the ambiguity bitmap goes to one warp (a ballot over 32 words at a
+  // time finds them).  For each (point, column) in it, the warp splits the dot product over
+  // its 32 lanes (lane l: coordinates l, l + 32, ...; binary32 FMA chains), joins the lanes'
+  // sums by a butterfly of shuffles and keeps, alongside, the sum R of the magnitudes of every
+  // rounded partial result.  u R / (1 - u), inflated for R's own rounding, plus the binary64
+  // sum's error bounds the distance of the result from the definition whatever the summation
+  // tree, and near zero it is far tighter than the a priori bound: a decided bit leaves the
+  // bitmap.  Every lane computes the same values (addition is commutative), so the loop stays
+  // uniform.
+  const int lane = threadIdx.x & 31;
+  for (int base = (threadIdx.x >> 5) * 32; base < BM * (BN / 32); base += NT) {
+    const uint32_t mw = (&amb[0][0])[base + lane];
+    uint32_t nz = __ballot_sync(0xFFFFFFFFu, mw != 0u && (base + lane) / (BN / 32) < npt);
+    while (nz) {
+      const int q = __ffs(nz) - 1;
+      nz &= nz - 1u;
+      const int p = (base + q) / (BN / 32), wi = (base + q) % (BN / 32);
+      uint32_t m = __shfl_sync(0xFFFFFFFFu, mw, q);
+      const long long xb = (i0 + p) * static_cast<long long>(a.d);
+      const float xu = xn[p];
+      uint32_t done = 0u, set = 0u;
+      while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1u;
+        const int col = c0 + wi * 32 + b;
+        const float* w = a.Wt + static_cast<size_t>(col) * a.d;
+        float s = 0.f, r = 0.f;
+        for (int t = lane; t < a.d; t += 32) {
+          s = fmaf(load_x<BF16>(a.X, xb + t), __ldg(w + t), s);
+          r = __fadd_rn(r, fabsf(s));
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          const float so = __shfl_xor_sync(0xFFFFFFFFu, s, off);
+          const float ro = __shfl_xor_sync(0xFFFFFFFFu, r, off);
+          s = __fadd_rn(s, so);
+          r = __fadd_rn(__fadd_rn(r, ro), fabsf(s));
+        }
+        const float bound = __fmaf_ru(a.runc, r, __fmaf_ru(__fmul_ru(a.run64, __ldg(a.cB + col)), xu, a.runabs));
+        if (fabsf(s) > bound) {
+          done |= 1u << b;
+          if (s > 0.f) set |= 1u << b;
+        }
+      }
+      if (lane == 0 && done) {
+        bits[p][wi] |= set;
+        amb[p][wi] &= ~done;
+      }
+    }
+  }
+  __syncthreads();
+
   // ---- pack, recheck, store / insert -----------------------------------------------------
   const int K = a.K;
-  const int lane = threadIdx.x & 31;
   for (int e = threadIdx.x; e < ntab * BM; e += NT) {
     const int t = e / BM, p = e % BM;
     const bool valid = p < npt;
