@@ -236,6 +236,38 @@ def test_near_orthogonal_points_are_exact(precision):
     _engine_used(det, precision)
 
 
+def test_near_orthogonal_points_high_d_are_exact():
+    """d = 1024 on the binary32 engine, where the warp recheck, Dot2 and the binary64
+    definition each decide some bits: points whose projection on a chosen column is 1e-3 down
+    to 1e-9 of ||x|| ||w_c||, and exact ties (two equal rows of W, x = a (e_r1 - e_r2): every
+    projection is exactly 0, so every bit is 0)."""
+    d, K, L, n = 1024, 16, 8, 1024
+    rng = np.random.default_rng(29)
+    W = rng.standard_normal((d, K * L)).astype(np.float32)
+    W[7] = W[500]
+    X = rng.standard_normal((n, d))
+    Wd = W.astype(np.float64)
+    eps = [1e-3, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9]
+    for i in range(n):
+        if i % 8 == 7:
+            X[i] = 0.0
+            X[i, 7], X[i, 500] = 1.5 + i, -(1.5 + i)
+            continue
+        wc = Wd[:, rng.integers(0, K * L)]
+        x = X[i] - (X[i] @ wc) / (wc @ wc) * wc
+        X[i] = x + eps[i % len(eps)] * np.linalg.norm(x) / np.linalg.norm(wc) * rng.choice([-1, 1]) * wc
+    X = X.astype(np.float32)
+    det, ref = _pair(d, K, L, W=W, precision="fp32")
+    Xd = _dev(X)
+    ids = ace.u32(det.hash(Xd))
+    assert np.array_equal(ids, ref.hash(X))
+    assert not ids[7::8].any()  # the exact ties
+    _compare_score(det.insert_score(Xd, 1.0), ref.insert_score(X, 1.0))
+    assert np.array_equal(det.counts(), ref.counts)
+    _compare_stats(det, ref)
+    assert det.stats()["rechecks"] > 0  # some bits reached Dot2 / binary64
+
+
 def test_tensor_core_engine_refuses_unfit_shapes():
     with pytest.raises(ace.AceError) as e:
         ace.Detector(1024, 16, 64, seed=1, precision="bf16")
