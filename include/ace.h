@@ -268,6 +268,13 @@ typedef struct {
   uint64_t timed[ACE_NPHASE];    /* launches that were timed                              */
 } ace_profile_t;
 int ace_profile_enable(ace_handle h, int enable);
+/*
+ * ace_profile_phases — restricts the events of the timing hook to the phases whose bit is set
+ * in mask (bit p = ACE_PHASE p; 0 restores all phases, the default), so that a timed run can
+ * bracket one kernel without paying for events around the others.  No counterpart in the
+ * paper (measurement only).  Errors: ACE_ERR_ARG (NULL handle).
+ */
+int ace_profile_phases(ace_handle h, unsigned mask);
 int ace_profile_read(ace_handle h, ace_profile_t* out);
 
 /*

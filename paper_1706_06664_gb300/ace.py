@@ -26,7 +26,7 @@ EXPORTS = [
     "ace_insert_score_host_async", "ace_host_wait", "ace_delete", "ace_project", "ace_hash",
     "ace_batch_insert_score", "ace_server_create", "ace_server_submit", "ace_server_wait", "ace_server_drain", "ace_server_destroy", "ace_stats",
     "ace_get_counts", "ace_get_projection", "ace_get_shape", "ace_last_error", "ace_version",
-    "ace_profile_enable", "ace_profile_read", "ace_insert_score_noalloc",
+    "ace_profile_enable", "ace_profile_phases", "ace_profile_read", "ace_insert_score_noalloc",
 ]
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 PHASES = ("hash", "score", "flags", "other", "recheck", "insert")
@@ -96,6 +96,7 @@ def load_library(path: str = LIB_PATH):
             "ace_get_projection": ([H, P], i32),
             "ace_get_shape": ([H, P, P, P], i32),
             "ace_profile_enable": ([H, i32], i32),
+            "ace_profile_phases": ([H, ctypes.c_uint32], i32),
             "ace_profile_read": ([H, ctypes.POINTER(ace_profile_t)], i32),
             "ace_last_error": ([], ctypes.c_char_p),
             "ace_version": ([], ctypes.c_char_p),
@@ -297,7 +298,11 @@ class Detector:
         _check(load_library().ace_get_counts(self._h, ctypes.c_void_p(out.ctypes.data), _stream_ptr(stream)))
         return out
 
-    def profile(self, enable: bool = True):
+    def profile(self, enable: bool = True, phases=None):
+        """Turns the per-phase timing hook on or off; `phases` (names from PHASES) limits the
+        events to those phases (None: all)."""
+        mask = 0 if phases is None else sum(1 << PHASES.index(p) for p in phases)
+        _check(load_library().ace_profile_phases(self._h, mask))
         _check(load_library().ace_profile_enable(self._h, 1 if enable else 0))
 
     def profile_read(self) -> dict:

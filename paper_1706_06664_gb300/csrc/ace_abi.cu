@@ -96,6 +96,7 @@ struct ace_detector {
   cudaEvent_t ev_hashed = nullptr, ev_resolved = nullptr;
   // profiling hook
   bool prof = false;
+  unsigned prof_mask = ~0u;  // phases bracketed while profiling
   uint64_t launches[ACE_NPHASE] = {0, 0, 0, 0, 0, 0};
   struct Mark {
     int phase;
@@ -125,7 +126,7 @@ struct PhaseScope {
   }
   PhaseScope(ace_detector* h_, int phase_, cudaStream_t s_) : h(h_), phase(phase_), s(s_) {
     h->launches[phase] += 1;
-    if (h->prof) {
+    if (h->prof && ((h->prof_mask >> phase) & 1u)) {
       cudaEvent_t a = take();
       b = take();
       cudaEventRecord(a, s);
@@ -1273,6 +1274,12 @@ int ace_get_shape(ace_handle h, int* d, int* K, int* L) {
 int ace_profile_enable(ace_handle h, int enable) {
   if (!h) return fail(ACE_ERR_ARG, "handle is NULL");
   h->prof = enable != 0;
+  return ACE_OK;
+}
+
+int ace_profile_phases(ace_handle h, unsigned mask) {
+  if (!h) return fail(ACE_ERR_ARG, "handle is NULL");
+  h->prof_mask = mask ? mask : ~0u;
   return ACE_OK;
 }
 
