@@ -268,6 +268,28 @@ def test_near_orthogonal_points_high_d_are_exact():
     assert det.stats()["rechecks"] > 0  # some bits reached Dot2 / binary64
 
 
+@pytest.mark.parametrize("precision", PRECS)
+def test_output_buffers_at_any_alignment(precision):
+    """Scores, sums and flags written to caller buffers that start 8, 4 and 1 bytes past an
+    aligned address, and to aligned ones, for a ragged batch: all equal the oracle's."""
+    w = workloads.small(seed=1, n=1001)
+    X = w["X"]
+    Xd = _dev(X)
+    for shift in (0, 1):
+        det, ref = _pair(w["d"], w["K"], w["L"], seed=17, precision=precision)
+        n = X.shape[0]
+        sc = torch.empty(n + 1, dtype=torch.float64, device="cuda")[shift:shift + n]
+        su = torch.empty(n + 1, dtype=torch.int32, device="cuda")[shift:shift + n]
+        fl = torch.empty(n + 1, dtype=torch.uint8, device="cuda")[shift:shift + n]
+        _compare_score(det.insert_score(Xd, 1.0, scores=sc, sums=su, flags=fl), ref.insert_score(X, 1.0))
+        # sums left to the library (aligned scratch), scores and flags as above
+        s2, _, f2 = det.score(Xd, 2.0, scores=sc, sums=None, flags=fl)
+        torch.cuda.synchronize()
+        r2 = ref.score(X, 2.0)
+        assert np.array_equal(s2.cpu().numpy(), r2[0]) and np.array_equal(f2.cpu().numpy(), r2[2])
+        det.close()
+
+
 def test_tensor_core_engine_refuses_unfit_shapes():
     with pytest.raises(ace.AceError) as e:
         ace.Detector(1024, 16, 64, seed=1, precision="bf16")
