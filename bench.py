@@ -254,11 +254,14 @@ def per_config(cases) -> dict:
                 torch.cuda.synchronize()
                 if r >= 3:
                     times.append(e0.elapsed_time(e1) / 1e3)
-            assert det.stats()["precision"] == want
+            used = det.stats()["precision"]
             det.close()
+            if used != want:
+                res[prec] = "engine not used for this shape"
+                continue
             t = statistics.median(times)
             res[prec] = {"points_per_s": n / t, "ms": t * 1e3, "projection_tflops": flop / t / 1e12}
-        if isinstance(res.get("bf16"), dict):
+        if isinstance(res.get("bf16"), dict) and isinstance(res.get("fp32"), dict):
             res["bf16_vs_fp32"] = res["bf16"]["points_per_s"] / res["fp32"]["points_per_s"]
         out[name] = res
         del Xd
@@ -592,19 +595,31 @@ def run_ours(args):
         "gpu_launches": int(sum(v["launches"] for v in prof.values())),
         "clocks": ck,
     }
-    cases = _config_cases() if rank == 0 and ws == 1 and (args.per_config or args.cpu_baseline) else None
-    if rank == 0 and ws == 1 and args.per_config:
-        line["per_config"] = per_config(cases)
+    # The sections below add context to the line; a failure in one is reported in its place
+    # rather than losing the measurement above.
+    def section(fn, *a):
+        try:
+            return fn(*a)
+        except Exception as e:  # noqa: BLE001 - reported in the JSON line
+            return {"error": f"{type(e).__name__}: {e}"[:300]}
+
+    cases = None
+    if rank == 0 and ws == 1 and (args.per_config or args.cpu_baseline):
+        cases = section(_config_cases)
+        if isinstance(cases, dict):  # the generators failed
+            line["per_config"], cases = cases, None
+    if rank == 0 and ws == 1 and args.per_config and cases is not None:
+        line["per_config"] = section(per_config, cases)
     if rank == 0 and args.cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(host_batches[0], seed)
-        if cases is not None:
-            line["cpu_baseline"]["per_config"] = oracle_per_config(cases)
+        line["cpu_baseline"] = section(cpu_baseline, host_batches[0], seed)
+        if cases is not None and "error" not in line["cpu_baseline"]:
+            line["cpu_baseline"]["per_config"] = section(oracle_per_config, cases)
     if rank == 0 and ws == 1 and args.serving:
-        line["serving"] = serving_isolated()
+        line["serving"] = section(serving_isolated)
     if rank == 0 and ws == 1 and args.batched:
-        line["batched"] = batched()
+        line["batched"] = section(batched)
     if rank == 0 and ws == 1 and args.proj_error:
-        line["projection_error"] = projection_errors()
+        line["projection_error"] = section(projection_errors)
     if rank == 0:
         print(json.dumps(line), flush=True)
     det.close()
