@@ -301,6 +301,21 @@ int ace_profile_read(ace_handle h, ace_profile_t* out);
 int ace_insert_score_noalloc(ace_handle h, const void* X_dev, int64_t n, int dtype, double alpha,
                              double* scores_dev, uint32_t* sums_dev, uint8_t* flags_dev, void* stream);
 
+/*
+ * ace_tc_probe — measurement hook for the tensor-core engines' error model.  Computes
+ * D = A . B^T (A: 128 x kdim, B: ncols x kdim, bfloat16 bit patterns, row-major, host; D:
+ * 128 x ncols binary32, host) on the tcgen05 tensor cores as kdim/16 MMA instructions of
+ * 128 x ncols x 16 accumulating into one TMEM accumulator in k order, the way the hash kernels
+ * accumulate Eq. 1's projections.  The guard bands of the tensor-core engines assume that one
+ * such instruction adds its 16 products and the accumulator with an error of at most
+ * 5.25 * 2^-23 times the sum of their magnitudes; a test feeds chosen sums through this hook to
+ * check that assumption on the device at hand.  (The paper has no counterpart: it computes
+ * Eq. 1 in one precision.)  kdim and ncols are multiples of 16 in [16, 256].  Synchronous
+ * (it allocates and frees its own device buffers).
+ * Errors: ACE_ERR_ARG, ACE_ERR_UNSUPPORTED (not an sm_103 device), ACE_ERR_TIMEOUT, ACE_ERR_CUDA.
+ */
+int ace_tc_probe(const uint16_t* A_host, const uint16_t* B_host, int kdim, int ncols, float* D_host);
+
 /* Library version string. */
 const char* ace_version(void);
 

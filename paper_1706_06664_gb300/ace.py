@@ -27,6 +27,7 @@ EXPORTS = [
     "ace_batch_insert_score", "ace_server_create", "ace_server_submit", "ace_server_wait", "ace_server_drain", "ace_server_destroy", "ace_stats",
     "ace_get_counts", "ace_get_projection", "ace_get_shape", "ace_last_error", "ace_version",
     "ace_profile_enable", "ace_profile_phases", "ace_profile_read", "ace_insert_score_noalloc",
+    "ace_tc_probe",
 ]
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 PHASES = ("hash", "score", "flags", "other", "recheck", "insert")
@@ -98,6 +99,7 @@ def load_library(path: str = LIB_PATH):
             "ace_profile_enable": ([H, i32], i32),
             "ace_profile_phases": ([H, ctypes.c_uint32], i32),
             "ace_profile_read": ([H, ctypes.POINTER(ace_profile_t)], i32),
+            "ace_tc_probe": ([P, P, i32, i32, P], i32),
             "ace_last_error": ([], ctypes.c_char_p),
             "ace_version": ([], ctypes.c_char_p),
         }
@@ -395,6 +397,18 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def tc_probe(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """ace_tc_probe: D = A . B^T on the tensor cores (A 128 x kd, B N x kd bfloat16 bit patterns
+    as uint16; kd and N multiples of 16 up to 256), accumulated as kd/16 MMA instructions."""
+    A = np.ascontiguousarray(A, dtype=np.uint16)
+    B = np.ascontiguousarray(B, dtype=np.uint16)
+    assert A.shape[0] == 128 and A.shape[1] == B.shape[1]
+    D = np.empty((128, B.shape[0]), dtype=np.float32)
+    _check(load_library().ace_tc_probe(ctypes.c_void_p(A.ctypes.data), ctypes.c_void_p(B.ctypes.data), A.shape[1],
+                                       B.shape[0], ctypes.c_void_p(D.ctypes.data)))
+    return D
 
 
 def u32(t) -> np.ndarray:

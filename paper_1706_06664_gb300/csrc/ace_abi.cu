@@ -15,7 +15,11 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "ace_internal.h"
+#include "gemm_plan.h"
 #include "tc_plan.h"
 
 namespace {
@@ -94,6 +98,11 @@ struct ace_detector {
   // rstream while the insert pass runs on the caller's stream
   cudaStream_t rstream = nullptr;
   cudaEvent_t ev_hashed = nullptr, ev_resolved = nullptr;
+  // streaming tensor-core path (large d, bfloat16 input; hash_gemm.cu)
+  bool gemm_ok = false;
+  ace::GemmArgs gm{};           // constant part of the launch
+  uint16_t* gimg = nullptr;     // [2 klp][dp] bfloat16 image of W' (hi rows, then lo rows)
+  CUtensorMap tm_img{};         // TMA description of gimg
   // profiling hook
   bool prof = false;
   unsigned prof_mask = ~0u;  // phases bracketed while profiling
@@ -152,6 +161,7 @@ void free_all(ace_detector* h) {
   h->marks.clear();
   h->pool.clear();
   cudaFree(h->bimg);
+  cudaFree(h->gimg);
   cudaFree(h->defer);
   cudaFree(h->defer_counts);
   cudaFree(h->wpad);
@@ -380,6 +390,140 @@ int plan_tc(ace_detector* h) {
   return ACE_OK;
 }
 
+// cuTensorMapEncodeTiled from the driver (through the runtime, so the library does not link
+// libcuda itself).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// A 2-D bfloat16 tensor map: rows x cols (cols innermost, row pitch cols * 2 bytes), boxes of
+// box_rows x 64 elements, 128-byte swizzle, zero fill outside the tensor.
+int encode_bf16_map(CUtensorMap* m, const void* base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return fail(ACE_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const cuuint64_t gdim[2] = {cols, rows};
+  const cuuint64_t gstride[1] = {cols * 2};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(ace::kGemmBK), box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim, gstride, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ACE_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+  return ACE_OK;
+}
+
+// Plans the streaming tensor-core path (hash_gemm.cu) for d > 64: the image of W' = w_c/||w_c||
+// split into bfloat16 hi and lo parts, laid out per 256-column unit of whole tables
+// (floor(256/K) tables per unit, zero rows after the last table), hi rows first, each row
+// d zero-padded to a multiple of 64; its tensor map; and the guard constants (see hash_gemm.cu).
+// Leaves gemm_ok false when the device is not sm_103 or the shape does not fit (d must be a
+// multiple of 8: the TMA engine needs the row pitch of X in whole 16-byte units).
+int plan_gemm(ace_detector* h) {
+  h->gemm_ok = false;
+  cudaDeviceProp p;
+  cudaError_t e = cudaGetDeviceProperties(&p, h->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  h->num_sms = p.multiProcessorCount;
+  if (p.major != 10 || p.minor != 3) return ACE_OK;
+  const int d = h->d, K = h->K, L = h->L, KL = h->KL;
+  if (d <= ace::kMaxD || d % 8 != 0) return ACE_OK;
+  if (ace::gemm_smem_bytes() > static_cast<int>(p.sharedMemPerBlockOptin)) return ACE_OK;
+  if (!tensor_map_encoder()) return ACE_OK;
+  const int dp = (d + ace::kGemmBK - 1) / ace::kGemmBK * ace::kGemmBK;
+  const int tpu = ace::kGemmBN / K;
+  const int nunits = (L + tpu - 1) / tpu;
+  const int klp = nunits * ace::kGemmBN;
+  std::vector<uint16_t> img(static_cast<size_t>(2) * klp * dp, 0);
+  std::vector<float> wn(KL, 0.f);
+  for (int c = 0; c < KL; ++c) {
+    double s2 = 0.0;
+    for (int i = 0; i < d; ++i) {
+      const double w = h->Wh[static_cast<size_t>(i) * KL + c];
+      s2 += w * w;
+    }
+    const double inv = s2 > 0.0 ? 1.0 / std::sqrt(s2) : 0.0;
+    wn[c] = s2 > 0.0 ? static_cast<float>(std::sqrt(s2)) : 0.f;
+    const int j = c / K, k = c % K;
+    const size_t row = static_cast<size_t>(j / tpu) * ace::kGemmBN + static_cast<size_t>(j % tpu) * K + k;
+    for (int i = 0; i < d; ++i) {
+      const float w1 = static_cast<float>(static_cast<double>(h->Wh[static_cast<size_t>(i) * KL + c]) * inv);
+      const uint16_t hi = bf16_rn(w1);
+      img[row * dp + i] = hi;
+      img[(static_cast<size_t>(klp) + row) * dp + i] = bf16_rn(w1 - bf16_value(hi));
+    }
+  }
+  cudaFree(h->gimg);
+  h->gimg = nullptr;
+  const size_t bytes = img.size() * sizeof(uint16_t);
+  if ((e = cudaMalloc(&h->gimg, bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc W' image");
+  if ((e = cudaMemcpy(h->gimg, img.data(), bytes, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(e, "copy W' image");
+  if (int rc = encode_bf16_map(&h->tm_img, h->gimg, static_cast<uint64_t>(dp), static_cast<uint64_t>(2) * klp,
+                               ace::kGemmBN))
+    return rc;
+  if (!h->wnorm) {
+    if ((e = cudaMalloc(&h->wnorm, KL * sizeof(float))) != cudaSuccess) return cuda_fail(e, "cudaMalloc column norms");
+    if ((e = cudaMemcpy(h->wnorm, wn.data(), KL * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cuda_fail(e, "copy column norms");
+  }
+  if (!h->defer_counts &&
+      (e = cudaMalloc(&h->defer_counts, sizeof(unsigned int) * static_cast<size_t>(h->num_sms))) != cudaSuccess)
+    return cuda_fail(e, "cudaMalloc deferred counters");
+
+  ace::GemmArgs& g = h->gm;
+  g = ace::GemmArgs{};
+  g.d = d;
+  g.dp = dp;
+  g.nkb = dp / ace::kGemmBK;
+  g.K = K;
+  g.L = L;
+  g.KL = KL;
+  g.tpu = tpu;
+  g.nunits = nunits;
+  g.nprod = 2;
+  g.klp = klp;
+  // guard constants relative to ||x|| (unit columns); see hash_gemm.cu
+  const double u32 = std::ldexp(1.0, -24), u64 = std::ldexp(1.0, -53);
+  const int S_hi = dp / 16, S_lo = dp / 16;
+  const double t_split = std::ldexp(1.0, -17);
+  const double t_acc = 5.25 * 1.5 * (S_hi * (1.0 + std::ldexp(1.0, -7)) + 1.0 + S_lo * std::ldexp(1.0, -8)) *
+                       std::ldexp(1.0, -23);
+  const double t_norm = std::ldexp(1.0, -23);
+  const double g64 = d * u64 / (1.0 - d * u64);
+  g.tau = std::nextafter(static_cast<float>((t_split + t_acc + t_norm + g64) * 1.01), FLT_MAX);
+  g.tau_abs = static_cast<float>(2.0 * dp * std::ldexp(1.0, -125));
+  const double g32 = d * u32 / (1.0 - d * u32);
+  g.xfac = std::nextafter(static_cast<float>(1.0 + 2.0 * g32 + std::ldexp(1.0, -20)), FLT_MAX);
+  g.qmin = std::ldexp(1.0f, -60);
+  g.wnorm = h->wnorm;
+  g.st = h->st;
+  g.Wt = h->Wt;
+  g.cB32 = h->cB;
+  g.xfac32 = h->xfac;
+  g.xabs32 = h->xabs;
+  g.babs32 = h->babs;
+  g.dot2c = h->dot2c;
+  g.dot2abs = h->dot2abs;
+  g.runc = h->runc;
+  g.run64 = h->run64;
+  g.runabs = h->runabs;
+  g.defer_counts = h->defer_counts;
+  g.smem_bytes = ace::gemm_smem_bytes();
+  h->gemm_ok = true;
+  return ACE_OK;
+}
+
 int make_detector(int d, int K, int L, const float* Wsrc, uint64_t seed, bool from_seed, ace_handle* out) {
   if (!out) return fail(ACE_ERR_ARG, "out is NULL");
   *out = nullptr;
@@ -439,6 +583,11 @@ int make_detector(int d, int K, int L, const float* Wsrc, uint64_t seed, bool fr
   if ((e = cudaMemset(h->st, 0, sizeof(ace::DevStats))) != cudaSuccess) return bad(e, "zero stats");
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bad(e, "create sync");
   if (int rc = plan_tc(h)) {
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  if (int rc = plan_gemm(h)) {
     free_all(h);
     delete h;
     return rc;
@@ -520,14 +669,88 @@ size_t id_bytes(ace_handle h) { return h->K <= 16 ? 2 : 4; }
 // Hashes a.n points into the ids scratch (a.ids, leading dimension a.ld).  With kInsert the
 // counts are incremented too: fused in the SIMT engine; on the tensor-core path by a pass over
 // the stored ids, which `tc_insert` = false leaves to the caller (chunked hashing of one batch).
+enum class Engine { kSimt, kResident, kStreaming };
+
+// The engine that hashes X: binary32 SIMT when asked for, or when no tensor-core design fits;
+// the resident tensor-core design for d <= 64 (any input type); the streaming one for larger
+// d with bfloat16 input at a 16-byte-aligned address (the TMA engine's rule).
+Engine pick_engine(ace_handle h, int x_bf16, const void* X) {
+  if (h->precision == ACE_PROJ_FP32) return Engine::kSimt;
+  if (h->tc_ok) return Engine::kResident;
+  if (h->gemm_ok && x_bf16 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) return Engine::kStreaming;
+  return Engine::kSimt;
+}
+
+// Bytes of table-major ids for n points (plus a word of slack: the streaming engine's recheck
+// flips bits of 16-bit ids with 32-bit atomics).
+size_t ids_need(ace_handle h, long long n) { return static_cast<size_t>(n) * h->L * (h->K <= 16 ? 2 : 4) + 16; }
+
+// Streaming tensor-core engine (hash_gemm.cu): ids (or projections), then the exact
+// resolution of the deferred (point, column) entries, then the count increments from the
+// stored ids when inserting.
+int run_gemm(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_insert) {
+  if (a.n > 0x7FFFFFFFLL) return fail(ACE_ERR_UNSUPPORTED, "the streaming engine takes at most 2^31-1 points per call");
+  const bool insert = (a.mode & ace::kInsert) != 0;
+  const bool proj = (a.mode & ace::kStoreProj) != 0;
+  void* ids = a.ids;
+  if (insert && (!ids || ids == h->ids)) {
+    if (int rc = grow(&h->ids, &h->ids_cap, ids_need(h, a.n), s, "ids scratch")) return rc;
+    ids = h->ids;
+  }
+  const long long ntiles = (a.n + ace::kGemmBM - 1) / ace::kGemmBM;
+  const long long grid = std::min(static_cast<long long>(h->num_sms), ntiles);
+  const size_t cap = static_cast<size_t>(a.n) * 4 + static_cast<size_t>(grid) * 4096;
+  void* p = h->defer;
+  if (int rc = grow(&p, &h->defer_bytes, cap * 8, s, "deferred list")) return rc;
+  h->defer = static_cast<unsigned long long*>(p);
+  ace::GemmArgs g = h->gm;
+  g.X = a.X;
+  g.n = a.n;
+  g.ntiles = ntiles;
+  g.mode = (a.mode & ~ace::kInsert) | (insert ? ace::kStoreIds : 0);
+  g.ids = ids;
+  g.ld = a.ld;
+  g.ids_rm = a.ids_rm;
+  g.proj = a.proj;
+  g.defer = h->defer;
+  g.seg_cap = h->defer_bytes / 8 / static_cast<size_t>(grid);
+  alignas(128) CUtensorMap tmx;
+  if (int rc = encode_bf16_map(&tmx, a.X, static_cast<uint64_t>(h->d), static_cast<uint64_t>(a.n), ace::kGemmBM))
+    return rc;
+  cudaError_t e;
+  if (!proj) h->last_precision = ACE_PROJ_BF16;
+  {
+    PhaseScope ps(h, ACE_PHASE_HASH, s);
+    e = ace::launch_hash_gemm(g, &tmx, &h->tm_img, h->num_sms, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "streaming tensor-core hash kernel launch");
+  if (proj) return ACE_OK;
+  {
+    PhaseScope ps(h, ACE_PHASE_RECHECK, s);
+    e = ace::launch_recheck_cols(g, static_cast<int>(grid), h->num_sms, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "column recheck kernel launch");
+  if (insert && tc_insert) {
+    PhaseScope ps(h, ACE_PHASE_INSERT, s);
+    e = ace::launch_insert_from_ids(ids, h->K <= 16, a.ld, a.n, h->K, h->L, h->counts, h->num_sms, s);
+    if (e != cudaSuccess) return cuda_fail(e, "insert kernel launch");
+  }
+  return ACE_OK;
+}
+
 int run_hash(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_insert = true) {
-  if (h->precision == ACE_PROJ_FP32 || !h->tc_ok) {
+  const Engine eng = pick_engine(h, a.x_bf16, a.X);
+  if (eng == Engine::kSimt && h->precision == ACE_PROJ_BF16)
+    return fail(ACE_ERR_UNSUPPORTED, "the tensor-core engine at d=%d needs bfloat16 input at a 16-byte-aligned address",
+                h->d);
+  if (eng == Engine::kSimt) {
     h->last_precision = ACE_PROJ_FP32;
     PhaseScope ps(h, ACE_PHASE_HASH, s);
     cudaError_t e = ace::launch_hash_simt(a, s);
     if (e != cudaSuccess) return cuda_fail(e, "hash kernel launch");
     return ACE_OK;
   }
+  if (eng == Engine::kStreaming) return run_gemm(h, a, s, tc_insert);
   // tensor-core engine (ids only), the binary64 resolution of the deferred tables, then the
   // count increments from the stored ids.  With 16-bit ids and K <= 15 the deferred tables are
   // tagged (kTagDeferred): their resolution, which counts them too, runs on rstream while the
@@ -535,9 +758,8 @@ int run_hash(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_inser
   const bool insert = (a.mode & ace::kInsert) != 0;
   const bool overlap = insert && tc_insert && h->K <= 15 && !a.ids_rm && h->rstream;
   void* ids = a.ids;
-  if (insert && !ids) {
-    if (int rc = grow(&h->ids, &h->ids_cap, static_cast<size_t>(a.n) * h->L * id_bytes(h), s, "ids scratch"))
-      return rc;
+  if (insert && (!ids || ids == h->ids)) {
+    if (int rc = grow(&h->ids, &h->ids_cap, ids_need(h, a.n), s, "ids scratch")) return rc;
     ids = h->ids;
   }
   const size_t cap = static_cast<size_t>(a.n) + 65536;
@@ -618,7 +840,7 @@ int score_common(ace_handle h, const void* X, long long n, int dtype, double alp
   if (insert && h->n_ins + static_cast<uint64_t>(n) > 0xFFFFFFFFull)
     return fail(ACE_ERR_OVERFLOW, "inserting %lld points would allow a count above 2^32-1", n);
   if (n == 0) return ACE_OK;
-  if ((rc = grow(&h->ids, &h->ids_cap, static_cast<size_t>(n) * h->L * id_bytes(h), s, "ids scratch"))) return rc;
+  if ((rc = grow(&h->ids, &h->ids_cap, ids_need(h, n), s, "ids scratch"))) return rc;
   uint32_t* sum_out = sums;
   if (!sum_out) {
     void* p = h->sums;
@@ -667,9 +889,9 @@ int ace_set_precision(ace_handle h, int precision) {
   if (!h) return fail(ACE_ERR_ARG, "handle is NULL");
   if (precision != ACE_PROJ_AUTO && precision != ACE_PROJ_FP32 && precision != ACE_PROJ_BF16)
     return fail(ACE_ERR_ARG, "unknown precision %d", precision);
-  if (precision == ACE_PROJ_BF16 && !h->tc_ok)
-    return fail(ACE_ERR_UNSUPPORTED, "the tensor-core path needs an sm_103 device and a shape whose operand image fits "
-                                     "in shared memory (d=%d K=%d L=%d)", h->d, h->K, h->L);
+  if (precision == ACE_PROJ_BF16 && !h->tc_ok && !h->gemm_ok)
+    return fail(ACE_ERR_UNSUPPORTED, "the tensor-core paths need an sm_103 device and either d <= 64 or d a multiple "
+                                     "of 8 (d=%d K=%d L=%d)", h->d, h->K, h->L);
   h->precision = precision;
   return ACE_OK;
 }
@@ -737,7 +959,7 @@ static int enqueue_host_batch(ace_handle h, int op, const void* X_host, int64_t 
   }
   const size_t row = static_cast<size_t>(h->d) * (dtype == ACE_F32 ? 4 : 2);
   const size_t xbytes = static_cast<size_t>(n) * row;
-  const size_t need_ids = static_cast<size_t>(n) * h->L * id_bytes(h);
+  const size_t need_ids = ids_need(h, n);
   // The slot's own staging buffer is idle here; sums and ids are used on `s` only (grow
   // synchronises it); the output staging is replaced below only once nothing is in flight.
   if (xbytes > sl.cap) {
@@ -800,7 +1022,7 @@ static int enqueue_host_batch(ace_handle h, int op, const void* X_host, int64_t 
                              static_cast<size_t>(nc) * row, cudaMemcpyHostToDevice, h->cstream));
     ACE_CUDA(cudaEventRecord(sl.chunk[c], h->cstream));
   }
-  const bool simt = h->precision == ACE_PROJ_FP32 || !h->tc_ok;
+  const bool simt = pick_engine(h, dtype == ACE_BF16, sl.x) == Engine::kSimt;
   for (int c = 0; c < nch; ++c) {
     const long long c0 = c * chunk, nc = std::min<long long>(chunk, n - c0);
     if (nc <= 0) break;
@@ -1053,7 +1275,7 @@ int ace_delete(ace_handle h, const void* X_dev, int64_t n, int dtype, void* stre
     return fail(ACE_ERR_ARG, "deleting %lld points from a detector holding %llu", static_cast<long long>(n),
                 static_cast<unsigned long long>(h->n_ins));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if ((rc = grow(&h->ids, &h->ids_cap, static_cast<size_t>(n) * h->L * id_bytes(h), s, "ids scratch"))) return rc;
+  if ((rc = grow(&h->ids, &h->ids_cap, ids_need(h, n), s, "ids scratch"))) return rc;
   const long long total = static_cast<long long>(count_elems(h));
   if (!h->hist) {
     cudaError_t e = cudaMalloc(&h->hist, static_cast<size_t>(total) * sizeof(uint32_t));
@@ -1171,7 +1393,9 @@ int ace_project(ace_handle h, const void* X_dev, int64_t n, int dtype, float* pr
   ace::HashArgs a = hash_args(h, X_dev, n, dtype, ace::kStoreProj);
   a.proj = proj_dev;
   cudaError_t e;
-  if (h->precision == ACE_PROJ_FP32 || !h->tc_ok) {
+  const Engine eng = pick_engine(h, a.x_bf16, X_dev);
+  if (eng == Engine::kStreaming) return run_gemm(h, a, s, false);
+  if (eng == Engine::kSimt) {
     e = ace::launch_hash_simt(a, s);
   } else {
     const size_t cap = static_cast<size_t>(n) + 65536;
@@ -1301,6 +1525,37 @@ int ace_profile_read(ace_handle h, ace_profile_t* out) {
   h->marks.clear();
   for (int p = 0; p < ACE_NPHASE; ++p) h->launches[p] = 0;
   return rc;
+}
+
+int ace_tc_probe(const uint16_t* A_host, const uint16_t* B_host, int kdim, int ncols, float* D_host) {
+  if (!A_host || !B_host || !D_host) return fail(ACE_ERR_ARG, "NULL argument");
+  if (kdim < 16 || kdim > 256 || kdim % 16 || ncols < 16 || ncols > 256 || ncols % 16)
+    return fail(ACE_ERR_ARG, "kdim and ncols must be multiples of 16 in [16, 256] (got %d, %d)", kdim, ncols);
+  int dev = 0;
+  ACE_CUDA(cudaGetDevice(&dev));
+  cudaDeviceProp p;
+  ACE_CUDA(cudaGetDeviceProperties(&p, dev));
+  if (p.major != 10 || p.minor != 3) return fail(ACE_ERR_UNSUPPORTED, "the tensor-core probe needs an sm_103 device");
+  const size_t ab = static_cast<size_t>(128) * kdim * 2, bb = static_cast<size_t>(ncols) * kdim * 2;
+  const size_t db = static_cast<size_t>(128) * ncols * 4;
+  unsigned char* buf = nullptr;
+  ACE_CUDA(cudaMalloc(&buf, ab + bb + db + 16));
+  uint16_t* A = reinterpret_cast<uint16_t*>(buf);
+  uint16_t* B = reinterpret_cast<uint16_t*>(buf + ab);
+  float* D = reinterpret_cast<float*>(buf + ab + bb);
+  int* status = reinterpret_cast<int*>(buf + ab + bb + db);
+  cudaError_t e = cudaMemcpy(A, A_host, ab, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(B, B_host, bb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(status, 0, sizeof(int));
+  if (e == cudaSuccess) e = ace::launch_tc_probe(A, B, kdim, ncols, D, status, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int st = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(D_host, D, db, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&st, status, sizeof st, cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core probe");
+  if (st) return fail(ACE_ERR_TIMEOUT, "tensor-core probe: the MMA completion wait gave up");
+  return ACE_OK;
 }
 
 const char* ace_last_error(void) { return g_err.c_str(); }

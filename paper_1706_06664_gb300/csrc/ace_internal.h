@@ -94,6 +94,10 @@ cudaError_t launch_delete_check(const uint32_t* hist, const uint32_t* counts, lo
                                 int num_sms, cudaStream_t s);
 cudaError_t launch_delete_apply(const uint32_t* hist, uint32_t* counts, long long total, int num_sms, cudaStream_t s);
 
+// Measurement hook: D = A . B^T as kd/16 tcgen05 MMAs of 128 x N x 16 (tc_probe.cu).
+cudaError_t launch_tc_probe(const uint16_t* A, const uint16_t* B, int kd, int N, float* D, int* status,
+                            cudaStream_t s);
+
 // Host-side generator of the projection matrix (SplitMix64 counter mode + Box-Muller).
 void generate_projection(int d, int K, int L, uint64_t seed, float* W);
 

@@ -1,0 +1,53 @@
+// Launch description of the streaming tensor-core hash kernel (hash_gemm.cu), shared by the
+// runtime and the kernels.  The streaming engine covers large d: the bfloat16 input X and the
+// projection image both stream through shared memory in 64-wide k-blocks, instead of the
+// resident design of hash_tc.cu whose whole W' image sits in shared memory (d <= 64).
+#pragma once
+
+#include <cstdint>
+
+#include "ace_internal.h"
+
+namespace ace {
+
+constexpr int kGemmBM = 128;     // points per tile = MMA M (one TMEM lane per point)
+constexpr int kGemmBN = 256;     // image columns per unit = MMA N
+constexpr int kGemmBK = 64;      // d per k-block: one 128-byte swizzle atom of bfloat16
+constexpr int kGemmStages = 4;   // shared-memory ring of (X k-block, image k-block) pairs
+
+// Deferred (point, column) entry: point << 17 | column << 1 | the bit the tensor cores stored.
+constexpr int kGemmEntryShift = 17;
+
+struct GemmArgs {
+  const void* X;              // n x d bfloat16 bits, row-major (the tensor map covers it)
+  long long n, ntiles;        // points, 128-point tiles
+  int d, dp, nkb;             // dp = d rounded up to 64; nkb = dp / 64 k-blocks
+  int K, L, KL;
+  int tpu, nunits;            // whole tables per 256-column unit; units per tile
+  int nprod;                  // 2: x.w'_lo then x.w'_hi (binary32 W split in two); 1: x.w'_hi only
+  int klp;                    // image rows of one part (nunits * 256); the lo part follows the hi part
+  float tau, tau_abs, xfac, qmin;  // row bound = tau * ||x||_up + tau_abs (or every column, q < qmin)
+  int mode;                   // HashMode bits (kStoreIds, kStoreIdsRowMajor, kStoreProj)
+  void* ids;                  // table-major ids [L][ld] (uint16 for K <= 16, else uint32)
+  long long ld;
+  uint32_t* ids_rm;           // [n][L] uint32 (kStoreIdsRowMajor)
+  float* proj;                // [n][KL] estimates (kStoreProj)
+  const float* wnorm;         // [KL] ||w_c||, to scale x.w'_c back to x.w_c (kStoreProj)
+  DevStats* st;
+  // exact resolution of the deferred columns (binary32 running bound, Dot2, binary64)
+  const float* Wt;            // [KL][d] binary32 W, columns contiguous
+  const float* cB32;          // [KL] the SIMT engine's a priori coefficient per column
+  float xfac32, xabs32, babs32, dot2c, dot2abs, runc, run64, runabs;
+  unsigned long long* defer;  // one segment of seg_cap entries per CTA
+  unsigned int* defer_counts; // entries per segment (written by each CTA at exit)
+  unsigned long long seg_cap;
+  int smem_bytes;
+};
+
+// Launches the hash kernel; tmX and tmW are CUtensorMap objects (128-byte aligned, 128 bytes)
+// describing X and the image.
+cudaError_t launch_hash_gemm(const GemmArgs& a, const void* tmX, const void* tmW, int num_sms, cudaStream_t s);
+cudaError_t launch_recheck_cols(const GemmArgs& a, int nseg, int num_sms, cudaStream_t s);
+int gemm_smem_bytes();
+
+}  // namespace ace

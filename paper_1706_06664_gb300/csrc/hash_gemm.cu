@@ -1,0 +1,605 @@
+// SRP hashing of large-d bfloat16 batches on the tcgen05 tensor cores, streamed.
+//
+// Eq. 1 for every point and every column is a dense contraction X (n x d) . W (d x KL); at
+// d = 1024 neither X nor W fits in shared memory, so both stream through a ring of
+// 128-byte-swizzled k-blocks loaded by the TMA engine (cp.async.bulk.tensor), and each
+// 128-point tile meets the projection image one 256-column unit at a time:
+//     acc(128 x 256, binary32, TMEM) = x . w'_lo  (all k-blocks)  then  + x . w'_hi
+// where w' = w_c / ||w_c|| (unit columns, rounded to binary32) is split on the host into
+// bfloat16 hi + lo parts.  x is bfloat16, so x_i w'_hi,i and x_i w'_lo,i are exact products
+// and the only errors are the dropped third part of w', the accumulation, and the
+// normalisation.  Error bound relative to ||x|| (host constants in ace_abi.cu, plan_gemm):
+//   - split: |w' - w_hi - w_lo| <= 2^-18 |w'| elementwise (two round-to-nearest bfloat16
+//     steps), so the dropped term is at most 2^-18 sum|x_i w'_i|; 2^-17 is used;
+//   - accumulation: tcgen05 aligns the 17 addends of one MMA instruction (16 products and the
+//     accumulator) to the largest exponent keeping two bits below its last place and truncates
+//     the sum to binary32: at most 5.25 * 2^-23 * (sum of |addends|) per instruction.  The lo
+//     product goes first over all of d (its instructions see addends of at most about
+//     2^-8 sum|x_i w'_i|), so over S_lo + S_hi instructions the error is at most
+//     5.25 * 2^-23 * (S_hi (1 + 2^-7) + 1 + 2^-8 S_lo) * sum|x_i w'_i| (1.5x margin applied);
+//   - normalisation (2^-23) and the binary64 reference itself (gamma64_d).
+// With sum|x_i w'_i| <= ||x||, the bound is one number per point, B = tau ||x||_up + tau_abs.
+// A column whose |accumulator| <= B is deferred as a (point, column) entry; recheck_cols
+// recomputes its bit exactly and flips the stored id bit if the tensor cores had it wrong.
+//
+// Roles (one CTA per SM, persistent over tiles; 8 warps):
+//   warp 0      TMA producer: one (X k-block, image k-block) pair per ring stage
+//   warp 1      TMEM allocation and MMA issue (one lane): 4 MMAs of 128 x 256 x 16 per stage
+//   warps 2-3   row bounds: ||x||^2 of each point of the tile from global memory (the TMA
+//               loads then find the rows in L2), the bound B, exact-zero and non-finite rows
+//   warps 4-7   epilogue: tcgen05.ld of the accumulator (thread = point), sign bits, guard
+//               classification, deferral entries, bucket ids (Eq. 2) stored table-major
+#include <cuda.h>
+
+#include "gemm_plan.h"
+#include "guard.cuh"
+#include "tc_ptx.cuh"
+
+namespace ace {
+namespace {
+
+using namespace tc;
+
+constexpr int kThreads = 256;
+constexpr int kStages = kGemmStages;
+constexpr uint32_t kABytes = kGemmBM * kGemmBK * 2;  // 16 KB
+constexpr uint32_t kBBytes = kGemmBN * kGemmBK * 2;  // 32 KB
+constexpr uint32_t kStageBytes = kABytes + kBBytes;
+constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
+
+struct GSmem {
+  uint64_t full[kStages], empty[kStages];
+  uint64_t t_full[2], t_empty[2];
+  uint64_t b_full[2], b_empty[2];
+  uint64_t drain;
+  uint32_t taddr;
+  int abort;
+  unsigned int ndef;
+  uint32_t bthr[2][kGemmBM];  // per tile slot and row: deferral threshold (bit pattern + 1)
+  uint32_t bzero[2][kGemmBM]; // per tile slot and row: the row is exactly zero
+};
+
+constexpr int kSmemBytes = static_cast<int>(kStages * kStageBytes + sizeof(GSmem) + 1024);
+
+__device__ __forceinline__ void set_abort(GSmem* S, DevStats* st) {
+  S->abort = 1;
+  atomicOr(&st->status, static_cast<unsigned>(ACE_STATUS_TIMEOUT));
+}
+
+__device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// 2-D tiled TMA load (box of the tensor map at coordinates (c0 = innermost, c1)) into shared
+// memory, completing `bytes` on the mbarrier.  c0 * 2 bytes is a multiple of 16 (c0 is a
+// multiple of 64 here).
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_prefetch(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// Shared-memory descriptor of a K-major operand in the 128-byte swizzled layout written by
+// the TMA engine: rows of 128 bytes, 8-row groups 1024 bytes apart (SBO), swizzle mode 2.
+// The tile base is 1024-byte aligned, so the k-th 16-element slice starts 32 k bytes in.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;           // LBO (not used by swizzled K-major layouts)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;   // SBO
+  d |= static_cast<uint64_t>(1) << 46;           // descriptor version
+  d |= static_cast<uint64_t>(2) << 61;           // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+
+// The exact bit of column c for point i (bfloat16 row): a binary32 FMA chain decided by the
+// SIMT engine's a priori bound, then Dot2, then the binary64 definition.  The slow path of a
+// CTA whose deferred segment is full.
+__device__ __noinline__ bool exact_col_bit(const GemmArgs& a, long long i, int c) {
+  const int d = a.d;
+  const float* wc = a.Wt + static_cast<size_t>(c) * d;
+  float q = 0.f, s32 = 0.f;
+  for (int t = 0; t < d; ++t) {
+    const float x = load_x<true>(a.X, i * d + t);
+    q = fmaf(x, x, q);
+    s32 = fmaf(x, __ldg(wc + t), s32);
+  }
+  const float xu = norm_upper(q, a.xfac32, a.xabs32);
+  atomicAdd(&a.st->rechecks, 1ull);
+  if (fabsf(s32) > fmaf(__ldg(a.cB32 + c), xu, a.babs32)) return s32 > 0.f;
+  const int sg = dot2_sign<true>(a.X, i, d, wc, 1, a.dot2c, a.dot2abs);
+  return sg != 0 ? sg > 0 : exact_bit<true>(a.X, i, d, a.Wt, c);
+}
+
+// KC > 0: specialised for K = KC (compile-time table offsets); KC = 0 handles any K.
+template <typename IdT, int KC, bool PROJ>
+__global__ void __launch_bounds__(kThreads, 1)
+    hash_gemm_kernel(const __grid_constant__ GemmArgs a, const __grid_constant__ CUtensorMap tmX,
+                     const __grid_constant__ CUtensorMap tmW) {
+  extern __shared__ uint8_t smem_raw[];
+  // the swizzled tiles need 1024-byte alignment
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* const smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  const uint32_t sbase = smem_u32(smem);
+  GSmem* const S = reinterpret_cast<GSmem*>(smem + kStages * kStageBytes);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long ntiles = a.ntiles, n = a.n;
+  const int nunits = a.nunits, nkb = a.nkb, nprod = a.nprod;
+  const int ksteps = nprod * nkb;
+
+  if (tid == 0) {
+    S->abort = 0;
+    S->ndef = 0;
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&S->full[s], 1);
+      mbar_init(&S->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&S->t_full[b], 1);
+      mbar_init(&S->t_empty[b], 128);
+      mbar_init(&S->b_full[b], 64);
+      mbar_init(&S->b_empty[b], 128);
+    }
+    mbar_init(&S->drain, 1);
+    mbar_fence_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&S->taddr, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S->taddr;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      tma_prefetch(&tmX);
+      tma_prefetch(&tmW);
+      long long it = 0;
+      bool ok = true;
+      for (long long m = blockIdx.x; ok && m < ntiles; m += gridDim.x) {
+        for (int u = 0; ok && u < nunits; ++u) {
+          for (int ks = 0; ks < ksteps; ++ks, ++it) {
+            const int s = static_cast<int>(it % kStages);
+            if (it >= kStages && !mbar_wait(&S->empty[s], static_cast<uint32_t>(((it / kStages) + 1) & 1), &S->abort,
+                                            kWaitCycles)) {
+              ok = false;
+              set_abort(S, a.st);
+              break;
+            }
+            const int p = ks / nkb, kb = ks - p * nkb;
+            // the lo part (rows klp.. of the image) first, then the hi part
+            const int brow = (nprod == 2 && p == 0 ? a.klp : 0) + u * kGemmBN;
+            const uint32_t sa = sbase + static_cast<uint32_t>(s) * kStageBytes;
+            expect_tx(&S->full[s], kStageBytes);
+            tma_load_2d(sa, &tmX, kb * kGemmBK, static_cast<int>(m * kGemmBM), &S->full[s]);
+            tma_load_2d(sa + kABytes, &tmW, kb * kGemmBK, brow, &S->full[s]);
+          }
+        }
+      }
+      // leave no copy in flight: the newest phase of every stage used has completed (bounded
+      // waits that ignore the abort flag)
+      const int never = 0;
+      for (long long k = it - 1; k >= 0 && k >= it - kStages; --k)
+        mbar_wait(&S->full[k % kStages], static_cast<uint32_t>((k / kStages) & 1), &never, kWaitCycles);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(kGemmBM, kGemmBN);
+      long long it = 0, u = 0;
+      bool ok = true;
+      for (long long m = blockIdx.x; ok && m < ntiles; m += gridDim.x) {
+        for (int un = 0; ok && un < nunits; ++un, ++u) {
+          const int b = static_cast<int>(u & 1);
+          if (u >= 2 && !mbar_wait(&S->t_empty[b], static_cast<uint32_t>(((u >> 1) + 1) & 1), &S->abort, kWaitCycles)) {
+            ok = false;
+            set_abort(S, a.st);
+            break;
+          }
+          tc_fence_after();
+          const uint32_t dt = tmem + static_cast<uint32_t>(b * kGemmBN);
+          uint32_t acc = 0;
+          for (int ks = 0; ks < ksteps; ++ks, ++it) {
+            const int s = static_cast<int>(it % kStages);
+            if (!mbar_wait(&S->full[s], static_cast<uint32_t>((it / kStages) & 1), &S->abort, kWaitCycles)) {
+              ok = false;
+              set_abort(S, a.st);
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = sbase + static_cast<uint32_t>(s) * kStageBytes;
+            const uint64_t ad = sdesc_sw128(sa), bd = sdesc_sw128(sa + kABytes);
+#pragma unroll
+            for (int kk = 0; kk < kGemmBK / 16; ++kk) {
+              mma_bf16(dt, ad + 2u * kk, bd + 2u * kk, idesc, acc);
+              acc = 1;
+            }
+            mma_commit(&S->empty[s]);
+          }
+          if (!ok) break;
+          mma_commit(&S->t_full[b]);
+        }
+      }
+      // every MMA issued has completed before TMEM is released (bounded by time only)
+      const int never = 0;
+      mma_commit(&S->drain);
+      if (!mbar_wait(&S->drain, 0, &never, kWaitCycles)) set_abort(S, a.st);
+    }
+    __syncwarp();
+  } else if (warp < 4) {
+    // ------------------------------------------------------------------ row bounds
+    // Warp w2 takes rows 64 w2 .. 64 w2 + 63 of each tile, four rows at a time; the lanes read
+    // a row's 16-byte chunks (coalesced) and join their binary32 sums of squares by shuffles.
+    // Any summation order is covered by the gamma_d inflation in xfac.
+    const int w2 = warp - 2;
+    const int nch = a.d / 8;
+    const float tau = a.tau, tau_abs = a.tau_abs, xfac = a.xfac, qmin = a.qmin;
+    const uint4* const X4 = reinterpret_cast<const uint4*>(a.X);
+    const bool count_nonfinite = !(a.mode & kStoreProj);
+    int ml = 0;
+    for (long long m = blockIdx.x; m < ntiles; m += gridDim.x, ++ml) {
+      const int t = ml & 1;
+      bool ok = S->abort == 0;
+      if (ok && ml >= 2) ok = mbar_wait(&S->b_empty[t], static_cast<uint32_t>(((ml >> 1) + 1) & 1), &S->abort, kWaitCycles);
+      if (!__all_sync(0xFFFFFFFFu, ok)) {
+        if (lane == 0) set_abort(S, a.st);
+        break;
+      }
+      for (int r0 = 0; r0 < 64; r0 += 4) {
+        float q[4] = {0.f, 0.f, 0.f, 0.f};
+        uint32_t nz[4] = {0u, 0u, 0u, 0u};
+        long long row[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) row[j] = m * kGemmBM + w2 * 64 + r0 + j;
+        for (int c = lane; c < nch; c += 32) {
+          uint4 v[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            v[j] = row[j] < n ? __ldg(X4 + row[j] * nch + c) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const uint32_t w[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float lo = bf16_lo(w[e]), hi = bf16_hi(w[e]);
+              q[j] = fmaf(lo, lo, q[j]);
+              q[j] = fmaf(hi, hi, q[j]);
+              nz[j] |= w[e] & 0x7FFF7FFFu;
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) {
+            q[j] += __shfl_xor_sync(0xFFFFFFFFu, q[j], off);
+            nz[j] |= __shfl_xor_sync(0xFFFFFFFFu, nz[j], off);
+          }
+        }
+        if (lane < 4) {
+          float qq = q[0];
+          uint32_t zz = nz[0];
+          long long ii = row[0];
+#pragma unroll
+          for (int j = 1; j < 4; ++j)
+            if (lane == j) {
+              qq = q[j];
+              zz = nz[j];
+              ii = row[j];
+            }
+          uint32_t thr, zero = 0u;
+          if (zz == 0u) {  // every coordinate is +-0: every projection is exactly 0, bit 0
+            thr = 0u;
+            zero = 1u;
+          } else if (!isfinite(qq) || qq < qmin) {
+            thr = 0xFFFFFFFFu;  // every column of the row is resolved exactly
+          } else {
+            const float B = fmaf(tau, sqrtf(qq * xfac) * 1.00000095367431640625f, tau_abs);
+            thr = __float_as_uint(B) + 1u;  // |v| <= B  <=>  bits(|v|) < bits(B) + 1
+          }
+          S->bthr[t][w2 * 64 + r0 + lane] = thr;
+          S->bzero[t][w2 * 64 + r0 + lane] = zero;
+          if (count_nonfinite && ii < n && !isfinite(qq)) atomicAdd(&a.st->nonfinite, 1ull);
+        }
+      }
+      mbar_arrive(&S->b_full[t]);
+    }
+  } else {
+    // ------------------------------------------------------------------ epilogue
+    const int q4 = warp & 3;
+    const int r = q4 * 32 + lane;  // TMEM lane = tile row
+    const int K = KC > 0 ? KC : a.K;
+    const int L = a.L, tpu = a.tpu, mode = a.mode;
+    const long long ld = a.ld;
+    const bool st_tm = (mode & kStoreIds) != 0, st_rm = (mode & kStoreIdsRowMajor) != 0;
+    IdT* const ids = reinterpret_cast<IdT*>(a.ids);
+    uint32_t* const ids_rm = a.ids_rm;
+    const unsigned long long seg_cap = a.seg_cap;
+    unsigned long long* const seg = a.defer + seg_cap * blockIdx.x;
+    const uint32_t kmask = K >= 32 ? 0xFFFFFFFFu : (1u << K) - 1u;
+    long long u = 0;
+    int ml = 0;
+    bool ok = true;
+    for (long long m = blockIdx.x; ok && m < ntiles; m += gridDim.x, ++ml) {
+      const int tslot = ml & 1;
+      ok = mbar_wait(&S->b_full[tslot], static_cast<uint32_t>((ml >> 1) & 1), &S->abort, kWaitCycles);
+      if (!__all_sync(0xFFFFFFFFu, ok)) {
+        ok = false;
+        if (lane == 0) set_abort(S, a.st);
+        break;
+      }
+      const uint32_t thr = S->bthr[tslot][r];
+      const bool zero_row = S->bzero[tslot][r] != 0u;
+      mbar_arrive(&S->b_empty[tslot]);
+      const long long i = m * kGemmBM + r;
+      const bool valid = i < n;
+      for (int un = 0; un < nunits; ++un, ++u) {
+        const int b = static_cast<int>(u & 1);
+        ok = mbar_wait(&S->t_full[b], static_cast<uint32_t>((u >> 1) & 1), &S->abort, kWaitCycles);
+        if (!__all_sync(0xFFFFFFFFu, ok)) {
+          ok = false;
+          if (lane == 0) set_abort(S, a.st);
+          break;
+        }
+        tc_fence_after();
+        const int j0 = un * tpu;
+        const int ntab = min(tpu, L - j0);
+        const int ncols = ntab * K;
+        const int c0 = j0 * K;  // detector column of unit column 0
+        const uint32_t tbase = tmem + (static_cast<uint32_t>(q4 * 32) << 16) + static_cast<uint32_t>(b * kGemmBN);
+        uint32_t sw[8], aw[8];
+        uint32_t v[64];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          tmem_ld64(tbase + 64u * h, v);
+          tmem_ld_wait(v);
+#pragma unroll
+          for (int qh = 0; qh < 2; ++qh) {
+            const int g = 2 * h + qh;
+            const uint32_t* vv = v + 32 * qh;
+            // sign bits: four funnel-shift chains, column k's sign at bit 31 - k, then reversed
+            uint32_t c_0 = 0u, c_1 = 0u, c_2 = 0u, c_3 = 0u;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              c_0 = __funnelshift_l(vv[k], c_0, 1);
+              c_1 = __funnelshift_l(vv[8 + k], c_1, 1);
+              c_2 = __funnelshift_l(vv[16 + k], c_2, 1);
+              c_3 = __funnelshift_l(vv[24 + k], c_3, 1);
+            }
+            sw[g] = ~__brev((c_0 << 24) | (c_1 << 16) | (c_2 << 8) | c_3);
+            uint32_t am = 0u;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) am |= ((vv[k] & 0x7FFFFFFFu) < thr ? 1u : 0u) << k;
+            aw[g] = am;
+            if constexpr (PROJ) {
+              if (valid) {
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                  const int uc = 32 * g + k;
+                  if (uc < ncols)
+                    a.proj[i * static_cast<long long>(a.KL) + c0 + uc] = __uint_as_float(vv[k]) * __ldg(a.wnorm + c0 + uc);
+                }
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&S->t_empty[b]);
+        if constexpr (PROJ) continue;
+        // columns past the unit's last table (zero image rows) carry no bit
+        uint32_t cnt = 0u;
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+          const int lo = 32 * g;
+          const uint32_t cm = ncols >= lo + 32 ? 0xFFFFFFFFu : (ncols > lo ? (1u << (ncols - lo)) - 1u : 0u);
+          if (zero_row) sw[g] = 0u;
+          aw[g] = valid ? (aw[g] & cm) : 0u;
+          cnt += __popc(aw[g]);
+        }
+        // deferred (point, column) entries: one shared-memory atomic per row that has any; past
+        // the segment's capacity the bit is resolved here
+        if (cnt) {
+          unsigned long long idx = atomicAdd(&S->ndef, cnt);
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            uint32_t mm = aw[g];
+            while (mm) {
+              const int k = __ffs(mm) - 1;
+              mm &= mm - 1u;
+              const int c = c0 + 32 * g + k;
+              const uint32_t tb = (sw[g] >> k) & 1u;
+              if (idx < seg_cap) {
+                seg[idx] = (static_cast<unsigned long long>(i) << kGemmEntryShift) |
+                           (static_cast<unsigned long long>(c) << 1) | tb;
+              } else {
+                const uint32_t eb = exact_col_bit(a, i, c) ? 1u : 0u;
+                sw[g] ^= (eb ^ tb) << k;
+              }
+              ++idx;
+            }
+          }
+        }
+        if (!valid) continue;
+        // bucket ids (Eq. 2): table t of the unit is bits [t K, t K + K)
+        if constexpr (KC == 16) {
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {
+            if (t < ntab) {
+              const uint32_t id = (sw[t >> 1] >> ((t & 1) * 16)) & 0xFFFFu;
+              if (st_tm) ids[static_cast<size_t>(j0 + t) * ld + i] = static_cast<IdT>(id);
+              if (st_rm) ids_rm[i * L + j0 + t] = id;
+            }
+          }
+        } else {
+          unsigned long long accb = 0ull;
+          int nacc = 0, t = 0;
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            accb |= static_cast<unsigned long long>(sw[g]) << nacc;
+            nacc += 32;
+            while (nacc >= K && t < ntab) {
+              const uint32_t id = static_cast<uint32_t>(accb) & kmask;
+              accb >>= K;
+              nacc -= K;
+              if (st_tm) ids[static_cast<size_t>(j0 + t) * ld + i] = static_cast<IdT>(id);
+              if (st_rm) ids_rm[i * L + j0 + t] = id;
+              ++t;
+            }
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0) {
+    a.defer_counts[blockIdx.x] = static_cast<unsigned int>(min(static_cast<unsigned long long>(S->ndef), a.seg_cap));
+    if (S->ndef && !(a.mode & kStoreProj)) atomicAdd(&a.st->deferred, static_cast<unsigned long long>(S->ndef));
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// Exact resolution of the deferred (point, column) entries.  One warp per entry: the lanes
+// split the dot product (lane l: 16-byte chunks l, l + 32, ... of the bfloat16 row and the
+// matching binary32 W column), each as a binary32 FMA chain, join the sums by a butterfly of
+// shuffles and keep the binary32 sum R of the magnitudes of every rounded partial result.
+// u R / ((1 - u)(1 - gamma_(d+64))) plus underflow and the binary64 sum's own error bounds the
+// distance to the definition whatever the summation tree (the SIMT engine's warp recheck),
+// and the a priori gamma_d bound holds as well; the smaller decides.  What neither decides
+// goes to Dot2 and then to the binary64 definition (one lane).  A bit that differs from the
+// stored one is flipped in the id with an atomic XOR (other columns of the same id may be
+// resolved by other warps at the same time).
+template <typename IdT>
+__global__ void __launch_bounds__(256) recheck_cols_kernel(const __grid_constant__ GemmArgs a, int nseg) {
+  const int lane = threadIdx.x & 31;
+  const unsigned nwarps = gridDim.x * (blockDim.x >> 5);
+  const unsigned gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const unsigned per_seg = max(1u, nwarps / static_cast<unsigned>(nseg));
+  if (gw >= per_seg * static_cast<unsigned>(nseg)) return;
+  const int seg = static_cast<int>(gw % static_cast<unsigned>(nseg));
+  const unsigned lw = gw / static_cast<unsigned>(nseg);
+  const unsigned long long cnt = a.defer_counts[seg];
+  const unsigned long long* const list = a.defer + a.seg_cap * static_cast<unsigned long long>(seg);
+  const int d = a.d, K = a.K, L = a.L, mode = a.mode;
+  const int nch = d / 8;
+  const long long ld = a.ld;
+  unsigned long long nre = 0;
+  for (unsigned long long e = lw; e < cnt; e += per_seg) {
+    const unsigned long long w = list[e];
+    const long long i = static_cast<long long>(w >> kGemmEntryShift);
+    const int c = static_cast<int>((w >> 1) & 0xFFFFull);
+    const uint32_t tb = static_cast<uint32_t>(w & 1ull);
+    const uint4* xr = reinterpret_cast<const uint4*>(a.X) + i * nch;
+    const float4* wr = reinterpret_cast<const float4*>(a.Wt + static_cast<size_t>(c) * d);
+    float s = 0.f, run = 0.f, q = 0.f;
+    for (int ch = lane; ch < nch; ch += 32) {
+      const uint4 xv = __ldg(xr + ch);
+      const float4 w0 = __ldg(wr + 2 * ch), w1 = __ldg(wr + 2 * ch + 1);
+      const float xs[8] = {bf16_lo(xv.x), bf16_hi(xv.x), bf16_lo(xv.y), bf16_hi(xv.y),
+                           bf16_lo(xv.z), bf16_hi(xv.z), bf16_lo(xv.w), bf16_hi(xv.w)};
+      const float ws[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        s = fmaf(xs[k], ws[k], s);
+        run = __fadd_rn(run, fabsf(s));
+        q = fmaf(xs[k], xs[k], q);
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float so = __shfl_xor_sync(0xFFFFFFFFu, s, off);
+      const float ro = __shfl_xor_sync(0xFFFFFFFFu, run, off);
+      q += __shfl_xor_sync(0xFFFFFFFFu, q, off);
+      s = __fadd_rn(s, so);
+      run = __fadd_rn(__fadd_rn(run, ro), fabsf(s));
+    }
+    const float xu = norm_upper(q, a.xfac32, a.xabs32);
+    const float cb = __ldg(a.cB32 + c);
+    const float brun = __fmaf_ru(a.runc, run, __fmaf_ru(__fmul_ru(a.run64, cb), xu, a.runabs));
+    const float bpri = fmaf(cb, xu, a.babs32);
+    bool bit;
+    if (fabsf(s) > fminf(brun, bpri)) {
+      bit = s > 0.f;
+    } else {
+      int sg = 0;
+      bool eb = false;
+      if (lane == 0) {
+        sg = dot2_sign<true>(a.X, i, d, a.Wt + static_cast<size_t>(c) * d, 1, a.dot2c, a.dot2abs);
+        eb = sg != 0 ? sg > 0 : exact_bit<true>(a.X, i, d, a.Wt, c);
+      }
+      bit = __shfl_sync(0xFFFFFFFFu, eb ? 1 : 0, 0) != 0;
+    }
+    if (lane == 0) {
+      ++nre;
+      if ((bit ? 1u : 0u) != tb) {
+        const int j = c / K, k = c - j * K;
+        if (mode & kStoreIds) {
+          IdT* p = reinterpret_cast<IdT*>(a.ids) + static_cast<size_t>(j) * ld + i;
+          if constexpr (sizeof(IdT) == 2) {
+            const uintptr_t ad = reinterpret_cast<uintptr_t>(p);
+            atomicXor(reinterpret_cast<unsigned int*>(ad & ~static_cast<uintptr_t>(3)),
+                      (1u << k) << ((ad & 2u) * 8u));
+          } else {
+            atomicXor(reinterpret_cast<unsigned int*>(p), 1u << k);
+          }
+        }
+        if (mode & kStoreIdsRowMajor) atomicXor(a.ids_rm + i * L + j, 1u << k);
+      }
+    }
+  }
+  if (lane == 0 && nre) atomicAdd(&a.st->rechecks, nre);
+}
+
+}  // namespace
+
+int gemm_smem_bytes() { return kSmemBytes; }
+
+cudaError_t launch_hash_gemm(const GemmArgs& a, const void* tmX, const void* tmW, int num_sms, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const long long grid = min(static_cast<long long>(num_sms), a.ntiles);
+  const CUtensorMap& mx = *static_cast<const CUtensorMap*>(tmX);
+  const CUtensorMap& mw = *static_cast<const CUtensorMap*>(tmW);
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    kern<<<static_cast<unsigned>(grid), kThreads, kSmemBytes, s>>>(a, mx, mw);
+    return cudaGetLastError();
+  };
+  if (a.mode & kStoreProj) return a.K > 16 ? go(hash_gemm_kernel<uint32_t, 0, true>) : go(hash_gemm_kernel<uint16_t, 0, true>);
+  if (a.K > 16) return go(hash_gemm_kernel<uint32_t, 0, false>);
+  if (a.K == 16) return go(hash_gemm_kernel<uint16_t, 16, false>);
+  return go(hash_gemm_kernel<uint16_t, 0, false>);
+}
+
+cudaError_t launch_recheck_cols(const GemmArgs& a, int nseg, int num_sms, cudaStream_t s) {
+  if (a.n <= 0 || nseg <= 0) return cudaSuccess;
+  auto go = [&](auto kern) -> cudaError_t {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = static_cast<unsigned>(num_sms * max(1, per_sm));
+    if (grid * 8u < static_cast<unsigned>(nseg)) return cudaErrorInvalidConfiguration;
+    kern<<<grid, 256, 0, s>>>(a, nseg);
+    return cudaGetLastError();
+  };
+  return a.K > 16 ? go(recheck_cols_kernel<uint32_t>) : go(recheck_cols_kernel<uint16_t>);
+}
+
+}  // namespace ace

@@ -1,0 +1,88 @@
+// Measurement hook: one chain of tcgen05 bfloat16 MMAs on caller-chosen operands.
+//
+// The tensor-core guard bands (hash_tc.cu, hash_gemm.cu) rest on a model of how one
+// kind::f16 MMA instruction accumulates its 16 products and the accumulator in binary32.
+// This kernel runs D = A . B^T (A 128 x kd, B N x kd, bfloat16, K-major) as kd/16 MMAs of
+// 128 x N x 16 into one TMEM accumulator, exactly like the hash kernels do, and returns D, so
+// that a test can feed chosen sums and check the model against the hardware.
+#include "ace_internal.h"
+#include "tc_ptx.cuh"
+
+namespace ace {
+namespace {
+
+using namespace tc;
+
+constexpr long long kProbeWait = 2000000000LL;  // about 1 s at 2 GHz
+
+__global__ void __launch_bounds__(128, 1)
+    tc_probe_kernel(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, int kd, int N,
+                    float* __restrict__ D, int* __restrict__ status) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t taddr;
+  uint8_t* const sa = sm;
+  uint8_t* const sb = sm + 128 * kd * 2;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // operands in the K-major, no-swizzle canonical layout (8 x 8 core matrices)
+  for (int e = tid; e < 128 * kd; e += 128)
+    *reinterpret_cast<uint16_t*>(sa + kmajor_offset(e / kd, e % kd, kd)) = A[e];
+  for (int e = tid; e < N * kd; e += 128)
+    *reinterpret_cast<uint16_t*>(sb + kmajor_offset(e / kd, e % kd, kd)) = B[e];
+  fence_proxy_async();
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&taddr, 256);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = taddr;
+  if (tid == 0) {
+    const uint32_t idesc = idesc_bf16(128, N);
+    const uint32_t sbo = static_cast<uint32_t>(kd) * 16u;
+    for (int ks = 0; ks < kd / 16; ++ks)
+      mma_bf16(tmem, smem_desc(smem_u32(sa) + 256u * ks, 128, sbo), smem_desc(smem_u32(sb) + 256u * ks, 128, sbo),
+               idesc, ks > 0 ? 1u : 0u);
+    mma_commit(&bar);
+  }
+  __syncwarp();
+  const int never = 0;
+  const bool ok = mbar_wait(&bar, 0, &never, kProbeWait);
+  if (!ok && tid == 0) *status = 1;
+  tc_fence_after();
+  if (ok) {
+    uint32_t v[64];
+    const int row = warp * 32 + (tid & 31);
+    for (int c = 0; c < N; c += 64) {
+      tmem_ld64(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(c), v);
+      tmem_ld_wait(v);
+#pragma unroll
+      for (int j = 0; j < 64; ++j)
+        if (c + j < N) D[static_cast<size_t>(row) * N + c + j] = __uint_as_float(v[j]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 256);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_tc_probe(const uint16_t* A, const uint16_t* B, int kd, int N, float* D, int* status,
+                            cudaStream_t s) {
+  const int smem = (128 + N) * kd * 2;
+  cudaError_t e = cudaFuncSetAttribute(tc_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  tc_probe_kernel<<<1, 128, smem, s>>>(A, B, kd, N, D, status);
+  return cudaGetLastError();
+}
+
+}  // namespace ace

@@ -291,11 +291,13 @@ def test_output_buffers_at_any_alignment(precision):
 
 
 def test_tensor_core_engine_refuses_unfit_shapes():
+    """No tensor-core design covers d > 64 with d not a multiple of 8; AUTO then runs the SIMT
+    engine."""
     with pytest.raises(ace.AceError) as e:
-        ace.Detector(1024, 16, 64, seed=1, precision="bf16")
+        ace.Detector(1028, 16, 64, seed=1, precision="bf16")
     assert e.value.code == ace.ACE_ERR_UNSUPPORTED
-    det = ace.Detector(1024, 16, 64, seed=1, precision="auto")  # falls back to the SIMT engine
-    X = torch.zeros((4, 1024), dtype=torch.float32, device="cuda")
+    det = ace.Detector(1028, 16, 64, seed=1, precision="auto")
+    X = torch.zeros((4, 1028), dtype=torch.bfloat16, device="cuda")
     det.insert(X)
     assert det.stats()["precision"] == ace.ACE_PROJ_FP32
 
