@@ -185,17 +185,20 @@ def cpu_baseline(X: np.ndarray, detector_seed: int, budget_s: float = 12.0) -> d
 
 
 def _config_cases():
-    """C1, C2 at full size and C3's shape at n = 100,000 (its generator costs about a second per
-    10,000 rows on the host; the d = 1024 projection is compute-bound, so the rate per point
-    does not depend on n at this size)."""
+    """C1 and C2 at full size (host batches) and C3 at its full size, n = 1,000,000, drawn on the
+    device (its host generator takes minutes at that size); the CPU oracle times C3 on a host
+    draw of the same recipe (its rate per point does not depend on n)."""
     from paper_1706_06664_gb300 import workloads
+    Xd, _ = workloads.highdim_device(seed=3, n=1_000_000)
+    c3 = {"X_dev": Xd, "d": 1024, "K": 16, "L": 64, "dtype": "bf16",
+          "X": workloads.highdim(seed=3, n=20_000)["X"]}
     return [("small", workloads.small(seed=1)), ("kdd-shaped", workloads.kdd(seed=2)),
-            ("high-dimensional (n=100,000 of 1,000,000)", workloads.highdim(seed=3, n=100_000))]
+            ("high-dimensional", c3)]
 
 
 def oracle_per_config(cases, budget_s: float = 1.5) -> dict:
     """The CPU oracle's insert+score rate per config, on all host cores and on one core:
-    insert_score on a fresh detector over a prefix of the config's batch sized to about
+    insert_score on a fresh detector over a prefix of the config's (host) batch sized to about
     budget_s seconds (a 200-point probe sets the size)."""
     import oracle
     out = {}
@@ -222,21 +225,39 @@ def oracle_per_config(cases, budget_s: float = 1.5) -> dict:
     return out
 
 
+def _step_roofline(n, d, K, L, x_bytes, ms, peaks):
+    """The whole call against the spec roofline: t_roof = max((X + W bytes) / HBM,
+    projection flop / bf16 peak), with the measured peaks; frac = t_roof / measured time."""
+    flop = 2.0 * n * d * K * L
+    byt = n * d * x_bytes + d * K * L * 4
+    t_roof = max(byt / (peaks["hbm_gbs"] * 1e9), flop / (peaks["bf16_tflops"] * 1e12))
+    return {"t_roof_ms": t_roof * 1e3, "frac": t_roof / (ms / 1e3),
+            "bound": "tensor" if flop / (peaks["bf16_tflops"] * 1e12) >= byt / (peaks["hbm_gbs"] * 1e9) else "hbm",
+            "peaks": f"{peaks['hbm_gbs']:.0f} GB/s, {peaks['bf16_tflops']:.0f} TFLOP/s bf16 ({peaks['src']})"}
+
+
 def per_config(cases) -> dict:
     """insert+score points/s per config on each engine it runs on, against the plain binary32
     (FP32) engine: CUDA events on the launching stream around each call, median of 10 calls
-    after 3 warm-up calls on one detector per engine, the batch resident in HBM.  The batched
-    (C4) and streaming (C5) configs have sections of their own."""
+    after 3 warm-up calls on one detector per engine, the batch resident in HBM; the hash
+    kernel's own time from the library's timing hook (its roofline fraction in algorithmic
+    flop against the measured bf16 peak), and the whole call against the spec roofline.
+    The batched (C4) and streaming (C5) configs have sections of their own."""
     import torch
     from paper_1706_06664_gb300 import ace
     stream = torch.cuda.current_stream()
+    peaks = _peaks()
     out = {}
     for name, w in cases:
-        X = w["X"]
-        Xd = torch.from_numpy(X.view(np.int16) if X.dtype == np.uint16 else X).cuda()
-        n = X.shape[0]
+        if "X_dev" in w:
+            Xd = w["X_dev"]
+        else:
+            X = w["X"]
+            Xd = torch.from_numpy(X.view(np.int16) if X.dtype == np.uint16 else X).cuda()
+        n = Xd.shape[0]
+        xb = 2 if w.get("dtype") == "bf16" else 4
         flop = 2.0 * n * w["d"] * w["K"] * w["L"]
-        res = {"n": n, "d": w["d"], "K": w["K"], "L": w["L"]}
+        res = {"n": n, "d": w["d"], "K": w["K"], "L": w["L"], "x_dtype": "bf16" if xb == 2 else "f32"}
         for prec, want in (("fp32", ace.ACE_PROJ_FP32), ("bf16", ace.ACE_PROJ_BF16)):
             try:
                 det = ace.Detector(w["d"], w["K"], w["L"], seed=11, precision=prec)
@@ -245,22 +266,45 @@ def per_config(cases) -> dict:
                     res[prec] = "engine not available for this shape"
                     continue
                 raise
+            reps = 13 if not (prec == "fp32" and n * w["d"] * w["K"] * w["L"] > 1e11) else 5
             times = []
-            for r in range(13):
+            for r in range(reps):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                if r == 3:
+                    det.profile_read()
+                    det.profile(True)
                 e0.record(stream)
                 det.insert_score(Xd, ALPHA, stream=stream)
                 e1.record(stream)
                 torch.cuda.synchronize()
                 if r >= 3:
                     times.append(e0.elapsed_time(e1) / 1e3)
-            used = det.stats()["precision"]
+            det.profile(False)
+            prof = det.profile_read()
+            st = det.stats()
+            used = st["precision"]
             det.close()
             if used != want:
                 res[prec] = "engine not used for this shape"
                 continue
             t = statistics.median(times)
-            res[prec] = {"points_per_s": n / t, "ms": t * 1e3, "projection_tflops": flop / t / 1e12}
+            phases = {k: v["ms"] / v["timed"] for k, v in prof.items() if v["timed"]}
+            entry = {"points_per_s": n / t, "ms": t * 1e3, "projection_tflops": flop / t / 1e12,
+                     "phases_ms": phases, "rechecks_per_point": st["rechecks"] / (n * reps),
+                     "deferred_per_point": st["deferred"] / (n * reps),
+                     "step_roofline": _step_roofline(n, w["d"], w["K"], w["L"], xb, t * 1e3, peaks)}
+            if "hash" in phases:
+                th = phases["hash"] / 1e3
+                if prec == "bf16":
+                    entry["hash_roofline"] = {"bound": "tensor", "achieved": flop / th / 1e12,
+                                              "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                                              "frac": flop / th / 1e12 / peaks["bf16_tflops"],
+                                              "peak_src": f"bf16 burst, {peaks['src']}"}
+                else:
+                    entry["hash_roofline"] = {"bound": "alu", "achieved": flop / th / 1e12, "peak": FP32_ALU_PEAK_TFLOPS,
+                                              "unit": "TFLOP/s", "frac": flop / th / 1e12 / FP32_ALU_PEAK_TFLOPS,
+                                              "peak_src": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"}
+            res[prec] = entry
         if isinstance(res.get("bf16"), dict) and isinstance(res.get("fp32"), dict):
             res["bf16_vs_fp32"] = res["bf16"]["points_per_s"] / res["fp32"]["points_per_s"]
         out[name] = res
@@ -418,7 +462,7 @@ def projection_errors() -> dict:
     from paper_1706_06664_gb300 import ace, workloads
     cases = [("small", workloads.small(seed=1, n=4000), ("fp32", "bf16")),
              ("kdd-shaped", workloads.kdd(seed=2, n=20000), ("fp32", "bf16")),
-             ("high-dimensional (d=1024, bf16 input)", workloads.highdim(seed=3, n=1000), ("fp32",))]
+             ("high-dimensional (d=1024, bf16 input)", workloads.highdim(seed=3, n=1000), ("fp32", "bf16"))]
     out = {}
     for name, w, precs in cases:
         X = w["X"]
@@ -586,6 +630,7 @@ def run_ours(args):
                    "l2": "inputs rotate over 3 resident batches (246 MB > 129 MB L2)",
                    "parallelism": f"replicas x{ws} (independent detectors, no collective)"},
         "roofline": roof,
+        "step_roofline": _step_roofline(n, D, KH, LT, 4, ms_max / args.steps, peaks),
         "phases_ms_per_step": {k: v["ms"] / pre for k, v in pre_prof.items()},
         "phases_note": f"from {pre} steps with every kernel bracketed by CUDA events, before the timed "
                        f"steps; in the timed steps only '{top}' (the roofline's kernel) is bracketed, "

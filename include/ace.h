@@ -85,12 +85,22 @@ typedef struct {
   uint64_t nonfinite_points;/* points with a NaN/Inf coordinate or an overflowing norm   */
   uint32_t status;          /* ACE_STATUS_* bits                                         */
   int32_t precision;        /* ACE_PROJ_* path used by the last hash                     */
-  uint64_t deferred;        /* (point, table) pairs the tensor-core engine left to exact */
-                            /* resolution (inside its error bound); 0 on the SIMT engine */
+  uint64_t deferred;        /* entries the tensor-core engines left to exact resolution  */
+                            /* (inside their error bound): (point, table) pairs for the   */
+                            /* resident engine (d <= 64), (point, column) pairs for the   */
+                            /* streaming one (larger d); 0 on the SIMT engine             */
+  int32_t tc_products;      /* bfloat16 products per tensor-core accumulation in the last */
+                            /* hash: 3 (resident engine, x and W split), 2 (streaming, W  */
+                            /* split), 1 (streaming, bfloat16-valued W), 0 (SIMT)         */
 } ace_stats_t;
 
+/* Creation flags (ace_create_ex). */
+enum {
+  ACE_W_BF16 = 1u /* round every drawn W entry to bfloat16 (nearest even), kept as binary32 */
+};
+
 /*
- * ace_create — Algorithm 1 "Hash Initialize" (§3.2) and array allocation.
+ * ace_create — Algorithm 1's hash initialisation (§3.2) and array allocation.
  * Draws the d x (K*L) projection matrix W, w ~ N(0,1) (§2.1), from `seed` with SplitMix64
  * in counter mode (draw t = SplitMix64 output for state seed + (t+1)*0x9E3779B97F4A7C15)
  * and Box-Muller on pairs of draws (u1 = (draw_2p >> 11) + 1) * 2^-53, u2 = (draw_2p+1 >> 11)
@@ -101,6 +111,18 @@ typedef struct {
  * Errors: ACE_ERR_ARG, ACE_ERR_OOM, ACE_ERR_CUDA.
  */
 int ace_create(int d, int K, int L, uint64_t seed, ace_handle* out);
+
+/*
+ * ace_create_ex — ace_create with creation flags.  ACE_W_BF16: each drawn W entry (binary32,
+ * as ace_create) is rounded to bfloat16, round to nearest even.  The paper fixes neither the
+ * precision of W nor how it is stored, only w ~ N(0,1) (§2.1; §3.4 regenerates projections
+ * from stored seeds); with bfloat16-valued W the streaming tensor-core engine forms every
+ * product x_i w_i exactly in one bfloat16 MMA instead of two, and every id stays the binary64
+ * definition's for that W.  An explicit W whose entries are all bfloat16 values
+ * (ace_create_with_projection) gets the same single-product path.
+ * Errors: as ace_create; ACE_ERR_ARG for unknown flags.
+ */
+int ace_create_ex(int d, int K, int L, uint64_t seed, unsigned flags, ace_handle* out);
 
 /* As ace_create, with an explicit host d x (K*L) row-major binary32 W (copied). */
 int ace_create_with_projection(int d, int K, int L, const float* W_host, ace_handle* out);
@@ -115,7 +137,7 @@ int ace_reset(ace_handle h, void* stream);
 int ace_set_precision(ace_handle h, int precision);
 
 /*
- * ace_insert — counting phase (Algorithm 1 pre-processing; §3.2 "Counting Phase"):
+ * ace_insert — counting phase (Algorithm 1 pre-processing; §3.2, counting phase):
  * for every point x of X (n x d), A_j[H_j(x)] += 1 for j = 1..L.  The result does not
  * depend on the order of the points.  n = 0 is a no-op.
  * Errors: ACE_ERR_ARG; ACE_ERR_OVERFLOW if n_ins + n would exceed 2^32 - 1 (a count could
@@ -124,7 +146,7 @@ int ace_set_precision(ace_handle h, int precision);
 int ace_insert(ace_handle h, const void* X_dev, int64_t n, int dtype, void* stream);
 
 /*
- * ace_score — query phase (Algorithm 1; §3.2 "Real-time (query) Phase") and the §5.3
+ * ace_score — query phase (Algorithm 1; §3.2, query phase) and the §5.3
  * threshold rule, against the arrays as they stand at the start of the call (scoring
  * never inserts).  For each point: sums_dev[i] = c_i = sum_j A_j[H_j(x_i)] (uint32),
  * scores_dev[i] = c_i / L (binary64), flags_dev[i] = 1 if scores_dev[i] < mu - alpha*sigma

@@ -56,6 +56,7 @@ def _load():
         P = ctypes.c_void_p
         i32, i64, u64, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
         lib.oracle_projection_from_seed.argtypes = [i32, i32, i32, u64, P]
+        lib.oracle_projection_from_seed_bf16.argtypes = [i32, i32, i32, u64, P]
         lib.oracle_splitmix64_draw.argtypes = [u64, u64]
         lib.oracle_splitmix64_draw.restype = u64
         lib.oracle_hash.argtypes = [P, i32, i64, i32, P, i32, i32, P]
@@ -100,10 +101,12 @@ def splitmix64_draw(seed: int, t: int) -> int:
     return int(_load().oracle_splitmix64_draw(ctypes.c_uint64(seed), ctypes.c_uint64(t)))
 
 
-def projection_from_seed(d: int, K: int, L: int, seed: int) -> np.ndarray:
-    """d x (K*L) binary32 Gaussian matrix (SplitMix64 counter mode + Box-Muller)."""
+def projection_from_seed(d: int, K: int, L: int, seed: int, w_bf16: bool = False) -> np.ndarray:
+    """d x (K*L) binary32 Gaussian matrix (SplitMix64 counter mode + Box-Muller); with w_bf16
+    every value is then rounded to bfloat16 (nearest even)."""
     W = np.empty((d, K * L), dtype=np.float32)
-    _load().oracle_projection_from_seed(d, K, L, ctypes.c_uint64(seed & (2**64 - 1)), _ptr(W))
+    fn = _load().oracle_projection_from_seed_bf16 if w_bf16 else _load().oracle_projection_from_seed
+    fn(d, K, L, ctypes.c_uint64(seed & (2**64 - 1)), _ptr(W))
     return W
 
 
@@ -189,10 +192,11 @@ def gather(ids: np.ndarray, counts: np.ndarray, K: int) -> np.ndarray:
 class Detector:
     """The oracle's detector state: W, the L count arrays, and the running sums."""
 
-    def __init__(self, d: int, K: int, L: int, seed: int | None = None, W: np.ndarray | None = None):
+    def __init__(self, d: int, K: int, L: int, seed: int | None = None, W: np.ndarray | None = None,
+                 w_bf16: bool = False):
         self.d, self.K, self.L = d, K, L
         if W is None:
-            W = projection_from_seed(d, K, L, seed if seed is not None else 0)
+            W = projection_from_seed(d, K, L, seed if seed is not None else 0, w_bf16=w_bf16)
         self.W = np.ascontiguousarray(W, dtype=np.float32)
         assert self.W.shape == (d, K * L)
         self.counts = np.zeros((L, 1 << K), dtype=np.uint32)

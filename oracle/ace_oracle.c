@@ -11,16 +11,16 @@
  * order written here.  Integer work (bucket ids, counts, sums) is exact.
  *
  * Paper map:
- *   oracle_projection_from_seed  Algorithm 1 "Hash Initialize": K*L independent Gaussian
+ *   oracle_projection_from_seed  Algorithm 1's hash initialisation: K*L independent Gaussian
  *                                projection vectors, w_i ~ N(0,1) (§2.1).  Generator:
  *                                SplitMix64 in counter mode + Box-Muller (see below).
  *   oracle_hash                  Eq. 1 (SRP bit h_w(x) = sign(w^T x)) and Eq. 2
  *                                (K bits concatenated into the meta-hash H_j), §3.2.
- *   oracle_insert                Algorithm 1 pre-processing phase; §3.2 "Counting Phase".
+ *   oracle_insert                Algorithm 1 pre-processing phase; §3.2 (counting phase).
  *   oracle_mu_incremental        Eq. 11 (mean update on insertion, §3.4.1), point by point.
  *   oracle_delete                §3.4.1 deletion: A_j[H_j(x)] -= 1 for every point of a batch.
  *   oracle_mu_decremental        Eq. 12 (mean update on deletion, §3.4.1), point by point.
- *   oracle_gather / oracle_score Algorithm 1 query phase; §3.2 "Real-time (query) Phase":
+ *   oracle_gather / oracle_score Algorithm 1 query phase; §3.2 (query phase):
  *                                S^(q) = (1/L) sum_j A_j[H_j(q)].
  *   oracle_stats_*               §5.3 threshold rule: report a point whose score is below
  *                                mu - alpha*sigma of the scores (alpha = 1 is the paper's
@@ -80,6 +80,22 @@ void oracle_projection_from_seed(int d, int K, int L, uint64_t seed, float* W) {
     double ang = two_pi * u2;
     double g = (f % 2u == 0u) ? r * cos(ang) : r * sin(ang);
     W[f] = (float)g;
+  }
+}
+
+/* The same matrix with every binary32 value then rounded to bfloat16 (the upper 16 bits  */
+/* of a binary32 pattern), round to nearest, ties to an even last bit; values are finite.   */
+/* Kept as binary32 values.                                                                */
+void oracle_projection_from_seed_bf16(int d, int K, int L, uint64_t seed, float* W) {
+  oracle_projection_from_seed(d, K, L, seed, W);
+  const uint64_t total = (uint64_t)d * (uint64_t)K * (uint64_t)L;
+  for (uint64_t f = 0; f < total; ++f) {
+    uint32_t bits;
+    memcpy(&bits, &W[f], sizeof bits);
+    uint32_t keep = bits >> 16, rest = bits & 0xFFFFu;
+    if (rest > 0x8000u || (rest == 0x8000u && (keep & 1u))) keep += 1u;
+    bits = keep << 16;
+    memcpy(&W[f], &bits, sizeof bits);
   }
 }
 

@@ -17,11 +17,12 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libace_gb300.so")
 ACE_OK, ACE_ERR_ARG, ACE_ERR_OOM, ACE_ERR_OVERFLOW, ACE_ERR_TIMEOUT, ACE_ERR_CUDA, ACE_ERR_UNSUPPORTED = range(7)
 ACE_F32, ACE_BF16 = 0, 1
 ACE_PROJ_AUTO, ACE_PROJ_FP32, ACE_PROJ_BF16 = -1, 0, 1
+ACE_W_BF16 = 1
 PRECISIONS = {"auto": ACE_PROJ_AUTO, "fp32": ACE_PROJ_FP32, "bf16": ACE_PROJ_BF16}
 
 # Every symbol include/ace.h declares (checked by the tests).
 EXPORTS = [
-    "ace_create", "ace_create_with_projection", "ace_destroy", "ace_reset", "ace_set_precision",
+    "ace_create", "ace_create_ex", "ace_create_with_projection", "ace_destroy", "ace_reset", "ace_set_precision",
     "ace_insert", "ace_score", "ace_insert_score", "ace_insert_score_host",
     "ace_insert_score_host_async", "ace_host_wait", "ace_delete", "ace_project", "ace_hash",
     "ace_batch_insert_score", "ace_server_create", "ace_server_submit", "ace_server_wait", "ace_server_drain", "ace_server_destroy", "ace_stats",
@@ -48,6 +49,7 @@ class ace_stats_t(ctypes.Structure):
         ("mu_ins", ctypes.c_double), ("mu", ctypes.c_double), ("sigma", ctypes.c_double),
         ("rechecks", ctypes.c_uint64), ("nonfinite_points", ctypes.c_uint64),
         ("status", ctypes.c_uint32), ("precision", ctypes.c_int32), ("deferred", ctypes.c_uint64),
+        ("tc_products", ctypes.c_int32),
     ]
 
 
@@ -72,6 +74,7 @@ def load_library(path: str = LIB_PATH):
         H = ctypes.c_void_p
         decl = {
             "ace_create": ([i32, i32, i32, u64, ctypes.POINTER(H)], i32),
+            "ace_create_ex": ([i32, i32, i32, u64, ctypes.c_uint32, ctypes.POINTER(H)], i32),
             "ace_create_with_projection": ([i32, i32, i32, P, ctypes.POINTER(H)], i32),
             "ace_destroy": ([H], i32),
             "ace_reset": ([H, P], i32),
@@ -146,12 +149,13 @@ class Detector:
     current CUDA device."""
 
     def __init__(self, d: int, K: int, L: int, seed: int = 0, W: np.ndarray | None = None,
-                 precision: str = "auto"):
+                 precision: str = "auto", w_bf16: bool = False):
         lib = load_library()
         self.d, self.K, self.L = int(d), int(K), int(L)
         h = ctypes.c_void_p()
         if W is None:
-            _check(lib.ace_create(self.d, self.K, self.L, ctypes.c_uint64(int(seed) & (2**64 - 1)), ctypes.byref(h)))
+            _check(lib.ace_create_ex(self.d, self.K, self.L, ctypes.c_uint64(int(seed) & (2**64 - 1)),
+                                     ACE_W_BF16 if w_bf16 else 0, ctypes.byref(h)))
         else:
             Wc = np.ascontiguousarray(W, dtype=np.float32)
             assert Wc.shape == (self.d, self.K * self.L)
@@ -292,7 +296,7 @@ class Detector:
             "Q": st.Q_lo | (st.Q_hi << 64), "S1": st.S1_lo | (st.S1_hi << 64), "S2": st.S2_lo | (st.S2_hi << 64),
             "mu_ins": st.mu_ins, "mu": st.mu, "sigma": st.sigma, "rechecks": st.rechecks,
             "nonfinite_points": st.nonfinite_points, "status": st.status, "precision": st.precision,
-            "deferred": st.deferred,
+            "deferred": st.deferred, "tc_products": st.tc_products,
         }
 
     def counts(self, stream=None) -> np.ndarray:

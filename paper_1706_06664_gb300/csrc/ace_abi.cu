@@ -52,6 +52,7 @@ struct ace_detector {
   int d = 0, K = 0, L = 0, KL = 0, device = 0;
   int precision = ACE_PROJ_AUTO;
   int last_precision = ACE_PROJ_FP32;
+  int last_products = 0;  // tensor-core products per accumulation in the last hash (0: SIMT)
   float* W = nullptr;       // [d][KL]
   float* Wt = nullptr;      // [KL][d]
   float* cB = nullptr;      // [KL]
@@ -102,6 +103,7 @@ struct ace_detector {
   bool gemm_ok = false;
   ace::GemmArgs gm{};           // constant part of the launch
   uint16_t* gimg = nullptr;     // [2 klp][dp] bfloat16 image of W' (hi rows, then lo rows)
+  float* gprof = nullptr;       // [2][dp/16] prefix and block norm maxima of the hi image
   CUtensorMap tm_img{};         // TMA description of gimg
   // profiling hook
   bool prof = false;
@@ -162,6 +164,7 @@ void free_all(ace_detector* h) {
   h->pool.clear();
   cudaFree(h->bimg);
   cudaFree(h->gimg);
+  cudaFree(h->gprof);
   cudaFree(h->defer);
   cudaFree(h->defer_counts);
   cudaFree(h->wpad);
@@ -444,9 +447,40 @@ int plan_gemm(ace_detector* h) {
   const int tpu = ace::kGemmBN / K;
   const int nunits = (L + tpu - 1) / tpu;
   const int klp = nunits * ace::kGemmBN;
-  std::vector<uint16_t> img(static_cast<size_t>(2) * klp * dp, 0);
+  // Single product when every W entry is a bfloat16 value (ace_create_ex with ACE_W_BF16, or an
+  // explicit W that happens to be): each column is scaled by a power of two to a norm in
+  // [1/2, 1) (exact), and x_i w_i is then one exact bfloat16 product.  Otherwise each column is
+  // normalised to unit length in binary32 and split into bfloat16 hi + lo parts (two products).
+  bool one = true;
+  std::vector<int> cexp(KL, 0);
+  for (int c = 0; c < KL && one; ++c) {
+    double s2 = 0.0;
+    for (int i = 0; i < d; ++i) {
+      const double w = h->Wh[static_cast<size_t>(i) * KL + c];
+      s2 += w * w;
+    }
+    int e = 0;
+    if (s2 > 0.0) std::frexp(std::sqrt(s2), &e);
+    cexp[c] = e;
+    for (int i = 0; i < d && one; ++i) {
+      const float ws = std::ldexp(h->Wh[static_cast<size_t>(i) * KL + c], -e);
+      one = std::isfinite(ws) && bf16_value(bf16_rn(ws)) == ws &&
+            (h->Wh[static_cast<size_t>(i) * KL + c] == 0.f || ws != 0.f);
+    }
+  }
+  const int nprod = one ? 1 : 2;
+  std::vector<uint16_t> img(static_cast<size_t>(nprod) * klp * dp, 0);
   std::vector<float> wn(KL, 0.f);
+  double rmax2 = 0.0;  // largest ||w' - w_hi - w_lo||^2 over the columns (exact in binary64)
   for (int c = 0; c < KL; ++c) {
+    const int j = c / K, k = c % K;
+    const size_t row = static_cast<size_t>(j / tpu) * ace::kGemmBN + static_cast<size_t>(j % tpu) * K + k;
+    if (one) {
+      wn[c] = std::ldexp(1.0f, cexp[c]);  // the scale back to x.w_c (ace_project)
+      for (int i = 0; i < d; ++i)
+        img[row * dp + i] = bf16_rn(std::ldexp(h->Wh[static_cast<size_t>(i) * KL + c], -cexp[c]));
+      continue;
+    }
     double s2 = 0.0;
     for (int i = 0; i < d; ++i) {
       const double w = h->Wh[static_cast<size_t>(i) * KL + c];
@@ -454,14 +488,17 @@ int plan_gemm(ace_detector* h) {
     }
     const double inv = s2 > 0.0 ? 1.0 / std::sqrt(s2) : 0.0;
     wn[c] = s2 > 0.0 ? static_cast<float>(std::sqrt(s2)) : 0.f;
-    const int j = c / K, k = c % K;
-    const size_t row = static_cast<size_t>(j / tpu) * ace::kGemmBN + static_cast<size_t>(j % tpu) * K + k;
+    double r2 = 0.0;
     for (int i = 0; i < d; ++i) {
       const float w1 = static_cast<float>(static_cast<double>(h->Wh[static_cast<size_t>(i) * KL + c]) * inv);
       const uint16_t hi = bf16_rn(w1);
+      const uint16_t lo = bf16_rn(w1 - bf16_value(hi));
       img[row * dp + i] = hi;
-      img[(static_cast<size_t>(klp) + row) * dp + i] = bf16_rn(w1 - bf16_value(hi));
+      img[(static_cast<size_t>(klp) + row) * dp + i] = lo;
+      const double r = static_cast<double>(w1) - bf16_value(hi) - bf16_value(lo);
+      r2 += r * r;
     }
+    rmax2 = std::max(rmax2, r2);
   }
   cudaFree(h->gimg);
   h->gimg = nullptr;
@@ -469,9 +506,38 @@ int plan_gemm(ace_detector* h) {
   if ((e = cudaMalloc(&h->gimg, bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc W' image");
   if ((e = cudaMemcpy(h->gimg, img.data(), bytes, cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_fail(e, "copy W' image");
-  if (int rc = encode_bf16_map(&h->tm_img, h->gimg, static_cast<uint64_t>(dp), static_cast<uint64_t>(2) * klp,
+  if (int rc = encode_bf16_map(&h->tm_img, h->gimg, static_cast<uint64_t>(dp), static_cast<uint64_t>(nprod) * klp,
                                ace::kGemmBN))
     return rc;
+  // WP_t = max over columns of ||w'_hi[0, 16t)||, WB_t = max of ||w'_hi[16t, 16t + 16)||, for
+  // the S = dp/16 MMA instructions of one pass (rounded up)
+  const int S = dp / 16;
+  std::vector<float> prof(2 * static_cast<size_t>(S), 0.f);
+  {
+    std::vector<double> wp(S, 0.0), wb(S, 0.0);
+    for (int row = 0; row < klp; ++row) {
+      double pre = 0.0;
+      for (int t = 0; t < S; ++t) {
+        wp[t] = std::max(wp[t], pre);
+        double blk = 0.0;
+        for (int i = 16 * t; i < 16 * t + 16; ++i) {
+          const double v = bf16_value(img[static_cast<size_t>(row) * dp + i]);
+          blk += v * v;
+        }
+        wb[t] = std::max(wb[t], blk);
+        pre += blk;
+      }
+    }
+    for (int t = 0; t < S; ++t) {
+      prof[t] = std::nextafter(static_cast<float>(std::sqrt(wp[t]) * (1.0 + 1e-12)), FLT_MAX);
+      prof[S + t] = std::nextafter(static_cast<float>(std::sqrt(wb[t]) * (1.0 + 1e-12)), FLT_MAX);
+    }
+  }
+  cudaFree(h->gprof);
+  h->gprof = nullptr;
+  if ((e = cudaMalloc(&h->gprof, prof.size() * sizeof(float))) != cudaSuccess) return cuda_fail(e, "cudaMalloc norm profile");
+  if ((e = cudaMemcpy(h->gprof, prof.data(), prof.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(e, "copy norm profile");
   if (!h->wnorm) {
     if ((e = cudaMalloc(&h->wnorm, KL * sizeof(float))) != cudaSuccess) return cuda_fail(e, "cudaMalloc column norms");
     if ((e = cudaMemcpy(h->wnorm, wn.data(), KL * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -491,17 +557,22 @@ int plan_gemm(ace_detector* h) {
   g.KL = KL;
   g.tpu = tpu;
   g.nunits = nunits;
-  g.nprod = 2;
+  g.nprod = nprod;
   g.klp = klp;
-  // guard constants relative to ||x|| (unit columns); see hash_gemm.cu
+  // guard constants (unit columns; see hash_gemm.cu): B = ca E + cx ||x||_up + tau_abs with
+  // ca = 5.25 2^-23 (1.25 margin), cx = ca (2^-6 S + 1) + split + normalisation + gamma64_d.
+  // The split term |x . (w' - w_hi - w_lo)| <= ||x|| ||w' - w_hi - w_lo|| uses the largest
+  // residual norm over the columns (each residual element is at most 2^-16 |w'_i|).
   const double u32 = std::ldexp(1.0, -24), u64 = std::ldexp(1.0, -53);
-  const int S_hi = dp / 16, S_lo = dp / 16;
-  const double t_split = std::ldexp(1.0, -17);
-  const double t_acc = 5.25 * 1.5 * (S_hi * (1.0 + std::ldexp(1.0, -7)) + 1.0 + S_lo * std::ldexp(1.0, -8)) *
-                       std::ldexp(1.0, -23);
-  const double t_norm = std::ldexp(1.0, -23);
+  const double ca = 5.25 * std::ldexp(1.0, -23) * 1.25;
+  const double t_split = std::sqrt(rmax2) * (1.0 + 1e-12);
+  const double t_norm = one ? 0.0 : std::ldexp(1.0, -23);  // power-of-two scaling is exact
   const double g64 = d * u64 / (1.0 - d * u64);
-  g.tau = std::nextafter(static_cast<float>((t_split + t_acc + t_norm + g64) * 1.01), FLT_MAX);
+  g.ca = std::nextafter(static_cast<float>(ca * 1.01), FLT_MAX);
+  g.cx = std::nextafter(static_cast<float>((ca * (std::ldexp(1.0, -6) * S + 1.0) + t_split + t_norm + g64) * 1.01),
+                        FLT_MAX);
+  g.S = S;
+  g.wprof = h->gprof;
   g.tau_abs = static_cast<float>(2.0 * dp * std::ldexp(1.0, -125));
   const double g32 = d * u32 / (1.0 - d * u32);
   g.xfac = std::nextafter(static_cast<float>(1.0 + 2.0 * g32 + std::ldexp(1.0, -20)), FLT_MAX);
@@ -524,9 +595,11 @@ int plan_gemm(ace_detector* h) {
   return ACE_OK;
 }
 
-int make_detector(int d, int K, int L, const float* Wsrc, uint64_t seed, bool from_seed, ace_handle* out) {
+int make_detector(int d, int K, int L, const float* Wsrc, uint64_t seed, bool from_seed, unsigned flags,
+                  ace_handle* out) {
   if (!out) return fail(ACE_ERR_ARG, "out is NULL");
   *out = nullptr;
+  if (flags & ~static_cast<unsigned>(ACE_W_BF16)) return fail(ACE_ERR_ARG, "unknown creation flags 0x%x", flags);
   if (d < 1 || K < 1 || K > 24 || L < 1 || static_cast<long long>(K) * L > 65536)
     return fail(ACE_ERR_ARG, "invalid shape d=%d K=%d L=%d (need d>=1, 1<=K<=24, L>=1, K*L<=65536)", d, K, L);
   if (!from_seed && !Wsrc) return fail(ACE_ERR_ARG, "W_host is NULL");
@@ -551,6 +624,7 @@ int make_detector(int d, int K, int L, const float* Wsrc, uint64_t seed, bool fr
   }
   if (from_seed) ace::generate_projection(d, K, L, seed, h->Wh.data());
   else std::memcpy(h->Wh.data(), Wsrc, dkl * sizeof(float));
+  if (flags & ACE_W_BF16) ace::round_projection_bf16(h->Wh.data(), dkl);
   for (size_t i = 0; i < dkl; ++i)
     if (!std::isfinite(h->Wh[i])) {
       delete h;
@@ -718,7 +792,10 @@ int run_gemm(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_inser
   if (int rc = encode_bf16_map(&tmx, a.X, static_cast<uint64_t>(h->d), static_cast<uint64_t>(a.n), ace::kGemmBM))
     return rc;
   cudaError_t e;
-  if (!proj) h->last_precision = ACE_PROJ_BF16;
+  if (!proj) {
+    h->last_precision = ACE_PROJ_BF16;
+    h->last_products = g.nprod;
+  }
   {
     PhaseScope ps(h, ACE_PHASE_HASH, s);
     e = ace::launch_hash_gemm(g, &tmx, &h->tm_img, h->num_sms, s);
@@ -745,6 +822,7 @@ int run_hash(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_inser
                 h->d);
   if (eng == Engine::kSimt) {
     h->last_precision = ACE_PROJ_FP32;
+    h->last_products = 0;
     PhaseScope ps(h, ACE_PHASE_HASH, s);
     cudaError_t e = ace::launch_hash_simt(a, s);
     if (e != cudaSuccess) return cuda_fail(e, "hash kernel launch");
@@ -779,6 +857,7 @@ int run_hash(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_inser
   t.defer = h->defer;
   t.seg_cap = h->defer_bytes / 8 / static_cast<size_t>(grid);
   h->last_precision = ACE_PROJ_BF16;
+  h->last_products = 3;
   cudaError_t e;
   {
     PhaseScope ps(h, ACE_PHASE_HASH, s);
@@ -861,11 +940,15 @@ using u128 = unsigned __int128;
 extern "C" {
 
 int ace_create(int d, int K, int L, uint64_t seed, ace_handle* out) {
-  return make_detector(d, K, L, nullptr, seed, true, out);
+  return make_detector(d, K, L, nullptr, seed, true, 0u, out);
+}
+
+int ace_create_ex(int d, int K, int L, uint64_t seed, unsigned flags, ace_handle* out) {
+  return make_detector(d, K, L, nullptr, seed, true, flags, out);
 }
 
 int ace_create_with_projection(int d, int K, int L, const float* W_host, ace_handle* out) {
-  return make_detector(d, K, L, W_host, 0, false, out);
+  return make_detector(d, K, L, W_host, 0, false, 0u, out);
 }
 
 int ace_destroy(ace_handle h) {
@@ -1470,6 +1553,7 @@ int ace_stats(ace_handle h, void* stream, ace_stats_t* out) {
   out->deferred = st.deferred;
   out->status = st.status;
   out->precision = h->last_precision;
+  out->tc_products = h->last_products;
   return ACE_OK;
 }
 
@@ -1628,15 +1712,24 @@ extern "C" int ace_insert_score_noalloc(ace_handle h, const void* X_dev, int64_t
   a.ids = ids;
   a.ld = n;
   h->last_precision = ACE_PROJ_FP32;
-  h->launches[ACE_PHASE_HASH] += 1;
-  cudaError_t e = ace::launch_hash_simt(a, s);
+  // each launch is counted, and bracketed by events while the timing hook is on (the events
+  // come from the handle's pool; no device memory is allocated)
+  cudaError_t e;
+  {
+    PhaseScope ps(h, ACE_PHASE_HASH, s);
+    e = ace::launch_hash_simt(a, s);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "hash kernel launch");
   h->n_ins += static_cast<uint64_t>(n);
-  h->launches[ACE_PHASE_SCORE] += 1;
-  e = ace::launch_score_gather(ids, h->K <= 16, n, n, h->K, h->L, alpha, h->counts, sum_out, h->st, s);
+  {
+    PhaseScope ps(h, ACE_PHASE_SCORE, s);
+    e = ace::launch_score_gather(ids, h->K <= 16, n, n, h->K, h->L, alpha, h->counts, sum_out, h->st, s);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "score kernel launch");
-  h->launches[ACE_PHASE_FLAGS] += 1;
-  e = ace::launch_flags(sum_out, n, h->div, h->st, scores_dev, flags_dev, s);
+  {
+    PhaseScope ps(h, ACE_PHASE_FLAGS, s);
+    e = ace::launch_flags(sum_out, n, h->div, h->st, scores_dev, flags_dev, s);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "flags kernel launch");
   return ACE_OK;
 }

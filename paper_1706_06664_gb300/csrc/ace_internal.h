@@ -100,5 +100,7 @@ cudaError_t launch_tc_probe(const uint16_t* A, const uint16_t* B, int kd, int N,
 
 // Host-side generator of the projection matrix (SplitMix64 counter mode + Box-Muller).
 void generate_projection(int d, int K, int L, uint64_t seed, float* W);
+// Rounds every entry to bfloat16 (round to nearest even), keeping binary32 storage.
+void round_projection_bf16(float* W, uint64_t total);
 
 }  // namespace ace

@@ -6,7 +6,8 @@
 // Method.  Write L = 2^z Lo with Lo odd; then c / L = (c / Lo) 2^-z and rounding commutes with
 // the power of two (the quotients here are far from the subnormal range).  Normalise c to
 // cn = c 2^sh in [2^31, 2^32).  With M = floor(2^96 / Lo), the 128-bit product A = cn M
-// satisfies X - 2^32 < A <= X for X = 2^96 cn / Lo.  Let p >= 111 be A's leading bit.  A
+// satisfies X - 2^32 < A <= X for X = 2^96 cn / Lo.  With Lo < 2^16 (the detector's K L <=
+// 65536 gives L <= 65536), A >= 2^127 / Lo - 2^32 has its leading bit p >= 111.  A
 // rounding midpoint m is an odd multiple of 2^(p-53), and X - m = (cn 2^96 - m Lo) / Lo whose
 // numerator is an even multiple of 2^(p-53) minus an odd one, so |X - m| >= 2^(p-53) / Lo >=
 // 2^(p-69) >= 2^42.  A is therefore on the same side of every midpoint as X (and no tie
@@ -14,6 +15,7 @@
 // quotient is exact.
 #pragma once
 
+#include <cassert>
 #include <cstdint>
 
 #if defined(__CUDACC__)
@@ -31,8 +33,10 @@ struct DivConst {
   int pow2;       // 1 when Lo = 1
 };
 
-// Host: the constants of divisor L (1 <= L < 2^31).
+// Host: the constants of divisor L.  Precondition: 1 <= L <= 65536 (so the odd part Lo of L
+// is below 2^16, which the rounding argument above needs).
 inline DivConst make_div_const(uint32_t L) {
+  assert(L >= 1u && L <= 65536u);
   DivConst k{};
   uint32_t lo = L;
   while ((lo & 1u) == 0u) {

@@ -26,7 +26,13 @@ struct GemmArgs {
   int tpu, nunits;            // whole tables per 256-column unit; units per tile
   int nprod;                  // 2: x.w'_lo then x.w'_hi (binary32 W split in two); 1: x.w'_hi only
   int klp;                    // image rows of one part (nunits * 256); the lo part follows the hi part
-  float tau, tau_abs, xfac, qmin;  // row bound = tau * ||x||_up + tau_abs (or every column, q < qmin)
+  // Row bound B = ca * E + cx * ||x||_up + tau_abs (every column when q < qmin or q is not
+  // finite), E = sum over the hi-pass MMA instructions t of ||x_<16t|| WP_t + ||x_Bt|| WB_t with
+  // WP_t, WB_t the largest norms over the columns of w'_hi's prefix [0, 16t) and block
+  // [16t, 16t + 16) (wprof[t], wprof[S + t]); see hash_gemm.cu.
+  float ca, cx, tau_abs, xfac, qmin;
+  int S;                      // MMA instructions per pass (dp / 16)
+  const float* wprof;         // [2][S] WP_t, then WB_t (rounded up)
   int mode;                   // HashMode bits (kStoreIds, kStoreIdsRowMajor, kStoreProj)
   void* ids;                  // table-major ids [L][ld] (uint16 for K <= 16, else uint32)
   long long ld;

@@ -8,25 +8,34 @@
 // where w' = w_c / ||w_c|| (unit columns, rounded to binary32) is split on the host into
 // bfloat16 hi + lo parts.  x is bfloat16, so x_i w'_hi,i and x_i w'_lo,i are exact products
 // and the only errors are the dropped third part of w', the accumulation, and the
-// normalisation.  Error bound relative to ||x|| (host constants in ace_abi.cu, plan_gemm):
-//   - split: |w' - w_hi - w_lo| <= 2^-18 |w'| elementwise (two round-to-nearest bfloat16
-//     steps), so the dropped term is at most 2^-18 sum|x_i w'_i|; 2^-17 is used;
+// normalisation.  Error bound of a point's accumulator (host constants in plan_gemm):
+//   - split: |w' - w_hi - w_lo| <= 2^-16 |w'| elementwise (two round-to-nearest steps with the
+//     bfloat16 unit roundoff 2^-8); the dropped term is at most ||x|| ||w' - w_hi - w_lo||,
+//     and the host uses the largest residual norm over the columns (about 2^-18 in practice);
 //   - accumulation: tcgen05 aligns the 17 addends of one MMA instruction (16 products and the
 //     accumulator) to the largest exponent keeping two bits below its last place and truncates
-//     the sum to binary32: at most 5.25 * 2^-23 * (sum of |addends|) per instruction.  The lo
-//     product goes first over all of d (its instructions see addends of at most about
-//     2^-8 sum|x_i w'_i|), so over S_lo + S_hi instructions the error is at most
-//     5.25 * 2^-23 * (S_hi (1 + 2^-7) + 1 + 2^-8 S_lo) * sum|x_i w'_i| (1.5x margin applied);
-//   - normalisation (2^-23) and the binary64 reference itself (gamma64_d).
-// With sum|x_i w'_i| <= ||x||, the bound is one number per point, B = tau ||x||_up + tau_abs.
+//     the sum to binary32 (a model of the hardware that tests/test_gpu_tc_model.py checks on
+//     the device): at most 5.25 * 2^-23 * (sum of |addends|) per instruction.  The lo product
+//     goes first over all of d, so its instructions see addends of at most about
+//     2^-8 ||x||.  Instruction t of the hi product adds the block B_t = [16t, 16t + 16) to an
+//     accumulator that holds the partial sum over [0, 16t) (plus the small lo total and the
+//     error so far), so by Cauchy-Schwarz its addends sum to at most
+//     ||x_<16t|| WP_t + ||x_Bt|| WB_t + 2^-7 ||x||, with WP_t and WB_t the largest norms of
+//     w'_hi's prefix and block over the columns.  Summed over the instructions:
+//     5.25 * 2^-23 * (E + (2^-6 S + 1) ||x||), E = sum_t ||x_<16t|| WP_t + ||x_Bt|| WB_t, a
+//     1.25x margin applied.  For a point whose energy is spread over d, E is about S/2 ||x||
+//     instead of the S ||x|| that bounding every partial sum by ||x|| would give;
+//   - normalisation (2^-23 ||x||) and the binary64 reference itself (gamma64_d ||x||).
+// The bound is one number per point, computed by the row-bound warps with upward rounding.
 // A column whose |accumulator| <= B is deferred as a (point, column) entry; recheck_cols
 // recomputes its bit exactly and flips the stored id bit if the tensor cores had it wrong.
 //
 // Roles (one CTA per SM, persistent over tiles; 8 warps):
 //   warp 0      TMA producer: one (X k-block, image k-block) pair per ring stage
 //   warp 1      TMEM allocation and MMA issue (one lane): 4 MMAs of 128 x 256 x 16 per stage
-//   warps 2-3   row bounds: ||x||^2 of each point of the tile from global memory (the TMA
-//               loads then find the rows in L2), the bound B, exact-zero and non-finite rows
+//   warps 2-3   row bounds: block and prefix norms of each point of the tile from global
+//               memory (the TMA loads then find the rows in L2), the bound B, exact-zero and
+//               non-finite rows
 //   warps 4-7   epilogue: tcgen05.ld of the accumulator (thread = point), sign bits, guard
 //               classification, deferral entries, bucket ids (Eq. 2) stored table-major
 #include <cuda.h>
@@ -241,14 +250,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
   } else if (warp < 4) {
     // ------------------------------------------------------------------ row bounds
-    // Warp w2 takes rows 64 w2 .. 64 w2 + 63 of each tile, four rows at a time; the lanes read
-    // a row's 16-byte chunks (coalesced) and join their binary32 sums of squares by shuffles.
-    // Any summation order is covered by the gamma_d inflation in xfac.
+    // Warp w2 takes rows 64 w2 .. 64 w2 + 63 of each tile, four rows at a time.  Lane l reads
+    // the 16-byte chunks l, l + 32, ... of a row (coalesced); chunks 2t and 2t + 1 (lanes l and
+    // l ^ 1 of one round) make the 16 coordinates of MMA instruction t.  Per row: the squared
+    // norm b_t of each block, the exclusive prefix P_t = sum of b_t' over t' < t (a scan over
+    // the lanes, carried from round to round), and E = sum_t sqrt(P_t) WP_t + sqrt(b_t) WB_t,
+    // every step rounded up (xfac covers the binary32 sums of squares in any order).
     const int w2 = warp - 2;
-    const int nch = a.d / 8;
-    const float tau = a.tau, tau_abs = a.tau_abs, xfac = a.xfac, qmin = a.qmin;
+    const int nch = a.d / 8, nch2 = 2 * a.S;  // chunks of data; chunks of the padded pass
+    const float ca = a.ca, cx = a.cx, tau_abs = a.tau_abs, xfac = a.xfac, qmin = a.qmin;
+    const float* const WP = a.wprof;
+    const float* const WB = a.wprof + a.S;
     const uint4* const X4 = reinterpret_cast<const uint4*>(a.X);
     const bool count_nonfinite = !(a.mode & kStoreProj);
+    const bool even = (lane & 1) == 0;
     int ml = 0;
     for (long long m = blockIdx.x; m < ntiles; m += gridDim.x, ++ml) {
       const int t = ml & 1;
@@ -259,44 +274,69 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       for (int r0 = 0; r0 < 64; r0 += 4) {
-        float q[4] = {0.f, 0.f, 0.f, 0.f};
+        float carry[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
         uint32_t nz[4] = {0u, 0u, 0u, 0u};
         long long row[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) row[j] = m * kGemmBM + w2 * 64 + r0 + j;
-        for (int c = lane; c < nch; c += 32) {
+        // every instruction of the pass, the ones over the zero padding of d too (their
+        // products are 0, but the accumulator is an addend)
+        for (int c0 = 0; c0 < nch2; c0 += 32) {
+          const int c = c0 + lane;
+          const int blk = c >> 1;
           uint4 v[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j)
-            v[j] = row[j] < n ? __ldg(X4 + row[j] * nch + c) : make_uint4(0u, 0u, 0u, 0u);
+            v[j] = (c < nch && row[j] < n) ? __ldg(X4 + row[j] * nch + c) : make_uint4(0u, 0u, 0u, 0u);
+          const float wp = even && c < nch2 ? __ldg(WP + blk) : 0.f;
+          const float wb = even && c < nch2 ? __ldg(WB + blk) : 0.f;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const uint32_t w[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+            float cs = 0.f;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               const float lo = bf16_lo(w[e]), hi = bf16_hi(w[e]);
-              q[j] = fmaf(lo, lo, q[j]);
-              q[j] = fmaf(hi, hi, q[j]);
+              cs = fmaf(lo, lo, cs);
+              cs = fmaf(hi, hi, cs);
               nz[j] |= w[e] & 0x7FFF7FFFu;
             }
+            const float b = cs + __shfl_xor_sync(0xFFFFFFFFu, cs, 1);  // block sum (both lanes)
+            const float ve = even ? b : 0.f;
+            float inc = ve;  // inclusive scan of the blocks over the lanes
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+              const float u = __shfl_up_sync(0xFFFFFFFFu, inc, off);
+              if (lane >= off) inc += u;
+            }
+            float ex = __shfl_up_sync(0xFFFFFFFFu, inc, 2);  // the previous block's inclusive sum
+            if (lane < 2) ex = 0.f;
+            const float tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+            if (even && c < nch2) {
+              const float P = __fadd_ru(ex, carry[j]);
+              E[j] = __fmaf_ru(__fsqrt_ru(__fmul_ru(P, xfac)), wp, E[j]);
+              E[j] = __fmaf_ru(__fsqrt_ru(__fmul_ru(b, xfac)), wb, E[j]);
+            }
+            carry[j] = __fadd_ru(carry[j], tot);
           }
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
 #pragma unroll
           for (int off = 16; off > 0; off >>= 1) {
-            q[j] += __shfl_xor_sync(0xFFFFFFFFu, q[j], off);
+            E[j] = __fadd_ru(E[j], __shfl_xor_sync(0xFFFFFFFFu, E[j], off));
             nz[j] |= __shfl_xor_sync(0xFFFFFFFFu, nz[j], off);
           }
         }
         if (lane < 4) {
-          float qq = q[0];
+          float qq = carry[0], ee = E[0];
           uint32_t zz = nz[0];
           long long ii = row[0];
 #pragma unroll
           for (int j = 1; j < 4; ++j)
             if (lane == j) {
-              qq = q[j];
+              qq = carry[j];
+              ee = E[j];
               zz = nz[j];
               ii = row[j];
             }
@@ -304,10 +344,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (zz == 0u) {  // every coordinate is +-0: every projection is exactly 0, bit 0
             thr = 0u;
             zero = 1u;
-          } else if (!isfinite(qq) || qq < qmin) {
+          } else if (!isfinite(qq) || !isfinite(ee) || qq < qmin) {
             thr = 0xFFFFFFFFu;  // every column of the row is resolved exactly
           } else {
-            const float B = fmaf(tau, sqrtf(qq * xfac) * 1.00000095367431640625f, tau_abs);
+            const float xu = __fsqrt_ru(__fmul_ru(qq, xfac));
+            const float B = __fmaf_ru(ca, ee, __fmaf_ru(cx, xu, tau_abs));
             thr = __float_as_uint(B) + 1u;  // |v| <= B  <=>  bits(|v|) < bits(B) + 1
           }
           S->bthr[t][w2 * 64 + r0 + lane] = thr;

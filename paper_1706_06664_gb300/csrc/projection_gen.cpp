@@ -1,4 +1,4 @@
-// Projection matrix of Algorithm 1 "Hash Initialize" (§3.2): K*L Gaussian vectors,
+// Projection matrix of Algorithm 1's hash initialisation step (§3.2): K*L Gaussian vectors,
 // w_i ~ N(0,1) (§2.1), drawn on the host from a 64-bit seed.
 //
 // Generator (published definitions): SplitMix64 of Steele, Lea and Flood (OOPSLA 2014),
@@ -11,8 +11,10 @@
 //
 // Built with -ffp-contract=off and -fno-builtin so that each binary64 step is one
 // correctly rounded operation and libm's cos/sin/log/sqrt are called as written.
+// With ACE_W_BF16 each binary32 value is then rounded to bfloat16 (round_projection_bf16).
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "ace_internal.h"
 
@@ -32,6 +34,20 @@ inline uint64_t mix64(uint64_t z) {
 inline uint64_t draw(uint64_t seed, uint64_t t) { return mix64(seed + (t + 1u) * 0x9E3779B97F4A7C15ull); }
 
 }  // namespace
+
+// bfloat16 bit pattern of a finite binary32 value, round to nearest even.
+inline uint16_t to_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return static_cast<uint16_t>((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+
+void round_projection_bf16(float* W, uint64_t total) {
+  for (uint64_t i = 0; i < total; ++i) {
+    const uint32_t u = static_cast<uint32_t>(to_bf16(W[i])) << 16;
+    std::memcpy(&W[i], &u, 4);
+  }
+}
 
 void generate_projection(int d, int K, int L, uint64_t seed, float* W) {
   const uint64_t total = static_cast<uint64_t>(d) * static_cast<uint64_t>(K) * static_cast<uint64_t>(L);

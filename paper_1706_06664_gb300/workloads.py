@@ -37,7 +37,7 @@ import math
 
 import numpy as np
 
-__all__ = ["small", "kdd", "highdim", "batched_specs", "batched_points", "stream_chunk", "request_sizes",
+__all__ = ["small", "kdd", "highdim", "highdim_device", "batched_specs", "batched_points", "stream_chunk", "request_sizes",
            "to_bf16_bits", "bf16_bits_to_f32", "gaussian_w"]
 
 
@@ -118,6 +118,32 @@ def highdim(seed: int = 3, n: int = 1_000_000, d: int = 1024, clusters: int = 64
         out[s:e] = to_bf16_bits(x.astype(np.float32))
     return {"name": "highdim", "X": out, "d": d, "K": 16, "L": 64, "alpha": 1.0,
             "labels": is_anom, "dtype": "bf16"}
+
+
+def highdim_device(seed: int = 3, n: int = 1_000_000, d: int = 1024, clusters: int = 64):
+    """The ``highdim`` recipe drawn on the current CUDA device with torch's generator (for the
+    full-size batch, whose host draw takes minutes): 64 centres uniform on the unit sphere,
+    x = normalize(c + (0.1/sqrt(d)) g), 0.5% anomalies normalize(g), rounded to bfloat16 (round
+    to nearest even).  Returns (X as an int16 tensor of bfloat16 bits on the device, anomaly
+    mask as a numpy array).  Same recipe as ``highdim``; a different random stream."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(int(seed) & (2**63 - 1))
+    C = torch.randn(clusters, d, device="cuda", generator=g, dtype=torch.float64)
+    C /= C.norm(dim=1, keepdim=True)
+    n_anom = max(1, n * 5 // 1000)
+    perm = torch.randperm(n, device="cuda", generator=g)
+    is_anom = torch.zeros(n, dtype=torch.bool, device="cuda")
+    is_anom[perm[:n_anom]] = True
+    which = torch.randint(0, clusters, (n,), device="cuda", generator=g)
+    out = torch.empty((n, d), dtype=torch.bfloat16, device="cuda")
+    chunk = 1 << 16
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        gg = torch.randn(e - s, d, device="cuda", generator=g, dtype=torch.float64)
+        x = torch.where(is_anom[s:e, None], gg, C[which[s:e]] + (0.1 / math.sqrt(d)) * gg)
+        x /= x.norm(dim=1, keepdim=True)
+        out[s:e] = x.to(torch.float32).to(torch.bfloat16)
+    return out.view(torch.int16), is_anom.cpu().numpy()
 
 
 def batched_specs(seed: int = 4, n_det: int = 2048, d_range=(16, 512), n_range=(100, 100_000)):

@@ -44,6 +44,20 @@ def test_batch_matches_each_detector_alone(K, L):
         _check(dets, refs, Xs, res)
 
 
+def test_batch_at_bench_shapes():
+    """The bench's shape range: 34 detectors with K=12, L=32, d log-uniform in [16, 512] and n
+    log-uniform in [100, 100,000], plus both extremes (d=512 with n=100,000; d=16 with n=100):
+    each detector's outputs, counts and statistics equal the oracle's run of it alone."""
+    K, L = 12, 32
+    specs = workloads.batched_specs(seed=9, n_det=32, d_range=(16, 512), n_range=(100, 100_000))
+    specs += [(512, 100_000, 77), (16, 100, 78)]
+    dets = [ace.Detector(d, K, L, seed=sd) for (d, n, sd) in specs]
+    refs = [oracle.Detector(d, K, L, W=det.projection()) for (d, n, sd), det in zip(specs, dets)]
+    Xs = _batch_points(specs, 0)
+    res = ace.batch_insert_score(dets, [torch.from_numpy(X).cuda() for X in Xs])
+    _check(dets, refs, Xs, res)
+
+
 def test_batch_rejects_duplicates_and_mixed_k():
     a = ace.Detector(20, 12, 8, seed=1)
     b = ace.Detector(20, 18, 4, seed=2)

@@ -59,10 +59,11 @@ def _compare_stats(det, ref, alpha=1.0):
 
 
 def test_projection_generator_matches_oracle():
-    for (d, K, L, seed) in [(32, 10, 20, 1), (41, 15, 50, 2), (7, 3, 5, 2**63 + 12345)]:
-        det = ace.Detector(d, K, L, seed=seed)
-        assert np.array_equal(det.projection(), oracle.projection_from_seed(d, K, L, seed))
-        det.close()
+    for (d, K, L, seed) in [(32, 10, 20, 1), (41, 15, 50, 2), (7, 3, 5, 2**63 + 12345), (1024, 16, 64, 9)]:
+        for w_bf16 in (False, True):
+            det = ace.Detector(d, K, L, seed=seed, w_bf16=w_bf16)
+            assert np.array_equal(det.projection(), oracle.projection_from_seed(d, K, L, seed, w_bf16=w_bf16))
+            det.close()
 
 
 @pytest.mark.parametrize("precision", PRECS)
@@ -359,41 +360,26 @@ def test_host_async_batches_in_order(precision):
     _compare_stats(a, ref)
 
 
-def test_kdd_full_size_sampled():
-    """KDD-shaped recipe at its full size (n=500,000), in the bench's launch configuration:
-    ids of a sample of points against the oracle, plus invariants that hold at any size."""
+def test_kdd_full_size_against_oracle():
+    """KDD-shaped recipe at its full size (n=500,000, d=41, K=15, L=50) in the bench's launch
+    configuration (one insert_score call on the whole batch), on both engines: every id,
+    count, sum, score and flag, and the statistics, against the oracle's run of the same batch
+    (computed once)."""
     w = workloads.kdd(seed=2)
     X = w["X"]
-    n = X.shape[0]
-    det = ace.Detector(w["d"], w["K"], w["L"], seed=5)
     Xd = _dev(X)
-    ids = ace.u32(det.hash(Xd))
-    rng = np.random.default_rng(0)
-    sample = np.sort(rng.choice(n, size=3000, replace=False))
-    sample = np.unique(np.concatenate([sample, [0, n - 1]]))
-    ref_ids = oracle.hash_ids(X[sample], det.projection(), w["K"], w["L"])
-    assert np.array_equal(ids[sample], ref_ids)
-    sc, su, fl = det.insert_score(Xd, 1.0)
-    torch.cuda.synchronize()
-    counts = det.counts()
-    assert np.all(counts.sum(axis=1, dtype=np.uint64) == n)
-    # counts equal the per-table histogram of the GPU ids (itself checked on the sample)
-    for j in (0, 17, 49):
-        assert np.array_equal(counts[j], np.bincount(ids[:, j], minlength=1 << w["K"]))
-    sums = ace.u32(su).astype(np.int64)
-    expect = np.zeros(n, dtype=np.int64)
-    for j in range(w["L"]):
-        expect += counts[j][ids[:, j]]
-    assert np.array_equal(sums, expect)
-    st = det.stats()
-    assert st["Q"] == int(sums.sum())
-    ref = oracle.Detector(w["d"], w["K"], w["L"], W=det.projection())
-    ref.counts[:] = counts
-    ref.n_ins = n
-    ref_sc, ref_su, ref_fl = ref._score_ids(ids, 1.0)
-    assert np.array_equal(ref_su, ace.u32(su))
-    assert np.array_equal(sc.cpu().numpy(), ref_sc) and np.array_equal(fl.cpu().numpy(), ref_fl)
-    assert st["mu"] == ref.stats()["mu"] and st["sigma"] == ref.stats()["sigma"]
+    ref = oracle.Detector(w["d"], w["K"], w["L"], seed=5)
+    ref_ids = ref.hash(X)
+    rs, ru, rf = ref.insert_score(X, 1.0)
+    for precision in PRECS:
+        det = _detector(w["d"], w["K"], w["L"], seed=5, precision=precision)
+        assert np.array_equal(det.projection(), ref.W)
+        assert np.array_equal(ace.u32(det.hash(Xd)), ref_ids)
+        _compare_score(det.insert_score(Xd, 1.0), (rs, ru, rf))
+        assert np.array_equal(det.counts(), ref.counts)
+        _compare_stats(det, ref)
+        _engine_used(det, precision)
+        det.close()
 
 
 @pytest.mark.parametrize("precision", PRECS)

@@ -81,6 +81,39 @@ def test_splitmix64_reference_vectors():
         assert oracle.splitmix64_draw(v["seed"], v["t"]) == v["out"]
 
 
+def test_projection_from_seed_hand_derived_values():
+    """Two Box-Muller pairs derived by hand from the generator's definition and the published
+    SplitMix64 outputs (tests/golden/projection_pins.json): the cos half at even flat indices,
+    the sin half at odd ones, and u1 in (0,1] (the first pair has draw 0 = 0, which gives
+    u1 = 2^-53 and r = sqrt(106 ln 2) instead of an infinite value)."""
+    g = _load("projection_pins.json")
+    for pr in g["pairs"]:
+        assert oracle.splitmix64_draw(pr["seed"], 0) == pr["draw0"]
+        assert oracle.splitmix64_draw(pr["seed"], 1) == pr["draw1"]
+        W = oracle.projection_from_seed(1, 2, 1, seed=pr["seed"])
+        bits = W.ravel().view(np.uint32)
+        assert int(bits[0]) == pr["flat0_f32_bits"] and int(bits[1]) == pr["flat1_f32_bits"], (W, pr)
+        assert abs(float(W.ravel()[0]) - float(pr["flat0"])) < 1e-6 * abs(float(pr["flat0"]))
+    assert math.isclose(float(g["pairs"][0]["r"]), math.sqrt(106 * math.log(2)), rel_tol=1e-15)
+    for pr in g["pairs"]:  # the bfloat16-valued variant (ACE_W_BF16) of the same draws
+        bits = oracle.projection_from_seed(1, 2, 1, seed=pr["seed"], w_bf16=True).ravel().view(np.uint32)
+        assert int(bits[0]) == pr["flat0_bf16_bits"] and int(bits[1]) == pr["flat1_bf16_bits"]
+
+
+def test_projection_bf16_variant_rounds_to_nearest_even():
+    """ACE_W_BF16 draws are the binary32 draws rounded to bfloat16, ties to even: over a million
+    entries (a dozen exact ties expected) they equal an independent rounding of the binary32
+    matrix, and each lies within half a bfloat16 unit of it."""
+    W = oracle.projection_from_seed(64, 16, 1024, seed=99)
+    Wb = oracle.projection_from_seed(64, 16, 1024, seed=99, w_bf16=True)
+    assert np.array_equal(workloads.bf16_bits_to_f32(workloads.to_bf16_bits(W)), Wb)
+    assert not (Wb.view(np.uint32) & 0xFFFF).any()
+    low = W.view(np.uint32) & 0xFFFF
+    ties = low == 0x8000
+    assert ties.sum() >= 1 and not ((Wb.view(np.uint32)[ties] >> 16) & 1).any()
+    assert (np.abs(W.astype(np.float64) - Wb) <= np.abs(W.astype(np.float64)) * 2.0**-8).all()
+
+
 def test_projection_from_seed_is_standard_normal():
     W = oracle.projection_from_seed(64, 16, 256, seed=12345).astype(np.float64).ravel()
     assert W.size == 64 * 16 * 256

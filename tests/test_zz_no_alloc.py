@@ -75,3 +75,60 @@ def test_noalloc_rejects_batches_beyond_the_static_scratch():
     assert b"static scratch" in lib.ace_last_error()
     st = det.stats()
     assert st["n_ins"] == 0 and st["n_scored"] == 0 and int(det.counts().sum()) == 0
+
+
+def test_noalloc_at_the_exact_limit_without_sums_and_one_past_it():
+    """A batch whose scratch need equals ACE_NOALLOC_SCRATCH_BYTES exactly (K=16, L=62: 124 bytes
+    of ids and 4 of sums per point, 2^18 points, no sums buffer, so the sums sit at the very end
+    of the static array) runs and matches ace_insert_score bit for bit; one point more is
+    refused and changes nothing."""
+    lib = ace.load_library()
+    d, K, L = 8, 16, 62
+    n = ace.NOALLOC_SCRATCH_BYTES // (L * 2 + 4)
+    assert n * (L * 2 + 4) == ace.NOALLOC_SCRATCH_BYTES and (n * L * 2) % 256 == 0
+    rng = np.random.default_rng(3)
+    X = torch.from_numpy(rng.standard_normal((n + 1, d)).astype(np.float32)).cuda()
+    ref = ace.Detector(d, K, L, seed=5, precision="fp32")
+    new = ace.Detector(d, K, L, seed=5, precision="fp32")
+    rs, _, rf = ref.insert_score(X[:n], 1.0, sums=False)
+    sc, _, fl = new.insert_score_noalloc(X[:n], 1.0, sums=False)
+    torch.cuda.synchronize()
+    assert torch.equal(sc, rs) and torch.equal(fl, rf)
+    assert np.array_equal(new.counts(), ref.counts())
+    with pytest.raises(ace.AceError) as e:
+        new.insert_score_noalloc(X, 1.0, sums=False)
+    assert e.value.code == ace.ACE_ERR_ARG
+    assert new.stats()["n_ins"] == n
+
+
+def test_noalloc_wide_ids_k_above_16():
+    """K > 16 (4-byte ids) through the allocation-free entry point, twice in a row, against
+    ace_insert_score: scores, sums and flags bit for bit."""
+    d, K, L = 24, 20, 8
+    rng = np.random.default_rng(4)
+    ref = ace.Detector(d, K, L, seed=6, precision="fp32")
+    new = ace.Detector(d, K, L, seed=6, precision="fp32")
+    for n in (10_000, 3_001):
+        X = torch.from_numpy(rng.standard_normal((n, d)).astype(np.float32)).cuda()
+        rs, ru, rf = ref.insert_score(X, 1.0)
+        sc, su, fl = new.insert_score_noalloc(X, 1.0)
+        torch.cuda.synchronize()
+        assert torch.equal(su, ru) and torch.equal(sc, rs) and torch.equal(fl, rf)
+    a, b = new.stats(), ref.stats()
+    for k in ("n_ins", "n_scored", "Q", "S1", "S2", "mu", "sigma"):
+        assert a[k] == b[k], k
+
+
+def test_noalloc_launches_are_timed_by_the_profiling_hook():
+    """With the timing hook on, the entry point's three kernels are counted and timed like
+    ace_insert_score's."""
+    d, K, L = 16, 12, 8
+    det = ace.Detector(d, K, L, seed=2, precision="fp32")
+    X = torch.from_numpy(np.random.default_rng(5).standard_normal((5000, d)).astype(np.float32)).cuda()
+    det.profile_read()
+    det.profile(True)
+    det.insert_score_noalloc(X, 1.0)
+    det.profile(False)
+    p = det.profile_read()
+    for ph in ("hash", "score", "flags"):
+        assert p[ph]["launches"] == 1 and p[ph]["timed"] == 1 and p[ph]["ms"] > 0.0, (ph, p[ph])
