@@ -269,6 +269,24 @@ int ace_get_counts(ace_handle h, uint32_t* counts_host, void* stream);
 /* Copies the d x (K*L) binary32 W to host memory. */
 int ace_get_projection(ace_handle h, float* W_host);
 
+/*
+ * Checkpoint of a detector (the paper keeps its arrays in memory; saving and restoring them
+ * lets a long stream be scored across process restarts).  The blob holds everything that
+ * determines later results: the shape, W, the L x 2^K counts, n_ins, and the running score
+ * statistics N, S1, S2 (and the recheck/status counters), with a checksum.
+ *   ace_save_size — bytes of the blob for this detector.
+ *   ace_save — writes the blob to host memory buf (cap bytes, at least ace_save_size);
+ *              synchronises `stream` (to read the counts as of all work enqueued on it).
+ *   ace_load — creates a new detector on the current CUDA device from a blob; every later
+ *              call on it gives exactly the results the saved detector would have given.
+ *              The engine selection starts at ACE_PROJ_AUTO.
+ * Errors: ACE_ERR_ARG (NULL, short buffer, bad magic, version, shape, size or checksum),
+ * ACE_ERR_OOM, ACE_ERR_CUDA.
+ */
+int ace_save_size(ace_handle h, size_t* bytes);
+int ace_save(ace_handle h, void* buf, size_t cap, void* stream);
+int ace_load(const void* buf, size_t bytes, ace_handle* out);
+
 /* Detector shape. */
 int ace_get_shape(ace_handle h, int* d, int* K, int* L);
 

@@ -28,7 +28,7 @@ EXPORTS = [
     "ace_batch_insert_score", "ace_server_create", "ace_server_submit", "ace_server_wait", "ace_server_drain", "ace_server_destroy", "ace_stats",
     "ace_get_counts", "ace_get_projection", "ace_get_shape", "ace_last_error", "ace_version",
     "ace_profile_enable", "ace_profile_phases", "ace_profile_read", "ace_insert_score_noalloc",
-    "ace_tc_probe",
+    "ace_tc_probe", "ace_save_size", "ace_save", "ace_load",
 ]
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 PHASES = ("hash", "score", "flags", "other", "recheck", "insert")
@@ -103,6 +103,9 @@ def load_library(path: str = LIB_PATH):
             "ace_profile_phases": ([H, ctypes.c_uint32], i32),
             "ace_profile_read": ([H, ctypes.POINTER(ace_profile_t)], i32),
             "ace_tc_probe": ([P, P, i32, i32, P], i32),
+            "ace_save_size": ([H, ctypes.POINTER(ctypes.c_size_t)], i32),
+            "ace_save": ([H, P, ctypes.c_size_t, P], i32),
+            "ace_load": ([P, ctypes.c_size_t, ctypes.POINTER(H)], i32),
             "ace_last_error": ([], ctypes.c_char_p),
             "ace_version": ([], ctypes.c_char_p),
         }
@@ -317,6 +320,29 @@ class Detector:
         _check(load_library().ace_profile_read(self._h, ctypes.byref(p)))
         return {name: {"launches": int(p.launches[i]), "ms": float(p.ms[i]), "timed": int(p.timed[i])}
                 for i, name in enumerate(PHASES)}
+
+    def save(self, stream=None) -> bytes:
+        """Checkpoint blob (ace_save): shape, W, counts and running statistics."""
+        lib = load_library()
+        nb = ctypes.c_size_t()
+        _check(lib.ace_save_size(self._h, ctypes.byref(nb)))
+        buf = ctypes.create_string_buffer(nb.value)
+        _check(lib.ace_save(self._h, buf, nb.value, _stream_ptr(stream)))
+        return buf.raw
+
+    @classmethod
+    def load(cls, blob: bytes, precision: str = "auto") -> "Detector":
+        """A new detector on the current CUDA device from a checkpoint blob (ace_load)."""
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.ace_load(blob, len(blob), ctypes.byref(h)))
+        self = cls.__new__(cls)
+        self._h = h
+        d, K, L = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib.ace_get_shape(h, ctypes.byref(d), ctypes.byref(K), ctypes.byref(L)))
+        self.d, self.K, self.L = d.value, K.value, L.value
+        self.set_precision(precision)
+        return self
 
     def projection(self) -> np.ndarray:
         out = np.empty((self.d, self.K * self.L), dtype=np.float32)

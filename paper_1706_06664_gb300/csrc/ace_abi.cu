@@ -104,6 +104,7 @@ struct ace_detector {
   ace::GemmArgs gm{};           // constant part of the launch
   uint16_t* gimg = nullptr;     // [2 klp][dp] bfloat16 image of W' (hi rows, then lo rows)
   float* gprof = nullptr;       // [2][dp/16] prefix and block norm maxima of the hi image
+  float* gcolf = nullptr;       // [klp] image column norms (single-product image only)
   CUtensorMap tm_img{};         // TMA description of gimg
   // profiling hook
   bool prof = false;
@@ -165,6 +166,7 @@ void free_all(ace_detector* h) {
   cudaFree(h->bimg);
   cudaFree(h->gimg);
   cudaFree(h->gprof);
+  cudaFree(h->gcolf);
   cudaFree(h->defer);
   cudaFree(h->defer_counts);
   cudaFree(h->wpad);
@@ -510,18 +512,28 @@ int plan_gemm(ace_detector* h) {
                                ace::kGemmBN))
     return rc;
   // WP_t = max over columns of ||w'_hi[0, 16t)||, WB_t = max of ||w'_hi[16t, 16t + 16)||, for
-  // the S = dp/16 MMA instructions of one pass (rounded up)
+  // the S = dp/16 MMA instructions of one pass (rounded up).  The single-product image's
+  // columns (norms in [1/2, 1)) are normalised for the profile, and each column's norm goes to
+  // colf, which scales the row bound per column.
   const int S = dp / 16;
   std::vector<float> prof(2 * static_cast<size_t>(S), 0.f);
+  std::vector<float> colf(one ? klp : 0, 0.f);
   {
     std::vector<double> wp(S, 0.0), wb(S, 0.0);
     for (int row = 0; row < klp; ++row) {
+      double nrm2 = 0.0;
+      for (int i = 0; i < dp; ++i) {
+        const double v = bf16_value(img[static_cast<size_t>(row) * dp + i]);
+        nrm2 += v * v;
+      }
+      const double sc = one && nrm2 > 0.0 ? 1.0 / std::sqrt(nrm2) : 1.0;
+      if (one) colf[row] = nrm2 > 0.0 ? std::nextafter(static_cast<float>(std::sqrt(nrm2) * (1.0 + 1e-12)), FLT_MAX) : 0.f;
       double pre = 0.0;
       for (int t = 0; t < S; ++t) {
         wp[t] = std::max(wp[t], pre);
         double blk = 0.0;
         for (int i = 16 * t; i < 16 * t + 16; ++i) {
-          const double v = bf16_value(img[static_cast<size_t>(row) * dp + i]);
+          const double v = bf16_value(img[static_cast<size_t>(row) * dp + i]) * sc;
           blk += v * v;
         }
         wb[t] = std::max(wb[t], blk);
@@ -538,6 +550,13 @@ int plan_gemm(ace_detector* h) {
   if ((e = cudaMalloc(&h->gprof, prof.size() * sizeof(float))) != cudaSuccess) return cuda_fail(e, "cudaMalloc norm profile");
   if ((e = cudaMemcpy(h->gprof, prof.data(), prof.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_fail(e, "copy norm profile");
+  cudaFree(h->gcolf);
+  h->gcolf = nullptr;
+  if (one) {
+    if ((e = cudaMalloc(&h->gcolf, colf.size() * sizeof(float))) != cudaSuccess) return cuda_fail(e, "cudaMalloc column norms");
+    if ((e = cudaMemcpy(h->gcolf, colf.data(), colf.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cuda_fail(e, "copy column norms");
+  }
   if (!h->wnorm) {
     if ((e = cudaMalloc(&h->wnorm, KL * sizeof(float))) != cudaSuccess) return cuda_fail(e, "cudaMalloc column norms");
     if ((e = cudaMemcpy(h->wnorm, wn.data(), KL * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -573,6 +592,7 @@ int plan_gemm(ace_detector* h) {
                         FLT_MAX);
   g.S = S;
   g.wprof = h->gprof;
+  g.colf = h->gcolf;
   g.tau_abs = static_cast<float>(2.0 * dp * std::ldexp(1.0, -125));
   const double g32 = d * u32 / (1.0 - d * u32);
   g.xfac = std::nextafter(static_cast<float>(1.0 + 2.0 * g32 + std::ldexp(1.0, -20)), FLT_MAX);
@@ -1568,6 +1588,121 @@ int ace_get_counts(ace_handle h, uint32_t* counts_host, void* stream) {
 int ace_get_projection(ace_handle h, float* W_host) {
   if (!h || !W_host) return fail(ACE_ERR_ARG, "NULL argument");
   std::memcpy(W_host, h->Wh.data(), h->Wh.size() * sizeof(float));
+  return ACE_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Checkpoint blob (ace_save / ace_load).  Little-endian, 8-byte fields:
+//   "ACEDET01", version 1, d, K, L, flags (bit 0: W is bfloat16-valued), n_ins,
+//   n_scored, S1 lo/hi, S2 lo/hi, rechecks, nonfinite, deferred, status,
+//   W (d*K*L binary32, row-major), counts (L*2^K uint32), FNV-1a 64 of everything before it.
+// ---------------------------------------------------------------------------------------
+namespace {
+constexpr char kBlobMagic[8] = {'A', 'C', 'E', 'D', 'E', 'T', '0', '1'};
+constexpr int kBlobHeaderWords = 16;  // after the magic
+
+uint64_t fnv1a64(const unsigned char* p, size_t n) {
+  uint64_t h = 0xCBF29CE484222325ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 0x100000001B3ull;
+  }
+  return h;
+}
+
+size_t blob_bytes(int d, int K, int L) {
+  return 8 + 8 * kBlobHeaderWords + static_cast<size_t>(d) * K * L * 4 + (static_cast<size_t>(1) << K) * L * 4 + 8;
+}
+}  // namespace
+
+int ace_save_size(ace_handle h, size_t* bytes) {
+  if (!h || !bytes) return fail(ACE_ERR_ARG, "NULL argument");
+  *bytes = blob_bytes(h->d, h->K, h->L);
+  return ACE_OK;
+}
+
+int ace_save(ace_handle h, void* buf, size_t cap, void* stream) {
+  if (!h || !buf) return fail(ACE_ERR_ARG, "NULL argument");
+  const size_t need = blob_bytes(h->d, h->K, h->L);
+  if (cap < need) return fail(ACE_ERR_ARG, "buffer of %zu bytes; the checkpoint needs %zu", cap, need);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned char* out = static_cast<unsigned char*>(buf);
+  const size_t wbytes = static_cast<size_t>(h->d) * h->KL * 4, cbytes = count_elems(h) * 4;
+  unsigned char* wdst = out + 8 + 8 * kBlobHeaderWords;
+  ace::DevStats st;
+  ACE_CUDA(cudaMemcpyAsync(&st, h->st, sizeof st, cudaMemcpyDeviceToHost, s));
+  ACE_CUDA(cudaMemcpyAsync(wdst + wbytes, h->counts, cbytes, cudaMemcpyDeviceToHost, s));
+  ACE_CUDA(cudaStreamSynchronize(s));
+  bool wb = true;
+  for (float w : h->Wh) wb = wb && bf16_value(bf16_rn(w)) == w;
+  uint64_t hdr[kBlobHeaderWords] = {1u,
+                                    static_cast<uint64_t>(h->d),
+                                    static_cast<uint64_t>(h->K),
+                                    static_cast<uint64_t>(h->L),
+                                    wb ? 1u : 0u,
+                                    h->n_ins,
+                                    st.n_scored,
+                                    st.S1[0],
+                                    st.S1[1],
+                                    st.S2[0],
+                                    st.S2[1],
+                                    st.rechecks,
+                                    st.nonfinite,
+                                    st.deferred,
+                                    st.status,
+                                    0u};
+  std::memcpy(out, kBlobMagic, 8);
+  std::memcpy(out + 8, hdr, sizeof hdr);
+  std::memcpy(wdst, h->Wh.data(), wbytes);
+  const uint64_t sum = fnv1a64(out, need - 8);
+  std::memcpy(out + need - 8, &sum, 8);
+  return ACE_OK;
+}
+
+int ace_load(const void* buf, size_t bytes, ace_handle* out) {
+  if (!buf || !out) return fail(ACE_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  const unsigned char* in = static_cast<const unsigned char*>(buf);
+  if (bytes < 8 + 8 * kBlobHeaderWords + 8 || std::memcmp(in, kBlobMagic, 8) != 0)
+    return fail(ACE_ERR_ARG, "not an ACE checkpoint");
+  uint64_t hdr[kBlobHeaderWords];
+  std::memcpy(hdr, in + 8, sizeof hdr);
+  if (hdr[0] != 1u) return fail(ACE_ERR_ARG, "checkpoint version %llu is not supported",
+                                static_cast<unsigned long long>(hdr[0]));
+  const uint64_t d = hdr[1], K = hdr[2], L = hdr[3];
+  if (d < 1 || d > (1u << 30) || K < 1 || K > 24 || L < 1 || K * L > 65536)
+    return fail(ACE_ERR_ARG, "checkpoint shape d=%llu K=%llu L=%llu is invalid", static_cast<unsigned long long>(d),
+                static_cast<unsigned long long>(K), static_cast<unsigned long long>(L));
+  const size_t need = blob_bytes(static_cast<int>(d), static_cast<int>(K), static_cast<int>(L));
+  if (bytes != need) return fail(ACE_ERR_ARG, "checkpoint of %zu bytes; its shape needs %zu", bytes, need);
+  uint64_t sum;
+  std::memcpy(&sum, in + need - 8, 8);
+  if (sum != fnv1a64(in, need - 8)) return fail(ACE_ERR_ARG, "checkpoint checksum mismatch (corrupted blob)");
+  const size_t wbytes = static_cast<size_t>(d) * K * L * 4;
+  std::vector<float> W(static_cast<size_t>(d) * K * L);
+  std::memcpy(W.data(), in + 8 + 8 * kBlobHeaderWords, wbytes);
+  ace_handle h = nullptr;
+  if (int rc = make_detector(static_cast<int>(d), static_cast<int>(K), static_cast<int>(L), W.data(), 0, false, 0u, &h))
+    return rc;
+  ace::DevStats st{};
+  st.n_scored = hdr[6];
+  st.S1[0] = hdr[7];
+  st.S1[1] = hdr[8];
+  st.S2[0] = hdr[9];
+  st.S2[1] = hdr[10];
+  st.rechecks = hdr[11];
+  st.nonfinite = hdr[12];
+  st.deferred = hdr[13];
+  st.status = static_cast<unsigned int>(hdr[14]);
+  cudaError_t e = cudaMemcpy(h->counts, in + 8 + 8 * kBlobHeaderWords + wbytes, count_elems(h) * 4,
+                             cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->st, &st, sizeof st, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    ace_destroy(h);
+    return cuda_fail(e, "checkpoint upload");
+  }
+  h->n_ins = hdr[5];
+  *out = h;
   return ACE_OK;
 }
 

@@ -33,6 +33,9 @@ struct GemmArgs {
   float ca, cx, tau_abs, xfac, qmin;
   int S;                      // MMA instructions per pass (dp / 16)
   const float* wprof;         // [2][S] WP_t, then WB_t (rounded up)
+  const float* colf;          // [nunits][256] per image column: its norm (rounded up) when the
+                              // columns are not unit vectors (the bound of column c is B colf[c],
+                              // WP and WB then being those of the normalised columns); else null
   int mode;                   // HashMode bits (kStoreIds, kStoreIdsRowMajor, kStoreProj)
   void* ids;                  // table-major ids [L][ld] (uint16 for K <= 16, else uint32)
   long long ld;

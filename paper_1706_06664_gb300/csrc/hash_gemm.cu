@@ -49,7 +49,9 @@ namespace {
 
 using namespace tc;
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 320;   // 10 warps
+constexpr int kBndWarps = 4;    // row-bound warps (2 .. 5)
+constexpr int kBndRows = 8;     // rows per row-bound warp in flight
 constexpr int kStages = kGemmStages;
 constexpr uint32_t kABytes = kGemmBM * kGemmBK * 2;  // 16 KB
 constexpr uint32_t kBBytes = kGemmBN * kGemmBK * 2;  // 32 KB
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(&S->t_full[b], 1);
       mbar_init(&S->t_empty[b], 128);
-      mbar_init(&S->b_full[b], 64);
+      mbar_init(&S->b_full[b], 32 * kBndWarps);
       mbar_init(&S->b_empty[b], 128);
     }
     mbar_init(&S->drain, 1);
@@ -248,22 +250,22 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!mbar_wait(&S->drain, 0, &never, kWaitCycles)) set_abort(S, a.st);
     }
     __syncwarp();
-  } else if (warp < 4) {
+  } else if (warp < 2 + kBndWarps) {
     // ------------------------------------------------------------------ row bounds
-    // Warp w2 takes rows 64 w2 .. 64 w2 + 63 of each tile, four rows at a time.  Lane l reads
-    // the 16-byte chunks l, l + 32, ... of a row (coalesced); chunks 2t and 2t + 1 (lanes l and
-    // l ^ 1 of one round) make the 16 coordinates of MMA instruction t.  Per row: the squared
-    // norm b_t of each block, the exclusive prefix P_t = sum of b_t' over t' < t (a scan over
-    // the lanes, carried from round to round), and E = sum_t sqrt(P_t) WP_t + sqrt(b_t) WB_t,
-    // every step rounded up (xfac covers the binary32 sums of squares in any order).
+    // Warp w2 takes rows 32 w2 .. 32 w2 + 31 of each tile, eight at a time, all their loads
+    // issued before any is used.  Lane l covers the MMA blocks 2l and 2l + 1 of a pass of 64
+    // blocks (elements [32 l, 32 l + 32) of the pass: four 16-byte chunks).  Per row: the
+    // squared norm b_t of each block, the exclusive prefix P_t of the b over the blocks before
+    // t (one scan over the lanes per pass, carried across passes), and
+    // E = sum_t sqrt(P_t) WP_t + sqrt(b_t) WB_t, every step of it rounded up (xfac covers the
+    // binary32 sums of squares, in any order).
     const int w2 = warp - 2;
-    const int nch = a.d / 8, nch2 = 2 * a.S;  // chunks of data; chunks of the padded pass
+    const int nch = a.d / 8, S_ = a.S;
     const float ca = a.ca, cx = a.cx, tau_abs = a.tau_abs, xfac = a.xfac, qmin = a.qmin;
     const float* const WP = a.wprof;
-    const float* const WB = a.wprof + a.S;
+    const float* const WB = a.wprof + S_;
     const uint4* const X4 = reinterpret_cast<const uint4*>(a.X);
     const bool count_nonfinite = !(a.mode & kStoreProj);
-    const bool even = (lane & 1) == 0;
     int ml = 0;
     for (long long m = blockIdx.x; m < ntiles; m += gridDim.x, ++ml) {
       const int t = ml & 1;
@@ -273,67 +275,75 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) set_abort(S, a.st);
         break;
       }
-      for (int r0 = 0; r0 < 64; r0 += 4) {
-        float carry[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
-        uint32_t nz[4] = {0u, 0u, 0u, 0u};
-        long long row[4];
+      for (int r0 = 0; r0 < 32; r0 += kBndRows) {
+        float carry[kBndRows], E[kBndRows];
+        uint32_t nz[kBndRows];
+        long long row[kBndRows];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) row[j] = m * kGemmBM + w2 * 64 + r0 + j;
-        // every instruction of the pass, the ones over the zero padding of d too (their
-        // products are 0, but the accumulator is an addend)
-        for (int c0 = 0; c0 < nch2; c0 += 32) {
-          const int c = c0 + lane;
-          const int blk = c >> 1;
-          uint4 v[4];
+        for (int j = 0; j < kBndRows; ++j) {
+          row[j] = m * kGemmBM + w2 * 32 + r0 + j;
+          carry[j] = 0.f;
+          E[j] = 0.f;
+          nz[j] = 0u;
+        }
+        for (int p = 0; p < S_; p += 64) {  // passes of 64 MMA blocks (d = 1024: one pass)
+          const int blk0 = p + 2 * lane;
+          const int c0 = 2 * blk0;  // first 16-byte chunk of the lane
+          uint4 v[kBndRows][4];
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
-            v[j] = (c < nch && row[j] < n) ? __ldg(X4 + row[j] * nch + c) : make_uint4(0u, 0u, 0u, 0u);
-          const float wp = even && c < nch2 ? __ldg(WP + blk) : 0.f;
-          const float wb = even && c < nch2 ? __ldg(WB + blk) : 0.f;
+          for (int j = 0; j < kBndRows; ++j)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const uint32_t w[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
-            float cs = 0.f;
+            for (int k = 0; k < 4; ++k)
+              v[j][k] = (c0 + k < nch && row[j] < n) ? __ldg(X4 + row[j] * nch + c0 + k) : make_uint4(0u, 0u, 0u, 0u);
+          const float wp0 = blk0 < S_ ? __ldg(WP + blk0) : 0.f, wb0 = blk0 < S_ ? __ldg(WB + blk0) : 0.f;
+          const float wp1 = blk0 + 1 < S_ ? __ldg(WP + blk0 + 1) : 0.f, wb1 = blk0 + 1 < S_ ? __ldg(WB + blk0 + 1) : 0.f;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const float lo = bf16_lo(w[e]), hi = bf16_hi(w[e]);
-              cs = fmaf(lo, lo, cs);
-              cs = fmaf(hi, hi, cs);
-              nz[j] |= w[e] & 0x7FFF7FFFu;
+          for (int j = 0; j < kBndRows; ++j) {
+            float bs[2] = {0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const uint32_t w[4] = {v[j][k].x, v[j][k].y, v[j][k].z, v[j][k].w};
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float lo = bf16_lo(w[e]), hi = bf16_hi(w[e]);
+                bs[k >> 1] = fmaf(lo, lo, bs[k >> 1]);
+                bs[k >> 1] = fmaf(hi, hi, bs[k >> 1]);
+                nz[j] |= w[e] & 0x7FFF7FFFu;
+              }
             }
-            const float b = cs + __shfl_xor_sync(0xFFFFFFFFu, cs, 1);  // block sum (both lanes)
-            const float ve = even ? b : 0.f;
-            float inc = ve;  // inclusive scan of the blocks over the lanes
+            const float lt = bs[0] + bs[1];
+            float inc = lt;  // inclusive scan of the lane totals
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
               const float u = __shfl_up_sync(0xFFFFFFFFu, inc, off);
               if (lane >= off) inc += u;
             }
-            float ex = __shfl_up_sync(0xFFFFFFFFu, inc, 2);  // the previous block's inclusive sum
-            if (lane < 2) ex = 0.f;
+            float ex = __shfl_up_sync(0xFFFFFFFFu, inc, 1);
+            if (lane == 0) ex = 0.f;
             const float tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
-            if (even && c < nch2) {
-              const float P = __fadd_ru(ex, carry[j]);
-              E[j] = __fmaf_ru(__fsqrt_ru(__fmul_ru(P, xfac)), wp, E[j]);
-              E[j] = __fmaf_ru(__fsqrt_ru(__fmul_ru(b, xfac)), wb, E[j]);
-            }
+            const float P0 = __fadd_ru(carry[j], ex), P1 = __fadd_ru(P0, bs[0]);
+            float e = __fmul_ru(__fsqrt_ru(__fmul_ru(P0, xfac)), wp0);
+            e = __fmaf_ru(__fsqrt_ru(__fmul_ru(bs[0], xfac)), wb0, e);
+            e = __fmaf_ru(__fsqrt_ru(__fmul_ru(P1, xfac)), wp1, e);
+            e = __fmaf_ru(__fsqrt_ru(__fmul_ru(bs[1], xfac)), wb1, e);
+            E[j] = __fadd_ru(E[j], e);
             carry[j] = __fadd_ru(carry[j], tot);
           }
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < kBndRows; ++j) {
 #pragma unroll
           for (int off = 16; off > 0; off >>= 1) {
             E[j] = __fadd_ru(E[j], __shfl_xor_sync(0xFFFFFFFFu, E[j], off));
             nz[j] |= __shfl_xor_sync(0xFFFFFFFFu, nz[j], off);
           }
         }
-        if (lane < 4) {
+        if (lane < kBndRows) {
           float qq = carry[0], ee = E[0];
           uint32_t zz = nz[0];
           long long ii = row[0];
 #pragma unroll
-          for (int j = 1; j < 4; ++j)
+          for (int j = 1; j < kBndRows; ++j)
             if (lane == j) {
               qq = carry[j];
               ee = E[j];
@@ -348,11 +358,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             thr = 0xFFFFFFFFu;  // every column of the row is resolved exactly
           } else {
             const float xu = __fsqrt_ru(__fmul_ru(qq, xfac));
-            const float B = __fmaf_ru(ca, ee, __fmaf_ru(cx, xu, tau_abs));
-            thr = __float_as_uint(B) + 1u;  // |v| <= B  <=>  bits(|v|) < bits(B) + 1
+            thr = __float_as_uint(__fmaf_ru(ca, ee, __fmaf_ru(cx, xu, tau_abs)));
           }
-          S->bthr[t][w2 * 64 + r0 + lane] = thr;
-          S->bzero[t][w2 * 64 + r0 + lane] = zero;
+          S->bthr[t][w2 * 32 + r0 + lane] = thr;
+          S->bzero[t][w2 * 32 + r0 + lane] = zero;
           if (count_nonfinite && ii < n && !isfinite(qq)) atomicAdd(&a.st->nonfinite, 1ull);
         }
       }
@@ -371,6 +380,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const unsigned long long seg_cap = a.seg_cap;
     unsigned long long* const seg = a.defer + seg_cap * blockIdx.x;
     const uint32_t kmask = K >= 32 ? 0xFFFFFFFFu : (1u << K) - 1u;
+    const float* const colf = a.colf;
     long long u = 0;
     int ml = 0;
     bool ok = true;
@@ -382,8 +392,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) set_abort(S, a.st);
         break;
       }
-      const uint32_t thr = S->bthr[tslot][r];
+      // B of the row (bit pattern); all ones: every column is resolved exactly
+      const uint32_t Bb = S->bthr[tslot][r];
       const bool zero_row = S->bzero[tslot][r] != 0u;
+      const bool every = Bb == 0xFFFFFFFFu;
+      const uint32_t thr1 = (every || zero_row) ? 0u : Bb + 1u;  // |v| <= B  <=>  bits(|v|) < bits(B) + 1
+      const float Bf = (every || zero_row) ? 0.f : __uint_as_float(Bb);
       mbar_arrive(&S->b_empty[tslot]);
       const long long i = m * kGemmBM + r;
       const bool valid = i < n;
@@ -422,9 +436,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             sw[g] = ~__brev((c_0 << 24) | (c_1 << 16) | (c_2 << 8) | c_3);
             uint32_t am = 0u;
+            if (colf) {  // columns of unequal norms: column c's bound is B * colf[c]
 #pragma unroll
-            for (int k = 0; k < 32; ++k) am |= ((vv[k] & 0x7FFFFFFFu) < thr ? 1u : 0u) << k;
-            aw[g] = am;
+              for (int k = 0; k < 32; ++k) {
+                const float tc = __fmul_ru(Bf, __ldg(colf + un * kGemmBN + 32 * g + k));
+                am |= (fabsf(__uint_as_float(vv[k])) <= tc ? 1u : 0u) << k;
+              }
+            } else {
+#pragma unroll
+              for (int k = 0; k < 32; ++k) am |= ((vv[k] & 0x7FFFFFFFu) < thr1 ? 1u : 0u) << k;
+            }
+            aw[g] = every ? 0xFFFFFFFFu : (zero_row ? 0u : am);
             if constexpr (PROJ) {
               if (valid) {
 #pragma unroll

@@ -37,10 +37,9 @@ def _row_band(W, Xf):
     S = dp // 16
     Wd = W.astype(np.float64)
     hi = np.zeros((dp, KL))
-    one = np.array_equal(_bf16(W), Wd)  # bfloat16-valued W: one product, columns scaled by 2^-e
-    if one:
-        e = np.frexp(np.linalg.norm(Wd, axis=0))[1]
-        hi[:d] = np.ldexp(Wd, -e[None, :])
+    one = np.array_equal(_bf16(W), Wd)  # bfloat16-valued W: one product; the bound of column c
+    if one:                              # is B ||w_c||, B from the normalised columns' profile
+        hi[:d] = Wd / np.linalg.norm(Wd, axis=0)[None, :]
         rmax, tnorm = 0.0, 0.0
     else:
         wu = (Wd / np.linalg.norm(Wd, axis=0)[None, :]).astype(np.float32)
