@@ -512,7 +512,7 @@ int plan_gemm(ace_detector* h) {
                                ace::kGemmBN))
     return rc;
   // WP_t = max over columns of ||w'_hi[0, 16t)||, WB_t = max of ||w'_hi[16t, 16t + 16)||, for
-  // the S = dp/16 MMA instructions of one pass (rounded up).  The single-product image's
+  // the S = dp/16 MMA instructions of one pass, folded per k-block (rounded up).  The single-product image's
   // columns (norms in [1/2, 1)) are normalised for the profile, and each column's norm goes to
   // colf, which scales the row bound per column.
   const int S = dp / 16;
@@ -540,9 +540,17 @@ int plan_gemm(ace_detector* h) {
         pre += blk;
       }
     }
-    for (int t = 0; t < S; ++t) {
-      prof[t] = std::nextafter(static_cast<float>(std::sqrt(wp[t]) * (1.0 + 1e-12)), FLT_MAX);
-      prof[S + t] = std::nextafter(static_cast<float>(std::sqrt(wb[t]) * (1.0 + 1e-12)), FLT_MAX);
+    // per k-block of four instructions: sum of the four WP_t, and sqrt of the sum of the four
+    // WB_t^2 (the kernel bounds the k-block's terms with these; see hash_gemm.cu)
+    const int nkb = dp / ace::kGemmBK;
+    for (int kb = 0; kb < nkb; ++kb) {
+      double sp = 0.0, sb = 0.0;
+      for (int t = 4 * kb; t < 4 * kb + 4; ++t) {
+        sp += std::sqrt(wp[t]);
+        sb += wb[t];
+      }
+      prof[kb] = std::nextafter(static_cast<float>(sp * (1.0 + 1e-12)), FLT_MAX);
+      prof[nkb + kb] = std::nextafter(static_cast<float>(std::sqrt(sb) * (1.0 + 1e-12)), FLT_MAX);
     }
   }
   cudaFree(h->gprof);

@@ -27,12 +27,13 @@ struct GemmArgs {
   int nprod;                  // 2: x.w'_lo then x.w'_hi (binary32 W split in two); 1: x.w'_hi only
   int klp;                    // image rows of one part (nunits * 256); the lo part follows the hi part
   // Row bound B = ca * E + cx * ||x||_up + tau_abs (every column when q < qmin or q is not
-  // finite), E = sum over the hi-pass MMA instructions t of ||x_<16t|| WP_t + ||x_Bt|| WB_t with
-  // WP_t, WB_t the largest norms over the columns of w'_hi's prefix [0, 16t) and block
-  // [16t, 16t + 16) (wprof[t], wprof[S + t]); see hash_gemm.cu.
+  // finite), E bounding the sum over the hi-pass MMA instructions t of
+  // ||x_<16t|| WP_t + ||x_Bt|| WB_t, with WP_t, WB_t the largest norms over the columns of
+  // w'_hi's prefix [0, 16t) and block [16t, 16t + 16); see hash_gemm.cu.
   float ca, cx, tau_abs, xfac, qmin;
   int S;                      // MMA instructions per pass (dp / 16)
-  const float* wprof;         // [2][S] WP_t, then WB_t (rounded up)
+  const float* wprof;         // [2][nkb] per k-block: sum of its four WP_t, then sqrt of the
+                              // sum of its four WB_t^2 (rounded up)
   const float* colf;          // [nunits][256] per image column: its norm (rounded up) when the
                               // columns are not unit vectors (the bound of column c is B colf[c],
                               // WP and WB then being those of the normalised columns); else null

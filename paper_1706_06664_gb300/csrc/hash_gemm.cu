@@ -23,8 +23,10 @@
 //     ||x_<16t|| WP_t + ||x_Bt|| WB_t + 2^-7 ||x||, with WP_t and WB_t the largest norms of
 //     w'_hi's prefix and block over the columns.  Summed over the instructions:
 //     5.25 * 2^-23 * (E + (2^-6 S + 1) ||x||), E = sum_t ||x_<16t|| WP_t + ||x_Bt|| WB_t, a
-//     1.25x margin applied.  For a point whose energy is spread over d, E is about S/2 ||x||
-//     instead of the S ||x|| that bounding every partial sum by ||x|| would give;
+//     1.25x margin applied.  E is evaluated per k-block of four instructions (the prefix at the
+//     k-block's end for all four, Cauchy-Schwarz over the four block terms).  For a point whose
+//     energy is spread over d, E is about S/2 ||x|| instead of the S ||x|| that bounding every
+//     partial sum by ||x|| would give;
 //   - normalisation (2^-23 ||x||) and the binary64 reference itself (gamma64_d ||x||).
 // The bound is one number per point, computed by the row-bound warps with upward rounding.
 // A column whose |accumulator| <= B is deferred as a (point, column) entry; recheck_cols
@@ -50,13 +52,13 @@ namespace {
 using namespace tc;
 
 constexpr int kThreads = 320;   // 10 warps
-constexpr int kBndWarps = 4;    // row-bound warps (2 .. 5)
-constexpr int kBndRows = 8;     // rows per row-bound warp in flight
+constexpr int kBndWarps = 4;    // row-bound warps (2 .. 5): one thread per tile row
 constexpr int kStages = kGemmStages;
 constexpr uint32_t kABytes = kGemmBM * kGemmBK * 2;  // 16 KB
 constexpr uint32_t kBBytes = kGemmBN * kGemmBK * 2;  // 32 KB
 constexpr uint32_t kStageBytes = kABytes + kBBytes;
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
+static_assert(kStages * kStageBytes + 4096 * 4 + 4096 + 1024 <= 227 * 1024, "shared memory");
 
 struct GSmem {
   uint64_t full[kStages], empty[kStages];
@@ -66,11 +68,12 @@ struct GSmem {
   uint32_t taddr;
   int abort;
   unsigned int ndef;
-  uint32_t bthr[2][kGemmBM];  // per tile slot and row: deferral threshold (bit pattern + 1)
+  uint32_t bthr[2][kGemmBM];  // per tile slot and row: the row bound B (bit pattern)
   uint32_t bzero[2][kGemmBM]; // per tile slot and row: the row is exactly zero
 };
 
-constexpr int kSmemBytes = static_cast<int>(kStages * kStageBytes + sizeof(GSmem) + 1024);
+constexpr int kColfMax = 4096;  // per-column norms kept in shared memory (16 units)
+constexpr int kSmemBytes = static_cast<int>(kStages * kStageBytes + sizeof(GSmem) + kColfMax * 4 + 1024);
 
 __device__ __forceinline__ void set_abort(GSmem* S, DevStats* st) {
   S->abort = 1;
@@ -141,6 +144,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* const smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   const uint32_t sbase = smem_u32(smem);
   GSmem* const S = reinterpret_cast<GSmem*>(smem + kStages * kStageBytes);
+  float* const colf_s = reinterpret_cast<float*>(smem + kStages * kStageBytes + sizeof(GSmem));
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long ntiles = a.ntiles, n = a.n;
@@ -152,7 +156,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     S->ndef = 0;
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&S->full[s], 1);
-      mbar_init(&S->empty[s], 1);
+      mbar_init(&S->empty[s], 1 + kBndWarps);  // the MMA commit and each row-bound warp
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&S->t_full[b], 1);
@@ -167,6 +171,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     tmem_alloc(&S->taddr, 512);
     tmem_relinquish();
   }
+  const bool colf_in_smem = a.colf && nunits * kGemmBN <= kColfMax;
+  if (colf_in_smem)
+    for (int c = tid; c < nunits * kGemmBN; c += kThreads) colf_s[c] = a.colf[c];
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -252,120 +259,90 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
   } else if (warp < 2 + kBndWarps) {
     // ------------------------------------------------------------------ row bounds
-    // Warp w2 takes rows 32 w2 .. 32 w2 + 31 of each tile, eight at a time, all their loads
-    // issued before any is used.  Lane l covers the MMA blocks 2l and 2l + 1 of a pass of 64
-    // blocks (elements [32 l, 32 l + 32) of the pass: four 16-byte chunks).  Per row: the
-    // squared norm b_t of each block, the exclusive prefix P_t of the b over the blocks before
-    // t (one scan over the lanes per pass, carried across passes), and
-    // E = sum_t sqrt(P_t) WP_t + sqrt(b_t) WB_t, every step of it rounded up (xfac covers the
-    // binary32 sums of squares, in any order).
-    const int w2 = warp - 2;
-    const int nch = a.d / 8, S_ = a.S;
+    // Thread r owns row r of the tile.  It follows the ring like the MMA issuer and releases
+    // every stage it has seen (one arrival per warp); during the first pass of the first unit
+    // of a tile, the stage's X k-block is the row's coordinates [64 kb, 64 kb + 64): the thread
+    // reads its 128 bytes from the swizzled tile (chunk j of row r sits at chunk j ^ (r mod 8)),
+    // and updates, in k order, the squared norms b_t of MMA blocks t = 4 kb .. 4 kb + 3, their
+    // running prefix P, and E = sum_t sqrt(P_t) WP_t + sqrt(b_t) WB_t, every step rounded up
+    // (xfac covers the binary32 sums of squares).  The row's bound is ready after the pass, long
+    // before the epilogue of that unit needs it.
+    const int r = tid - 64;  // 0 .. 127
     const float ca = a.ca, cx = a.cx, tau_abs = a.tau_abs, xfac = a.xfac, qmin = a.qmin;
-    const float* const WP = a.wprof;
-    const float* const WB = a.wprof + S_;
-    const uint4* const X4 = reinterpret_cast<const uint4*>(a.X);
+    const float* const WP = a.wprof;           // per k-block: sum of the four WP_t
+    const float* const WB = a.wprof + a.nkb;   // per k-block: sqrt of the sum of the four WB_t^2
     const bool count_nonfinite = !(a.mode & kStoreProj);
+    const uint32_t rsw = static_cast<uint32_t>(r & 7);
+    const uint32_t roff = static_cast<uint32_t>((r >> 3) * 1024 + (r & 7) * 128);
+    long long it = 0;
     int ml = 0;
-    for (long long m = blockIdx.x; m < ntiles; m += gridDim.x, ++ml) {
+    bool ok = true;
+    for (long long m = blockIdx.x; ok && m < ntiles; m += gridDim.x, ++ml) {
       const int t = ml & 1;
-      bool ok = S->abort == 0;
-      if (ok && ml >= 2) ok = mbar_wait(&S->b_empty[t], static_cast<uint32_t>(((ml >> 1) + 1) & 1), &S->abort, kWaitCycles);
+      if (ml >= 2) ok = mbar_wait(&S->b_empty[t], static_cast<uint32_t>(((ml >> 1) + 1) & 1), &S->abort, kWaitCycles);
       if (!__all_sync(0xFFFFFFFFu, ok)) {
+        ok = false;
         if (lane == 0) set_abort(S, a.st);
         break;
       }
-      for (int r0 = 0; r0 < 32; r0 += kBndRows) {
-        float carry[kBndRows], E[kBndRows];
-        uint32_t nz[kBndRows];
-        long long row[kBndRows];
+      float P = 0.f, E = 0.f;
+      uint32_t nz = 0u;
+      for (int un = 0; ok && un < nunits; ++un) {
+        for (int ks = 0; ks < ksteps; ++ks, ++it) {
+          const int s = static_cast<int>(it % kStages);
+          ok = mbar_wait(&S->full[s], static_cast<uint32_t>((it / kStages) & 1), &S->abort, kWaitCycles);
+          if (!__all_sync(0xFFFFFFFFu, ok)) {
+            ok = false;
+            if (lane == 0) set_abort(S, a.st);
+            break;
+          }
+          if (un == 0 && ks < nkb) {
+            const uint8_t* arow = smem + static_cast<uint32_t>(s) * kStageBytes + roff;
+            float bq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int j = 0; j < kBndRows; ++j) {
-          row[j] = m * kGemmBM + w2 * 32 + r0 + j;
-          carry[j] = 0.f;
-          E[j] = 0.f;
-          nz[j] = 0u;
-        }
-        for (int p = 0; p < S_; p += 64) {  // passes of 64 MMA blocks (d = 1024: one pass)
-          const int blk0 = p + 2 * lane;
-          const int c0 = 2 * blk0;  // first 16-byte chunk of the lane
-          uint4 v[kBndRows][4];
-#pragma unroll
-          for (int j = 0; j < kBndRows; ++j)
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-              v[j][k] = (c0 + k < nch && row[j] < n) ? __ldg(X4 + row[j] * nch + c0 + k) : make_uint4(0u, 0u, 0u, 0u);
-          const float wp0 = blk0 < S_ ? __ldg(WP + blk0) : 0.f, wb0 = blk0 < S_ ? __ldg(WB + blk0) : 0.f;
-          const float wp1 = blk0 + 1 < S_ ? __ldg(WP + blk0 + 1) : 0.f, wb1 = blk0 + 1 < S_ ? __ldg(WB + blk0 + 1) : 0.f;
-#pragma unroll
-          for (int j = 0; j < kBndRows; ++j) {
-            float bs[2] = {0.f, 0.f};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const uint32_t w[4] = {v[j][k].x, v[j][k].y, v[j][k].z, v[j][k].w};
+            for (int j = 0; j < 8; ++j) {
+              const uint4 v = *reinterpret_cast<const uint4*>(arow + ((static_cast<uint32_t>(j) ^ rsw) << 4));
+              const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
                 const float lo = bf16_lo(w[e]), hi = bf16_hi(w[e]);
-                bs[k >> 1] = fmaf(lo, lo, bs[k >> 1]);
-                bs[k >> 1] = fmaf(hi, hi, bs[k >> 1]);
-                nz[j] |= w[e] & 0x7FFF7FFFu;
+                bq[j >> 1] = fmaf(lo, lo, bq[j >> 1]);
+                bq[j >> 1] = fmaf(hi, hi, bq[j >> 1]);
+                nz |= w[e] & 0x7FFF7FFFu;
               }
             }
-            const float lt = bs[0] + bs[1];
-            float inc = lt;  // inclusive scan of the lane totals
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-              const float u = __shfl_up_sync(0xFFFFFFFFu, inc, off);
-              if (lane >= off) inc += u;
+            // per k-block (four MMA blocks): sum_t sqrt(P_t) WP_t <= sqrt(P_end) sum_t WP_t with
+            // P_end the prefix through this k-block, and sum_t sqrt(b_t) WB_t <=
+            // sqrt(sum_t b_t) sqrt(sum_t WB_t^2) (Cauchy-Schwarz over the four blocks); the host
+            // folds the two sums into WP[kb] and WB[kb].  sqrtf is correctly rounded, so
+            // (1 + 2^-22) makes each square root an upper bound.
+            const float bk = __fadd_ru(__fadd_ru(bq[0], bq[1]), __fadd_ru(bq[2], bq[3]));
+            P = __fadd_ru(P, bk);
+            const float sp = __fmul_ru(sqrtf(__fmul_ru(P, xfac)), 1.00000023841857910156f);
+            const float sb = __fmul_ru(sqrtf(__fmul_ru(bk, xfac)), 1.00000023841857910156f);
+            E = __fmaf_ru(sp, __ldg(WP + ks), E);
+            E = __fmaf_ru(sb, __ldg(WB + ks), E);
+            if (ks == nkb - 1) {
+              uint32_t thr, zero = 0u;
+              if (nz == 0u) {  // every coordinate is +-0: every projection is exactly 0, bit 0
+                thr = 0u;
+                zero = 1u;
+              } else if (!isfinite(P) || !isfinite(E) || P < qmin) {
+                thr = 0xFFFFFFFFu;  // every column of the row is resolved exactly
+              } else {
+                const float xu = __fsqrt_ru(__fmul_ru(P, xfac));
+                thr = __float_as_uint(__fmaf_ru(ca, E, __fmaf_ru(cx, xu, tau_abs)));
+              }
+              S->bthr[t][r] = thr;
+              S->bzero[t][r] = zero;
+              if (count_nonfinite && m * kGemmBM + r < n && !isfinite(P)) atomicAdd(&a.st->nonfinite, 1ull);
+              mbar_arrive(&S->b_full[t]);
             }
-            float ex = __shfl_up_sync(0xFFFFFFFFu, inc, 1);
-            if (lane == 0) ex = 0.f;
-            const float tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
-            const float P0 = __fadd_ru(carry[j], ex), P1 = __fadd_ru(P0, bs[0]);
-            float e = __fmul_ru(__fsqrt_ru(__fmul_ru(P0, xfac)), wp0);
-            e = __fmaf_ru(__fsqrt_ru(__fmul_ru(bs[0], xfac)), wb0, e);
-            e = __fmaf_ru(__fsqrt_ru(__fmul_ru(P1, xfac)), wp1, e);
-            e = __fmaf_ru(__fsqrt_ru(__fmul_ru(bs[1], xfac)), wb1, e);
-            E[j] = __fadd_ru(E[j], e);
-            carry[j] = __fadd_ru(carry[j], tot);
           }
-        }
-#pragma unroll
-        for (int j = 0; j < kBndRows; ++j) {
-#pragma unroll
-          for (int off = 16; off > 0; off >>= 1) {
-            E[j] = __fadd_ru(E[j], __shfl_xor_sync(0xFFFFFFFFu, E[j], off));
-            nz[j] |= __shfl_xor_sync(0xFFFFFFFFu, nz[j], off);
-          }
-        }
-        if (lane < kBndRows) {
-          float qq = carry[0], ee = E[0];
-          uint32_t zz = nz[0];
-          long long ii = row[0];
-#pragma unroll
-          for (int j = 1; j < kBndRows; ++j)
-            if (lane == j) {
-              qq = carry[j];
-              ee = E[j];
-              zz = nz[j];
-              ii = row[j];
-            }
-          uint32_t thr, zero = 0u;
-          if (zz == 0u) {  // every coordinate is +-0: every projection is exactly 0, bit 0
-            thr = 0u;
-            zero = 1u;
-          } else if (!isfinite(qq) || !isfinite(ee) || qq < qmin) {
-            thr = 0xFFFFFFFFu;  // every column of the row is resolved exactly
-          } else {
-            const float xu = __fsqrt_ru(__fmul_ru(qq, xfac));
-            thr = __float_as_uint(__fmaf_ru(ca, ee, __fmaf_ru(cx, xu, tau_abs)));
-          }
-          S->bthr[t][w2 * 32 + r0 + lane] = thr;
-          S->bzero[t][w2 * 32 + r0 + lane] = zero;
-          if (count_nonfinite && ii < n && !isfinite(qq)) atomicAdd(&a.st->nonfinite, 1ull);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&S->empty[s]);
         }
       }
-      mbar_arrive(&S->b_full[t]);
     }
   } else {
     // ------------------------------------------------------------------ epilogue
@@ -380,7 +357,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const unsigned long long seg_cap = a.seg_cap;
     unsigned long long* const seg = a.defer + seg_cap * blockIdx.x;
     const uint32_t kmask = K >= 32 ? 0xFFFFFFFFu : (1u << K) - 1u;
-    const float* const colf = a.colf;
+    const float* const colf = colf_in_smem ? colf_s : a.colf;
     long long u = 0;
     int ml = 0;
     bool ok = true;
@@ -439,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (colf) {  // columns of unequal norms: column c's bound is B * colf[c]
 #pragma unroll
               for (int k = 0; k < 32; ++k) {
-                const float tc = __fmul_ru(Bf, __ldg(colf + un * kGemmBN + 32 * g + k));
+                const float tc = __fmul_ru(Bf, colf[un * kGemmBN + 32 * g + k]);
                 am |= (fabsf(__uint_as_float(vv[k])) <= tc ? 1u : 0u) << k;
               }
             } else {

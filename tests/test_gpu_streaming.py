@@ -49,11 +49,14 @@ def _row_band(W, Xf):
     blk = (hi.reshape(S, 16, KL) ** 2).sum(axis=1)            # S x KL
     pre = np.vstack([np.zeros((1, KL)), np.cumsum(blk, axis=0)[:-1]])
     WP, WB = np.sqrt(pre.max(axis=1)), np.sqrt(blk.max(axis=1))
+    # per k-block of four instructions: the prefix at the k-block's end for all four, and
+    # Cauchy-Schwarz over the four block terms
+    WPk = WP.reshape(-1, 4).sum(axis=1)
+    WBk = np.sqrt((WB.reshape(-1, 4) ** 2).sum(axis=1))
     Xp = np.zeros((Xf.shape[0], dp))
     Xp[:, :d] = Xf
-    xb = (Xp.reshape(-1, S, 16) ** 2).sum(axis=2)              # n x S
-    xpre = np.hstack([np.zeros((Xf.shape[0], 1)), np.cumsum(xb, axis=1)[:, :-1]])
-    E = np.sqrt(xpre) @ WP + np.sqrt(xb) @ WB
+    xk = (Xp.reshape(-1, dp // 64, 64) ** 2).sum(axis=2)       # n x nkb
+    E = np.sqrt(np.cumsum(xk, axis=1)) @ WPk + np.sqrt(xk) @ WBk
     xn = np.linalg.norm(Xf, axis=1)
     ca = 5.25 * 2.0**-23 * 1.25
     cx = ca * (2.0**-6 * S + 1) + rmax + tnorm + d * 2.0**-53 / (1 - d * 2.0**-53)
