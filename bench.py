@@ -190,7 +190,7 @@ def _config_cases():
     draw of the same recipe (its rate per point does not depend on n)."""
     from paper_1706_06664_gb300 import workloads
     Xd, _ = workloads.highdim_device(seed=3, n=1_000_000)
-    c3 = {"X_dev": Xd, "d": 1024, "K": 16, "L": 64, "dtype": "bf16",
+    c3 = {"X_dev": Xd, "d": 1024, "K": 16, "L": 64, "dtype": "bf16", "w_bf16_variant": True,
           "X": workloads.highdim(seed=3, n=20_000)["X"]}
     return [("small", workloads.small(seed=1)), ("kdd-shaped", workloads.kdd(seed=2)),
             ("high-dimensional", c3)]
@@ -258,9 +258,12 @@ def per_config(cases) -> dict:
         xb = 2 if w.get("dtype") == "bf16" else 4
         flop = 2.0 * n * w["d"] * w["K"] * w["L"]
         res = {"n": n, "d": w["d"], "K": w["K"], "L": w["L"], "x_dtype": "bf16" if xb == 2 else "f32"}
-        for prec, want in (("fp32", ace.ACE_PROJ_FP32), ("bf16", ace.ACE_PROJ_BF16)):
+        variants = [("fp32", ace.ACE_PROJ_FP32, False), ("bf16", ace.ACE_PROJ_BF16, False)]
+        if w.get("w_bf16_variant"):
+            variants.append(("bf16_w_bf16", ace.ACE_PROJ_BF16, True))
+        for prec, want, wb in variants:
             try:
-                det = ace.Detector(w["d"], w["K"], w["L"], seed=11, precision=prec)
+                det = ace.Detector(w["d"], w["K"], w["L"], seed=11, precision=prec[:4], w_bf16=wb)
             except ace.AceError as e:
                 if e.code == ace.ACE_ERR_UNSUPPORTED:
                     res[prec] = "engine not available for this shape"
@@ -290,12 +293,13 @@ def per_config(cases) -> dict:
             t = statistics.median(times)
             phases = {k: v["ms"] / v["timed"] for k, v in prof.items() if v["timed"]}
             entry = {"points_per_s": n / t, "ms": t * 1e3, "projection_tflops": flop / t / 1e12,
+                     "tc_products": st["tc_products"],
                      "phases_ms": phases, "rechecks_per_point": st["rechecks"] / (n * reps),
                      "deferred_per_point": st["deferred"] / (n * reps),
                      "step_roofline": _step_roofline(n, w["d"], w["K"], w["L"], xb, t * 1e3, peaks)}
             if "hash" in phases:
                 th = phases["hash"] / 1e3
-                if prec == "bf16":
+                if prec.startswith("bf16"):
                     entry["hash_roofline"] = {"bound": "tensor", "achieved": flop / th / 1e12,
                                               "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                                               "frac": flop / th / 1e12 / peaks["bf16_tflops"],
@@ -305,8 +309,9 @@ def per_config(cases) -> dict:
                                               "unit": "TFLOP/s", "frac": flop / th / 1e12 / FP32_ALU_PEAK_TFLOPS,
                                               "peak_src": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"}
             res[prec] = entry
-        if isinstance(res.get("bf16"), dict) and isinstance(res.get("fp32"), dict):
-            res["bf16_vs_fp32"] = res["bf16"]["points_per_s"] / res["fp32"]["points_per_s"]
+        for v in ("bf16", "bf16_w_bf16"):
+            if isinstance(res.get(v), dict) and isinstance(res.get("fp32"), dict):
+                res[f"{v}_vs_fp32"] = res[v]["points_per_s"] / res["fp32"]["points_per_s"]
         out[name] = res
         del Xd
     return out

@@ -181,6 +181,23 @@ int ace_insert_score_host(ace_handle h, const void* X_host, int64_t n, int dtype
 int ace_delete(ace_handle h, const void* X_dev, int64_t n, int dtype, void* stream);
 
 /*
+ * ace_window_enable — sliding window over the inserted points, for drifting streams (§3.4.1:
+ * removing points by decrementing their counts keeps the mean of Eq. 11 / Eq. 12 exact).
+ * After ace_window_enable(h, W), h's arrays count only the last W points inserted (in call
+ * order, rows of a batch in order): before a batch of n points is inserted (ace_insert,
+ * ace_insert_score, the host-buffer and server paths), the oldest max(0, held + n - W) points
+ * are removed, their counts decremented on the device.  The ids of the held points are kept
+ * in a device ring of W * L ids (2 bytes each for K <= 16, else 4).  A batch larger than W
+ * is refused with ACE_ERR_ARG.  ace_stats' n_ins and mu_ins then describe the held points;
+ * the score statistics (N, S1, S2) keep running over every score returned.  W = 0 turns the
+ * window off.  The window can be set only while the detector holds no points (new, or after
+ * ace_reset, which empties it).  ace_delete, ace_batch_insert_score, the allocation-free
+ * entry point and ace_save refuse a windowed detector (ACE_ERR_ARG).  Synchronises the device.
+ * Errors: ACE_ERR_ARG, ACE_ERR_OOM, ACE_ERR_CUDA.
+ */
+int ace_window_enable(ace_handle h, int64_t window_points);
+
+/*
  * ace_batch_insert_score — ace_insert_score on `count` distinct detectors at once, each with
  * its own X_dev[g] (n[g] x d_g, device; one dtype for the whole batch) and optional outputs
  * (scores_dev, sums_dev, flags_dev: arrays of `count` device pointers, or NULL; an entry may

@@ -13,6 +13,9 @@ same call semantics as the library's C ABI:
 * ``score(X, alpha)`` Algorithm 1 query phase, then the §5.3 threshold rule
                       (score < mu - alpha*sigma over every score returned so far).
 * ``insert_score``    insert the whole batch, then score it against the updated arrays.
+* ``WindowDetector``  the same over a sliding window of the last W inserted points: before a
+                      batch is inserted, the oldest points beyond W are removed by §3.4.1
+                      deletion (Eq. 12), so the arrays always count the most recent points.
 """
 from __future__ import annotations
 
@@ -259,3 +262,36 @@ class Detector:
             "mu_ins": mu_ins, "mu": out[0] if rc == 0 else 0.0, "sigma": out[1] if rc == 0 else 0.0,
             "threshold": out[2] if rc == 0 else 0.0,
         }
+
+
+class WindowDetector(Detector):
+    """A detector whose arrays count only the last `window` inserted points (in insertion
+    order: earlier batches first, rows of a batch in order).  Inserting a batch of n <= window
+    points first removes the oldest max(0, held + n - window) points, each by §3.4.1 deletion
+    of its ids (the decrements of Eq. 12), then inserts the batch.  Scoring is unchanged."""
+
+    def __init__(self, d: int, K: int, L: int, window: int, seed: int | None = None, W: np.ndarray | None = None):
+        super().__init__(d, K, L, seed=seed, W=W)
+        if window < 1:
+            raise ValueError("window must be at least 1")
+        self.window = int(window)
+        self.held = np.zeros((0, L), dtype=np.uint32)  # ids of the points in the window, oldest first
+
+    def insert(self, X):
+        ids = self.hash(X)
+        n = ids.shape[0]
+        if n > self.window:
+            raise ValueError("a batch larger than the window")
+        m = max(0, self.held.shape[0] + n - self.window)
+        if m:
+            delete_ids(self.held[:m], self.counts, self.K)
+            self.held = self.held[m:]
+            self.n_ins -= m
+        insert_ids(ids, self.counts, self.K)
+        self.held = np.concatenate([self.held, ids], axis=0)
+        self.n_ins += n
+        return ids
+
+    def insert_score(self, X, alpha: float = 1.0):
+        ids = self.insert(X)
+        return self._score_ids(ids, alpha)

@@ -81,6 +81,10 @@ struct ace_detector {
   size_t stage_cap = 0;  // elements
   cudaStream_t cstream = nullptr;  // copy stream of the host-buffer entry (created on first use)
   uint64_t n_ins = 0;
+  // sliding window (ace_window_enable): the ids of the points held, table-major [L][win_cap],
+  // a ring whose oldest point sits at slot win_start; n_ins = points held
+  void* ring = nullptr;
+  long long win_cap = 0, win_start = 0;
   ace::DivConst div{};    // constants of the score division by L
   std::vector<float> Wh;  // host copy of W
   // tensor-core path
@@ -164,6 +168,7 @@ void free_all(ace_detector* h) {
   h->marks.clear();
   h->pool.clear();
   cudaFree(h->bimg);
+  cudaFree(h->ring);
   cudaFree(h->gimg);
   cudaFree(h->gprof);
   cudaFree(h->gcolf);
@@ -787,6 +792,44 @@ Engine pick_engine(ace_handle h, int x_bf16, const void* X) {
 // flips bits of 16-bit ids with 32-bit atomics).
 size_t ids_need(ace_handle h, long long n) { return static_cast<size_t>(n) * h->L * (h->K <= 16 ? 2 : 4) + 16; }
 
+// Sliding window, before a batch of n points is inserted: the batch must fit, and the oldest
+// points beyond the window are removed (§3.4.1 deletion: their counts decremented).
+int window_prepare(ace_handle h, long long n, cudaStream_t s) {
+  if (!h->ring || n == 0) return ACE_OK;
+  if (n > h->win_cap)
+    return fail(ACE_ERR_ARG, "a batch of %lld points is larger than the window of %lld", n, h->win_cap);
+  const long long held = static_cast<long long>(h->n_ins);
+  const long long m = std::max(0LL, held + n - h->win_cap);
+  if (m == 0) return ACE_OK;
+  cudaError_t e;
+  {
+    PhaseScope ps(h, ACE_PHASE_OTHER, s);
+    e = ace::launch_window_evict(h->ring, h->K <= 16, h->win_cap, h->win_start, m, h->K, h->L, h->counts, h->num_sms > 0 ? h->num_sms : 152, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "window eviction launch");
+  h->win_start = (h->win_start + m) % h->win_cap;
+  h->n_ins -= static_cast<uint64_t>(m);
+  return ACE_OK;
+}
+
+// Sliding window, after the batch's ids are in `ids` (table-major, leading dimension ld): they
+// go to the ring slots after the newest point (the slots of the points just removed).
+int window_commit(ace_handle h, const void* ids, long long ld, long long n, cudaStream_t s) {
+  if (!h->ring || n == 0) return ACE_OK;
+  const size_t idb = h->K <= 16 ? 2 : 4;
+  long long dst = (h->win_start + static_cast<long long>(h->n_ins)) % h->win_cap;
+  long long done = 0;
+  while (done < n) {
+    const long long len = std::min(n - done, h->win_cap - dst);
+    ACE_CUDA(cudaMemcpy2DAsync(static_cast<char*>(h->ring) + static_cast<size_t>(dst) * idb, h->win_cap * idb,
+                               static_cast<const char*>(ids) + static_cast<size_t>(done) * idb, ld * idb, len * idb,
+                               static_cast<size_t>(h->L), cudaMemcpyDeviceToDevice, s));
+    done += len;
+    dst = (dst + len) % h->win_cap;
+  }
+  return ACE_OK;
+}
+
 // Streaming tensor-core engine (hash_gemm.cu): ids (or projections), then the exact
 // resolution of the deferred (point, column) entries, then the count increments from the
 // stored ids when inserting.
@@ -947,6 +990,8 @@ int score_common(ace_handle h, const void* X, long long n, int dtype, double alp
   if (insert && h->n_ins + static_cast<uint64_t>(n) > 0xFFFFFFFFull)
     return fail(ACE_ERR_OVERFLOW, "inserting %lld points would allow a count above 2^32-1", n);
   if (n == 0) return ACE_OK;
+  if (insert && h->ring && n > h->win_cap)
+    return fail(ACE_ERR_ARG, "a batch of %lld points is larger than the window of %lld", n, h->win_cap);
   if ((rc = grow(&h->ids, &h->ids_cap, ids_need(h, n), s, "ids scratch"))) return rc;
   uint32_t* sum_out = sums;
   if (!sum_out) {
@@ -955,8 +1000,10 @@ int score_common(ace_handle h, const void* X, long long n, int dtype, double alp
     h->sums = static_cast<uint32_t*>(p);
     sum_out = h->sums;
   }
+  if (insert && (rc = window_prepare(h, n, s))) return rc;
   ace::HashArgs a = hash_args(h, X, n, dtype, ace::kStoreIds | (insert ? ace::kInsert : 0));
   if ((rc = run_hash(h, a, s))) return rc;
+  if (insert && (rc = window_commit(h, h->ids, n, n, s))) return rc;
   if (insert) h->n_ins += static_cast<uint64_t>(n);
   return score_tail(h, n, alpha, scores, sum_out, flags, s);
 }
@@ -993,6 +1040,30 @@ int ace_reset(ace_handle h, void* stream) {
   ACE_CUDA(cudaMemsetAsync(h->counts, 0, count_elems(h) * sizeof(uint32_t), s));
   ACE_CUDA(cudaMemsetAsync(h->st, 0, sizeof(ace::DevStats), s));
   h->n_ins = 0;
+  h->win_start = 0;
+  return ACE_OK;
+}
+
+int ace_window_enable(ace_handle h, int64_t window_points) {
+  if (!h) return fail(ACE_ERR_ARG, "handle is NULL");
+  if (window_points < 0) return fail(ACE_ERR_ARG, "window_points < 0");
+  if (h->n_ins != 0) return fail(ACE_ERR_ARG, "the window must be set while the detector holds no points");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "window");
+  cudaFree(h->ring);
+  h->ring = nullptr;
+  h->win_cap = 0;
+  h->win_start = 0;
+  if (window_points == 0) return ACE_OK;
+  if (window_points > 0xFFFFFFFFLL) return fail(ACE_ERR_ARG, "window_points above 2^32-1");
+  const size_t bytes = static_cast<size_t>(window_points) * h->L * (h->K <= 16 ? 2 : 4);
+  e = cudaMalloc(&h->ring, bytes);
+  if (e != cudaSuccess) {
+    h->ring = nullptr;
+    cudaGetLastError();
+    return fail(ACE_ERR_OOM, "window ring of %zu bytes: %s", bytes, cudaGetErrorString(e));
+  }
+  h->win_cap = window_points;
   return ACE_OK;
 }
 
@@ -1014,8 +1085,16 @@ int ace_insert(ace_handle h, const void* X_dev, int64_t n, int dtype, void* stre
     return fail(ACE_ERR_OVERFLOW, "inserting %lld points would allow a count above 2^32-1", static_cast<long long>(n));
   if (n == 0) return ACE_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  ace::HashArgs a = hash_args(h, X_dev, n, dtype, ace::kInsert);
+  if (h->ring) {  // the window keeps the batch's ids: they go through the scratch
+    if (n > h->win_cap)
+      return fail(ACE_ERR_ARG, "a batch of %lld points is larger than the window of %lld", static_cast<long long>(n),
+                  h->win_cap);
+    if ((rc = grow(&h->ids, &h->ids_cap, ids_need(h, n), s, "ids scratch"))) return rc;
+    if ((rc = window_prepare(h, n, s))) return rc;
+  }
+  ace::HashArgs a = hash_args(h, X_dev, n, dtype, ace::kInsert | (h->ring ? ace::kStoreIds : 0));
   if ((rc = run_hash(h, a, s))) return rc;
+  if (h->ring && (rc = window_commit(h, h->ids, n, n, s))) return rc;
   h->n_ins += static_cast<uint64_t>(n);
   return ACE_OK;
 }
@@ -1125,6 +1204,9 @@ static int enqueue_host_batch(ace_handle h, int op, const void* X_host, int64_t 
   const int nch = static_cast<int>(std::min<long long>((n + chunk - 1) / chunk, kMaxChunks));
   chunk = (n + nch - 1) / nch;
   chunk = (chunk + 127) / 128 * 128;
+  if (do_insert && h->ring && n > h->win_cap)
+    return fail(ACE_ERR_ARG, "a batch of %lld points is larger than the window of %lld", static_cast<long long>(n),
+                h->win_cap);
   ACE_CUDA(cudaStreamWaitEvent(h->cstream, sl.done, 0));
   for (int c = 0; c < nch; ++c) {
     const long long c0 = c * chunk, nc = std::min<long long>(chunk, n - c0);
@@ -1134,6 +1216,7 @@ static int enqueue_host_batch(ace_handle h, int op, const void* X_host, int64_t 
     ACE_CUDA(cudaEventRecord(sl.chunk[c], h->cstream));
   }
   const bool simt = pick_engine(h, dtype == ACE_BF16, sl.x) == Engine::kSimt;
+  if (do_insert && (rc = window_prepare(h, n, s))) return rc;
   for (int c = 0; c < nch; ++c) {
     const long long c0 = c * chunk, nc = std::min<long long>(chunk, n - c0);
     if (nc <= 0) break;
@@ -1149,6 +1232,7 @@ static int enqueue_host_batch(ace_handle h, int op, const void* X_host, int64_t 
     cudaError_t e = ace::launch_insert_from_ids(h->ids, h->K <= 16, n, n, h->K, h->L, h->counts, h->num_sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "insert kernel launch");
   }
+  if (do_insert && (rc = window_commit(h, h->ids, n, n, s))) return rc;
   if (do_insert) h->n_ins += static_cast<uint64_t>(n);
   if (do_score) {
     if ((rc = score_tail(h, n, alpha, scores_host ? h->scstage : nullptr, h->sums, flags_host ? h->flstage : nullptr,
@@ -1381,6 +1465,7 @@ int ace_server_destroy(ace_server s) {
 int ace_delete(ace_handle h, const void* X_dev, int64_t n, int dtype, void* stream) {
   int rc = check_x(h, X_dev, n, dtype);
   if (rc) return rc;
+  if (h->ring) return fail(ACE_ERR_ARG, "a windowed detector removes its oldest points itself");
   if (n == 0) return ACE_OK;
   if (static_cast<uint64_t>(n) > h->n_ins)
     return fail(ACE_ERR_ARG, "deleting %lld points from a detector holding %llu", static_cast<long long>(n),
@@ -1440,6 +1525,7 @@ int ace_batch_insert_score(const ace_handle* dets, int count, const void* const*
     ace_handle h = dets[g];
     if (int rc = check_x(h, X_dev[g], n[g], dtype)) return rc;
     if ((h->K <= 16) != id16) return fail(ACE_ERR_ARG, "a batch mixes K <= 16 and K > 16");
+    if (h->ring) return fail(ACE_ERR_ARG, "detector %d has a window (not supported in batches)", g);
     if (h->n_ins + static_cast<uint64_t>(n[g]) > 0xFFFFFFFFull)
       return fail(ACE_ERR_OVERFLOW, "detector %d: inserting %lld points would allow a count above 2^32-1", g,
                   static_cast<long long>(n[g]));
@@ -1631,6 +1717,7 @@ int ace_save_size(ace_handle h, size_t* bytes) {
 
 int ace_save(ace_handle h, void* buf, size_t cap, void* stream) {
   if (!h || !buf) return fail(ACE_ERR_ARG, "NULL argument");
+  if (h->ring) return fail(ACE_ERR_ARG, "checkpoints of windowed detectors are not supported");
   const size_t need = blob_bytes(h->d, h->K, h->L);
   if (cap < need) return fail(ACE_ERR_ARG, "buffer of %zu bytes; the checkpoint needs %zu", cap, need);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1836,6 +1923,7 @@ extern "C" int ace_insert_score_noalloc(ace_handle h, const void* X_dev, int64_t
   int rc = check_x(h, X_dev, n, dtype);
   if (rc) return rc;
   if (!std::isfinite(alpha)) return fail(ACE_ERR_ARG, "alpha must be finite");
+  if (h->ring) return fail(ACE_ERR_ARG, "a windowed detector is not supported by the allocation-free entry point");
   if (h->n_ins + static_cast<uint64_t>(n) > 0xFFFFFFFFull)
     return fail(ACE_ERR_OVERFLOW, "inserting %lld points would allow a count above 2^32-1", static_cast<long long>(n));
   const size_t ids_bytes = (static_cast<size_t>(n) * h->L * id_bytes(h) + 255) & ~static_cast<size_t>(255);

@@ -92,6 +92,8 @@ cudaError_t launch_flags_batched(const ScoreJob* jobs_dev, const long long* star
                                  cudaStream_t s);
 cudaError_t launch_delete_check(const uint32_t* hist, const uint32_t* counts, long long total, unsigned int* flag,
                                 int num_sms, cudaStream_t s);
+cudaError_t launch_window_evict(const void* ring, int ids16, long long cap, long long start, long long m, int K, int L,
+                                uint32_t* counts, int num_sms, cudaStream_t s);
 cudaError_t launch_delete_apply(const uint32_t* hist, uint32_t* counts, long long total, int num_sms, cudaStream_t s);
 
 // Measurement hook: D = A . B^T as kd/16 tcgen05 MMAs of 128 x N x 16 (tc_probe.cu).

@@ -323,7 +323,37 @@ __global__ void __launch_bounds__(256) delete_apply_kernel(const uint32_t* __res
     counts[t] -= hist[t];
 }
 
+// Sliding-window eviction (§3.4.1 deletion of the oldest points): for the m oldest points of
+// the ring [L][cap] (starting at slot `start`, wrapping), A_j[id] -= 1 for every table j.
+template <typename IdT>
+__global__ void __launch_bounds__(256) window_evict_kernel(const IdT* __restrict__ ring, long long cap, long long start,
+                                                           long long m, int K, int L, uint32_t* __restrict__ counts) {
+  const long long total = m * L;
+  for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int j = static_cast<int>(e / m);
+    long long p = start + (e - static_cast<long long>(j) * m);
+    if (p >= cap) p -= cap;
+    // (16-bit ids of the tensor-core insert path may carry the deferred-table tag, bit 15 > K)
+    const uint32_t id = static_cast<uint32_t>(ring[static_cast<size_t>(j) * cap + p]) & ((1u << K) - 1u);
+    atomicSub(counts + (static_cast<size_t>(j) << K) + id, 1u);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_window_evict(const void* ring, int ids16, long long cap, long long start, long long m, int K, int L,
+                                uint32_t* counts, int num_sms, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  const long long blocks = std::min<long long>((m * L + 255) / 256, static_cast<long long>(num_sms) * 8);
+  if (ids16)
+    window_evict_kernel<uint16_t><<<static_cast<unsigned>(blocks), 256, 0, s>>>(static_cast<const uint16_t*>(ring), cap,
+                                                                                start, m, K, L, counts);
+  else
+    window_evict_kernel<uint32_t><<<static_cast<unsigned>(blocks), 256, 0, s>>>(static_cast<const uint32_t*>(ring), cap,
+                                                                                start, m, K, L, counts);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_score_batched(const ScoreJob* jobs_dev, const long long* start_dev, int ndet, bool id16, int num_sms,
                                  cudaStream_t s) {

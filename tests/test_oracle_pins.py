@@ -424,3 +424,39 @@ def test_nonfinite_inputs_follow_binary64_semantics():
     bits = ((ids[1][:, None] >> np.arange(4, dtype=np.uint32)) & 1).ravel()
     expect = (W[0] > 0).astype(np.uint32)  # inf * w has the sign of w (w != 0)
     assert np.array_equal(bits, expect)
+
+
+def test_window_hand_example():
+    """Sliding window of two points over the hand example, one point at a time: counts, Q and
+    mu_ins after each insert equal the hand-counted values (tests/golden/hand_example_window.json)."""
+    g = _load("hand_example.json")
+    gw = _load("hand_example_window.json")
+    W = np.array(g["W_columns"], dtype=np.float32).T.copy()
+    X = np.array(g["X"], dtype=np.float32)
+    det = oracle.WindowDetector(3, 2, 2, window=gw["window"], W=W)
+    for i in range(4):
+        det.insert(X[i:i + 1])
+        st = det.stats()
+        assert det.counts.tolist() == gw["counts_after"][i]
+        assert st["n_ins"] == gw["held_after"][i] and st["Q"] == gw["Q_after"][i]
+        assert st["mu_ins"] == gw["mu_ins_after"][i]
+
+
+def test_window_equals_plain_detector_on_the_last_points():
+    """After any sequence of batches, a window detector's arrays equal those of a plain
+    detector fed only the last `window` points (a path through insertion alone)."""
+    rng = np.random.default_rng(8)
+    d, K, L, win = 12, 5, 6, 1000
+    W = rng.standard_normal((d, K * L)).astype(np.float32)
+    det = oracle.WindowDetector(d, K, L, window=win, W=W)
+    seen = []
+    for n in (300, 700, 1, 999, 1000, 250, 5):
+        X = rng.standard_normal((n, d)).astype(np.float32)
+        det.insert(X)
+        seen.append(X)
+        last = np.concatenate(seen)[-win:]
+        plain = oracle.Detector(d, K, L, W=W)
+        plain.insert(last)
+        assert np.array_equal(det.counts, plain.counts) and det.n_ins == last.shape[0]
+    with pytest.raises(ValueError):
+        det.insert(rng.standard_normal((win + 1, d)).astype(np.float32))
