@@ -106,6 +106,7 @@ struct ace_detector {
   // streaming tensor-core path (large d, bfloat16 input; hash_gemm.cu)
   bool gemm_ok = false;
   ace::GemmArgs gm{};           // constant part of the launch
+  unsigned int gemm_calls = 0;  // tags the deferred entries of each call
   uint16_t* gimg = nullptr;     // [2 klp][dp] bfloat16 image of W' (hi rows, then lo rows)
   float* gprof = nullptr;       // [2][dp/16] prefix and block norm maxima of the hi image
   float* gcolf = nullptr;       // [klp] image column norms (single-product image only)
@@ -846,8 +847,10 @@ int run_gemm(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_inser
   const long long grid = std::min(static_cast<long long>(h->num_sms), ntiles);
   const size_t cap = static_cast<size_t>(a.n) * 4 + static_cast<size_t>(grid) * 4096;
   void* p = h->defer;
+  const size_t had = h->defer_bytes;
   if (int rc = grow(&p, &h->defer_bytes, cap * 8, s, "deferred list")) return rc;
   h->defer = static_cast<unsigned long long*>(p);
+  if (h->defer_bytes != had) ACE_CUDA(cudaMemsetAsync(h->defer, 0, h->defer_bytes, s));  // no stale written flags
   ace::GemmArgs g = h->gm;
   g.X = a.X;
   g.n = a.n;
@@ -859,6 +862,9 @@ int run_gemm(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_inser
   g.proj = a.proj;
   g.defer = h->defer;
   g.seg_cap = h->defer_bytes / 8 / static_cast<size_t>(grid);
+  // the kernel's own recheck warps resolve the deferred entries while the tile's rows are in L2
+  g.inline_rc = proj ? 0 : 1;
+  g.call_tag = h->gemm_calls++;
   alignas(128) CUtensorMap tmx;
   if (int rc = encode_bf16_map(&tmx, a.X, static_cast<uint64_t>(h->d), static_cast<uint64_t>(a.n), ace::kGemmBM))
     return rc;
@@ -873,11 +879,11 @@ int run_gemm(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_inser
   }
   if (e != cudaSuccess) return cuda_fail(e, "streaming tensor-core hash kernel launch");
   if (proj) return ACE_OK;
-  {
+  if (!g.inline_rc) {
     PhaseScope ps(h, ACE_PHASE_RECHECK, s);
     e = ace::launch_recheck_cols(g, static_cast<int>(grid), h->num_sms, s);
+    if (e != cudaSuccess) return cuda_fail(e, "column recheck kernel launch");
   }
-  if (e != cudaSuccess) return cuda_fail(e, "column recheck kernel launch");
   if (insert && tc_insert) {
     PhaseScope ps(h, ACE_PHASE_INSERT, s);
     e = ace::launch_insert_from_ids(ids, h->K <= 16, a.ld, a.n, h->K, h->L, h->counts, h->num_sms, s);

@@ -15,7 +15,8 @@ constexpr int kGemmBN = 256;     // image columns per unit = MMA N
 constexpr int kGemmBK = 64;      // d per k-block: one 128-byte swizzle atom of bfloat16
 constexpr int kGemmStages = 4;   // shared-memory ring of (X k-block, image k-block) pairs
 
-// Deferred (point, column) entry: point << 17 | column << 1 | the bit the tensor cores stored.
+// Deferred (point, column) entry: point << 17 | column << 1 | the bit the tensor cores stored
+// (plus, with the in-kernel recheck, a written flag and the call's tag in the top bits).
 constexpr int kGemmEntryShift = 17;
 
 struct GemmArgs {
@@ -52,6 +53,8 @@ struct GemmArgs {
   unsigned int* defer_counts; // entries per segment (written by each CTA at exit)
   unsigned long long seg_cap;
   int smem_bytes;
+  int inline_rc;              // 1: the kernel's own recheck warps resolve the deferred entries
+  unsigned int call_tag;      // distinguishes this call's entries from a previous call's
 };
 
 // Launches the hash kernel; tmX and tmW are CUtensorMap objects (128-byte aligned, 128 bytes)

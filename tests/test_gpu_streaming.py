@@ -343,3 +343,28 @@ def test_highdim_full_size_sampled():
     ref.n_ins = n
     _, _, ref_fl = ref._score_ids(ids, 1.0)
     assert np.array_equal(fl.cpu().numpy(), ref_fl)
+
+
+def test_nonfinite_rows_at_high_d():
+    """d = 1024: a batch mixing ordinary rows with rows holding NaN or infinities, and rows of
+    one tiny coordinate (squared norm below the engine's floor): every column of such a row is
+    resolved by the exact tiers; ids equal the binary64 definition."""
+    d, K, L, n = 1024, 16, 8, 1500
+    rng = np.random.default_rng(17)
+    X = rng.standard_normal((n, d)).astype(np.float32) / 32
+    X[::50, 3] = np.nan
+    X[7::50, 11] = np.inf
+    X[9::50, 12] = -np.inf
+    X[11::50, 40], X[11::50, 41] = np.inf, -np.inf
+    X[13::50] = 0.0
+    X[13::50, 5] = 2.0**-40
+    Xb = workloads.to_bf16_bits(np.nan_to_num(X, nan=0.0, posinf=0.0, neginf=0.0))
+    Xb[::50, 3] = 0x7FC0
+    Xb[7::50, 11], Xb[9::50, 12] = 0x7F80, 0xFF80
+    Xb[11::50, 40], Xb[11::50, 41] = 0x7F80, 0xFF80
+    det, ref = _pair(d, K, L, seed=8)
+    Xd = _dev(Xb)
+    assert np.array_equal(ace.u32(det.hash(Xd)), ref.hash(Xb))
+    _compare(det.insert_score(Xd, 1.0), ref.insert_score(Xb, 1.0))
+    assert np.array_equal(det.counts(), ref.counts)
+    assert det.stats()["nonfinite_points"] == 4 * n // 50 and det.stats()["status"] == 0
