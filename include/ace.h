@@ -133,6 +133,19 @@ int ace_destroy(ace_handle h);
 /* Zeroes the arrays and every running statistic; keeps W.  Asynchronous on `stream`. */
 int ace_reset(ace_handle h, void* stream);
 
+/*
+ * ace_set_graph — graph replay for repeated calls (small batches are bound by launch
+ * latency): with enable = 1, an ace_score or ace_insert_score call whose arguments (X pointer,
+ * n, dtype, alpha, output pointers, stream, engine) equal the previous call's reuses a CUDA
+ * graph of that call's kernels: the first call with new arguments runs directly, the second
+ * captures its launches, later ones replay them.  Results are those of direct calls (the
+ * graph reads X and writes the outputs at replay time; n_ins and the overflow check are kept
+ * on the host per call).  Not used while the timing hook is on or a window is set.  The
+ * capture uses the caller's stream, which must not be capturing already.  No counterpart in
+ * the paper (an execution detail).  Errors: ACE_ERR_ARG.
+ */
+int ace_set_graph(ace_handle h, int enable);
+
 /* Selects the projection engine (ACE_PROJ_*).  Results do not depend on it. */
 int ace_set_precision(ace_handle h, int precision);
 

@@ -28,7 +28,7 @@ EXPORTS = [
     "ace_batch_insert_score", "ace_server_create", "ace_server_submit", "ace_server_wait", "ace_server_drain", "ace_server_destroy", "ace_stats",
     "ace_get_counts", "ace_get_projection", "ace_get_shape", "ace_last_error", "ace_version",
     "ace_profile_enable", "ace_profile_phases", "ace_profile_read", "ace_insert_score_noalloc",
-    "ace_tc_probe", "ace_save_size", "ace_save", "ace_load", "ace_window_enable",
+    "ace_tc_probe", "ace_save_size", "ace_save", "ace_load", "ace_window_enable", "ace_set_graph",
 ]
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 PHASES = ("hash", "score", "flags", "other", "recheck", "insert")
@@ -104,6 +104,7 @@ def load_library(path: str = LIB_PATH):
             "ace_profile_read": ([H, ctypes.POINTER(ace_profile_t)], i32),
             "ace_tc_probe": ([P, P, i32, i32, P], i32),
             "ace_window_enable": ([H, i64], i32),
+            "ace_set_graph": ([H, i32], i32),
             "ace_save_size": ([H, ctypes.POINTER(ctypes.c_size_t)], i32),
             "ace_save": ([H, P, ctypes.c_size_t, P], i32),
             "ace_load": ([P, ctypes.c_size_t, ctypes.POINTER(H)], i32),
@@ -321,6 +322,10 @@ class Detector:
         _check(load_library().ace_profile_read(self._h, ctypes.byref(p)))
         return {name: {"launches": int(p.launches[i]), "ms": float(p.ms[i]), "timed": int(p.timed[i])}
                 for i, name in enumerate(PHASES)}
+
+    def set_graph(self, enable: bool = True):
+        """Replay a captured CUDA graph for repeated score / insert_score calls (ace_set_graph)."""
+        _check(load_library().ace_set_graph(self._h, 1 if enable else 0))
 
     def window(self, points: int):
         """Sliding window over the last `points` inserted points (ace_window_enable; 0: off)."""

@@ -106,11 +106,33 @@ struct ace_detector {
   // streaming tensor-core path (large d, bfloat16 input; hash_gemm.cu)
   bool gemm_ok = false;
   ace::GemmArgs gm{};           // constant part of the launch
-  unsigned int gemm_calls = 0;  // tags the deferred entries of each call
   uint16_t* gimg = nullptr;     // [2 klp][dp] bfloat16 image of W' (hi rows, then lo rows)
   float* gprof = nullptr;       // [2][dp/16] prefix and block norm maxima of the hi image
   float* gcolf = nullptr;       // [klp] image column norms (single-product image only)
+  uint16_t* gwt16 = nullptr;    // [KL][d] bfloat16 W, columns contiguous (single-product only)
   CUtensorMap tm_img{};         // TMA description of gimg
+  // graph replay (ace_set_graph): the launches of a repeated score / insert_score call are
+  // captured once and replayed while its arguments and buffers stay the same
+  struct GraphKey {
+    const void* X = nullptr;
+    long long n = -1;
+    int dtype = -1, precision = -2;
+    double alpha = 0.0;
+    const void *sc = nullptr, *su = nullptr, *fl = nullptr, *ids = nullptr, *sums = nullptr, *defer = nullptr;
+    cudaStream_t s = nullptr;
+    bool insert = false;
+    bool operator==(const GraphKey& o) const {
+      return X == o.X && n == o.n && dtype == o.dtype && precision == o.precision && alpha == o.alpha && sc == o.sc &&
+             su == o.su && fl == o.fl && ids == o.ids && sums == o.sums && defer == o.defer && s == o.s &&
+             insert == o.insert;
+    }
+  };
+  bool graph_on = false;
+  GraphKey gkey{};
+  bool gseen = false;                   // the key's call ran once uncaptured (buffers sized)
+  cudaGraphExec_t gexec = nullptr;
+  uint64_t glaunch[ACE_NPHASE] = {};    // kernels the captured graph launches, per phase
+  int gprec = ACE_PROJ_FP32, gprod = 0; // engine the captured call used
   // profiling hook
   bool prof = false;
   unsigned prof_mask = ~0u;  // phases bracketed while profiling
@@ -158,6 +180,8 @@ struct PhaseScope {
 size_t count_elems(const ace_detector* h) { return (static_cast<size_t>(1) << h->K) * static_cast<size_t>(h->L); }
 
 void free_all(ace_detector* h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  h->gexec = nullptr;
   if (h->ev_hashed) cudaEventDestroy(h->ev_hashed);
   if (h->ev_resolved) cudaEventDestroy(h->ev_resolved);
   if (h->rstream) cudaStreamDestroy(h->rstream);
@@ -173,6 +197,7 @@ void free_all(ace_detector* h) {
   cudaFree(h->gimg);
   cudaFree(h->gprof);
   cudaFree(h->gcolf);
+  cudaFree(h->gwt16);
   cudaFree(h->defer);
   cudaFree(h->defer_counts);
   cudaFree(h->wpad);
@@ -566,7 +591,15 @@ int plan_gemm(ace_detector* h) {
     return cuda_fail(e, "copy norm profile");
   cudaFree(h->gcolf);
   h->gcolf = nullptr;
+  cudaFree(h->gwt16);
+  h->gwt16 = nullptr;
   if (one) {
+    std::vector<uint16_t> wt16(static_cast<size_t>(KL) * d);
+    for (int c = 0; c < KL; ++c)
+      for (int i = 0; i < d; ++i) wt16[static_cast<size_t>(c) * d + i] = bf16_rn(h->Wh[static_cast<size_t>(i) * KL + c]);
+    if ((e = cudaMalloc(&h->gwt16, wt16.size() * 2)) != cudaSuccess) return cuda_fail(e, "cudaMalloc bfloat16 W");
+    if ((e = cudaMemcpy(h->gwt16, wt16.data(), wt16.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cuda_fail(e, "copy bfloat16 W");
     if ((e = cudaMalloc(&h->gcolf, colf.size() * sizeof(float))) != cudaSuccess) return cuda_fail(e, "cudaMalloc column norms");
     if ((e = cudaMemcpy(h->gcolf, colf.data(), colf.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
       return cuda_fail(e, "copy column norms");
@@ -607,6 +640,7 @@ int plan_gemm(ace_detector* h) {
   g.S = S;
   g.wprof = h->gprof;
   g.colf = h->gcolf;
+  g.Wt16 = h->gwt16;
   g.tau_abs = static_cast<float>(2.0 * dp * std::ldexp(1.0, -125));
   const double g32 = d * u32 / (1.0 - d * u32);
   g.xfac = std::nextafter(static_cast<float>(1.0 + 2.0 * g32 + std::ldexp(1.0, -20)), FLT_MAX);
@@ -847,10 +881,8 @@ int run_gemm(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_inser
   const long long grid = std::min(static_cast<long long>(h->num_sms), ntiles);
   const size_t cap = static_cast<size_t>(a.n) * 4 + static_cast<size_t>(grid) * 4096;
   void* p = h->defer;
-  const size_t had = h->defer_bytes;
   if (int rc = grow(&p, &h->defer_bytes, cap * 8, s, "deferred list")) return rc;
   h->defer = static_cast<unsigned long long*>(p);
-  if (h->defer_bytes != had) ACE_CUDA(cudaMemsetAsync(h->defer, 0, h->defer_bytes, s));  // no stale written flags
   ace::GemmArgs g = h->gm;
   g.X = a.X;
   g.n = a.n;
@@ -862,9 +894,6 @@ int run_gemm(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_inser
   g.proj = a.proj;
   g.defer = h->defer;
   g.seg_cap = h->defer_bytes / 8 / static_cast<size_t>(grid);
-  // the kernel's own recheck warps resolve the deferred entries while the tile's rows are in L2
-  g.inline_rc = proj ? 0 : 1;
-  g.call_tag = h->gemm_calls++;
   alignas(128) CUtensorMap tmx;
   if (int rc = encode_bf16_map(&tmx, a.X, static_cast<uint64_t>(h->d), static_cast<uint64_t>(a.n), ace::kGemmBM))
     return rc;
@@ -879,11 +908,11 @@ int run_gemm(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_inser
   }
   if (e != cudaSuccess) return cuda_fail(e, "streaming tensor-core hash kernel launch");
   if (proj) return ACE_OK;
-  if (!g.inline_rc) {
+  {
     PhaseScope ps(h, ACE_PHASE_RECHECK, s);
     e = ace::launch_recheck_cols(g, static_cast<int>(grid), h->num_sms, s);
-    if (e != cudaSuccess) return cuda_fail(e, "column recheck kernel launch");
   }
+  if (e != cudaSuccess) return cuda_fail(e, "column recheck kernel launch");
   if (insert && tc_insert) {
     PhaseScope ps(h, ACE_PHASE_INSERT, s);
     e = ace::launch_insert_from_ids(ids, h->K <= 16, a.ld, a.n, h->K, h->L, h->counts, h->num_sms, s);
@@ -988,8 +1017,91 @@ int score_tail(ace_handle h, long long n, double alpha, double* scores, uint32_t
   return ACE_OK;
 }
 
+int score_common_direct(ace_handle h, const void* X, long long n, int dtype, double alpha, double* scores,
+                        uint32_t* sums, uint8_t* flags, cudaStream_t s, bool insert);
+
+// score / insert_score with graph replay (ace_set_graph): the first call with a given set of
+// arguments runs directly (its buffers grow to size), the second captures its launches into a
+// CUDA graph, later ones replay it.  The host bookkeeping (n_ins, the overflow check) is
+// arithmetic on the arguments and runs on every call; nothing in the kernels depends on it.
 int score_common(ace_handle h, const void* X, long long n, int dtype, double alpha, double* scores, uint32_t* sums,
                  uint8_t* flags, cudaStream_t s, bool insert) {
+  if (!h || !h->graph_on || h->ring || h->prof || n <= 0)
+    return score_common_direct(h, X, n, dtype, alpha, scores, sums, flags, s, insert);
+  int rc = check_x(h, X, n, dtype);
+  if (rc) return rc;
+  if (!std::isfinite(alpha)) return fail(ACE_ERR_ARG, "alpha must be finite");
+  if (insert && h->n_ins + static_cast<uint64_t>(n) > 0xFFFFFFFFull)
+    return fail(ACE_ERR_OVERFLOW, "inserting %lld points would allow a count above 2^32-1", n);
+  ace_detector::GraphKey k;
+  k.X = X;
+  k.n = n;
+  k.dtype = dtype;
+  k.precision = h->precision;
+  k.alpha = alpha;
+  k.sc = scores;
+  k.su = sums;
+  k.fl = flags;
+  k.ids = h->ids;
+  k.sums = h->sums;
+  k.defer = h->defer;
+  k.s = s;
+  k.insert = insert;
+  if (h->gexec && k == h->gkey) {
+    ACE_CUDA(cudaGraphLaunch(h->gexec, s));
+    for (int p = 0; p < ACE_NPHASE; ++p) h->launches[p] += h->glaunch[p];
+    if (insert) h->n_ins += static_cast<uint64_t>(n);
+    h->last_precision = h->gprec;
+    h->last_products = h->gprod;
+    return ACE_OK;
+  }
+  if (!(h->gseen && k == h->gkey)) {  // first call with these arguments: run it directly
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    rc = score_common_direct(h, X, n, dtype, alpha, scores, sums, flags, s, insert);
+    k.ids = h->ids;  // the call may have grown the scratch
+    k.sums = h->sums;
+    k.defer = h->defer;
+    h->gkey = k;
+    h->gseen = rc == ACE_OK;
+    return rc;
+  }
+  // second call: capture (the buffers are already sized, so nothing allocates or synchronises)
+  uint64_t before[ACE_NPHASE];
+  for (int p = 0; p < ACE_NPHASE; ++p) before[p] = h->launches[p];
+  const uint64_t nins = h->n_ins;
+  ACE_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+  rc = score_common_direct(h, X, n, dtype, alpha, scores, sums, flags, s, insert);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  h->n_ins = nins;  // the captured call did not run: the replay below does
+  if (rc != ACE_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    h->gseen = false;
+    return rc != ACE_OK ? rc : cuda_fail(e, "graph capture");
+  }
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->gseen = false;
+    return cuda_fail(e, "graph instantiation");
+  }
+  h->gexec = ex;
+  for (int p = 0; p < ACE_NPHASE; ++p) {
+    h->glaunch[p] = h->launches[p] - before[p];
+    h->launches[p] = before[p];
+  }
+  h->gprec = h->last_precision;
+  h->gprod = h->last_products;
+  ACE_CUDA(cudaGraphLaunch(h->gexec, s));
+  for (int p = 0; p < ACE_NPHASE; ++p) h->launches[p] += h->glaunch[p];
+  if (insert) h->n_ins += static_cast<uint64_t>(n);
+  return ACE_OK;
+}
+
+int score_common_direct(ace_handle h, const void* X, long long n, int dtype, double alpha, double* scores,
+                        uint32_t* sums, uint8_t* flags, cudaStream_t s, bool insert) {
   int rc = check_x(h, X, n, dtype);
   if (rc) return rc;
   if (!std::isfinite(alpha)) return fail(ACE_ERR_ARG, "alpha must be finite");
@@ -1070,6 +1182,17 @@ int ace_window_enable(ace_handle h, int64_t window_points) {
     return fail(ACE_ERR_OOM, "window ring of %zu bytes: %s", bytes, cudaGetErrorString(e));
   }
   h->win_cap = window_points;
+  return ACE_OK;
+}
+
+int ace_set_graph(ace_handle h, int enable) {
+  if (!h) return fail(ACE_ERR_ARG, "handle is NULL");
+  h->graph_on = enable != 0;
+  if (!h->graph_on) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    h->gseen = false;
+  }
   return ACE_OK;
 }
 

@@ -15,8 +15,7 @@ constexpr int kGemmBN = 256;     // image columns per unit = MMA N
 constexpr int kGemmBK = 64;      // d per k-block: one 128-byte swizzle atom of bfloat16
 constexpr int kGemmStages = 4;   // shared-memory ring of (X k-block, image k-block) pairs
 
-// Deferred (point, column) entry: point << 17 | column << 1 | the bit the tensor cores stored
-// (plus, with the in-kernel recheck, a written flag and the call's tag in the top bits).
+// Deferred (point, column) entry: point << 17 | column << 1 | the bit the tensor cores stored.
 constexpr int kGemmEntryShift = 17;
 
 struct GemmArgs {
@@ -47,14 +46,14 @@ struct GemmArgs {
   DevStats* st;
   // exact resolution of the deferred columns (binary32 running bound, Dot2, binary64)
   const float* Wt;            // [KL][d] binary32 W, columns contiguous
+  const uint16_t* Wt16;       // [KL][d] the same as bfloat16 bits when every entry is a
+                              // bfloat16 value (half the recheck's W traffic), else null
   const float* cB32;          // [KL] the SIMT engine's a priori coefficient per column
   float xfac32, xabs32, babs32, dot2c, dot2abs, runc, run64, runabs;
   unsigned long long* defer;  // one segment of seg_cap entries per CTA
   unsigned int* defer_counts; // entries per segment (written by each CTA at exit)
   unsigned long long seg_cap;
   int smem_bytes;
-  int inline_rc;              // 1: the kernel's own recheck warps resolve the deferred entries
-  unsigned int call_tag;      // distinguishes this call's entries from a previous call's
 };
 
 // Launches the hash kernel; tmX and tmW are CUtensorMap objects (128-byte aligned, 128 bytes)

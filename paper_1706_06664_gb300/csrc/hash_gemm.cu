@@ -51,20 +51,13 @@ namespace {
 
 using namespace tc;
 
-constexpr int kThreads = 384;   // 12 warps
+constexpr int kThreads = 320;   // 10 warps
 constexpr int kBndWarps = 4;    // row-bound warps (2 .. 5): one thread per tile row
-constexpr int kEpi0Warp = 2 + kBndWarps;  // epilogue warps 6 .. 9
-constexpr int kRchWarp0 = kEpi0Warp + 4;  // in-kernel recheck warps 10 .. 11
 constexpr int kStages = kGemmStages;
 constexpr uint32_t kABytes = kGemmBM * kGemmBK * 2;  // 16 KB
 constexpr uint32_t kBBytes = kGemmBN * kGemmBK * 2;  // 32 KB
 constexpr uint32_t kStageBytes = kABytes + kBBytes;
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
-// Deferred entry: bit 63 = written (in-kernel recheck), bits 58-62 = the call's tag, bits
-// 17-47 = point (the streaming engine takes at most 2^31 - 1 points per call), bits 1-16 =
-// column, bit 0 = the bit the tensor cores stored.
-constexpr unsigned long long kEntryReady = 1ull << 63;
-constexpr unsigned long long kEntryPointMask = (1ull << 48) - 1ull;
 static_assert(kStages * kStageBytes + 4096 * 4 + 4096 + 1024 <= 227 * 1024, "shared memory");
 
 struct GSmem {
@@ -75,8 +68,6 @@ struct GSmem {
   uint32_t taddr;
   int abort;
   unsigned int ndef;
-  unsigned int claim;         // next segment entry an in-kernel recheck warp takes
-  unsigned int epi_exit;      // epilogue threads that have made their last reservation
   uint32_t bthr[2][kGemmBM];  // per tile slot and row: the row bound B (bit pattern)
   uint32_t bzero[2][kGemmBM]; // per tile slot and row: the row is exactly zero
 };
@@ -142,78 +133,6 @@ __device__ __noinline__ bool exact_col_bit(const GemmArgs& a, long long i, int c
   return sg != 0 ? sg > 0 : exact_bit<true>(a.X, i, d, a.Wt, c);
 }
 
-// Exact resolution of one deferred (point, column) entry by one warp: the lanes split the dot
-// product (lane l: 16-byte chunks l, l + 32, ... of the bfloat16 row and the matching binary32
-// W column), each as a binary32 FMA chain, join the sums by a butterfly of shuffles and keep the
-// binary32 sum R of the magnitudes of every rounded partial result.
-// u R / ((1 - u)(1 - gamma_(d+64))) plus underflow and the binary64 sum's own error bounds the
-// distance to the definition whatever the summation tree (the SIMT engine's warp recheck),
-// and the a priori gamma_d bound holds as well; the smaller decides.  What neither decides
-// goes to Dot2 and then to the binary64 definition (one lane).  A bit that differs from the
-// stored one is flipped in the id with an atomic XOR (other columns of the same id may be
-// resolved by other warps at the same time).
-template <typename IdT>
-__device__ __forceinline__ void resolve_col_entry(const GemmArgs& a, unsigned long long w, int lane) {
-  const int d = a.d, K = a.K, L = a.L, mode = a.mode;
-  const int nch = d / 8;
-  const long long i = static_cast<long long>((w & kEntryPointMask) >> kGemmEntryShift);
-  const int c = static_cast<int>((w >> 1) & 0xFFFFull);
-  const uint32_t tb = static_cast<uint32_t>(w & 1ull);
-  const uint4* xr = reinterpret_cast<const uint4*>(a.X) + i * nch;
-  const float4* wr = reinterpret_cast<const float4*>(a.Wt + static_cast<size_t>(c) * d);
-  float s = 0.f, run = 0.f, q = 0.f;
-  for (int ch = lane; ch < nch; ch += 32) {
-    const uint4 xv = __ldg(xr + ch);
-    const float4 w0 = __ldg(wr + 2 * ch), w1 = __ldg(wr + 2 * ch + 1);
-    const float xs[8] = {bf16_lo(xv.x), bf16_hi(xv.x), bf16_lo(xv.y), bf16_hi(xv.y),
-                         bf16_lo(xv.z), bf16_hi(xv.z), bf16_lo(xv.w), bf16_hi(xv.w)};
-    const float ws[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      s = fmaf(xs[k], ws[k], s);
-      run = __fadd_rn(run, fabsf(s));
-      q = fmaf(xs[k], xs[k], q);
-    }
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const float so = __shfl_xor_sync(0xFFFFFFFFu, s, off);
-    const float ro = __shfl_xor_sync(0xFFFFFFFFu, run, off);
-    q += __shfl_xor_sync(0xFFFFFFFFu, q, off);
-    s = __fadd_rn(s, so);
-    run = __fadd_rn(__fadd_rn(run, ro), fabsf(s));
-  }
-  const float xu = norm_upper(q, a.xfac32, a.xabs32);
-  const float cb = __ldg(a.cB32 + c);
-  const float brun = __fmaf_ru(a.runc, run, __fmaf_ru(__fmul_ru(a.run64, cb), xu, a.runabs));
-  const float bpri = fmaf(cb, xu, a.babs32);
-  bool bit;
-  if (fabsf(s) > fminf(brun, bpri)) {
-    bit = s > 0.f;
-  } else {
-    int sg = 0;
-    bool eb = false;
-    if (lane == 0) {
-      sg = dot2_sign<true>(a.X, i, d, a.Wt + static_cast<size_t>(c) * d, 1, a.dot2c, a.dot2abs);
-      eb = sg != 0 ? sg > 0 : exact_bit<true>(a.X, i, d, a.Wt, c);
-    }
-    bit = __shfl_sync(0xFFFFFFFFu, eb ? 1 : 0, 0) != 0;
-  }
-  if (lane == 0 && (bit ? 1u : 0u) != tb) {
-    const int j = c / K, k = c - j * K;
-    if (mode & kStoreIds) {
-      IdT* p = reinterpret_cast<IdT*>(a.ids) + static_cast<size_t>(j) * a.ld + i;
-      if constexpr (sizeof(IdT) == 2) {
-        const uintptr_t ad = reinterpret_cast<uintptr_t>(p);
-        atomicXor(reinterpret_cast<unsigned int*>(ad & ~static_cast<uintptr_t>(3)), (1u << k) << ((ad & 2u) * 8u));
-      } else {
-        atomicXor(reinterpret_cast<unsigned int*>(p), 1u << k);
-      }
-    }
-    if (mode & kStoreIdsRowMajor) atomicXor(a.ids_rm + i * L + j, 1u << k);
-  }
-}
-
 // KC > 0: specialised for K = KC (compile-time table offsets); KC = 0 handles any K.
 template <typename IdT, int KC, bool PROJ>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -235,8 +154,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (tid == 0) {
     S->abort = 0;
     S->ndef = 0;
-    S->claim = 0;
-    S->epi_exit = 0;
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&S->full[s], 1);
       mbar_init(&S->empty[s], 1 + kBndWarps);  // the MMA commit and each row-bound warp
@@ -255,7 +172,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     tmem_relinquish();
   }
   const bool colf_in_smem = a.colf && nunits * kGemmBN <= kColfMax;
-  const bool inline_rc = a.inline_rc != 0 && !PROJ;
   if (colf_in_smem)
     for (int c = tid; c < nunits * kGemmBN; c += kThreads) colf_s[c] = a.colf[c];
   tc_fence_before();
@@ -428,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-  } else if (warp < kRchWarp0) {
+  } else {
     // ------------------------------------------------------------------ epilogue
     const int q4 = warp & 3;
     const int r = q4 * 32 + lane;  // TMEM lane = tile row
@@ -442,7 +358,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned long long* const seg = a.defer + seg_cap * blockIdx.x;
     const uint32_t kmask = K >= 32 ? 0xFFFFFFFFu : (1u << K) - 1u;
     const float* const colf = colf_in_smem ? colf_s : a.colf;
-    const unsigned long long etag = static_cast<unsigned long long>(a.call_tag & 31u) << 58;
     long long u = 0;
     int ml = 0;
     bool ok = true;
@@ -535,20 +450,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           cnt += __popc(aw[g]);
         }
         // deferred (point, column) entries: one shared-memory atomic per row that has any; past
-        // the segment's capacity the bit is resolved here, before the ids are stored
-        unsigned long long idx0 = 0;
+        // the segment's capacity the bit is resolved here
         if (cnt) {
-          idx0 = atomicAdd(&S->ndef, cnt);
-          unsigned long long idx = idx0;
+          unsigned long long idx = atomicAdd(&S->ndef, cnt);
 #pragma unroll
           for (int g = 0; g < 8; ++g) {
             uint32_t mm = aw[g];
             while (mm) {
               const int k = __ffs(mm) - 1;
               mm &= mm - 1u;
-              if (idx >= seg_cap) {
-                const int c = c0 + 32 * g + k;
-                const uint32_t tb = (sw[g] >> k) & 1u;
+              const int c = c0 + 32 * g + k;
+              const uint32_t tb = (sw[g] >> k) & 1u;
+              if (idx < seg_cap) {
+                seg[idx] = (static_cast<unsigned long long>(i) << kGemmEntryShift) |
+                           (static_cast<unsigned long long>(c) << 1) | tb;
+              } else {
                 const uint32_t eb = exact_col_bit(a, i, c) ? 1u : 0u;
                 sw[g] ^= (eb ^ tb) << k;
               }
@@ -556,8 +472,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         }
+        if (!valid) continue;
         // bucket ids (Eq. 2): table t of the unit is bits [t K, t K + K)
-        if (valid) {
         if constexpr (KC == 16) {
 #pragma unroll
           for (int t = 0; t < 16; ++t) {
@@ -584,103 +500,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         }
-        }
-        // the entries go out after the ids they refer to (the in-kernel recheck flips id bits
-        // as soon as it sees an entry)
-        if (cnt) {
-          if (inline_rc) __threadfence();
-          unsigned long long idx = idx0;
-#pragma unroll
-          for (int g = 0; g < 8; ++g) {
-            uint32_t mm = aw[g];
-            while (mm) {
-              const int k = __ffs(mm) - 1;
-              mm &= mm - 1u;
-              if (idx < seg_cap) {
-                const int c = c0 + 32 * g + k;
-                const uint32_t tb = (sw[g] >> k) & 1u;  // unchanged: only overflowed bits were fixed
-                const unsigned long long e = (static_cast<unsigned long long>(i) << kGemmEntryShift) |
-                                             (static_cast<unsigned long long>(c) << 1) | tb;
-                if (inline_rc) {
-                  volatile unsigned long long* vs = seg + idx;
-                  *vs = e | etag | kEntryReady;
-                } else {
-                  seg[idx] = e;
-                }
-              }
-              ++idx;
-            }
-          }
-        }
       }
-    }
-    atomicAdd(&S->epi_exit, 1u);  // after this thread's last reservation
-  } else {
-    // ------------------------------------------------------------------ in-kernel recheck
-    // Two warps resolve the CTA's deferred entries while the kernel runs (the rows of the tile
-    // are still in L2): a warp claims the next entry index, waits until the epilogue has
-    // reserved and written it (bounded; progress resets the bound), and resolves it like
-    // recheck_cols_kernel.  They stop when every epilogue thread has made its last
-    // reservation and the claims have passed the last entry.
-    if (inline_rc && !PROJ) {
-      const unsigned long long* const seg = a.defer + a.seg_cap * blockIdx.x;
-      const unsigned long long etag = static_cast<unsigned long long>(a.call_tag & 31u) << 58;
-      unsigned long long nre = 0;
-      for (;;) {
-        int state = 0;  // 1: entry ready, 2: stop
-        unsigned int e = 0;
-        if (lane == 0) {
-          e = atomicAdd(&S->claim, 1u);
-          long long last = clock64();
-          unsigned int seen = 0xFFFFFFFFu;
-          while (state == 0) {
-            const unsigned int nd = *reinterpret_cast<volatile unsigned int*>(&S->ndef);
-            if (e < nd) {
-              if (e >= a.seg_cap) {
-                state = 3;  // resolved by the epilogue itself
-              } else {
-                const unsigned long long w = *reinterpret_cast<const volatile unsigned long long*>(seg + e);
-                if ((w & kEntryReady) && (w & (31ull << 58)) == etag) state = 1;
-              }
-            } else if (*reinterpret_cast<volatile unsigned int*>(&S->epi_exit) == 128u) {
-              if (e >= *reinterpret_cast<volatile unsigned int*>(&S->ndef)) state = 2;
-            }
-            if (state) break;
-            if (*reinterpret_cast<volatile int*>(&S->abort)) {
-              state = 2;
-              break;
-            }
-            if (nd != seen) {
-              seen = nd;
-              last = clock64();
-            } else if (clock64() - last > kWaitCycles) {
-              set_abort(S, a.st);
-              state = 2;
-              break;
-            }
-            __nanosleep(200);
-          }
-        }
-        state = __shfl_sync(0xFFFFFFFFu, state, 0);
-        e = __shfl_sync(0xFFFFFFFFu, e, 0);
-        if (state == 2) break;
-        if (state == 3) continue;
-        __threadfence();
-        const unsigned long long w = *reinterpret_cast<const volatile unsigned long long*>(seg + e);
-        __syncwarp();
-        if (lane == 0) *reinterpret_cast<volatile unsigned long long*>(const_cast<unsigned long long*>(seg) + e) = 0ull;
-        resolve_col_entry<IdT>(a, w, lane);
-        ++nre;
-      }
-      if (lane == 0 && nre) atomicAdd(&a.st->rechecks, nre);
     }
   }
 
   tc_fence_before();
   __syncthreads();
   if (tid == 0) {
-    a.defer_counts[blockIdx.x] =
-        inline_rc ? 0u : static_cast<unsigned int>(min(static_cast<unsigned long long>(S->ndef), a.seg_cap));
+    a.defer_counts[blockIdx.x] = static_cast<unsigned int>(min(static_cast<unsigned long long>(S->ndef), a.seg_cap));
     if (S->ndef && !(a.mode & kStoreProj)) atomicAdd(&a.st->deferred, static_cast<unsigned long long>(S->ndef));
   }
   if (warp == 1) {
@@ -689,9 +516,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// The deferred entries left to a separate pass (the streaming kernel resolves them itself
-// when the in-kernel recheck is on): warps spread over the per-CTA segments.
-template <typename IdT>
+// Exact resolution of the deferred (point, column) entries.  One warp per entry: the lanes
+// split the dot product (lane l: 16-byte chunks l, l + 32, ... of the bfloat16 row and the
+// matching binary32 W column), each as a binary32 FMA chain, join the sums by a butterfly of
+// shuffles and keep the binary32 sum R of the magnitudes of every rounded partial result.
+// u R / ((1 - u)(1 - gamma_(d+64))) plus underflow and the binary64 sum's own error bounds the
+// distance to the definition whatever the summation tree (the SIMT engine's warp recheck),
+// and the a priori gamma_d bound holds as well; the smaller decides.  What neither decides
+// goes to Dot2 and then to the binary64 definition (one lane).  A bit that differs from the
+// stored one is flipped in the id with an atomic XOR (other columns of the same id may be
+// resolved by other warps at the same time).
+template <typename IdT, bool W16>
 __global__ void __launch_bounds__(256) recheck_cols_kernel(const __grid_constant__ GemmArgs a, int nseg) {
   const int lane = threadIdx.x & 31;
   const unsigned nwarps = gridDim.x * (blockDim.x >> 5);
@@ -702,10 +537,85 @@ __global__ void __launch_bounds__(256) recheck_cols_kernel(const __grid_constant
   const unsigned lw = gw / static_cast<unsigned>(nseg);
   const unsigned long long cnt = a.defer_counts[seg];
   const unsigned long long* const list = a.defer + a.seg_cap * static_cast<unsigned long long>(seg);
+  const int d = a.d, K = a.K, L = a.L, mode = a.mode;
+  const int nch = d / 8;
+  const long long ld = a.ld;
   unsigned long long nre = 0;
   for (unsigned long long e = lw; e < cnt; e += per_seg) {
-    resolve_col_entry<IdT>(a, list[e], lane);
-    ++nre;
+    const unsigned long long w = list[e];
+    const long long i = static_cast<long long>(w >> kGemmEntryShift);
+    const int c = static_cast<int>((w >> 1) & 0xFFFFull);
+    const uint32_t tb = static_cast<uint32_t>(w & 1ull);
+    const uint4* xr = reinterpret_cast<const uint4*>(a.X) + i * nch;
+    const float4* wr = reinterpret_cast<const float4*>(a.Wt + static_cast<size_t>(c) * d);
+    const uint4* wr16 = reinterpret_cast<const uint4*>(a.Wt16) + static_cast<size_t>(c) * nch;
+    float s = 0.f, run = 0.f, q = 0.f;
+    for (int ch = lane; ch < nch; ch += 32) {
+      const uint4 xv = __ldg(xr + ch);
+      float ws[8];
+      if constexpr (W16) {  // bfloat16-valued W: the same binary32 values from half the bytes
+        const uint4 wv = __ldg(wr16 + ch);
+        const uint32_t u[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          ws[2 * e] = bf16_lo(u[e]);
+          ws[2 * e + 1] = bf16_hi(u[e]);
+        }
+      } else {
+        const float4 w0 = __ldg(wr + 2 * ch), w1 = __ldg(wr + 2 * ch + 1);
+        ws[0] = w0.x; ws[1] = w0.y; ws[2] = w0.z; ws[3] = w0.w;
+        ws[4] = w1.x; ws[5] = w1.y; ws[6] = w1.z; ws[7] = w1.w;
+      }
+      const float xs[8] = {bf16_lo(xv.x), bf16_hi(xv.x), bf16_lo(xv.y), bf16_hi(xv.y),
+                           bf16_lo(xv.z), bf16_hi(xv.z), bf16_lo(xv.w), bf16_hi(xv.w)};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        s = fmaf(xs[k], ws[k], s);
+        run = __fadd_rn(run, fabsf(s));
+        q = fmaf(xs[k], xs[k], q);
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float so = __shfl_xor_sync(0xFFFFFFFFu, s, off);
+      const float ro = __shfl_xor_sync(0xFFFFFFFFu, run, off);
+      q += __shfl_xor_sync(0xFFFFFFFFu, q, off);
+      s = __fadd_rn(s, so);
+      run = __fadd_rn(__fadd_rn(run, ro), fabsf(s));
+    }
+    const float xu = norm_upper(q, a.xfac32, a.xabs32);
+    const float cb = __ldg(a.cB32 + c);
+    const float brun = __fmaf_ru(a.runc, run, __fmaf_ru(__fmul_ru(a.run64, cb), xu, a.runabs));
+    const float bpri = fmaf(cb, xu, a.babs32);
+    bool bit;
+    if (fabsf(s) > fminf(brun, bpri)) {
+      bit = s > 0.f;
+    } else {
+      int sg = 0;
+      bool eb = false;
+      if (lane == 0) {
+        sg = dot2_sign<true>(a.X, i, d, a.Wt + static_cast<size_t>(c) * d, 1, a.dot2c, a.dot2abs);
+        eb = sg != 0 ? sg > 0 : exact_bit<true>(a.X, i, d, a.Wt, c);
+      }
+      bit = __shfl_sync(0xFFFFFFFFu, eb ? 1 : 0, 0) != 0;
+    }
+    if (lane == 0) {
+      ++nre;
+      if ((bit ? 1u : 0u) != tb) {
+        const int j = c / K, k = c - j * K;
+        if (mode & kStoreIds) {
+          IdT* p = reinterpret_cast<IdT*>(a.ids) + static_cast<size_t>(j) * ld + i;
+          if constexpr (sizeof(IdT) == 2) {
+            const uintptr_t ad = reinterpret_cast<uintptr_t>(p);
+            atomicXor(reinterpret_cast<unsigned int*>(ad & ~static_cast<uintptr_t>(3)),
+                      (1u << k) << ((ad & 2u) * 8u));
+          } else {
+            atomicXor(reinterpret_cast<unsigned int*>(p), 1u << k);
+          }
+        }
+        if (mode & kStoreIdsRowMajor) atomicXor(a.ids_rm + i * L + j, 1u << k);
+      }
+    }
   }
   if (lane == 0 && nre) atomicAdd(&a.st->rechecks, nre);
 }
@@ -742,7 +652,8 @@ cudaError_t launch_recheck_cols(const GemmArgs& a, int nseg, int num_sms, cudaSt
     kern<<<grid, 256, 0, s>>>(a, nseg);
     return cudaGetLastError();
   };
-  return a.K > 16 ? go(recheck_cols_kernel<uint32_t>) : go(recheck_cols_kernel<uint16_t>);
+  if (a.Wt16) return a.K > 16 ? go(recheck_cols_kernel<uint32_t, true>) : go(recheck_cols_kernel<uint16_t, true>);
+  return a.K > 16 ? go(recheck_cols_kernel<uint32_t, false>) : go(recheck_cols_kernel<uint16_t, false>);
 }
 
 }  // namespace ace
