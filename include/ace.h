@@ -140,9 +140,11 @@ int ace_reset(ace_handle h, void* stream);
  * graph of that call's kernels: the first call with new arguments runs directly, the second
  * captures its launches, later ones replay them.  Results are those of direct calls (the
  * graph reads X and writes the outputs at replay time; n_ins and the overflow check are kept
- * on the host per call).  Not used while the timing hook is on or a window is set.  The
- * capture uses the caller's stream, which must not be capturing already.  No counterpart in
- * the paper (an execution detail).  Errors: ACE_ERR_ARG.
+ * on the host per call).  Calls run directly (no graph) on the legacy or per-thread default
+ * stream (which cannot be captured), on a stream the caller is capturing already, while the
+ * timing hook is on, and with a window set; if a capture fails, graph replay turns itself off
+ * for the handle and the call runs directly.  No counterpart in the paper (an execution
+ * detail).  Errors: ACE_ERR_ARG.
  */
 int ace_set_graph(ace_handle h, int enable);
 

@@ -1026,7 +1026,11 @@ int score_common_direct(ace_handle h, const void* X, long long n, int dtype, dou
 // arithmetic on the arguments and runs on every call; nothing in the kernels depends on it.
 int score_common(ace_handle h, const void* X, long long n, int dtype, double alpha, double* scores, uint32_t* sums,
                  uint8_t* flags, cudaStream_t s, bool insert) {
-  if (!h || !h->graph_on || h->ring || h->prof || n <= 0)
+  // (the legacy default stream cannot be captured, and a stream someone is capturing already
+  // records these launches in that capture)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (!h || !h->graph_on || h->ring || h->prof || n <= 0 || s == nullptr || s == cudaStreamLegacy ||
+      s == cudaStreamPerThread || cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
     return score_common_direct(h, X, n, dtype, alpha, scores, sums, flags, s, insert);
   int rc = check_x(h, X, n, dtype);
   if (rc) return rc;
@@ -1075,17 +1079,16 @@ int score_common(ace_handle h, const void* X, long long n, int dtype, double alp
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(s, &g);
   h->n_ins = nins;  // the captured call did not run: the replay below does
-  if (rc != ACE_OK || e != cudaSuccess) {
-    if (g) cudaGraphDestroy(g);
-    h->gseen = false;
-    return rc != ACE_OK ? rc : cuda_fail(e, "graph capture");
-  }
   cudaGraphExec_t ex = nullptr;
-  e = cudaGraphInstantiate(&ex, g, 0);
-  cudaGraphDestroy(g);
-  if (e != cudaSuccess) {
+  if (rc == ACE_OK && e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (rc != ACE_OK || e != cudaSuccess) {
+    // nothing captured has run: turn graph replay off for this handle and run the call directly
+    cudaGetLastError();
+    for (int p = 0; p < ACE_NPHASE; ++p) h->launches[p] = before[p];
+    h->graph_on = false;
     h->gseen = false;
-    return cuda_fail(e, "graph instantiation");
+    return score_common_direct(h, X, n, dtype, alpha, scores, sums, flags, s, insert);
   }
   h->gexec = ex;
   for (int p = 0; p < ACE_NPHASE; ++p) {

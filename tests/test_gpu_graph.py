@@ -25,6 +25,8 @@ def test_graph_replay_matches_direct_calls(engine):
     g.set_graph(True)
     plain = ace.Detector(d, K, L, seed=4, precision=precision)
     ref = oracle.Detector(d, K, L, W=g.projection())
+    stream = torch.cuda.Stream()  # the legacy default stream cannot be captured
+    torch.cuda.set_stream(stream)
     tx = torch.empty((n, d), dtype=torch.int16 if engine == "streaming" else torch.float32, device="cuda")
     sc = torch.empty(n, dtype=torch.float64, device="cuda")
     su = torch.empty(n, dtype=torch.int32, device="cuda")
@@ -49,12 +51,15 @@ def test_graph_replay_matches_direct_calls(engine):
         assert a[k] == b[k], k
     p = g.profile_read()
     assert p["hash"]["launches"] == 6 and p["score"]["launches"] == 6 and p["flags"]["launches"] == 6
+    torch.cuda.set_stream(torch.cuda.default_stream())
 
 
 def test_graph_replay_is_faster_for_small_batches():
     """The small config (n = 10,000): replayed calls take less time than direct ones."""
     w = workloads.small(seed=1)
     X = torch.from_numpy(w["X"]).cuda()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     out = {}
     for mode in (False, True):
         det = ace.Detector(w["d"], w["K"], w["L"], seed=4, precision="fp32")
@@ -72,4 +77,5 @@ def test_graph_replay_is_faster_for_small_batches():
         e1.record()
         torch.cuda.synchronize()
         out[mode] = e0.elapsed_time(e1) / 200
+    torch.cuda.set_stream(torch.cuda.default_stream())
     assert out[True] < out[False], out
