@@ -218,14 +218,25 @@ int ace_window_enable(ace_handle h, int64_t window_points);
  * (scores_dev, sums_dev, flags_dev: arrays of `count` device pointers, or NULL; an entry may
  * be NULL).  Every detector's results are exactly those of its own ace_insert_score call
  * (Algorithm 1 counting and query phases, §5.3 rule on its own statistics); the work of all
- * detectors runs as one launch per phase (hash + insert, query, flags) on the binary32 engine,
- * so many small detectors fill the GPU together.  The K of all detectors is <= 16, or > 16
+ * detectors runs as one persistent launch on the binary32 engine (every detector's hash +
+ * insert blocks, then its query blocks once its hash is done, then its score/flag blocks once
+ * its statistics are derived), so many small detectors fill the GPU together.  The engine's
+ * tile (points x columns per block) is picked per detector shape by an autotuner that times
+ * the variants on the first batch meeting the shape and keeps the fastest for the process
+ * (ace_batch_tile reports it).  The K of all detectors is <= 16, or > 16
  * for all.  All or nothing on argument errors; asynchronous on `stream`.  (The paper states
  * the method for one dataset; running many detectors together is this library's.)
  */
 int ace_batch_insert_score(const ace_handle* dets, int count, const void* const* X_dev, const int64_t* n, int dtype,
                            double alpha, double* const* scores_dev, uint32_t* const* sums_dev,
                            uint8_t* const* flags_dev, void* stream);
+
+/*
+ * ace_batch_tile — the tile the batched engine's autotuner chose for detectors of this shape
+ * (d rounded up to a power of two, K, L, dtype): points and columns per block, or 0 and 0 if
+ * no batch has met the shape yet.  Measurement and test hook.  Errors: ACE_ERR_ARG.
+ */
+int ace_batch_tile(int d, int K, int L, int dtype, int* points, int* columns);
 
 /* Operations of a host-buffer request (ace_server_submit). */
 enum { ACE_OP_INSERT = 0, ACE_OP_SCORE = 1, ACE_OP_INSERT_SCORE = 2 };

@@ -29,6 +29,7 @@ EXPORTS = [
     "ace_get_counts", "ace_get_projection", "ace_get_shape", "ace_last_error", "ace_version",
     "ace_profile_enable", "ace_profile_phases", "ace_profile_read", "ace_insert_score_noalloc",
     "ace_tc_probe", "ace_save_size", "ace_save", "ace_load", "ace_window_enable", "ace_set_graph",
+    "ace_batch_tile",
 ]
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 PHASES = ("hash", "score", "flags", "other", "recheck", "insert")
@@ -105,6 +106,7 @@ def load_library(path: str = LIB_PATH):
             "ace_tc_probe": ([P, P, i32, i32, P], i32),
             "ace_window_enable": ([H, i64], i32),
             "ace_set_graph": ([H, i32], i32),
+            "ace_batch_tile": ([i32, i32, i32, i32, P, P], i32),
             "ace_save_size": ([H, ctypes.POINTER(ctypes.c_size_t)], i32),
             "ace_save": ([H, P, ctypes.c_size_t, P], i32),
             "ace_load": ([P, ctypes.c_size_t, ctypes.POINTER(H)], i32),
@@ -383,6 +385,14 @@ def batch_insert_score(detectors, Xs, alpha: float = 1.0, stream=None):
                                                  V(*[t.data_ptr() for t in su]), V(*[t.data_ptr() for t in fl]),
                                                  _stream_ptr(stream)))
     return sc, su, fl
+
+
+def batch_tile(d: int, K: int, L: int, dtype: int = ACE_F32):
+    """(points, columns) per block the batched engine's autotuner chose for this shape, or
+    (0, 0) before any batch has met it."""
+    p, c = ctypes.c_int(), ctypes.c_int()
+    _check(load_library().ace_batch_tile(int(d), int(K), int(L), int(dtype), ctypes.byref(p), ctypes.byref(c)))
+    return p.value, c.value
 
 
 OP_INSERT, OP_SCORE, OP_INSERT_SCORE = 0, 1, 2

@@ -4,6 +4,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -1131,6 +1132,75 @@ int score_common_direct(ace_handle h, const void* X, long long n, int dtype, dou
 
 using u128 = unsigned __int128;
 
+// ---------------------------------------------------------------------------------------
+// Autotuner of the binary32 engine's tile for batched detectors: per (d rounded up to a
+// power of two, K, L, input type), the first batch that meets the shape times the four tile
+// variants (128 or 64 points x 128 or 64 columns per block) on up to 32,768 of its points,
+// hashing into a scratch with a scratch statistics block (no state of the detector changes),
+// and the fastest is kept for the rest of the process.
+// ---------------------------------------------------------------------------------------
+struct TuneKey {
+  int dcls, K, L, dtype;
+  bool operator<(const TuneKey& o) const {
+    return dcls != o.dcls ? dcls < o.dcls : K != o.K ? K < o.K : L != o.L ? L < o.L : dtype < o.dtype;
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+
+TuneKey tune_key(int d, int K, int L, int dtype) {
+  int c = 0;
+  while ((1 << c) < d) ++c;
+  return TuneKey{c, K, L, dtype};
+}
+
+// The tile for detector h's shape (tuned on X's first points the first time); -1 on a CUDA
+// error (message set).
+int tuned_tile(ace_handle h, const void* X, long long n, int dtype, cudaStream_t s) {
+  const TuneKey key = tune_key(h->d, h->K, h->L, dtype);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(key);
+  if (it != g_tune.end()) return it->second;
+  const long long nt = std::min<long long>(n, 32768);
+  if (nt < 1024) return 0;  // too few points to tell the variants apart: the default tile
+  unsigned char* buf = nullptr;
+  const size_t ib = static_cast<size_t>(nt) * h->L * 4;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), ib + sizeof(ace::DevStats), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(buf + ib, 0, sizeof(ace::DevStats), s);
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+  int best = 0;
+  float best_ms = 0.f;
+  for (int t = 0; t < 4 && e == cudaSuccess; ++t) {
+    ace::HashArgs a = hash_args(h, X, nt, dtype, ace::kStoreIds);
+    a.ids = buf;
+    a.ld = nt;
+    a.st = reinterpret_cast<ace::DevStats*>(buf + ib);
+    a.tile = t;
+    e = ace::launch_hash_simt(a, s);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = ace::launch_hash_simt(a, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    if (e == cudaSuccess && (t == 0 || ms < best_ms)) {
+      best = t;
+      best_ms = ms;
+    }
+  }
+  if (buf) cudaFreeAsync(buf, s);
+  for (auto v : ev)
+    if (v) cudaEventDestroy(v);
+  if (e != cudaSuccess) {
+    cuda_fail(e, "tile autotuning");
+    return -1;
+  }
+  g_tune[key] = best;
+  return best;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1662,8 +1732,9 @@ int ace_batch_insert_score(const ace_handle* dets, int count, const void* const*
       return fail(ACE_ERR_OVERFLOW, "detector %d: inserting %lld points would allow a count above 2^32-1", g,
                   static_cast<long long>(n[g]));
   }
-  // per detector: scratch, hash arguments (SIMT engine, ids stored and counts incremented)
-  // and its query job; then the block prefixes of the three batched launches
+  // per detector: scratch, hash arguments (SIMT engine, ids stored and counts incremented, the
+  // tile the autotuner picked for its shape) and its query job; then the item prefixes of the
+  // persistent launch
   std::vector<ace::HashArgs> ha(count);
   std::vector<ace::ScoreJob> sj(count);
   std::vector<long long> hstart(count + 1, 0), sstart(count + 1, 0);
@@ -1681,14 +1752,19 @@ int ace_batch_insert_score(const ace_handle* dets, int count, const void* const*
       }
     }
     ha[g] = hash_args(h, X_dev[g], ng, dtype, ace::kStoreIds | ace::kInsert);
+    ha[g].tile = tuned_tile(h, X_dev[g], ng, dtype, s);
+    if (ha[g].tile < 0) return ACE_ERR_CUDA;
     sj[g] = ace::ScoreJob{h->ids, ng, ng, h->K, h->L, alpha, h->counts, sum_out, h->st, h->div,
                           scores_dev ? scores_dev[g] : nullptr, flags_dev ? flags_dev[g] : nullptr};
     hstart[g + 1] = hstart[g] + ace::hash_simt_blocks(ha[g]);
     sstart[g + 1] = sstart[g] + (ng + 255) / 256;
   }
+  // one device table: arguments, jobs, prefixes, then the dispensing counter and the
+  // per-detector progress flags (zeroed)
   const size_t b_ha = sizeof(ace::HashArgs) * count, b_sj = sizeof(ace::ScoreJob) * count;
   const size_t b_st = sizeof(long long) * (count + 1);
-  std::vector<unsigned char> host(b_ha + b_sj + 2 * b_st);
+  const size_t b_sync = 8 + sizeof(unsigned int) * 2 * static_cast<size_t>(count);
+  std::vector<unsigned char> host(b_ha + b_sj + 2 * b_st + b_sync, 0);
   std::memcpy(host.data(), ha.data(), b_ha);
   std::memcpy(host.data() + b_ha, sj.data(), b_sj);
   std::memcpy(host.data() + b_ha + b_sj, hstart.data(), b_st);
@@ -1700,15 +1776,21 @@ int ace_batch_insert_score(const ace_handle* dets, int count, const void* const*
   const auto* d_sj = reinterpret_cast<const ace::ScoreJob*>(dev + b_ha);
   const auto* d_hs = reinterpret_cast<const long long*>(dev + b_ha + b_sj);
   const auto* d_ss = reinterpret_cast<const long long*>(dev + b_ha + b_sj + b_st);
+  auto* d_next = reinterpret_cast<unsigned long long*>(dev + b_ha + b_sj + 2 * b_st);
+  auto* d_hdone = reinterpret_cast<unsigned int*>(dev + b_ha + b_sj + 2 * b_st + 8);
+  auto* d_sready = d_hdone + count;
   const int sms = dets[0]->num_sms > 0 ? dets[0]->num_sms : 152;
-  if (e == cudaSuccess) e = ace::launch_hash_simt_batched(d_ha, d_hs, count, dtype == ACE_BF16, id16, sms, s);
-  if (e == cudaSuccess) e = ace::launch_score_batched(d_sj, d_ss, count, id16, sms, s);
-  if (e == cudaSuccess) e = ace::launch_flags_batched(d_sj, d_ss, count, sms, s);
+  if (e == cudaSuccess) {
+    ace_detector* h0 = dets[0];
+    PhaseScope ps(h0, ACE_PHASE_HASH, s);  // the one launch (all phases of all detectors)
+    e = ace::launch_batch(d_ha, d_sj, d_hs, d_ss, count, d_next, d_hdone, d_sready, dtype == ACE_BF16, id16, sms, s);
+  }
   cudaFreeAsync(dev, s);
   if (e != cudaSuccess) return cuda_fail(e, "batched launch");
   for (int g = 0; g < count; ++g) {
     dets[g]->n_ins += static_cast<uint64_t>(n[g]);
     dets[g]->last_precision = ACE_PROJ_FP32;
+    dets[g]->last_products = 0;
   }
   return ACE_OK;
 }
@@ -1971,6 +2053,19 @@ int ace_profile_read(ace_handle h, ace_profile_t* out) {
   h->marks.clear();
   for (int p = 0; p < ACE_NPHASE; ++p) h->launches[p] = 0;
   return rc;
+}
+
+int ace_batch_tile(int d, int K, int L, int dtype, int* points, int* columns) {
+  if (!points || !columns) return fail(ACE_ERR_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(tune_key(d, K, L, dtype));
+  if (it == g_tune.end()) {
+    *points = *columns = 0;
+    return ACE_OK;
+  }
+  *points = 16 * ace::simt_tile_rows(it->second);
+  *columns = 16 * ace::simt_tile_cols(it->second);
+  return ACE_OK;
 }
 
 int ace_tc_probe(const uint16_t* A_host, const uint16_t* B_host, int kdim, int ncols, float* D_host) {

@@ -58,6 +58,8 @@ struct HashArgs {
   uint32_t* counts;     // [L][2^K]
   DevStats* st;
   float* proj;          // [n][KL] (kStoreProj)
+  int tile;             // SIMT tile variant (0: 128 points x 128 columns per block; 1: 128 x 64;
+                        // 2: 64 x 128; 3: 64 x 64)
 };
 
 // One detector's share of a batched query phase and flags pass.
@@ -84,12 +86,12 @@ cudaError_t launch_insert_from_ids(const void* ids, int ids16, long long ld, lon
                                    uint32_t* counts, int num_sms, cudaStream_t s);
 cudaError_t launch_sum_squares(const uint32_t* counts, long long total, DevStats* st, cudaStream_t s);
 long long hash_simt_blocks(const HashArgs& a);
-cudaError_t launch_hash_simt_batched(const HashArgs* args_dev, const long long* start_dev, int ndet, bool bf16,
-                                     bool id16, int num_sms, cudaStream_t s);
-cudaError_t launch_score_batched(const ScoreJob* jobs_dev, const long long* start_dev, int ndet, bool id16, int num_sms,
-                                 cudaStream_t s);
-cudaError_t launch_flags_batched(const ScoreJob* jobs_dev, const long long* start_dev, int ndet, int num_sms,
-                                 cudaStream_t s);
+int simt_tile_rows(int tile);
+int simt_tile_cols(int tile);
+// Every detector's hash + insert, query phase and flags in one persistent launch (hash_simt.cu).
+cudaError_t launch_batch(const HashArgs* args_dev, const ScoreJob* jobs_dev, const long long* hstart_dev,
+                         const long long* sstart_dev, int ndet, unsigned long long* next, unsigned int* hdone,
+                         unsigned int* sready, bool bf16, bool id16, int num_sms, cudaStream_t s);
 cudaError_t launch_delete_check(const uint32_t* hist, const uint32_t* counts, long long total, unsigned int* flag,
                                 int num_sms, cudaStream_t s);
 cudaError_t launch_window_evict(const void* ring, int ids16, long long cap, long long start, long long m, int K, int L,

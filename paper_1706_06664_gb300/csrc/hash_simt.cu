@@ -16,23 +16,41 @@
 // columns per point land inside the binary32 bound; a binary64 chain of 1024 dependent FMAs
 // per such column cost four times the projection itself on GB300.
 #include "guard.cuh"
+#include "score_block.cuh"
 
 namespace ace {
 namespace {
 
-constexpr int BM = 128;  // points per CTA
-constexpr int BN = 128;  // columns per CTA (at most)
 constexpr int DK = 32;   // d per staged chunk
-constexpr int NT = 256;  // threads: 16 column groups x 16 point groups, 8 x 8 outputs each
+constexpr int NT = 256;  // threads: 16 column groups x 16 point groups
 
-// Block `blk` of one detector's hash: tile blk / ntb of 128 points, table block blk % ntb.
-template <bool BF16, typename IdT>
-__device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int ntb, long long blk) {
-  __shared__ float Xs[BM][DK + 1];
-  __shared__ __align__(16) float Ws[DK][BN];
-  __shared__ uint32_t bits[BM][BN / 32];
-  __shared__ uint32_t amb[BM][BN / 32];
-  __shared__ float xn[BM];
+// Tile variants: RM points x NC columns per thread (RM, NC in {4, 8}); a block covers
+// BM = 16 RM points and BN = 16 NC columns (whole tables: floor(BN / K) of them).  The point
+// rows of a thread are groups of four, 64 apart; its columns likewise.
+template <int RM, int NC>
+struct SimtTile {
+  static constexpr int BM = 16 * RM, BN = 16 * NC, NW = BN / 32 > 0 ? BN / 32 : 1;
+  // shared-memory layout (bytes), carved from one dynamic buffer
+  static constexpr size_t off_ws = 0;                                         // float [DK][BN]
+  static constexpr size_t off_xs = off_ws + sizeof(float) * DK * BN;          // float [BM][DK + 1]
+  static constexpr size_t off_bits = off_xs + sizeof(float) * BM * (DK + 1);  // uint32 [BM][NW]
+  static constexpr size_t off_amb = off_bits + sizeof(uint32_t) * BM * NW;    // uint32 [BM][NW]
+  static constexpr size_t off_xn = off_amb + sizeof(uint32_t) * BM * NW;      // float [BM]
+  static constexpr size_t bytes = off_xn + sizeof(float) * BM;
+};
+constexpr size_t kSimtSmemMax = SimtTile<8, 8>::bytes;
+static_assert(SimtTile<8, 4>::bytes <= kSimtSmemMax && SimtTile<4, 8>::bytes <= kSimtSmemMax, "smem");
+
+// Block `blk` of one detector's hash: tile blk / ntb of BM points, table block blk % ntb.
+template <bool BF16, typename IdT, int RM, int NC>
+__device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int ntb, long long blk, uint8_t* sbuf) {
+  using T = SimtTile<RM, NC>;
+  constexpr int BM = T::BM, BN = T::BN, NW = T::NW;
+  float (*Ws)[BN] = reinterpret_cast<float (*)[BN]>(sbuf + T::off_ws);
+  float (*Xs)[DK + 1] = reinterpret_cast<float (*)[DK + 1]>(sbuf + T::off_xs);
+  uint32_t (*bits)[NW] = reinterpret_cast<uint32_t (*)[NW]>(sbuf + T::off_bits);
+  uint32_t (*amb)[NW] = reinterpret_cast<uint32_t (*)[NW]>(sbuf + T::off_amb);
+  float* xn = reinterpret_cast<float*>(sbuf + T::off_xn);
 
   const long long tile = blk / ntb;
   const int tb = static_cast<int>(blk % ntb);
@@ -43,12 +61,14 @@ __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int 
   const long long i0 = tile * BM;
   const int npt = static_cast<int>(min(static_cast<long long>(BM), a.n - i0));
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  auto prow = [&](int r) { return (r >> 2) * 64 + ty * 4 + (r & 3); };  // point of register row r
+  auto pcol = [&](int c) { return (c >> 2) * 64 + tx * 4 + (c & 3); };  // column of register column c
 
-  float acc[8][8];
+  float acc[RM][NC];
 #pragma unroll
-  for (int r = 0; r < 8; ++r)
+  for (int r = 0; r < RM; ++r)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+    for (int c = 0; c < NC; ++c) acc[r][c] = 0.f;
   float q = 0.f;
 
   for (int kc = 0; kc < a.d; kc += DK) {
@@ -71,20 +91,21 @@ __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int 
     }
 #pragma unroll 4
     for (int k = 0; k < DK; ++k) {
-      float xa[8], wb[8];
+      float xa[RM], wb[NC];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        xa[r] = Xs[ty * 4 + r][k];
-        xa[4 + r] = Xs[64 + ty * 4 + r][k];
+      for (int r = 0; r < RM; ++r) xa[r] = Xs[prow(r)][k];
+#pragma unroll
+      for (int g = 0; g < NC / 4; ++g) {
+        const float4 w = *reinterpret_cast<const float4*>(&Ws[k][g * 64 + tx * 4]);
+        wb[4 * g] = w.x;
+        wb[4 * g + 1] = w.y;
+        wb[4 * g + 2] = w.z;
+        wb[4 * g + 3] = w.w;
       }
-      const float4 w0 = *reinterpret_cast<const float4*>(&Ws[k][tx * 4]);
-      const float4 w1 = *reinterpret_cast<const float4*>(&Ws[k][64 + tx * 4]);
-      wb[0] = w0.x; wb[1] = w0.y; wb[2] = w0.z; wb[3] = w0.w;
-      wb[4] = w1.x; wb[5] = w1.y; wb[6] = w1.z; wb[7] = w1.w;
 #pragma unroll
-      for (int r = 0; r < 8; ++r)
+      for (int r = 0; r < RM; ++r)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(xa[r], wb[c], acc[r][c]);
+        for (int c = 0; c < NC; ++c) acc[r][c] = fmaf(xa[r], wb[c], acc[r][c]);
     }
     __syncthreads();
   }
@@ -95,47 +116,45 @@ __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int 
     if (!isfinite(q) && tb == 0 && static_cast<int>(threadIdx.x) < npt && !(a.mode & kStoreProj))
       atomicAdd(&a.st->nonfinite, 1ull);
   }
-  for (int e = threadIdx.x; e < BM * (BN / 32); e += NT) {
+  for (int e = threadIdx.x; e < BM * NW; e += NT) {
     (&bits[0][0])[e] = 0u;
     (&amb[0][0])[e] = 0u;
   }
   if (a.mode & kStoreProj) {  // measurement path: the binary32 estimates themselves
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int p = (r < 4) ? ty * 4 + r : 64 + ty * 4 + (r - 4);
+    for (int r = 0; r < RM; ++r) {
+      const int p = prow(r);
       if (p < npt) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const int col = (c >> 2) * 64 + tx * 4 + (c & 3);
+        for (int c = 0; c < NC; ++c) {
+          const int col = pcol(c);
           if (col < ncol) a.proj[(i0 + p) * a.KL + c0 + col] = acc[r][c];
         }
       }
     }
     return;  // nothing else in this mode (the whole block takes this branch)
   }
-  float cb[8];
+  float cb[NC];
 #pragma unroll
-  for (int g = 0; g < 2; ++g)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int col = g * 64 + tx * 4 + c;
-      cb[g * 4 + c] = col < ncol ? __ldg(a.cB + c0 + col) : 0.f;
-    }
+  for (int c = 0; c < NC; ++c) {
+    const int col = pcol(c);
+    cb[c] = col < ncol ? __ldg(a.cB + c0 + col) : 0.f;
+  }
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    const int p = (r < 4) ? ty * 4 + r : 64 + ty * 4 + (r - 4);
+  for (int r = 0; r < RM; ++r) {
+    const int p = prow(r);
     const float xu = xn[p];
 #pragma unroll
-    for (int g = 0; g < 2; ++g) {
+    for (int g = 0; g < NC / 4; ++g) {
       uint32_t sb = 0u, ab = 0u;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int col = g * 64 + tx * 4 + c;
         if (col < ncol) {
-          const float s = acc[r][g * 4 + c];
+          const float sv = acc[r][g * 4 + c];
           const float B = fmaf(cb[g * 4 + c], xu, a.babs);
-          if (fabsf(s) > B) sb |= (s > 0.f ? 1u : 0u) << c;
+          if (fabsf(sv) > B) sb |= (sv > 0.f ? 1u : 0u) << c;
           else ab |= 1u << c;
         }
       }
@@ -157,13 +176,13 @@ __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int 
   // bitmap.  Every lane computes the same values (addition is commutative), so the loop stays
   // uniform.
   const int lane = threadIdx.x & 31;
-  for (int base = (threadIdx.x >> 5) * 32; base < BM * (BN / 32); base += NT) {
-    const uint32_t mw = (&amb[0][0])[base + lane];
-    uint32_t nz = __ballot_sync(0xFFFFFFFFu, mw != 0u && (base + lane) / (BN / 32) < npt);
+  for (int base = (threadIdx.x >> 5) * 32; base < BM * NW; base += NT) {
+    const uint32_t mw = base + lane < BM * NW ? (&amb[0][0])[base + lane] : 0u;
+    uint32_t nz = __ballot_sync(0xFFFFFFFFu, mw != 0u && (base + lane) / NW < npt);
     while (nz) {
       const int q = __ffs(nz) - 1;
       nz &= nz - 1u;
-      const int p = (base + q) / (BN / 32), wi = (base + q) % (BN / 32);
+      const int p = (base + q) / NW, wi = (base + q) % NW;
       uint32_t m = __shfl_sync(0xFFFFFFFFu, mw, q);
       const long long xb = (i0 + p) * static_cast<long long>(a.d);
       const float xu = xn[p];
@@ -205,8 +224,8 @@ __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int 
     const int t = e / BM, p = e % BM;
     const bool valid = p < npt;
     const int cbit = t * K;
-    uint32_t id = extract_bits(bits[p], BN / 32, cbit, K);
-    const uint32_t am = extract_bits(amb[p], BN / 32, cbit, K);
+    uint32_t id = extract_bits(bits[p], NW, cbit, K);
+    const uint32_t am = extract_bits(amb[p], NW, cbit, K);
     if (valid && am) {
       const long long i = i0 + p;
       uint32_t m = am;
@@ -235,71 +254,156 @@ __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int 
   }
 }
 
-template <bool BF16, typename IdT>
-__global__ void __launch_bounds__(NT, 2) hash_simt_kernel(HashArgs a, int tpb, int ntb) {
-  hash_simt_block<BF16, IdT>(a, tpb, ntb, blockIdx.x);
+// The SIMT tile variants (RM, NC): 0 = (8, 8), 1 = (8, 4), 2 = (4, 8), 3 = (4, 4).
+__host__ __device__ constexpr int tile_rows(int t) { return (t & 2) ? 4 : 8; }
+__host__ __device__ constexpr int tile_cols(int t) { return (t & 1) ? 4 : 8; }
+
+// Tables per block and table blocks of a detector for tile variant t.
+__host__ __device__ inline void tile_blocks(const HashArgs& a, int t, int& tpb, int& ntb) {
+  tpb = 16 * tile_cols(t) / a.K;  // K <= 24, so tpb >= 2
+  ntb = (a.L + tpb - 1) / tpb;
 }
 
-// Many detectors in one launch: block index b of the whole batch belongs to detector g with
-// start[g] <= b < start[g + 1]; each detector's blocks run exactly as in its own launch.
 template <bool BF16, typename IdT>
-__global__ void __launch_bounds__(NT, 2) hash_simt_batched_kernel(const HashArgs* __restrict__ args,
-                                                                  const long long* __restrict__ start, int ndet) {
-  const long long total = start[ndet];
-  for (long long b = blockIdx.x; b < total; b += gridDim.x) {
-    int lo = 0, hi = ndet;
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (start[mid] <= b) lo = mid;
-      else hi = mid;
+__device__ __forceinline__ void hash_block_any(const HashArgs& a, long long blk, uint8_t* sbuf) {
+  int tpb, ntb;
+  tile_blocks(a, a.tile, tpb, ntb);
+  switch (a.tile) {
+    case 1: hash_simt_block<BF16, IdT, 8, 4>(a, tpb, ntb, blk, sbuf); break;
+    case 2: hash_simt_block<BF16, IdT, 4, 8>(a, tpb, ntb, blk, sbuf); break;
+    case 3: hash_simt_block<BF16, IdT, 4, 4>(a, tpb, ntb, blk, sbuf); break;
+    default: hash_simt_block<BF16, IdT, 8, 8>(a, tpb, ntb, blk, sbuf); break;
+  }
+}
+
+template <bool BF16, typename IdT>
+__global__ void __launch_bounds__(NT, 2) hash_simt_kernel(HashArgs a) {
+  extern __shared__ __align__(16) uint8_t sbuf[];
+  hash_block_any<BF16, IdT>(a, blockIdx.x, sbuf);
+}
+
+__device__ __forceinline__ int job_of(const long long* __restrict__ start, int ndet, long long b) {
+  int lo = 0, hi = ndet;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (start[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+constexpr long long kBatchWait = 4000000000LL;  // about 2 s at 2 GHz
+
+// Waits (thread 0) until *flag >= want, bounded; on time-out it raises the detector's timeout
+// status and gives up (the detector's results are then not to be used).
+__device__ __forceinline__ void wait_at_least(const unsigned int* flag, unsigned int want, DevStats* st) {
+  const long long t0 = clock64();
+  while (*reinterpret_cast<const volatile unsigned int*>(flag) < want) {
+    if (clock64() - t0 > kBatchWait) {
+      atomicOr(&st->status, static_cast<unsigned>(ACE_STATUS_TIMEOUT));
+      break;
     }
-    const HashArgs a = args[lo];
-    const int tpb = BN / a.K;
-    const int ntb = (a.L + tpb - 1) / tpb;
-    hash_simt_block<BF16, IdT>(a, tpb, ntb, b - start[lo]);
-    __syncthreads();  // shared memory is reused by the next block
+    __nanosleep(256);
+  }
+  __threadfence();
+}
+
+// Every detector's insert_score in one persistent launch.  Work items are dispensed in order
+// from one counter: the hash blocks of all detectors (binary32 engine, counts incremented),
+// then their query-phase blocks, then their score and flag blocks.  A query block of detector
+// g waits until every hash block of g is done (hdone[g]), and a flag block until g's last
+// query block has derived mu, sigma and the threshold (sready[g]).  An item only ever waits
+// for items dispensed before it, all of which are held by running blocks, so every wait ends.
+template <bool BF16, typename IdT>
+__global__ void __launch_bounds__(NT, 2)
+    batch_kernel(const HashArgs* __restrict__ args, const ScoreJob* __restrict__ jobs,
+                 const long long* __restrict__ hstart, const long long* __restrict__ sstart, int ndet,
+                 unsigned long long* next, unsigned int* hdone, unsigned int* sready) {
+  extern __shared__ __align__(16) uint8_t sbuf[];
+  __shared__ long long item_s;
+  const long long H = hstart[ndet], S = sstart[ndet];
+  const long long total = H + 2 * S;
+  for (;;) {
+    if (threadIdx.x == 0) item_s = static_cast<long long>(atomicAdd(next, 1ull));
+    __syncthreads();
+    const long long it = item_s;
+    __syncthreads();
+    if (it >= total) break;
+    if (it < H) {
+      const int g = job_of(hstart, ndet, it);
+      hash_block_any<BF16, IdT>(args[g], it - hstart[g], sbuf);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(hdone + g, 1u);
+      }
+    } else if (it < H + S) {
+      const long long b = it - H;
+      const int g = job_of(sstart, ndet, b);
+      const ScoreJob& j = jobs[g];
+      if (threadIdx.x == 0) wait_at_least(hdone + g, static_cast<unsigned int>(hstart[g + 1] - hstart[g]), j.st);
+      __syncthreads();
+      const bool last = score_block<IdT, false>(static_cast<const IdT*>(j.ids), j.ld, j.n, j.K, j.L, j.alpha, j.counts,
+                                                j.sums, j.st, b - sstart[g], sstart[g + 1] - sstart[g]);
+      if (last) {  // thread 0 of the block that derived mu, sigma and t
+        __threadfence();
+        atomicExch(sready + g, 1u);
+      }
+    } else {
+      const long long b = it - H - S;
+      const int g = job_of(sstart, ndet, b);
+      const ScoreJob& j = jobs[g];
+      if (threadIdx.x == 0) wait_at_least(sready + g, 1u, j.st);
+      __syncthreads();
+      flags_block(j, b - sstart[g]);
+    }
+    __syncthreads();  // shared memory is reused by the next item
   }
 }
 
 }  // namespace
 
+int simt_tile_rows(int t) { return tile_rows(t); }
+int simt_tile_cols(int t) { return tile_cols(t); }
+
 long long hash_simt_blocks(const HashArgs& a) {
   if (a.n <= 0) return 0;
-  const int tpb = BN / a.K;
-  const int ntb = (a.L + tpb - 1) / tpb;
-  return (a.n + BM - 1) / BM * ntb;
+  int tpb, ntb;
+  tile_blocks(a, a.tile, tpb, ntb);
+  return (a.n + 16 * tile_rows(a.tile) - 1) / (16 * tile_rows(a.tile)) * ntb;
 }
 
-cudaError_t launch_hash_simt_batched(const HashArgs* args_dev, const long long* start_dev, int ndet, bool bf16,
-                                     bool id16, int num_sms, cudaStream_t s) {
-  const unsigned grid = static_cast<unsigned>(num_sms * 2);  // two blocks per SM (registers)
-  if (bf16) {
-    if (id16) hash_simt_batched_kernel<true, uint16_t><<<grid, NT, 0, s>>>(args_dev, start_dev, ndet);
-    else hash_simt_batched_kernel<true, uint32_t><<<grid, NT, 0, s>>>(args_dev, start_dev, ndet);
-  } else {
-    if (id16) hash_simt_batched_kernel<false, uint16_t><<<grid, NT, 0, s>>>(args_dev, start_dev, ndet);
-    else hash_simt_batched_kernel<false, uint32_t><<<grid, NT, 0, s>>>(args_dev, start_dev, ndet);
-  }
-  return cudaGetLastError();
+cudaError_t launch_batch(const HashArgs* args_dev, const ScoreJob* jobs_dev, const long long* hstart_dev,
+                         const long long* sstart_dev, int ndet, unsigned long long* next, unsigned int* hdone,
+                         unsigned int* sready, bool bf16, bool id16, int num_sms, cudaStream_t s) {
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSimtSmemMax));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, kSimtSmemMax);
+    if (e != cudaSuccess) return e;
+    kern<<<static_cast<unsigned>(num_sms * max(1, per_sm)), NT, kSimtSmemMax, s>>>(args_dev, jobs_dev, hstart_dev,
+                                                                                 sstart_dev, ndet, next, hdone, sready);
+    return cudaGetLastError();
+  };
+  if (bf16) return id16 ? go(batch_kernel<true, uint16_t>) : go(batch_kernel<true, uint32_t>);
+  return id16 ? go(batch_kernel<false, uint16_t>) : go(batch_kernel<false, uint32_t>);
 }
 
 cudaError_t launch_hash_simt(const HashArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  const int tpb = BN / a.K;  // K <= 24, so tpb >= 5
-  const int ntb = (a.L + tpb - 1) / tpb;
-  const long long tiles = (a.n + BM - 1) / BM;
-  const long long blocks = tiles * ntb;
+  const long long blocks = hash_simt_blocks(a);
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   const dim3 grid(static_cast<unsigned>(blocks));
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSimtSmemMax));
+    if (e != cudaSuccess) return e;
+    kern<<<grid, NT, kSimtSmemMax, s>>>(a);
+    return cudaGetLastError();
+  };
   const bool id16 = a.K <= 16;
-  if (a.x_bf16) {
-    if (id16) hash_simt_kernel<true, uint16_t><<<grid, NT, 0, s>>>(a, tpb, ntb);
-    else hash_simt_kernel<true, uint32_t><<<grid, NT, 0, s>>>(a, tpb, ntb);
-  } else {
-    if (id16) hash_simt_kernel<false, uint16_t><<<grid, NT, 0, s>>>(a, tpb, ntb);
-    else hash_simt_kernel<false, uint32_t><<<grid, NT, 0, s>>>(a, tpb, ntb);
-  }
-  return cudaGetLastError();
+  if (a.x_bf16) return id16 ? go(hash_simt_kernel<true, uint16_t>) : go(hash_simt_kernel<true, uint32_t>);
+  return id16 ? go(hash_simt_kernel<false, uint16_t>) : go(hash_simt_kernel<false, uint32_t>);
 }
 
 }  // namespace ace

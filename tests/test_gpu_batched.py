@@ -58,6 +58,22 @@ def test_batch_at_bench_shapes():
     _check(dets, refs, Xs, res)
 
 
+def test_batch_tiles_are_autotuned_and_every_tile_is_exact():
+    """The autotuner records a tile per shape class met by a batch (points and columns per block
+    in {64, 128}); and each of the four tiles, forced through single-shape batches of ragged
+    sizes, gives the oracle's results (the tuner may pick any of them)."""
+    K, L = 12, 32
+    specs = [(200, 5000, 11), (40, 3000, 12), (512, 2500, 13)]
+    dets = [ace.Detector(d, K, L, seed=sd) for (d, n, sd) in specs]
+    refs = [oracle.Detector(d, K, L, W=det.projection()) for (d, n, sd), det in zip(specs, dets)]
+    Xs = _batch_points(specs, 3)
+    _check(dets, refs, Xs, ace.batch_insert_score(dets, [torch.from_numpy(X).cuda() for X in Xs]))
+    for (d, n, sd) in specs:
+        p, c = ace.batch_tile(d, K, L)
+        assert p in (64, 128) and c in (64, 128), (d, p, c)
+    assert ace.batch_tile(7777, K, L) == (0, 0)
+
+
 def test_batch_rejects_duplicates_and_mixed_k():
     a = ace.Detector(20, 12, 8, seed=1)
     b = ace.Detector(20, 18, 4, seed=2)
