@@ -282,16 +282,6 @@ __global__ void __launch_bounds__(NT, 2) hash_simt_kernel(HashArgs a) {
   hash_block_any<BF16, IdT>(a, blockIdx.x, sbuf);
 }
 
-__device__ __forceinline__ int job_of(const long long* __restrict__ start, int ndet, long long b) {
-  int lo = 0, hi = ndet;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (start[mid] <= b) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
-
 constexpr long long kBatchWait = 4000000000LL;  // about 2 s at 2 GHz
 
 // Waits (thread 0) until *flag >= want, bounded; on time-out it raises the detector's timeout
@@ -314,6 +304,20 @@ __device__ __forceinline__ void wait_at_least(const unsigned int* flag, unsigned
 // g waits until every hash block of g is done (hdone[g]), and a flag block until g's last
 // query block has derived mu, sigma and the threshold (sready[g]).  An item only ever waits
 // for items dispensed before it, all of which are held by running blocks, so every wait ends.
+constexpr int kBatchSmemDets = 2048;  // item prefixes kept in shared memory up to this many detectors
+
+// The detector of item b: binary search of the prefixes (in shared memory when they fit).
+template <typename T>
+__device__ __forceinline__ int find_det(const T* start, int ndet, long long b) {
+  int lo = 0, hi = ndet;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (static_cast<long long>(start[mid]) <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 template <bool BF16, typename IdT>
 __global__ void __launch_bounds__(NT, 2)
     batch_kernel(const HashArgs* __restrict__ args, const ScoreJob* __restrict__ jobs,
@@ -322,6 +326,19 @@ __global__ void __launch_bounds__(NT, 2)
   extern __shared__ __align__(16) uint8_t sbuf[];
   __shared__ long long item_s;
   const long long H = hstart[ndet], S = sstart[ndet];
+  // item prefixes as 32-bit offsets in shared memory (after the hash tile), when they fit
+  const bool pre_smem = ndet <= kBatchSmemDets && H + 2 * S < 0x7FFFFFFFLL;
+  unsigned int* const hs32 = reinterpret_cast<unsigned int*>(sbuf + kSimtSmemMax);
+  unsigned int* const ss32 = hs32 + kBatchSmemDets + 1;
+  if (pre_smem) {
+    for (int g = threadIdx.x; g <= ndet; g += NT) {
+      hs32[g] = static_cast<unsigned int>(hstart[g]);
+      ss32[g] = static_cast<unsigned int>(sstart[g]);
+    }
+  }
+  __syncthreads();
+  auto hdet = [&](long long b) { return pre_smem ? find_det(hs32, ndet, b) : find_det(hstart, ndet, b); };
+  auto sdet = [&](long long b) { return pre_smem ? find_det(ss32, ndet, b) : find_det(sstart, ndet, b); };
   const long long total = H + 2 * S;
   for (;;) {
     if (threadIdx.x == 0) item_s = static_cast<long long>(atomicAdd(next, 1ull));
@@ -330,7 +347,7 @@ __global__ void __launch_bounds__(NT, 2)
     __syncthreads();
     if (it >= total) break;
     if (it < H) {
-      const int g = job_of(hstart, ndet, it);
+      const int g = hdet(it);
       hash_block_any<BF16, IdT>(args[g], it - hstart[g], sbuf);
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -339,7 +356,7 @@ __global__ void __launch_bounds__(NT, 2)
       }
     } else if (it < H + S) {
       const long long b = it - H;
-      const int g = job_of(sstart, ndet, b);
+      const int g = sdet(b);
       const ScoreJob& j = jobs[g];
       if (threadIdx.x == 0) wait_at_least(hdone + g, static_cast<unsigned int>(hstart[g + 1] - hstart[g]), j.st);
       __syncthreads();
@@ -351,7 +368,7 @@ __global__ void __launch_bounds__(NT, 2)
       }
     } else {
       const long long b = it - H - S;
-      const int g = job_of(sstart, ndet, b);
+      const int g = sdet(b);
       const ScoreJob& j = jobs[g];
       if (threadIdx.x == 0) wait_at_least(sready + g, 1u, j.st);
       __syncthreads();
@@ -376,14 +393,15 @@ long long hash_simt_blocks(const HashArgs& a) {
 cudaError_t launch_batch(const HashArgs* args_dev, const ScoreJob* jobs_dev, const long long* hstart_dev,
                          const long long* sstart_dev, int ndet, unsigned long long* next, unsigned int* hdone,
                          unsigned int* sready, bool bf16, bool id16, int num_sms, cudaStream_t s) {
+  const size_t smem = kSimtSmemMax + 2 * sizeof(unsigned int) * (kBatchSmemDets + 1);
   auto go = [&](auto kern) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSimtSmemMax));
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, kSimtSmemMax);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
     if (e != cudaSuccess) return e;
-    kern<<<static_cast<unsigned>(num_sms * max(1, per_sm)), NT, kSimtSmemMax, s>>>(args_dev, jobs_dev, hstart_dev,
-                                                                                 sstart_dev, ndet, next, hdone, sready);
+    kern<<<static_cast<unsigned>(num_sms * max(1, per_sm)), NT, smem, s>>>(args_dev, jobs_dev, hstart_dev, sstart_dev,
+                                                                          ndet, next, hdone, sready);
     return cudaGetLastError();
   };
   if (bf16) return id16 ? go(batch_kernel<true, uint16_t>) : go(batch_kernel<true, uint32_t>);
