@@ -348,7 +348,8 @@ __global__ void __launch_bounds__(NT, 2)
     if (it >= total) break;
     if (it < H) {
       const int g = hdet(it);
-      hash_block_any<BF16, IdT>(args[g], it - hstart[g], sbuf);
+      const HashArgs a = args[g];  // a copy: the block's loops read these fields many times
+      hash_block_any<BF16, IdT>(a, it - (pre_smem ? static_cast<long long>(hs32[g]) : hstart[g]), sbuf);
       __syncthreads();
       if (threadIdx.x == 0) {
         __threadfence();
@@ -357,7 +358,7 @@ __global__ void __launch_bounds__(NT, 2)
     } else if (it < H + S) {
       const long long b = it - H;
       const int g = sdet(b);
-      const ScoreJob& j = jobs[g];
+      const ScoreJob j = jobs[g];
       if (threadIdx.x == 0) wait_at_least(hdone + g, static_cast<unsigned int>(hstart[g + 1] - hstart[g]), j.st);
       __syncthreads();
       const bool last = score_block<IdT, false>(static_cast<const IdT*>(j.ids), j.ld, j.n, j.K, j.L, j.alpha, j.counts,
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(NT, 2)
     } else {
       const long long b = it - H - S;
       const int g = sdet(b);
-      const ScoreJob& j = jobs[g];
+      const ScoreJob j = jobs[g];
       if (threadIdx.x == 0) wait_at_least(sready + g, 1u, j.st);
       __syncthreads();
       flags_block(j, b - sstart[g]);
