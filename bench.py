@@ -37,6 +37,10 @@ METRIC = "insert+score points/s per config vs plain FP32 GPU path; % roofline; p
 UNIT = "points/s"
 WORKLOAD = "kdd-shaped n=500000 d=41 K=15 L=50 alpha=1 (23-cluster mixture, 1% uniform anomalies)"
 N_POINTS, D, KH, LT, ALPHA = 500_000, 41, 15, 50, 1.0
+# The high-dimensional workload (--workload highdim; profiling and per-config runs): bfloat16
+# points drawn on the device, d = 1024, K = 16, L = 64.
+HIGHDIM = {"n": 1_000_000, "d": 1024, "K": 16, "L": 64,
+           "name": "high-dimensional n=1000000 d=1024 K=16 L=64 bf16 (64 clusters on the unit sphere, 0.5% anomalies)"}
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 x max SM clock
 
 REF_BUDGET_S = 90.0  # timed CPU work of one --impl reference run
@@ -59,7 +63,8 @@ def _peaks():
 # sources that determine each timed kernel's code (its traffic figure is void once one changes)
 KERNEL_SOURCES = {
     "hash_tc": ("hash_tc.cu", "tc_ptx.cuh", "tc_plan.h", "guard.cuh", "ace_internal.h", "exact_div.h"),
-    "hash_simt": ("hash_simt.cu", "guard.cuh", "ace_internal.h", "exact_div.h"),
+    "hash_simt": ("hash_simt.cu", "guard.cuh", "ace_internal.h", "exact_div.h", "score_block.cuh"),
+    "hash_gemm": ("hash_gemm.cu", "gemm_plan.h", "tc_ptx.cuh", "guard.cuh", "ace_internal.h", "exact_div.h"),
 }
 
 
@@ -164,6 +169,12 @@ def _max_over_ranks(x: float, dist, device):
 def _batches(rank: int, n: int):
     from paper_1706_06664_gb300 import workloads
     return [workloads.kdd(seed=2 + 1000 * rank + 10 * b, n=n)["X"] for b in range(3)]
+
+
+def _device_batches(rank: int, n: int, count: int = 2):
+    """The high-dimensional batches, drawn on the device (2 x 2 GB at n = 1,000,000)."""
+    from paper_1706_06664_gb300 import workloads
+    return [workloads.highdim_device(seed=3 + 1000 * rank + 10 * b, n=n)[0] for b in range(count)]
 
 
 def cpu_baseline(X: np.ndarray, detector_seed: int, budget_s: float = 12.0) -> dict:
@@ -363,7 +374,7 @@ def _e2e(args, det, host_batches, stream, dist, dev, n, ws):
     # the streaming host entry: each step enqueues its batch (copy in, insert + score, copy
     # out); the copy of one step overlaps the computation of the previous one
     for i in range(2):
-        det.insert_score_host_async(hx[i % 3], ALPHA, o_sc, o_su, o_fl, stream=stream)
+        det.insert_score_host_async(hx[i % len(hx)], ALPHA, o_sc, o_su, o_fl, stream=stream)
     det.host_wait()
     det.reset()
     torch.cuda.synchronize()
@@ -371,7 +382,7 @@ def _e2e(args, det, host_batches, stream, dist, dev, n, ws):
         dist.barrier()
     t0 = time.perf_counter()
     for i in range(args.steps):
-        det.insert_score_host_async(hx[i % 3], ALPHA, o_sc, o_su, o_fl, stream=stream)
+        det.insert_score_host_async(hx[i % len(hx)], ALPHA, o_sc, o_su, o_fl, stream=stream)
     det.host_wait()
     e2e_s = _max_over_ranks(time.perf_counter() - t0, dist, dev)
     return {"value": n * args.steps * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(hx[0].nbytes),
@@ -541,10 +552,14 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     n = args.n
-    host_batches = _batches(rank, n)
-    X = [torch.from_numpy(b).to(dev) for b in host_batches]
+    if args.workload == "highdim":
+        X = _device_batches(rank, n)
+        host_batches = None  # drawn on the device; the e2e pass copies them to pinned host memory
+    else:
+        host_batches = _batches(rank, n)
+        X = [torch.from_numpy(b).to(dev) for b in host_batches]
     seed = 1234 + rank
-    det = ace.Detector(D, KH, LT, seed=seed, precision=args.precision)
+    det = ace.Detector(D, KH, LT, seed=seed, precision=args.precision, w_bf16=args.w_bf16)
     stream = torch.cuda.current_stream(dev)
     sc = torch.empty(n, dtype=torch.float64, device=dev)
     su = torch.empty(n, dtype=torch.int32, device=dev)
@@ -600,6 +615,8 @@ def run_ours(args):
     # ---- end to end through the host-buffer entry point --------------------------------
     e2e = None
     if args.e2e:
+        if host_batches is None:
+            host_batches = [x.cpu().numpy().view(np.uint16) for x in X]
         e2e = _e2e(args, det, host_batches, stream, dist, dev, n, ws)
 
     # ---- roofline of the dominant kernel --------------------------------------------
@@ -611,7 +628,7 @@ def run_ours(args):
     if top == "hash":
         t = per_launch_ms["hash"] / 1e3
         if precision == ace.ACE_PROJ_BF16:
-            kkey = "hash_tc"
+            kkey = "hash_tc" if D <= 64 else "hash_gemm"
             roof = {"bound": "tensor", "achieved": flops / t / 1e12, "peak": peaks["bf16_tflops"],
                     "unit": "TFLOP/s", "peak_src": f"bf16 burst, {peaks['src']}"}
         else:
@@ -632,10 +649,13 @@ def run_ours(args):
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16" if precision == ace.ACE_PROJ_BF16 else "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": ["fp32", "bf16"][precision] if precision in (0, 1) else precision,
-                   "l2": "inputs rotate over 3 resident batches (246 MB > 129 MB L2)",
+                   "l2": ("inputs rotate over 2 resident batches (2 x 2 GB > 129 MB L2)" if args.workload == "highdim"
+                          else "inputs rotate over 3 resident batches (246 MB > 129 MB L2)"),
+                   "w": "bfloat16-valued" if args.w_bf16 else "binary32",
                    "parallelism": f"replicas x{ws} (independent detectors, no collective)"},
         "roofline": roof,
-        "step_roofline": _step_roofline(n, D, KH, LT, 4, ms_max / args.steps, peaks),
+        "step_roofline": _step_roofline(n, D, KH, LT, 2 if args.workload == "highdim" else 4, ms_max / args.steps,
+                                        peaks),
         "phases_ms_per_step": {k: v["ms"] / pre for k, v in pre_prof.items()},
         "phases_note": f"from {pre} steps with every kernel bracketed by CUDA events, before the timed "
                        f"steps; in the timed steps only '{top}' (the roofline's kernel) is bracketed, "
@@ -660,7 +680,7 @@ def run_ours(args):
             line["per_config"], cases = cases, None
     if rank == 0 and ws == 1 and args.per_config and cases is not None:
         line["per_config"] = section(per_config, cases)
-    if rank == 0 and args.cpu_baseline:
+    if rank == 0 and args.cpu_baseline and host_batches is not None and args.workload == "kdd":
         line["cpu_baseline"] = section(cpu_baseline, host_batches[0], seed)
         if cases is not None and "error" not in line["cpu_baseline"]:
             line["cpu_baseline"]["per_config"] = section(oracle_per_config, cases)
@@ -686,7 +706,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16"])
-    ap.add_argument("--n", type=int, default=N_POINTS, help="points per batch (profiling runs only)")
+    ap.add_argument("--n", type=int, default=None, help="points per batch (profiling runs only)")
+    ap.add_argument("--workload", default="kdd", choices=["kdd", "highdim"],
+                    help="kdd: the headline KDD-shaped workload; highdim: d = 1024 bfloat16 (profiling runs)")
+    ap.add_argument("--w-bf16", dest="w_bf16", action="store_true", help="draw W in bfloat16 (ace_create_ex)")
     ap.add_argument("--ref-sample", type=int, default=100_000, help="points per reference step")
     ap.add_argument("--ref-budget", type=float, default=REF_BUDGET_S, help="seconds of timed reference work")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
@@ -697,6 +720,13 @@ def main():
     ap.add_argument("--no-per-config", dest="per_config", action="store_false")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    global D, KH, LT, WORKLOAD
+    if args.workload == "highdim":
+        D, KH, LT, WORKLOAD = HIGHDIM["d"], HIGHDIM["K"], HIGHDIM["L"], HIGHDIM["name"]
+        if args.n is None:
+            args.n = HIGHDIM["n"]
+    if args.n is None:
+        args.n = N_POINTS
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
