@@ -65,6 +65,7 @@ KERNEL_SOURCES = {
     "hash_tc": ("hash_tc.cu", "tc_ptx.cuh", "tc_plan.h", "guard.cuh", "ace_internal.h", "exact_div.h"),
     "hash_simt": ("hash_simt.cu", "guard.cuh", "ace_internal.h", "exact_div.h", "score_block.cuh"),
     "hash_gemm": ("hash_gemm.cu", "gemm_plan.h", "tc_ptx.cuh", "guard.cuh", "ace_internal.h", "exact_div.h"),
+    "hash_gemm_fp8": ("hash_gemm.cu", "gemm_plan.h", "tc_ptx.cuh", "guard.cuh", "ace_internal.h", "exact_div.h"),
 }
 
 
@@ -631,6 +632,11 @@ def run_ours(args):
             kkey = "hash_tc" if D <= 64 else "hash_gemm"
             roof = {"bound": "tensor", "achieved": flops / t / 1e12, "peak": peaks["bf16_tflops"],
                     "unit": "TFLOP/s", "peak_src": f"bf16 burst, {peaks['src']}"}
+        elif precision == ace.ACE_PROJ_FP8:
+            kkey = "hash_gemm_fp8"
+            roof = {"bound": "tensor", "achieved": flops / t / 1e12, "peak": 2.0 * peaks["bf16_tflops"],
+                    "unit": "TFLOP/s",
+                    "peak_src": f"fp8 dense = 2 x bf16 burst ({peaks['src']}; nominal 4.5 / 2.25 PFLOP/s ratio)"}
         else:
             kkey = "hash_simt"
             roof = {"bound": "alu", "achieved": flops / t / 1e12, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -647,8 +653,8 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16" if precision == ace.ACE_PROJ_BF16 else "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": ["fp32", "bf16"][precision] if precision in (0, 1) else precision,
+        "dtype": {ace.ACE_PROJ_BF16: "bf16", ace.ACE_PROJ_FP8: "e4m3"}.get(precision, "f32"), "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": ["fp32", "bf16", "fp8"][precision] if precision in (0, 1, 2) else precision,
                    "l2": ("inputs rotate over 2 resident batches (2 x 2 GB > 129 MB L2)" if args.workload == "highdim"
                           else "inputs rotate over 3 resident batches (246 MB > 129 MB L2)"),
                    "w": "bfloat16-valued" if args.w_bf16 else "binary32",
@@ -705,7 +711,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16", "fp8"])
     ap.add_argument("--n", type=int, default=None, help="points per batch (profiling runs only)")
     ap.add_argument("--workload", default="kdd", choices=["kdd", "highdim"],
                     help="kdd: the headline KDD-shaped workload; highdim: d = 1024 bfloat16 (profiling runs)")

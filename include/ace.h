@@ -63,7 +63,10 @@ enum { ACE_F32 = 0, ACE_BF16 = 1 };
 enum {
   ACE_PROJ_AUTO = -1, /* fastest available path for the detector's shape (default)       */
   ACE_PROJ_FP32 = 0,  /* binary32 FMA on the SIMT cores                                   */
-  ACE_PROJ_BF16 = 1   /* bfloat16 split operands on tcgen05 tensor cores, binary32 accum.  */
+  ACE_PROJ_BF16 = 1,  /* bfloat16 split operands on tcgen05 tensor cores, binary32 accum.  */
+  ACE_PROJ_FP8 = 2    /* E4M3 split operands (X = X1 + X2 per row with a power-of-two row
+                         scale, W = W1 + W2 per column), four kind::f8f6f4 products in binary32:
+                         streaming engine and bfloat16-valued W (ACE_W_BF16) only          */
 };
 
 /* Device-status bits reported by ace_stats (sticky until ace_reset). */
@@ -89,9 +92,10 @@ typedef struct {
                             /* (inside their error bound): (point, table) pairs for the   */
                             /* resident engine (d <= 64), (point, column) pairs for the   */
                             /* streaming one (larger d); 0 on the SIMT engine             */
-  int32_t tc_products;      /* bfloat16 products per tensor-core accumulation in the last */
-                            /* hash: 3 (resident engine, x and W split), 2 (streaming, W  */
-                            /* split), 1 (streaming, bfloat16-valued W), 0 (SIMT)         */
+  int32_t tc_products;      /* products per tensor-core accumulation in the last hash:   */
+                            /* 3 (resident engine, x and W split in bfloat16), 2          */
+                            /* (streaming, W split), 1 (streaming, bfloat16-valued W),    */
+                            /* 4 (streaming E4M3: X1 W1, X1 W2, X2 W1, X2 W2), 0 (SIMT)   */
 } ace_stats_t;
 
 /* Creation flags (ace_create_ex). */
@@ -148,7 +152,10 @@ int ace_reset(ace_handle h, void* stream);
  */
 int ace_set_graph(ace_handle h, int enable);
 
-/* Selects the projection engine (ACE_PROJ_*).  Results do not depend on it. */
+/* Selects the projection engine (ACE_PROJ_*).  Results do not depend on it.  ACE_PROJ_BF16
+ * and ACE_PROJ_FP8 fail with ACE_ERR_UNSUPPORTED where their engine does not apply (FP8: an
+ * sm_103 device, d > 64 and a multiple of 8, a detector whose W entries are all bfloat16
+ * values, and bfloat16 input at a 16-byte-aligned address when hashing). */
 int ace_set_precision(ace_handle h, int precision);
 
 /*
@@ -398,6 +405,16 @@ int ace_insert_score_noalloc(ace_handle h, const void* X_dev, int64_t n, int dty
  * Errors: ACE_ERR_ARG, ACE_ERR_UNSUPPORTED (not an sm_103 device), ACE_ERR_TIMEOUT, ACE_ERR_CUDA.
  */
 int ace_tc_probe(const uint16_t* A_host, const uint16_t* B_host, int kdim, int ncols, float* D_host);
+
+/*
+ * ace_tc_probe_fp8 — the same hook for E4M3 operands: A (128 x kdim) and B (ncols x kdim) hold
+ * E4M3 bytes (row-major, host), and D = A . B^T is computed as kdim/32 kind::f8f6f4 MMA
+ * instructions of 128 x ncols x 32 accumulating into one binary32 TMEM accumulator in k
+ * order, the way the FP8 projection (ACE_PROJ_FP8) accumulates.  kdim is a multiple of 32 and
+ * ncols a multiple of 16, both in [32, 256] and [16, 256].  Synchronous.  Errors as
+ * ace_tc_probe.
+ */
+int ace_tc_probe_fp8(const uint8_t* A_host, const uint8_t* B_host, int kdim, int ncols, float* D_host);
 
 /* Library version string. */
 const char* ace_version(void);

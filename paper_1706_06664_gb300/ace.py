@@ -16,9 +16,9 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libace_gb300.so")
 
 ACE_OK, ACE_ERR_ARG, ACE_ERR_OOM, ACE_ERR_OVERFLOW, ACE_ERR_TIMEOUT, ACE_ERR_CUDA, ACE_ERR_UNSUPPORTED = range(7)
 ACE_F32, ACE_BF16 = 0, 1
-ACE_PROJ_AUTO, ACE_PROJ_FP32, ACE_PROJ_BF16 = -1, 0, 1
+ACE_PROJ_AUTO, ACE_PROJ_FP32, ACE_PROJ_BF16, ACE_PROJ_FP8 = -1, 0, 1, 2
 ACE_W_BF16 = 1
-PRECISIONS = {"auto": ACE_PROJ_AUTO, "fp32": ACE_PROJ_FP32, "bf16": ACE_PROJ_BF16}
+PRECISIONS = {"auto": ACE_PROJ_AUTO, "fp32": ACE_PROJ_FP32, "bf16": ACE_PROJ_BF16, "fp8": ACE_PROJ_FP8}
 
 # Every symbol include/ace.h declares (checked by the tests).
 EXPORTS = [
@@ -28,7 +28,7 @@ EXPORTS = [
     "ace_batch_insert_score", "ace_server_create", "ace_server_submit", "ace_server_wait", "ace_server_drain", "ace_server_destroy", "ace_stats",
     "ace_get_counts", "ace_get_projection", "ace_get_shape", "ace_last_error", "ace_version",
     "ace_profile_enable", "ace_profile_phases", "ace_profile_read", "ace_insert_score_noalloc",
-    "ace_tc_probe", "ace_save_size", "ace_save", "ace_load", "ace_window_enable", "ace_set_graph",
+    "ace_tc_probe", "ace_tc_probe_fp8", "ace_save_size", "ace_save", "ace_load", "ace_window_enable", "ace_set_graph",
     "ace_batch_tile",
 ]
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
@@ -104,6 +104,7 @@ def load_library(path: str = LIB_PATH):
             "ace_profile_phases": ([H, ctypes.c_uint32], i32),
             "ace_profile_read": ([H, ctypes.POINTER(ace_profile_t)], i32),
             "ace_tc_probe": ([P, P, i32, i32, P], i32),
+            "ace_tc_probe_fp8": ([P, P, i32, i32, P], i32),
             "ace_window_enable": ([H, i64], i32),
             "ace_set_graph": ([H, i32], i32),
             "ace_batch_tile": ([i32, i32, i32, i32, P, P], i32),
@@ -458,6 +459,18 @@ def tc_probe(A: np.ndarray, B: np.ndarray) -> np.ndarray:
     D = np.empty((128, B.shape[0]), dtype=np.float32)
     _check(load_library().ace_tc_probe(ctypes.c_void_p(A.ctypes.data), ctypes.c_void_p(B.ctypes.data), A.shape[1],
                                        B.shape[0], ctypes.c_void_p(D.ctypes.data)))
+    return D
+
+
+def tc_probe_fp8(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """ace_tc_probe_fp8: D = A . B^T on the tensor cores (A 128 x kd, B N x kd E4M3 bytes as
+    uint8; kd a multiple of 32, N of 16, up to 256), accumulated as kd/32 MMA instructions."""
+    A = np.ascontiguousarray(A, dtype=np.uint8)
+    B = np.ascontiguousarray(B, dtype=np.uint8)
+    assert A.shape[0] == 128 and A.shape[1] == B.shape[1]
+    D = np.empty((128, B.shape[0]), dtype=np.float32)
+    _check(load_library().ace_tc_probe_fp8(ctypes.c_void_p(A.ctypes.data), ctypes.c_void_p(B.ctypes.data),
+                                           A.shape[1], B.shape[0], ctypes.c_void_p(D.ctypes.data)))
     return D
 
 

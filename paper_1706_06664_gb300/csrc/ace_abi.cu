@@ -22,6 +22,7 @@
 #include "ace_internal.h"
 #include "gemm_plan.h"
 #include "tc_plan.h"
+#include "tc_ptx.cuh"
 
 namespace {
 
@@ -112,6 +113,13 @@ struct ace_detector {
   float* gcolf = nullptr;       // [klp] image column norms (single-product image only)
   uint16_t* gwt16 = nullptr;    // [KL][d] bfloat16 W, columns contiguous (single-product only)
   CUtensorMap tm_img{};         // TMA description of gimg
+  // E4M3 variant of the streaming engine (ACE_PROJ_FP8; bfloat16-valued W only)
+  bool gemm8_ok = false;
+  ace::GemmArgs gm8{};
+  uint8_t* gimg8 = nullptr;     // [nunits][nkb][W1, W2][256 x 64] canonical E4M3 blocks
+  float* gprof8 = nullptr;      // [2][nkb] W1 profile (K = 32 instructions folded per k-block)
+  float* gcolf8 = nullptr;      // [klp] norms of the scaled image columns
+  float* gwnorm8 = nullptr;     // [KL] accumulator scale back to x.w_c (ace_project)
   // graph replay (ace_set_graph): the launches of a repeated score / insert_score call are
   // captured once and replayed while its arguments and buffers stay the same
   struct GraphKey {
@@ -199,6 +207,10 @@ void free_all(ace_detector* h) {
   cudaFree(h->gprof);
   cudaFree(h->gcolf);
   cudaFree(h->gwt16);
+  cudaFree(h->gimg8);
+  cudaFree(h->gprof8);
+  cudaFree(h->gcolf8);
+  cudaFree(h->gwnorm8);
   cudaFree(h->defer);
   cudaFree(h->defer_counts);
   cudaFree(h->wpad);
@@ -460,6 +472,155 @@ int encode_bf16_map(CUtensorMap* m, const void* base, uint64_t cols, uint64_t ro
   return ACE_OK;
 }
 
+// E4M3 (1 sign, 4 exponent bits with bias 7, 3 mantissa bits; no infinities, largest 448):
+// round to nearest even, saturating beyond 448, and the value of a code.
+uint8_t e4m3_rn(double v) {
+  const uint8_t sg = std::signbit(v) ? 0x80 : 0x00;
+  const double a = std::fabs(v);
+  if (a == 0.0) return sg;
+  if (a > 448.0) return sg | 0x7E;
+  int ex = 0;
+  std::frexp(a, &ex);
+  int E = ex - 1;  // a in [2^E, 2^(E+1))
+  if (E < -6) {    // subnormal: m 2^-9, m in 0..8 (8 is the smallest normal, code 0x08)
+    return sg | static_cast<uint8_t>(std::nearbyint(std::ldexp(a, 9)));
+  }
+  double m = std::nearbyint(std::ldexp(a, 3 - E));  // 8 .. 16
+  if (m == 16.0) {
+    m = 8.0;
+    ++E;
+  }
+  if (E > 8 || (E == 8 && m > 14.0)) return sg | 0x7E;
+  return sg | static_cast<uint8_t>(((E + 7) << 3) | (static_cast<int>(m) - 8));
+}
+double e4m3_value(uint8_t b) {
+  const int e = (b >> 3) & 15, m = b & 7;
+  const double v = e == 0 ? std::ldexp(static_cast<double>(m), -9) : std::ldexp(8.0 + m, e - 10);
+  return (b & 0x80) ? -v : v;
+}
+
+// Plans the E4M3 variant from the single-product bfloat16 image (every W entry a bfloat16
+// value; columns already scaled by 2^-e_c to norms in [1/2, 1)).  Each image column v is scaled
+// again by 2^f (its largest |v_i| to [128, 256)) and split as W1 = e4m3(2^f v), W2 = e4m3(2^f v
+// - W1), W3 = the rest (nonzero only where an element falls into E4M3's subnormal range).  The
+// accumulator of column c then holds 2^(s + f) x.v for a row scaled by 2^s.  Guard terms (one
+// MMA instruction of K = 32 adds its 32 products and the accumulator with an error of at most
+// kF8Acc * 2^-23 times the sum of their magnitudes, the model tests/test_gpu_tc_model.py checks
+// on the device; normalised-column units, the bound of column c being B colf[c]):
+//   pass 1 (X1.W1, S8 = dp/32 instructions): E over y's prefix and block norms with W1's
+//     profile, plus (||X2|| + ||X3||) sum_t (WP_t^1/2 + WB_t^1/2) for ||X1_S|| <= ||y_S|| +
+//     ||y - X1||, plus S8 T0 for the pass-0 total the accumulator carries;
+//   pass 0 (3 S8 instructions): at most (3 S8 + 1) T0, T0 bounding the magnitudes of all the
+//     small products;
+//   dropped: ||X3|| ||v|| + ||X1 + X2|| ||W3|| <= (||X3|| + rres (||y|| + ||X3||)) colf;
+//   the binary64 reference (gamma64_d ||y||).
+constexpr double kF8Acc = 5.25;
+int plan_gemm_fp8(ace_detector* h, const std::vector<uint16_t>& img, const std::vector<int>& cexp, int dp, int tpu,
+                  int nunits, int klp) {
+  h->gemm8_ok = false;
+  const int d = h->d, K = h->K, KL = h->KL;
+  const int nkb = dp / ace::kGemmBK, S8 = dp / 32;
+  const size_t plane = static_cast<size_t>(ace::kGemmBN) * ace::kGemmBK;
+  std::vector<uint8_t> img8(static_cast<size_t>(nunits) * nkb * 2 * plane, 0);
+  std::vector<float> colf8(klp, 0.f);
+  std::vector<int> fexp(klp, 0);
+  std::vector<double> wp(S8, 0.0), wb(S8, 0.0);
+  double w1m = 0.0, w2m = 0.0, rres = 0.0;
+  std::vector<double> vs(dp), w1(dp), w2(dp);
+  for (int row = 0; row < klp; ++row) {
+    double mx = 0.0;
+    for (int i = 0; i < dp; ++i) mx = std::max(mx, std::fabs(static_cast<double>(bf16_value(img[static_cast<size_t>(row) * dp + i]))));
+    if (mx == 0.0) continue;  // a padding row: zero planes
+    int ex = 0;
+    std::frexp(mx, &ex);
+    const int f = 8 - ex;  // mx 2^f in [128, 256)
+    fexp[row] = f;
+    double n2 = 0.0, n1 = 0.0, n22 = 0.0, n3 = 0.0;
+    for (int i = 0; i < dp; ++i) {
+      vs[i] = std::ldexp(static_cast<double>(bf16_value(img[static_cast<size_t>(row) * dp + i])), f);
+      const uint8_t b1 = e4m3_rn(vs[i]);
+      w1[i] = e4m3_value(b1);
+      const uint8_t b2 = e4m3_rn(vs[i] - w1[i]);
+      w2[i] = e4m3_value(b2);
+      const double r3 = vs[i] - w1[i] - w2[i];  // exact in binary64
+      n2 += vs[i] * vs[i];
+      n1 += w1[i] * w1[i];
+      n22 += w2[i] * w2[i];
+      n3 += r3 * r3;
+      const int u = row / ace::kGemmBN, rr = row % ace::kGemmBN, kb = i / ace::kGemmBK, k = i % ace::kGemmBK;
+      const size_t blk = (static_cast<size_t>(u) * nkb + kb) * 2 * plane;
+      img8[blk + ace::tc::kmajor_offset8(rr, k, ace::kGemmBK)] = b1;
+      img8[blk + plane + ace::tc::kmajor_offset8(rr, k, ace::kGemmBK)] = b2;
+    }
+    const double nrm = std::sqrt(n2);
+    colf8[row] = std::nextafter(static_cast<float>(nrm * (1.0 + 1e-12)), FLT_MAX);
+    w1m = std::max(w1m, std::sqrt(n1) / nrm);
+    w2m = std::max(w2m, std::sqrt(n22) / nrm);
+    rres = std::max(rres, std::sqrt(n3) / nrm);
+    double pre = 0.0;
+    for (int t = 0; t < S8; ++t) {
+      wp[t] = std::max(wp[t], pre);
+      double blk = 0.0;
+      for (int i = 32 * t; i < 32 * t + 32; ++i) blk += (w1[i] / nrm) * (w1[i] / nrm);
+      wb[t] = std::max(wb[t], blk);
+      pre += blk;
+    }
+  }
+  std::vector<float> prof(2 * static_cast<size_t>(nkb), 0.f);
+  double sumw = 0.0;
+  for (int kb = 0; kb < nkb; ++kb) {
+    double sp = 0.0, sb = 0.0;
+    for (int t = 2 * kb; t < 2 * kb + 2; ++t) {
+      sp += std::sqrt(wp[t]);
+      sb += wb[t];
+      sumw += std::sqrt(wp[t]) + std::sqrt(wb[t]);
+    }
+    prof[kb] = std::nextafter(static_cast<float>(sp * (1.0 + 1e-12)), FLT_MAX);
+    prof[nkb + kb] = std::nextafter(static_cast<float>(std::sqrt(sb) * (1.0 + 1e-12)), FLT_MAX);
+  }
+  std::vector<float> wn8(KL, 0.f);
+  for (int c = 0; c < KL; ++c) {
+    const int j = c / K, k = c % K;
+    const int row = (j / tpu) * ace::kGemmBN + (j % tpu) * K + k;
+    wn8[c] = std::ldexp(1.0f, cexp[c] - fexp[row]);
+  }
+  cudaError_t e;
+  auto upload = [&](auto** dst, const auto& v, const char* what) -> int {
+    cudaFree(*dst);
+    *dst = nullptr;
+    const size_t bytes = v.size() * sizeof(v[0]);
+    if ((e = cudaMalloc(dst, bytes)) != cudaSuccess) return cuda_fail(e, what);
+    if ((e = cudaMemcpy(*dst, v.data(), bytes, cudaMemcpyHostToDevice)) != cudaSuccess) return cuda_fail(e, what);
+    return ACE_OK;
+  };
+  if (int rc = upload(&h->gimg8, img8, "E4M3 image")) return rc;
+  if (int rc = upload(&h->gprof8, prof, "E4M3 norm profile")) return rc;
+  if (int rc = upload(&h->gcolf8, colf8, "E4M3 column norms")) return rc;
+  if (int rc = upload(&h->gwnorm8, wn8, "E4M3 column scales")) return rc;
+  ace::GemmArgs g = h->gm;
+  g.fp8 = 1;
+  g.img8 = h->gimg8;
+  g.nprod = 2;
+  g.S = S8;
+  g.wprof = h->gprof8;
+  g.colf = h->gcolf8;
+  g.wnorm = h->gwnorm8;
+  const double u64 = std::ldexp(1.0, -53);
+  const double g64 = d * u64 / (1.0 - d * u64);
+  const double ca = kF8Acc * std::ldexp(1.0, -23) * 1.25;
+  auto up = [](double v) { return std::nextafter(static_cast<float>(v * 1.01), FLT_MAX); };
+  g.ca = up(ca);
+  g.cx = up(rres * (1.0 + 1e-9) + g64);
+  g.ksw = up(ca * sumw);
+  g.kt0 = up(ca * (4.0 * S8 + 1.0));
+  g.c3 = up(1.0 + rres);
+  g.w1m = up(w1m);
+  g.w2m = up(w2m);
+  h->gm8 = g;
+  h->gemm8_ok = true;
+  return ACE_OK;
+}
+
 // Plans the streaming tensor-core path (hash_gemm.cu) for d > 64: the image of W' = w_c/||w_c||
 // split into bfloat16 hi and lo parts, laid out per 256-column unit of whole tables
 // (floor(256/K) tables per unit, zero rows after the last table), hi rows first, each row
@@ -661,6 +822,7 @@ int plan_gemm(ace_detector* h) {
   g.defer_counts = h->defer_counts;
   g.smem_bytes = ace::gemm_smem_bytes();
   h->gemm_ok = true;
+  if (one) return plan_gemm_fp8(h, img, cexp, dp, tpu, nunits, klp);
   return ACE_OK;
 }
 
@@ -819,6 +981,8 @@ enum class Engine { kSimt, kResident, kStreaming };
 // d with bfloat16 input at a 16-byte-aligned address (the TMA engine's rule).
 Engine pick_engine(ace_handle h, int x_bf16, const void* X) {
   if (h->precision == ACE_PROJ_FP32) return Engine::kSimt;
+  if (h->precision == ACE_PROJ_FP8)
+    return h->gemm8_ok && x_bf16 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0 ? Engine::kStreaming : Engine::kSimt;
   if (h->tc_ok) return Engine::kResident;
   if (h->gemm_ok && x_bf16 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) return Engine::kStreaming;
   return Engine::kSimt;
@@ -884,7 +1048,8 @@ int run_gemm(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_inser
   void* p = h->defer;
   if (int rc = grow(&p, &h->defer_bytes, cap * 8, s, "deferred list")) return rc;
   h->defer = static_cast<unsigned long long*>(p);
-  ace::GemmArgs g = h->gm;
+  const bool f8 = h->precision == ACE_PROJ_FP8;
+  ace::GemmArgs g = f8 ? h->gm8 : h->gm;
   g.X = a.X;
   g.n = a.n;
   g.ntiles = ntiles;
@@ -900,8 +1065,8 @@ int run_gemm(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_inser
     return rc;
   cudaError_t e;
   if (!proj) {
-    h->last_precision = ACE_PROJ_BF16;
-    h->last_products = g.nprod;
+    h->last_precision = f8 ? ACE_PROJ_FP8 : ACE_PROJ_BF16;
+    h->last_products = f8 ? 4 : g.nprod;
   }
   {
     PhaseScope ps(h, ACE_PHASE_HASH, s);
@@ -924,7 +1089,7 @@ int run_gemm(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_inser
 
 int run_hash(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_insert = true) {
   const Engine eng = pick_engine(h, a.x_bf16, a.X);
-  if (eng == Engine::kSimt && h->precision == ACE_PROJ_BF16)
+  if (eng == Engine::kSimt && (h->precision == ACE_PROJ_BF16 || h->precision == ACE_PROJ_FP8))
     return fail(ACE_ERR_UNSUPPORTED, "the tensor-core engine at d=%d needs bfloat16 input at a 16-byte-aligned address",
                 h->d);
   if (eng == Engine::kSimt) {
@@ -1277,8 +1442,13 @@ int ace_set_graph(ace_handle h, int enable) {
 
 int ace_set_precision(ace_handle h, int precision) {
   if (!h) return fail(ACE_ERR_ARG, "handle is NULL");
-  if (precision != ACE_PROJ_AUTO && precision != ACE_PROJ_FP32 && precision != ACE_PROJ_BF16)
+  if (precision != ACE_PROJ_AUTO && precision != ACE_PROJ_FP32 && precision != ACE_PROJ_BF16 &&
+      precision != ACE_PROJ_FP8)
     return fail(ACE_ERR_ARG, "unknown precision %d", precision);
+  if (precision == ACE_PROJ_FP8 && !h->gemm8_ok)
+    return fail(ACE_ERR_UNSUPPORTED, "the E4M3 projection needs the streaming tensor-core engine (an sm_103 device, "
+                                     "d > 64 and a multiple of 8) and a W whose entries are all bfloat16 values "
+                                     "(ACE_W_BF16); d=%d K=%d L=%d", h->d, h->K, h->L);
   if (precision == ACE_PROJ_BF16 && !h->tc_ok && !h->gemm_ok)
     return fail(ACE_ERR_UNSUPPORTED, "the tensor-core paths need an sm_103 device and either d <= 64 or d a multiple "
                                      "of 8 (d=%d K=%d L=%d)", h->d, h->K, h->L);
@@ -2074,27 +2244,31 @@ int ace_batch_tile(int d, int K, int L, int dtype, int* points, int* columns) {
   return ACE_OK;
 }
 
-int ace_tc_probe(const uint16_t* A_host, const uint16_t* B_host, int kdim, int ncols, float* D_host) {
+namespace {
+int tc_probe_any(const void* A_host, const void* B_host, int kdim, int ncols, float* D_host, bool fp8) {
   if (!A_host || !B_host || !D_host) return fail(ACE_ERR_ARG, "NULL argument");
-  if (kdim < 16 || kdim > 256 || kdim % 16 || ncols < 16 || ncols > 256 || ncols % 16)
-    return fail(ACE_ERR_ARG, "kdim and ncols must be multiples of 16 in [16, 256] (got %d, %d)", kdim, ncols);
+  const int kq = fp8 ? 32 : 16;
+  if (kdim < kq || kdim > 256 || kdim % kq || ncols < 16 || ncols > 256 || ncols % 16)
+    return fail(ACE_ERR_ARG, "kdim must be a multiple of %d and ncols of 16, both in [%d, 256] (got %d, %d)", kq, kq,
+                kdim, ncols);
   int dev = 0;
   ACE_CUDA(cudaGetDevice(&dev));
   cudaDeviceProp p;
   ACE_CUDA(cudaGetDeviceProperties(&p, dev));
   if (p.major != 10 || p.minor != 3) return fail(ACE_ERR_UNSUPPORTED, "the tensor-core probe needs an sm_103 device");
-  const size_t ab = static_cast<size_t>(128) * kdim * 2, bb = static_cast<size_t>(ncols) * kdim * 2;
+  const size_t eb = fp8 ? 1 : 2;
+  const size_t ab = static_cast<size_t>(128) * kdim * eb, bb = static_cast<size_t>(ncols) * kdim * eb;
   const size_t db = static_cast<size_t>(128) * ncols * 4;
   unsigned char* buf = nullptr;
   ACE_CUDA(cudaMalloc(&buf, ab + bb + db + 16));
-  uint16_t* A = reinterpret_cast<uint16_t*>(buf);
-  uint16_t* B = reinterpret_cast<uint16_t*>(buf + ab);
+  unsigned char* A = buf;
+  unsigned char* B = buf + ab;
   float* D = reinterpret_cast<float*>(buf + ab + bb);
   int* status = reinterpret_cast<int*>(buf + ab + bb + db);
   cudaError_t e = cudaMemcpy(A, A_host, ab, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(B, B_host, bb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(status, 0, sizeof(int));
-  if (e == cudaSuccess) e = ace::launch_tc_probe(A, B, kdim, ncols, D, status, nullptr);
+  if (e == cudaSuccess) e = ace::launch_tc_probe(A, B, kdim, ncols, fp8, D, status, nullptr);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   int st = 0;
   if (e == cudaSuccess) e = cudaMemcpy(D_host, D, db, cudaMemcpyDeviceToHost);
@@ -2103,6 +2277,15 @@ int ace_tc_probe(const uint16_t* A_host, const uint16_t* B_host, int kdim, int n
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core probe");
   if (st) return fail(ACE_ERR_TIMEOUT, "tensor-core probe: the MMA completion wait gave up");
   return ACE_OK;
+}
+}  // namespace
+
+int ace_tc_probe(const uint16_t* A_host, const uint16_t* B_host, int kdim, int ncols, float* D_host) {
+  return tc_probe_any(A_host, B_host, kdim, ncols, D_host, false);
+}
+
+int ace_tc_probe_fp8(const uint8_t* A_host, const uint8_t* B_host, int kdim, int ncols, float* D_host) {
+  return tc_probe_any(A_host, B_host, kdim, ncols, D_host, true);
 }
 
 const char* ace_last_error(void) { return g_err.c_str(); }

@@ -99,7 +99,7 @@ cudaError_t launch_window_evict(const void* ring, int ids16, long long cap, long
 cudaError_t launch_delete_apply(const uint32_t* hist, uint32_t* counts, long long total, int num_sms, cudaStream_t s);
 
 // Measurement hook: D = A . B^T as kd/16 tcgen05 MMAs of 128 x N x 16 (tc_probe.cu).
-cudaError_t launch_tc_probe(const uint16_t* A, const uint16_t* B, int kd, int N, float* D, int* status,
+cudaError_t launch_tc_probe(const void* A, const void* B, int kd, int N, bool fp8, float* D, int* status,
                             cudaStream_t s);
 
 // Host-side generator of the projection matrix (SplitMix64 counter mode + Box-Muller).

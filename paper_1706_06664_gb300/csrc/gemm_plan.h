@@ -14,6 +14,7 @@ constexpr int kGemmBM = 128;     // points per tile = MMA M (one TMEM lane per p
 constexpr int kGemmBN = 256;     // image columns per unit = MMA N
 constexpr int kGemmBK = 64;      // d per k-block: one 128-byte swizzle atom of bfloat16
 constexpr int kGemmStages = 4;   // shared-memory ring of (X k-block, image k-block) pairs
+constexpr int kGemmStagesF8 = 3; // the E4M3 ring: X k-block, two image planes, two X planes
 
 // Deferred (point, column) entry: point << 17 | column << 1 | the bit the tensor cores stored.
 constexpr int kGemmEntryShift = 17;
@@ -24,13 +25,20 @@ struct GemmArgs {
   int d, dp, nkb;             // dp = d rounded up to 64; nkb = dp / 64 k-blocks
   int K, L, KL;
   int tpu, nunits;            // whole tables per 256-column unit; units per tile
-  int nprod;                  // 2: x.w'_lo then x.w'_hi (binary32 W split in two); 1: x.w'_hi only
+  int nprod;                  // 2: x.w'_lo then x.w'_hi (binary32 W split in two); 1: x.w'_hi only;
+                              // E4M3 (fp8): 2 passes, the three small products then X1.W1
+  int fp8;                    // E4M3 operands: X = X1 + X2 (+ X3) per row, w' = W1 + W2 (+ W3)
+  const uint8_t* img8;        // E4M3 image: [unit][k-block][W1, W2][256 rows x 64 bytes], each
+                              // block in the K-major no-swizzle canonical layout (16 KB)
   int klp;                    // image rows of one part (nunits * 256); the lo part follows the hi part
   // Row bound B = ca * E + cx * ||x||_up + tau_abs (every column when q < qmin or q is not
   // finite), E bounding the sum over the hi-pass MMA instructions t of
   // ||x_<16t|| WP_t + ||x_Bt|| WB_t, with WP_t, WB_t the largest norms over the columns of
   // w'_hi's prefix [0, 16t) and block [16t, 16t + 16); see hash_gemm.cu.
   float ca, cx, tau_abs, xfac, qmin;
+  // E4M3 only: B += ksw (||X2|| + ||X3||) + kt0 T0 + c3 ||X3||, with
+  // T0 = ||X2|| (w1m + w2m) + ||X1|| w2m bounding the magnitudes of the three small products
+  float ksw, kt0, c3, w1m, w2m;
   int S;                      // MMA instructions per pass (dp / 16)
   const float* wprof;         // [2][nkb] per k-block: sum of its four WP_t, then sqrt of the
                               // sum of its four WB_t^2 (rounded up)

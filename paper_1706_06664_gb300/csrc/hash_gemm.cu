@@ -41,6 +41,7 @@
 //   warps 4-7   epilogue: tcgen05.ld of the accumulator (thread = point), sign bits, guard
 //               classification, deferral entries, bucket ids (Eq. 2) stored table-major
 #include <cuda.h>
+#include <cuda_fp8.h>
 
 #include "gemm_plan.h"
 #include "guard.cuh"
@@ -57,11 +58,22 @@ constexpr int kStages = kGemmStages;
 constexpr uint32_t kABytes = kGemmBM * kGemmBK * 2;  // 16 KB
 constexpr uint32_t kBBytes = kGemmBN * kGemmBK * 2;  // 32 KB
 constexpr uint32_t kStageBytes = kABytes + kBBytes;
+// E4M3 stage: the bfloat16 X k-block (TMA, as above), the image's W1 and W2 planes (256 rows x
+// 64 bytes each, bulk copies of canonical blocks) and the X1 and X2 planes the row warps
+// convert (128 rows x 64 bytes each)
+constexpr int kStagesF8 = kGemmStagesF8;
+constexpr uint32_t kPlaneBytes = kGemmBN * kGemmBK;   // 16 KB
+constexpr uint32_t kXPlaneBytes = kGemmBM * kGemmBK;  // 8 KB
+constexpr uint32_t kOffW1 = kABytes, kOffW2 = kABytes + kPlaneBytes;
+constexpr uint32_t kOffX1 = kABytes + 2 * kPlaneBytes, kOffX2 = kOffX1 + kXPlaneBytes;
+constexpr uint32_t kStageBytesF8 = kOffX2 + kXPlaneBytes;  // 64 KB
+static_assert(kStagesF8 * kStageBytesF8 == kStages * kStageBytes, "both rings span the same bytes");
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 static_assert(kStages * kStageBytes + 4096 * 4 + 4096 + 1024 <= 227 * 1024, "shared memory");
 
 struct GSmem {
   uint64_t full[kStages], empty[kStages];
+  uint64_t a_ready[kStages];  // E4M3: the stage's X1/X2 planes are written (one arrival per row)
   uint64_t t_full[2], t_empty[2];
   uint64_t b_full[2], b_empty[2];
   uint64_t drain;
@@ -70,6 +82,7 @@ struct GSmem {
   unsigned int ndef;
   uint32_t bthr[2][kGemmBM];  // per tile slot and row: the row bound B (bit pattern)
   uint32_t bzero[2][kGemmBM]; // per tile slot and row: the row is exactly zero
+  float bunscale[2][kGemmBM]; // E4M3: 2^-s of the row's scale 2^s (projection output only)
 };
 
 constexpr int kColfMax = 4096;  // per-column norms kept in shared memory (16 units)
@@ -93,6 +106,23 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
           dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
       : "memory");
+}
+
+// 1-D bulk copy global -> shared (both 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Two binary32 values to E4M3 (round to nearest even, saturating to +-448): the first in the
+// low byte.  And back (exact: every E4M3 value is a binary16 value).
+__device__ __forceinline__ uint32_t to_e4m3x2(float a, float b) {
+  return static_cast<uint32_t>(__nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3));
+}
+__device__ __forceinline__ float2 from_e4m3x2(uint32_t v) {
+  const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(v), __NV_E4M3);
+  return __half22float2(__half2(h));
 }
 
 __device__ __forceinline__ void tma_prefetch(const CUtensorMap* map) {
@@ -134,11 +164,14 @@ __device__ __noinline__ bool exact_col_bit(const GemmArgs& a, long long i, int c
 }
 
 // KC > 0: specialised for K = KC (compile-time table offsets); KC = 0 handles any K.
-template <typename IdT, int KC, bool PROJ>
+// F8: E4M3 operands (see the notes at launch_hash_gemm).
+template <typename IdT, int KC, bool PROJ, bool F8>
 __global__ void __launch_bounds__(kThreads, 1)
     hash_gemm_kernel(const __grid_constant__ GemmArgs a, const __grid_constant__ CUtensorMap tmX,
                      const __grid_constant__ CUtensorMap tmW) {
   extern __shared__ uint8_t smem_raw[];
+  constexpr int ST = F8 ? kStagesF8 : kStages;
+  constexpr uint32_t SB = F8 ? kStageBytesF8 : kStageBytes;
   // the swizzled tiles need 1024-byte alignment
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* const smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -154,9 +187,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (tid == 0) {
     S->abort = 0;
     S->ndef = 0;
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < ST; ++s) {
       mbar_init(&S->full[s], 1);
-      mbar_init(&S->empty[s], 1 + kBndWarps);  // the MMA commit and each row-bound warp
+      // the MMA commit and each row-bound warp; E4M3: the MMA commit only (it follows the
+      // row warps' arrivals on a_ready, after they have read the stage's X k-block)
+      mbar_init(&S->empty[s], F8 ? 1 : 1 + kBndWarps);
+      mbar_init(&S->a_ready[s], kGemmBM);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&S->t_full[b], 1);
@@ -189,34 +225,43 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (long long m = blockIdx.x; ok && m < ntiles; m += gridDim.x) {
         for (int u = 0; ok && u < nunits; ++u) {
           for (int ks = 0; ks < ksteps; ++ks, ++it) {
-            const int s = static_cast<int>(it % kStages);
-            if (it >= kStages && !mbar_wait(&S->empty[s], static_cast<uint32_t>(((it / kStages) + 1) & 1), &S->abort,
-                                            kWaitCycles)) {
+            const int s = static_cast<int>(it % ST);
+            if (it >= ST && !mbar_wait(&S->empty[s], static_cast<uint32_t>(((it / ST) + 1) & 1), &S->abort,
+                                       kWaitCycles)) {
               ok = false;
               set_abort(S, a.st);
               break;
             }
             const int p = ks / nkb, kb = ks - p * nkb;
-            // the lo part (rows klp.. of the image) first, then the hi part
-            const int brow = (nprod == 2 && p == 0 ? a.klp : 0) + u * kGemmBN;
-            const uint32_t sa = sbase + static_cast<uint32_t>(s) * kStageBytes;
-            expect_tx(&S->full[s], kStageBytes);
-            tma_load_2d(sa, &tmX, kb * kGemmBK, static_cast<int>(m * kGemmBM), &S->full[s]);
-            tma_load_2d(sa + kABytes, &tmW, kb * kGemmBK, brow, &S->full[s]);
+            const uint32_t sa = sbase + static_cast<uint32_t>(s) * SB;
+            if constexpr (F8) {
+              // pass 0 (the small products) needs both image planes, pass 1 (X1.W1) only W1
+              const uint8_t* blk = a.img8 + (static_cast<size_t>(u) * nkb + kb) * 2 * kPlaneBytes;
+              expect_tx(&S->full[s], kABytes + (p == 0 ? 2u : 1u) * kPlaneBytes);
+              tma_load_2d(sa, &tmX, kb * kGemmBK, static_cast<int>(m * kGemmBM), &S->full[s]);
+              bulk_load(sa + kOffW1, blk, kPlaneBytes, &S->full[s]);
+              if (p == 0) bulk_load(sa + kOffW2, blk + kPlaneBytes, kPlaneBytes, &S->full[s]);
+            } else {
+              // the lo part (rows klp.. of the image) first, then the hi part
+              const int brow = (nprod == 2 && p == 0 ? a.klp : 0) + u * kGemmBN;
+              expect_tx(&S->full[s], kStageBytes);
+              tma_load_2d(sa, &tmX, kb * kGemmBK, static_cast<int>(m * kGemmBM), &S->full[s]);
+              tma_load_2d(sa + kABytes, &tmW, kb * kGemmBK, brow, &S->full[s]);
+            }
           }
         }
       }
       // leave no copy in flight: the newest phase of every stage used has completed (bounded
       // waits that ignore the abort flag)
       const int never = 0;
-      for (long long k = it - 1; k >= 0 && k >= it - kStages; --k)
-        mbar_wait(&S->full[k % kStages], static_cast<uint32_t>((k / kStages) & 1), &never, kWaitCycles);
+      for (long long k = it - 1; k >= 0 && k >= it - ST; --k)
+        mbar_wait(&S->full[k % ST], static_cast<uint32_t>((k / ST) & 1), &never, kWaitCycles);
     }
     __syncwarp();
   } else if (warp == 1) {
     // ------------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(kGemmBM, kGemmBN);
+      const uint32_t idesc = F8 ? idesc_e4m3(kGemmBM, kGemmBN) : idesc_bf16(kGemmBM, kGemmBN);
       long long it = 0, u = 0;
       bool ok = true;
       for (long long m = blockIdx.x; ok && m < ntiles; m += gridDim.x) {
@@ -231,19 +276,42 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t dt = tmem + static_cast<uint32_t>(b * kGemmBN);
           uint32_t acc = 0;
           for (int ks = 0; ks < ksteps; ++ks, ++it) {
-            const int s = static_cast<int>(it % kStages);
-            if (!mbar_wait(&S->full[s], static_cast<uint32_t>((it / kStages) & 1), &S->abort, kWaitCycles)) {
+            const int s = static_cast<int>(it % ST);
+            const uint32_t par = static_cast<uint32_t>((it / ST) & 1);
+            if (!mbar_wait(&S->full[s], par, &S->abort, kWaitCycles) ||
+                (F8 && !mbar_wait(&S->a_ready[s], par, &S->abort, kWaitCycles))) {
               ok = false;
               set_abort(S, a.st);
               break;
             }
             tc_fence_after();
-            const uint32_t sa = sbase + static_cast<uint32_t>(s) * kStageBytes;
-            const uint64_t ad = sdesc_sw128(sa), bd = sdesc_sw128(sa + kABytes);
+            const uint32_t sa = sbase + static_cast<uint32_t>(s) * SB;
+            if constexpr (F8) {
+              // two K = 32 slices per k-block; no-swizzle canonical planes (8-row groups 512
+              // bytes apart, K-adjacent core matrices 128 bytes apart).  Pass 0 accumulates the
+              // small products X2.W2, X2.W1, X1.W2; pass 1 adds X1.W1.
+              const bool small = ks < nkb;
 #pragma unroll
-            for (int kk = 0; kk < kGemmBK / 16; ++kk) {
-              mma_bf16(dt, ad + 2u * kk, bd + 2u * kk, idesc, acc);
-              acc = 1;
+              for (int kk = 0; kk < kGemmBK / 32; ++kk) {
+                const uint32_t ko = 256u * kk;
+                const uint64_t x1 = smem_desc(sa + kOffX1 + ko, 128, 512), w1 = smem_desc(sa + kOffW1 + ko, 128, 512);
+                if (small) {
+                  const uint64_t x2 = smem_desc(sa + kOffX2 + ko, 128, 512), w2 = smem_desc(sa + kOffW2 + ko, 128, 512);
+                  mma_e4m3(dt, x2, w2, idesc, acc);
+                  mma_e4m3(dt, x2, w1, idesc, 1u);
+                  mma_e4m3(dt, x1, w2, idesc, 1u);
+                } else {
+                  mma_e4m3(dt, x1, w1, idesc, acc);
+                }
+                acc = 1;
+              }
+            } else {
+              const uint64_t ad = sdesc_sw128(sa), bd = sdesc_sw128(sa + kABytes);
+#pragma unroll
+              for (int kk = 0; kk < kGemmBK / 16; ++kk) {
+                mma_bf16(dt, ad + 2u * kk, bd + 2u * kk, idesc, acc);
+                acc = 1;
+              }
             }
             mma_commit(&S->empty[s]);
           }
@@ -277,6 +345,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     long long it = 0;
     int ml = 0;
     bool ok = true;
+    // E4M3: this row's 16-byte chunks in the stage's canonical X1 / X2 planes (chunk j2, the
+    // coordinates [16 j2, 16 j2 + 16) of the k-block, 128 j2 bytes further)
+    const uint32_t xoff = static_cast<uint32_t>((r >> 3) * 512 + (r & 7) * 16);
     for (long long m = blockIdx.x; ok && m < ntiles; m += gridDim.x, ++ml) {
       const int t = ml & 1;
       if (ml >= 2) ok = mbar_wait(&S->b_empty[t], static_cast<uint32_t>(((ml >> 1) + 1) & 1), &S->abort, kWaitCycles);
@@ -287,17 +358,121 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       float P = 0.f, E = 0.f;
       uint32_t nz = 0u;
+      float sc = 1.f, q2 = 0.f, q3 = 0.f;  // E4M3: the row's scale 2^s, ||X2||^2, ||X3||^2 (rounded up)
+      bool big = false;                    // E4M3: an element of the scaled row reached 2^15
       for (int un = 0; ok && un < nunits; ++un) {
         for (int ks = 0; ks < ksteps; ++ks, ++it) {
-          const int s = static_cast<int>(it % kStages);
-          ok = mbar_wait(&S->full[s], static_cast<uint32_t>((it / kStages) & 1), &S->abort, kWaitCycles);
+          const int s = static_cast<int>(it % ST);
+          ok = mbar_wait(&S->full[s], static_cast<uint32_t>((it / ST) & 1), &S->abort, kWaitCycles);
           if (!__all_sync(0xFFFFFFFFu, ok)) {
             ok = false;
             if (lane == 0) set_abort(S, a.st);
             break;
           }
+          if constexpr (F8) {
+            // Convert row r's k-block to E4M3 planes: y = 2^s x (exact), X1 = e4m3(y),
+            // X2 = e4m3(y - X1) (pass 0 only), X3 = y - X1 - X2 (the differences are exact in
+            // binary32 while |y| < 2^15).  The scale comes from the row's first k-block: its
+            // largest |x| maps to [32, 64), leaving a factor 7 below the E4M3 maximum 448; an
+            // element beyond that is saturated and its excess lands in X3 (a wider band).
+            // During pass 0 of the first unit the row is also measured: the norms of y's blocks
+            // (E, as in the bfloat16 path), ||X2|| and ||X3||.
+            uint8_t* const stg = smem + static_cast<uint32_t>(s) * SB;
+            const uint8_t* arow = stg + roff;
+            const bool small = ks < nkb, first = un == 0 && small;
+            if (un == 0 && ks == 0) {
+              float mx = 0.f;
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const uint4 v = *reinterpret_cast<const uint4*>(arow + ((static_cast<uint32_t>(j) ^ rsw) << 4));
+                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) mx = fmaxf(mx, fmaxf(fabsf(bf16_lo(w[e])), fabsf(bf16_hi(w[e]))));
+              }
+              int sx = 0;
+              if (mx > 0.f && isfinite(mx)) sx = min(100, max(-100, 5 - ilogbf(mx)));
+              sc = __uint_as_float(static_cast<uint32_t>(127 + sx) << 23);
+              S->bunscale[t][r] = __uint_as_float(static_cast<uint32_t>(127 - sx) << 23);
+            }
+            float bq[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int j2 = 0; j2 < 4; ++j2) {
+              uint32_t o1[4] = {0u, 0u, 0u, 0u}, o2[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+              for (int hh = 0; hh < 2; ++hh) {
+                const int j = 2 * j2 + hh;
+                const uint4 v = *reinterpret_cast<const uint4*>(arow + ((static_cast<uint32_t>(j) ^ rsw) << 4));
+                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  const float y0 = bf16_lo(w[e]) * sc, y1 = bf16_hi(w[e]) * sc;
+                  const uint32_t b1 = to_e4m3x2(y0, y1);
+                  const float2 f1 = from_e4m3x2(b1);
+                  const float r0 = y0 - f1.x, r1 = y1 - f1.y;
+                  // elements 8 hh + 2e and 8 hh + 2e + 1 of the chunk: bytes of word 2 hh + e / 2
+                  o1[2 * hh + (e >> 1)] |= b1 << (16 * (e & 1));
+                  if (small) {
+                    const uint32_t b2 = to_e4m3x2(r0, r1);
+                    o2[2 * hh + (e >> 1)] |= b2 << (16 * (e & 1));
+                    if (first) {
+                      const float2 f2 = from_e4m3x2(b2);
+                      const float t0 = r0 - f2.x, t1 = r1 - f2.y;
+                      bq[j >> 1] = fmaf(y0, y0, bq[j >> 1]);
+                      bq[j >> 1] = fmaf(y1, y1, bq[j >> 1]);
+                      q2 = __fmaf_ru(f2.x, f2.x, q2);
+                      q2 = __fmaf_ru(f2.y, f2.y, q2);
+                      q3 = __fmaf_ru(t0, t0, q3);
+                      q3 = __fmaf_ru(t1, t1, q3);
+                      nz |= w[e] & 0x7FFF7FFFu;
+                      big |= !(fabsf(y0) < 32768.f) || !(fabsf(y1) < 32768.f);
+                    }
+                  }
+                }
+              }
+              *reinterpret_cast<uint4*>(stg + kOffX1 + xoff + 128u * j2) = make_uint4(o1[0], o1[1], o1[2], o1[3]);
+              if (small)
+                *reinterpret_cast<uint4*>(stg + kOffX2 + xoff + 128u * j2) = make_uint4(o2[0], o2[1], o2[2], o2[3]);
+            }
+            fence_proxy_async();
+            mbar_arrive(&S->a_ready[s]);
+            if (first) {
+              // the E terms of the k-block, as in the bfloat16 path below (with y for x)
+              const float bk = __fadd_ru(__fadd_ru(bq[0], bq[1]), __fadd_ru(bq[2], bq[3]));
+              P = __fadd_ru(P, bk);
+              const float sp = __fmul_ru(sqrtf(__fmul_ru(P, xfac)), 1.00000023841857910156f);
+              const float sb = __fmul_ru(sqrtf(__fmul_ru(bk, xfac)), 1.00000023841857910156f);
+              E = __fmaf_ru(sp, __ldg(WP + ks), E);
+              E = __fmaf_ru(sb, __ldg(WB + ks), E);
+              if (ks == nkb - 1) {
+                uint32_t thr, zero = 0u;
+                if (nz == 0u) {
+                  thr = 0u;
+                  zero = 1u;
+                } else if (!isfinite(P) || !isfinite(E) || !isfinite(q2) || !isfinite(q3) || big || P < qmin) {
+                  thr = 0xFFFFFFFFu;
+                } else {
+                  // B = ca E + cx ||y|| + ksw (||X2|| + ||X3||) + kt0 T0 + c3 ||X3|| + tau_abs,
+                  // T0 = ||X2|| (w1m + w2m) + ||X1|| w2m, ||X1|| <= ||y|| + ||X2|| + ||X3||
+                  const float yu = __fsqrt_ru(__fmul_ru(P, xfac));
+                  const float x2u = __fsqrt_ru(q2), x3u = __fsqrt_ru(q3);
+                  const float x1u = __fadd_ru(__fadd_ru(yu, x2u), x3u);
+                  const float T0 = __fmaf_ru(x2u, __fadd_ru(a.w1m, a.w2m), __fmul_ru(x1u, a.w2m));
+                  float B = __fmaf_ru(ca, E, __fmaf_ru(cx, yu, tau_abs));
+                  B = __fmaf_ru(a.ksw, __fadd_ru(x2u, x3u), B);
+                  B = __fmaf_ru(a.kt0, T0, B);
+                  B = __fmaf_ru(a.c3, x3u, B);
+                  thr = __float_as_uint(B);
+                }
+                S->bthr[t][r] = thr;
+                S->bzero[t][r] = zero;
+                if (count_nonfinite && m * kGemmBM + r < n && !isfinite(P)) atomicAdd(&a.st->nonfinite, 1ull);
+                mbar_arrive(&S->b_full[t]);
+              }
+            }
+            continue;
+          }
           if (un == 0 && ks < nkb) {
-            const uint8_t* arow = smem + static_cast<uint32_t>(s) * kStageBytes + roff;
+            const uint8_t* arow = smem + static_cast<uint32_t>(s) * SB + roff;
             float bq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -375,6 +550,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool every = Bb == 0xFFFFFFFFu;
       const uint32_t thr1 = (every || zero_row) ? 0u : Bb + 1u;  // |v| <= B  <=>  bits(|v|) < bits(B) + 1
       const float Bf = (every || zero_row) ? 0.f : __uint_as_float(Bb);
+      const float unscale = F8 ? S->bunscale[tslot][r] : 1.f;  // E4M3: the accumulators carry 2^s
       mbar_arrive(&S->b_empty[tslot]);
       const long long i = m * kGemmBM + r;
       const bool valid = i < n;
@@ -430,7 +606,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int k = 0; k < 32; ++k) {
                   const int uc = 32 * g + k;
                   if (uc < ncols)
-                    a.proj[i * static_cast<long long>(a.KL) + c0 + uc] = __uint_as_float(vv[k]) * __ldg(a.wnorm + c0 + uc);
+                    a.proj[i * static_cast<long long>(a.KL) + c0 + uc] =
+                        __uint_as_float(vv[k]) * unscale * __ldg(a.wnorm + c0 + uc);
                 }
               }
             }
@@ -635,10 +812,18 @@ cudaError_t launch_hash_gemm(const GemmArgs& a, const void* tmX, const void* tmW
     kern<<<static_cast<unsigned>(grid), kThreads, kSmemBytes, s>>>(a, mx, mw);
     return cudaGetLastError();
   };
-  if (a.mode & kStoreProj) return a.K > 16 ? go(hash_gemm_kernel<uint32_t, 0, true>) : go(hash_gemm_kernel<uint16_t, 0, true>);
-  if (a.K > 16) return go(hash_gemm_kernel<uint32_t, 0, false>);
-  if (a.K == 16) return go(hash_gemm_kernel<uint16_t, 16, false>);
-  return go(hash_gemm_kernel<uint16_t, 0, false>);
+  if (a.fp8) {
+    if (a.mode & kStoreProj)
+      return a.K > 16 ? go(hash_gemm_kernel<uint32_t, 0, true, true>) : go(hash_gemm_kernel<uint16_t, 0, true, true>);
+    if (a.K > 16) return go(hash_gemm_kernel<uint32_t, 0, false, true>);
+    if (a.K == 16) return go(hash_gemm_kernel<uint16_t, 16, false, true>);
+    return go(hash_gemm_kernel<uint16_t, 0, false, true>);
+  }
+  if (a.mode & kStoreProj)
+    return a.K > 16 ? go(hash_gemm_kernel<uint32_t, 0, true, false>) : go(hash_gemm_kernel<uint16_t, 0, true, false>);
+  if (a.K > 16) return go(hash_gemm_kernel<uint32_t, 0, false, false>);
+  if (a.K == 16) return go(hash_gemm_kernel<uint16_t, 16, false, false>);
+  return go(hash_gemm_kernel<uint16_t, 0, false, false>);
 }
 
 cudaError_t launch_recheck_cols(const GemmArgs& a, int nseg, int num_sms, cudaStream_t s) {

@@ -1,10 +1,11 @@
-// Measurement hook: one chain of tcgen05 bfloat16 MMAs on caller-chosen operands.
+// Measurement hook: one chain of tcgen05 MMAs on caller-chosen operands.
 //
-// The tensor-core guard bands (hash_tc.cu, hash_gemm.cu) rest on a model of how one
-// kind::f16 MMA instruction accumulates its 16 products and the accumulator in binary32.
-// This kernel runs D = A . B^T (A 128 x kd, B N x kd, bfloat16, K-major) as kd/16 MMAs of
-// 128 x N x 16 into one TMEM accumulator, exactly like the hash kernels do, and returns D, so
-// that a test can feed chosen sums and check the model against the hardware.
+// The tensor-core guard bands (hash_tc.cu, hash_gemm.cu) rest on a model of how one MMA
+// instruction accumulates its products and the accumulator in binary32.  This kernel runs
+// D = A . B^T (A 128 x kd, B N x kd, K-major) into one TMEM accumulator, exactly like the hash
+// kernels do, and returns D, so that a test can feed chosen sums and check the model against
+// the hardware: bfloat16 operands as kd/16 kind::f16 MMAs of 128 x N x 16, or E4M3 operands
+// as kd/32 kind::f8f6f4 MMAs of 128 x N x 32.
 #include "ace_internal.h"
 #include "tc_ptx.cuh"
 
@@ -15,20 +16,33 @@ using namespace tc;
 
 constexpr long long kProbeWait = 2000000000LL;  // about 1 s at 2 GHz
 
+// FP8: A and B hold E4M3 bytes (kd a multiple of 32); else bfloat16 bit patterns (kd a
+// multiple of 16).
+template <bool FP8>
 __global__ void __launch_bounds__(128, 1)
-    tc_probe_kernel(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, int kd, int N,
+    tc_probe_kernel(const void* __restrict__ Av, const void* __restrict__ Bv, int kd, int N,
                     float* __restrict__ D, int* __restrict__ status) {
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ uint64_t bar;
   __shared__ uint32_t taddr;
+  constexpr int kEb = FP8 ? 1 : 2;  // bytes per element
   uint8_t* const sa = sm;
-  uint8_t* const sb = sm + 128 * kd * 2;
+  uint8_t* const sb = sm + 128 * kd * kEb;
   const int tid = threadIdx.x, warp = tid >> 5;
-  // operands in the K-major, no-swizzle canonical layout (8 x 8 core matrices)
-  for (int e = tid; e < 128 * kd; e += 128)
-    *reinterpret_cast<uint16_t*>(sa + kmajor_offset(e / kd, e % kd, kd)) = A[e];
-  for (int e = tid; e < N * kd; e += 128)
-    *reinterpret_cast<uint16_t*>(sb + kmajor_offset(e / kd, e % kd, kd)) = B[e];
+  // operands in the K-major, no-swizzle canonical layout (core matrices of 8 rows x 16 bytes)
+  if constexpr (FP8) {
+    const uint8_t* A = static_cast<const uint8_t*>(Av);
+    const uint8_t* B = static_cast<const uint8_t*>(Bv);
+    for (int e = tid; e < 128 * kd; e += 128) sa[kmajor_offset8(e / kd, e % kd, kd)] = A[e];
+    for (int e = tid; e < N * kd; e += 128) sb[kmajor_offset8(e / kd, e % kd, kd)] = B[e];
+  } else {
+    const uint16_t* A = static_cast<const uint16_t*>(Av);
+    const uint16_t* B = static_cast<const uint16_t*>(Bv);
+    for (int e = tid; e < 128 * kd; e += 128)
+      *reinterpret_cast<uint16_t*>(sa + kmajor_offset(e / kd, e % kd, kd)) = A[e];
+    for (int e = tid; e < N * kd; e += 128)
+      *reinterpret_cast<uint16_t*>(sb + kmajor_offset(e / kd, e % kd, kd)) = B[e];
+  }
   fence_proxy_async();
   if (tid == 0) {
     mbar_init(&bar, 1);
@@ -43,11 +57,15 @@ __global__ void __launch_bounds__(128, 1)
   tc_fence_after();
   const uint32_t tmem = taddr;
   if (tid == 0) {
-    const uint32_t idesc = idesc_bf16(128, N);
-    const uint32_t sbo = static_cast<uint32_t>(kd) * 16u;
-    for (int ks = 0; ks < kd / 16; ++ks)
-      mma_bf16(tmem, smem_desc(smem_u32(sa) + 256u * ks, 128, sbo), smem_desc(smem_u32(sb) + 256u * ks, 128, sbo),
-               idesc, ks > 0 ? 1u : 0u);
+    // one instruction spans two K-adjacent core matrices (32 bytes of each row)
+    const uint32_t sbo = static_cast<uint32_t>(kd) * 8u * kEb;
+    const int nk = kd / (32 / kEb);
+    for (int ks = 0; ks < nk; ++ks) {
+      const uint64_t ad = smem_desc(smem_u32(sa) + 256u * ks, 128, sbo);
+      const uint64_t bd = smem_desc(smem_u32(sb) + 256u * ks, 128, sbo);
+      if constexpr (FP8) mma_e4m3(tmem, ad, bd, idesc_e4m3(128, N), ks > 0 ? 1u : 0u);
+      else mma_bf16(tmem, ad, bd, idesc_bf16(128, N), ks > 0 ? 1u : 0u);
+    }
     mma_commit(&bar);
   }
   __syncwarp();
@@ -76,13 +94,16 @@ __global__ void __launch_bounds__(128, 1)
 
 }  // namespace
 
-cudaError_t launch_tc_probe(const uint16_t* A, const uint16_t* B, int kd, int N, float* D, int* status,
+cudaError_t launch_tc_probe(const void* A, const void* B, int kd, int N, bool fp8, float* D, int* status,
                             cudaStream_t s) {
-  const int smem = (128 + N) * kd * 2;
-  cudaError_t e = cudaFuncSetAttribute(tc_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  tc_probe_kernel<<<1, 128, smem, s>>>(A, B, kd, N, D, status);
-  return cudaGetLastError();
+  const int smem = (128 + N) * kd * (fp8 ? 1 : 2);
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<1, 128, smem, s>>>(A, B, kd, N, D, status);
+    return cudaGetLastError();
+  };
+  return fp8 ? go(tc_probe_kernel<true>) : go(tc_probe_kernel<false>);
 }
 
 }  // namespace ace

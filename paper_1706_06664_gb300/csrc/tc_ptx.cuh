@@ -1,5 +1,6 @@
 // Inline-PTX wrappers for the sm_103a tensor-core path: mbarriers, TMEM allocation,
-// tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulators in TMEM), tcgen05.commit,
+// tcgen05.mma (kind::f16 with BF16 inputs, kind::f8f6f4 with E4M3 inputs; FP32 accumulators
+// in TMEM), tcgen05.commit,
 // tcgen05.ld, and the shared-memory / instruction descriptors.
 #pragma once
 
@@ -78,11 +79,24 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
          (static_cast<uint32_t>(M >> 4) << 24);
 }
 
+// Instruction descriptor of kind::f8f6f4 with D = F32 and A = B = E4M3 (format code 0), both
+// K-major, M x N.  One instruction covers K = 32 (32 bytes of each operand row).
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
+}
+
 // Byte offset of element (r, k) in the K-major, no-swizzle canonical layout of 16-bit
 // elements: 8 x 8 core matrices (8 rows of 16 bytes), K-adjacent core matrices LBO = 128
 // bytes apart, 8-row groups SBO = kt * 16 bytes apart (kt = K extent, a multiple of 8).
 __host__ __device__ constexpr uint32_t kmajor_offset(int r, int k, int kt) {
   return static_cast<uint32_t>((r >> 3) * (kt * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// Byte offset of element (r, k) in the same layout for 8-bit elements: core matrices of 8 rows
+// of 16 bytes (16 elements), K-adjacent core matrices 128 bytes apart, 8-row groups kt * 8
+// bytes apart (kt = K extent, a multiple of 16).
+__host__ __device__ constexpr uint32_t kmajor_offset8(int r, int k, int kt) {
+  return static_cast<uint32_t>((r >> 3) * (kt * 8) + (k >> 4) * 128 + (r & 7) * 16 + (k & 15));
 }
 
 // ---- MMA, commit, TMEM load --------------------------------------------------------------
@@ -91,6 +105,14 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
