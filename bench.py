@@ -390,25 +390,34 @@ def _e2e(args, det, host_batches, stream, dist, dev, n, ws):
             "d2h_bytes_per_step": int(o_sc.nbytes + o_su.nbytes + o_fl.nbytes)}
 
 
-def serving(seed: int = 31, pool_points: int = 1 << 20, n_det: int = 64, n_req: int = 3000) -> dict:
+def serving(seed: int = 31, window_points: int = 1 << 20, n_windows: int = 4, n_det: int = 64,
+            n_req: int = 3000) -> dict:
     """Streaming-serving shape: 64 detectors (d=128, K=15, L=50), request sizes log-uniform
-    in [1, 8192], inserts and scores 50/50 on random detectors, points from a window of the
-    drifting stream.  Capacity from the better of two closed-loop bursts (a single burst
-    varied by up to 2x from run to run); then Poisson arrivals at 0.5x and 0.8x that rate,
-    paced by a spin that yields the CPU; latency = submission to completion (outputs in host
-    memory).  Run in a process of its own (serving_isolated) so that no state of the other
-    measurements carries over."""
+    in [1, 8192], inserts and scores 50/50 on random detectors, points from four windows of
+    1,048,576 consecutive points of the 100,000,000-point drifting stream, at its start, a
+    quarter, half and three quarters of the way (so requests see means from across the
+    drift).  Capacity from the better of two closed-loop bursts (a single burst varied by up to
+    2x from run to run); then Poisson arrivals at 0.5x, 0.8x and 1.0x that rate, paced by a
+    spin that yields the CPU; latency = submission to completion (outputs in host memory).  Run
+    in a process of its own (serving_isolated) so that no state of the other measurements
+    carries over."""
     import torch
     from paper_1706_06664_gb300 import ace, workloads
     d, K, L = 128, 15, 50
+    total = 100_000_000
     dets = [ace.Detector(d, K, L, seed=1000 + i) for i in range(n_det)]
-    pool = torch.from_numpy(workloads.stream_chunk(seed, 0, pool_points, total=100_000_000, d=d)).pin_memory().numpy()
+    starts = [w * (total // n_windows) for w in range(n_windows)]
+    pool = torch.from_numpy(np.concatenate([workloads.stream_chunk(seed, st, window_points, total=total, d=d)
+                                            for st in starts])).pin_memory().numpy()
+    pool_points = pool.shape[0]
     rng = np.random.default_rng(seed)
     srv = ace.Server(dets, mem_budget_bytes=1 << 30)
 
     def workload(count, salt):
         sizes = workloads.request_sizes(seed + salt, count)
-        offs = np.concatenate([[0], np.cumsum(sizes)[:-1]]) % (pool_points - 8192)
+        # a random window, then consecutive requests walk through it
+        win = rng.integers(0, n_windows, size=count)
+        offs = win * window_points + (np.concatenate([[0], np.cumsum(sizes)[:-1]]) % (window_points - 8192))
         ops = rng.integers(0, 2, size=count)  # 0 insert, 1 score
         dsel = rng.integers(0, n_det, size=count)
         out = torch.empty(int(sizes.sum()) * 13 + 64 * (count + 1), dtype=torch.uint8).pin_memory().numpy()
@@ -446,16 +455,18 @@ def serving(seed: int = 31, pool_points: int = 1 << 20, n_det: int = 64, n_req: 
         if best is None or float(w[0].sum()) / el > best[1]:
             best = (n_req / el, float(w[0].sum()) / el, lat)
     cap_req, cap_pts, lat = best
-    res = {"workload": f"drifting stream d={d} K={K} L={L}, {n_det} detectors, requests log-uniform 1-8192, "
-                       f"50/50 insert/score, {n_req} requests per run",
+    res = {"workload": f"drifting stream d={d} K={K} L={L} ({total} points; requests drawn from {n_windows} "
+                       f"windows of {window_points} points at {starts}), {n_det} detectors, requests log-uniform "
+                       f"1-8192, 50/50 insert/score, {n_req} requests per run",
            "capacity": {"points_per_s": cap_pts, "requests_per_s": cap_req,
                         "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3)}}
-    for f in (0.5, 0.8):
+    for f in (0.5, 0.8, 1.0):
         w = workload(n_req, 3 + int(f * 10))
         arrivals = np.cumsum(rng.exponential(1.0 / (f * cap_req), size=n_req))
         lat, el = submit_all(*w, arrivals=arrivals)
         res[f"load_{f}"] = {"points_per_s": float(w[0].sum()) / el, "p50_ms": float(np.percentile(lat, 50) * 1e3),
                             "p99_ms": float(np.percentile(lat, 99) * 1e3)}
+    res["scheduler"] = srv.info()  # threads; requests admitted inside another insert's launch set
     srv.close()
     for dd in dets:
         dd.close()

@@ -258,13 +258,19 @@ enum { ACE_OP_INSERT = 0, ACE_OP_SCORE = 1, ACE_OP_INSERT_SCORE = 2 };
  * ACE_OP_SCORE (query phase and §5.3 rule) or ACE_OP_INSERT_SCORE — on detector `det` with
  * X_host (n x d, pinned for asynchrony) and optional output buffers (ignored for inserts),
  * and returns a ticket at once; X_host and the outputs must stay valid until the ticket is
- * waited for.  A scheduler thread admits queued requests as slots (two per detector) and
- * memory free up; each detector's requests run in submission order on its own stream, so
- * every result is the same as in a run of that detector's requests alone, while different
- * detectors overlap on the device.  ace_server_wait blocks until the ticket's request has
- * completed and returns its latency from submission to completion in seconds (or its error
- * code); each ticket is waited for once.  ace_server_drain waits for everything submitted;
- * ace_server_destroy drains, stops the scheduler and releases the server (not the detectors).
+ * waited for.  Up to four scheduler threads (detector i belongs to thread i mod their number)
+ * admit queued requests as slots (two per detector) and memory free up; each detector's
+ * requests run in submission order on its own stream, so every result is the same as in a
+ * run of that detector's requests alone, while different detectors overlap on the device.
+ * Inserts that follow one another in a detector's order (no other request of it between them;
+ * not on a windowed detector) are admitted together as one launch set of up to 65,536 points,
+ * which leaves the same counts as inserting them one by one.  A detector may appear only once.
+ * ace_server_wait blocks until the ticket's request has completed and returns its latency from
+ * submission to completion in seconds (or its error code); each ticket is waited for once.
+ * ace_server_drain waits for everything submitted; ace_server_destroy drains, stops the
+ * scheduler threads and releases the server (not the detectors).  ace_server_info reports the
+ * number of scheduler threads and how many requests were admitted inside another's launch
+ * set (either pointer may be NULL).
  */
 typedef struct ace_server_s* ace_server;
 int ace_server_create(const ace_handle* dets, int n_dets, size_t mem_budget_bytes, ace_server* out);
@@ -273,6 +279,7 @@ int ace_server_submit(ace_server s, int det, int op, const void* X_host, int64_t
 int ace_server_wait(ace_server s, uint64_t ticket, double* latency_s);
 int ace_server_drain(ace_server s);
 int ace_server_destroy(ace_server s);
+int ace_server_info(ace_server s, int* threads, uint64_t* coalesced);
 
 /*
  * ace_insert_score_host_async — ace_insert_score_host without the wait: enqueues the copy

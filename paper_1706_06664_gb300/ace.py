@@ -25,7 +25,7 @@ EXPORTS = [
     "ace_create", "ace_create_ex", "ace_create_with_projection", "ace_destroy", "ace_reset", "ace_set_precision",
     "ace_insert", "ace_score", "ace_insert_score", "ace_insert_score_host",
     "ace_insert_score_host_async", "ace_host_wait", "ace_delete", "ace_project", "ace_hash",
-    "ace_batch_insert_score", "ace_server_create", "ace_server_submit", "ace_server_wait", "ace_server_drain", "ace_server_destroy", "ace_stats",
+    "ace_batch_insert_score", "ace_server_create", "ace_server_submit", "ace_server_wait", "ace_server_drain", "ace_server_destroy", "ace_server_info", "ace_stats",
     "ace_get_counts", "ace_get_projection", "ace_get_shape", "ace_last_error", "ace_version",
     "ace_profile_enable", "ace_profile_phases", "ace_profile_read", "ace_insert_score_noalloc",
     "ace_tc_probe", "ace_tc_probe_fp8", "ace_save_size", "ace_save", "ace_load", "ace_window_enable", "ace_set_graph",
@@ -94,6 +94,7 @@ def load_library(path: str = LIB_PATH):
             "ace_server_wait": ([P, ctypes.c_uint64, P], i32),
             "ace_server_drain": ([P], i32),
             "ace_server_destroy": ([P], i32),
+            "ace_server_info": ([P, P, P], i32),
             "ace_insert_score_noalloc": ([H, P, i64, i32, f64, P, P, P, P], i32),
             "ace_hash": ([H, P, i64, i32, P, P], i32),
             "ace_stats": ([H, P, ctypes.POINTER(ace_stats_t)], i32),
@@ -436,6 +437,12 @@ class Server:
 
     def drain(self):
         _check(load_library().ace_server_drain(self._h))
+
+    def info(self) -> dict:
+        """Scheduler threads, and requests admitted inside another request's launch set."""
+        t, c = ctypes.c_int(), ctypes.c_uint64()
+        _check(load_library().ace_server_info(self._h, ctypes.byref(t), ctypes.byref(c)))
+        return {"threads": t.value, "coalesced": c.value}
 
     def close(self):
         if self._h:

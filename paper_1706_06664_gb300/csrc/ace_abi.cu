@@ -503,10 +503,13 @@ double e4m3_value(uint8_t b) {
 // value; columns already scaled by 2^-e_c to norms in [1/2, 1)).  Each image column v is scaled
 // again by 2^f (its largest |v_i| to [128, 256)) and split as W1 = e4m3(2^f v), W2 = e4m3(2^f v
 // - W1), W3 = the rest (nonzero only where an element falls into E4M3's subnormal range).  The
-// accumulator of column c then holds 2^(s + f) x.v for a row scaled by 2^s.  Guard terms (one
-// MMA instruction of K = 32 adds its 32 products and the accumulator with an error of at most
-// kF8Acc * 2^-23 times the sum of their magnitudes, the model tests/test_gpu_tc_model.py checks
-// on the device; normalised-column units, the bound of column c being B colf[c]):
+// accumulator of column c then holds 2^(s + f) x.v for a row scaled by 2^s.  Guard terms
+// (normalised-column units, the bound of column c being B colf[c]).  One kind::f8f6f4
+// instruction adds 33 addends (32 products and the accumulator): aligned to the largest
+// exponent 2^E with two bits kept below its last place, each loses less than 2^(E-25), and the
+// truncation of the sum to binary32 less than one unit in its last place, so the error is at
+// most (33/4 + 1) 2^-23 = 9.25 2^-23 times the sum of their magnitudes (the same model as the
+// 5.25 of kind::f16's 17 addends; tests/test_gpu_tc_model.py checks it on the device):
 //   pass 1 (X1.W1, S8 = dp/32 instructions): E over y's prefix and block norms with W1's
 //     profile, plus (||X2|| + ||X3||) sum_t (WP_t^1/2 + WB_t^1/2) for ||X1_S|| <= ||y_S|| +
 //     ||y - X1||, plus S8 T0 for the pass-0 total the accumulator carries;
@@ -514,7 +517,7 @@ double e4m3_value(uint8_t b) {
 //     small products;
 //   dropped: ||X3|| ||v|| + ||X1 + X2|| ||W3|| <= (||X3|| + rres (||y|| + ||X3||)) colf;
 //   the binary64 reference (gamma64_d ||y||).
-constexpr double kF8Acc = 5.25;
+constexpr double kF8Acc = 9.25;
 int plan_gemm_fp8(ace_detector* h, const std::vector<uint16_t>& img, const std::vector<int>& cexp, int dp, int tpu,
                   int nunits, int klp) {
   h->gemm8_ok = false;
@@ -1501,13 +1504,25 @@ int ace_host_wait(ace_handle h) {
   return rc;
 }
 
+// A piece of host X: n rows at X.
+struct HostSeg {
+  const void* X;
+  int64_t n;
+};
+
 // One host-buffer batch on `stream`: op ACE_OP_INSERT, ACE_OP_SCORE or ACE_OP_INSERT_SCORE.
+// With `segs` (inserts only), the batch is the concatenation of nseg pieces of host X (n
+// their total; X_host unused): each piece is copied to its place in the staging buffer and
+// the batch is hashed and counted as one, which gives the counts of inserting the pieces one
+// after another (counts do not depend on the order of points).
 static int enqueue_host_batch(ace_handle h, int op, const void* X_host, int64_t n, int dtype, double alpha,
-                              double* scores_host, uint32_t* sums_host, uint8_t* flags_host, void* stream) {
+                              double* scores_host, uint32_t* sums_host, uint8_t* flags_host, void* stream,
+                              const HostSeg* segs = nullptr, int nseg = 0) {
   if (op != ACE_OP_INSERT && op != ACE_OP_SCORE && op != ACE_OP_INSERT_SCORE)
     return fail(ACE_ERR_ARG, "unknown operation %d", op);
+  if (segs && op != ACE_OP_INSERT) return fail(ACE_ERR_ARG, "only inserts take several pieces");
   const bool do_insert = op != ACE_OP_SCORE, do_score = op != ACE_OP_INSERT;
-  int rc = check_x(h, X_host, n, dtype);
+  int rc = check_x(h, segs ? segs[0].X : X_host, n, dtype);
   if (rc) return rc;
   if (!std::isfinite(alpha)) return fail(ACE_ERR_ARG, "alpha must be finite");
   if (do_insert && h->n_ins + static_cast<uint64_t>(n) > 0xFFFFFFFFull)
@@ -1579,19 +1594,34 @@ static int enqueue_host_batch(ace_handle h, int op, const void* X_host, int64_t 
   const int kMaxChunks = static_cast<int>(sizeof(sl.chunk) / sizeof(sl.chunk[0]));
   long long chunk = std::max<long long>(kMinChunk, (static_cast<long long>(n) + 7) / 8);
   chunk = (chunk + 127) / 128 * 128;
-  const int nch = static_cast<int>(std::min<long long>((n + chunk - 1) / chunk, kMaxChunks));
+  int nch = static_cast<int>(std::min<long long>((n + chunk - 1) / chunk, kMaxChunks));
   chunk = (n + nch - 1) / nch;
   chunk = (chunk + 127) / 128 * 128;
+  if (segs) {  // pieces: one copy each, then the batch is hashed as one chunk
+    nch = 1;
+    chunk = n;
+  }
   if (do_insert && h->ring && n > h->win_cap)
     return fail(ACE_ERR_ARG, "a batch of %lld points is larger than the window of %lld", static_cast<long long>(n),
                 h->win_cap);
   ACE_CUDA(cudaStreamWaitEvent(h->cstream, sl.done, 0));
-  for (int c = 0; c < nch; ++c) {
-    const long long c0 = c * chunk, nc = std::min<long long>(chunk, n - c0);
-    if (nc <= 0) break;
-    ACE_CUDA(cudaMemcpyAsync(static_cast<char*>(sl.x) + c0 * row, static_cast<const char*>(X_host) + c0 * row,
-                             static_cast<size_t>(nc) * row, cudaMemcpyHostToDevice, h->cstream));
-    ACE_CUDA(cudaEventRecord(sl.chunk[c], h->cstream));
+  if (segs) {
+    size_t off = 0;
+    for (int i = 0; i < nseg; ++i) {
+      if (segs[i].n > 0)
+        ACE_CUDA(cudaMemcpyAsync(static_cast<char*>(sl.x) + off, segs[i].X, static_cast<size_t>(segs[i].n) * row,
+                                 cudaMemcpyHostToDevice, h->cstream));
+      off += static_cast<size_t>(segs[i].n) * row;
+    }
+    ACE_CUDA(cudaEventRecord(sl.chunk[0], h->cstream));
+  } else {
+    for (int c = 0; c < nch; ++c) {
+      const long long c0 = c * chunk, nc = std::min<long long>(chunk, n - c0);
+      if (nc <= 0) break;
+      ACE_CUDA(cudaMemcpyAsync(static_cast<char*>(sl.x) + c0 * row, static_cast<const char*>(X_host) + c0 * row,
+                               static_cast<size_t>(nc) * row, cudaMemcpyHostToDevice, h->cstream));
+      ACE_CUDA(cudaEventRecord(sl.chunk[c], h->cstream));
+    }
   }
   const bool simt = pick_engine(h, dtype == ACE_BF16, sl.x) == Engine::kSimt;
   if (do_insert && (rc = window_prepare(h, n, s))) return rc;
@@ -1640,14 +1670,18 @@ int ace_insert_score_host(ace_handle h, const void* X_host, int64_t n, int dtype
 }
 
 // ---------------------------------------------------------------------------------------
-// Request server (continuous batching over several detectors).  Requests are kept in
-// submission order; a scheduler thread admits the first admissible one whenever a slot or
-// memory frees up: at most two per detector are in flight (its two staging slots), their
-// staged bytes stay within the budget, and a detector whose oldest waiting request cannot
-// start yet keeps its later requests waiting too, so each detector sees its requests in
-// submission order — its results are the same alone and in any mix.  Each detector runs on
-// its own stream, so different detectors' work overlaps on the device; completion is
-// stamped by a host callback on that stream.
+// Request server (continuous batching over several detectors).  The detectors are divided
+// among a few scheduler threads (detector i belongs to thread i mod W), each with its own
+// queue of requests in submission order; a thread admits the first admissible request of its
+// queue whenever a slot or memory frees up: at most two per detector are in flight (its two
+// staging slots), the staged bytes of all threads stay within the budget, and a detector whose
+// oldest waiting request cannot start keeps its later requests waiting too, so each detector
+// sees its requests in submission order — its results are the same alone and in any mix.
+// Inserts that follow one another in a detector's order (no other request of that detector
+// between them) are admitted together as one launch set (their points copied side by side,
+// hashed and counted once), which gives the same counts as inserting them one by one.  Each
+// detector runs on its own stream, so different detectors' work overlaps on the device;
+// completion is stamped by a host callback on that stream.
 // ---------------------------------------------------------------------------------------
 }  // extern "C"
 
@@ -1666,70 +1700,126 @@ struct ace_server_s {
     int rc = ACE_OK;
     bool done = false;
     ace_server_s* srv = nullptr;
+    std::vector<Req*> merged;  // inserts admitted with this one (completed with it)
   };
+  static constexpr int kMaxWorkers = 4;
+  static constexpr int64_t kMergeMax = 65536;  // points of one coalesced insert
   std::vector<ace_handle> dets;
   std::vector<cudaStream_t> streams;
   std::vector<int> inflight;
   size_t budget = 0, bytes_inflight = 0;
-  std::deque<Req*> pending;
+  std::vector<std::deque<Req*>> pending;  // per scheduler thread
   std::unordered_map<uint64_t, Req*> reqs;
   uint64_t next_id = 1;
   int device = 0;
   std::mutex mu;
   std::condition_variable cv;
-  std::thread worker;
+  std::vector<std::thread> workers;
   bool stop = false;
+  uint64_t coalesced = 0;  // requests admitted as part of another's launch set
+
+  int nworkers() const { return static_cast<int>(pending.size()); }
 
   static void CUDART_CB on_done(void* p) {
     Req* r = static_cast<Req*>(p);
     ace_server_s* s = r->srv;
     std::lock_guard<std::mutex> lk(s->mu);
-    r->t_done = std::chrono::steady_clock::now();
-    r->done = true;
+    const auto now = std::chrono::steady_clock::now();
     s->inflight[r->det] -= 1;
     s->bytes_inflight -= r->bytes;
+    r->t_done = now;
+    r->done = true;
+    for (Req* q : r->merged) {
+      s->bytes_inflight -= q->bytes;
+      q->t_done = now;
+      q->done = true;
+    }
     s->cv.notify_all();
   }
 
-  // The first admissible waiting request (caller holds mu), or nullptr.
-  Req* pick() {
+  // The first admissible waiting request of thread w's queue (caller holds mu), or nullptr;
+  // for an insert, the inserts that directly follow it in its detector's order join it.
+  Req* pick(int w) {
+    std::deque<Req*>& q = pending[w];
     std::vector<char> held(dets.size(), 0);
-    for (auto it = pending.begin(); it != pending.end(); ++it) {
+    for (auto it = q.begin(); it != q.end(); ++it) {
       Req* r = *it;
       if (held[r->det]) continue;
       const bool slot = inflight[r->det] < 2;
       const bool mem = bytes_inflight == 0 || bytes_inflight + r->bytes <= budget;
-      if (slot && mem) {
-        pending.erase(it);
-        return r;
+      if (!(slot && mem)) {
+        held[r->det] = 1;  // keep this detector's later requests behind this one
+        continue;
       }
-      held[r->det] = 1;  // keep this detector's later requests behind this one
+      const auto first = it;
+      size_t bytes = r->bytes;
+      int64_t n = r->n;
+      if (r->op == ACE_OP_INSERT && !dets[r->det]->ring) {
+        for (auto jt = std::next(it); jt != q.end(); ++jt) {
+          Req* o = *jt;
+          if (o->det != r->det) continue;
+          if (o->op != ACE_OP_INSERT || o->dtype != r->dtype || n + o->n > kMergeMax ||
+              bytes_inflight + bytes + o->bytes > budget)
+            break;
+          r->merged.push_back(o);
+          bytes += o->bytes;
+          n += o->n;
+        }
+      }
+      q.erase(first);
+      for (Req* o : r->merged) q.erase(std::find(q.begin(), q.end(), o));
+      coalesced += r->merged.size();
+      return r;
     }
     return nullptr;
   }
 
-  void run() {
+  void release(Req* r, int rc) {  // caller holds mu: a request that could not be enqueued
+    const auto now = std::chrono::steady_clock::now();
+    inflight[r->det] -= 1;
+    bytes_inflight -= r->bytes;
+    r->rc = rc;
+    r->t_done = now;
+    r->done = true;
+    for (Req* q : r->merged) {
+      bytes_inflight -= q->bytes;
+      q->rc = rc;
+      q->t_done = now;
+      q->done = true;
+    }
+    cv.notify_all();
+  }
+
+  void run(int w) {
     cudaSetDevice(device);
+    std::vector<HostSeg> segs;
     std::unique_lock<std::mutex> lk(mu);
     for (;;) {
       Req* r = nullptr;
-      cv.wait(lk, [&] { return (r = pick()) != nullptr || (stop && pending.empty()); });
+      cv.wait(lk, [&] { return (r = pick(w)) != nullptr || (stop && pending[w].empty()); });
       if (!r) break;
       inflight[r->det] += 1;
       bytes_inflight += r->bytes;
+      for (Req* q : r->merged) bytes_inflight += q->bytes;
       lk.unlock();
-      int rc = enqueue_host_batch(dets[r->det], r->op, r->X, r->n, r->dtype, r->alpha, r->scores, r->sums, r->flags,
-                                  streams[r->det]);
+      int rc;
+      if (r->merged.empty()) {
+        rc = enqueue_host_batch(dets[r->det], r->op, r->X, r->n, r->dtype, r->alpha, r->scores, r->sums, r->flags,
+                                streams[r->det]);
+      } else {
+        segs.clear();
+        int64_t n = r->n;
+        segs.push_back({r->X, r->n});
+        for (Req* q : r->merged) {
+          segs.push_back({q->X, q->n});
+          n += q->n;
+        }
+        rc = enqueue_host_batch(dets[r->det], ACE_OP_INSERT, nullptr, n, r->dtype, 1.0, nullptr, nullptr, nullptr,
+                                streams[r->det], segs.data(), static_cast<int>(segs.size()));
+      }
       if (rc == ACE_OK && cudaLaunchHostFunc(streams[r->det], on_done, r) != cudaSuccess) rc = ACE_ERR_CUDA;
       lk.lock();
-      if (rc != ACE_OK) {
-        r->rc = rc;
-        r->t_done = std::chrono::steady_clock::now();
-        r->done = true;
-        inflight[r->det] -= 1;
-        bytes_inflight -= r->bytes;
-        cv.notify_all();
-      }
+      if (rc != ACE_OK) release(r, rc);
     }
   }
 };
@@ -1741,11 +1831,15 @@ int ace_server_create(const ace_handle* dets, int n_dets, size_t mem_budget_byte
   *out = nullptr;
   for (int i = 0; i < n_dets; ++i)
     if (!dets[i]) return fail(ACE_ERR_ARG, "detector %d is NULL", i);
+  for (int i = 0; i < n_dets; ++i)
+    for (int j = 0; j < i; ++j)
+      if (dets[i] == dets[j]) return fail(ACE_ERR_ARG, "detector %d appears twice", i);
   ace_server_s* s = new (std::nothrow) ace_server_s();
   if (!s) return fail(ACE_ERR_OOM, "host allocation failed");
   s->dets.assign(dets, dets + n_dets);
   s->inflight.assign(n_dets, 0);
   s->budget = mem_budget_bytes;
+  s->pending.resize(std::min(n_dets, ace_server_s::kMaxWorkers));
   cudaGetDevice(&s->device);
   s->streams.assign(n_dets, nullptr);
   for (int i = 0; i < n_dets; ++i) {
@@ -1757,7 +1851,7 @@ int ace_server_create(const ace_handle* dets, int n_dets, size_t mem_budget_byte
       return cuda_fail(e, "server stream");
     }
   }
-  s->worker = std::thread([s] { s->run(); });
+  for (int w = 0; w < s->nworkers(); ++w) s->workers.emplace_back([s, w] { s->run(w); });
   *out = s;
   return ACE_OK;
 }
@@ -1788,7 +1882,7 @@ int ace_server_submit(ace_server s, int det, int op, const void* X_host, int64_t
     std::lock_guard<std::mutex> lk(s->mu);
     r->id = s->next_id++;
     s->reqs[r->id] = r;
-    s->pending.push_back(r);
+    s->pending[det % s->nworkers()].push_back(r);
   }
   s->cv.notify_all();
   *ticket = r->id;
@@ -1814,11 +1908,20 @@ int ace_server_drain(ace_server s) {
   if (!s) return fail(ACE_ERR_ARG, "server is NULL");
   std::unique_lock<std::mutex> lk(s->mu);
   s->cv.wait(lk, [&] {
-    if (!s->pending.empty()) return false;
+    for (const auto& q : s->pending)
+      if (!q.empty()) return false;
     for (int v : s->inflight)
       if (v) return false;
     return true;
   });
+  return ACE_OK;
+}
+
+int ace_server_info(ace_server s, int* threads, uint64_t* coalesced) {
+  if (!s) return fail(ACE_ERR_ARG, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (threads) *threads = s->nworkers();
+  if (coalesced) *coalesced = s->coalesced;
   return ACE_OK;
 }
 
@@ -1830,7 +1933,8 @@ int ace_server_destroy(ace_server s) {
     s->stop = true;
   }
   s->cv.notify_all();
-  if (s->worker.joinable()) s->worker.join();
+  for (auto& t : s->workers)
+    if (t.joinable()) t.join();
   for (auto st : s->streams) {
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);

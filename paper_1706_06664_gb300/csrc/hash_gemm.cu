@@ -125,6 +125,15 @@ __device__ __forceinline__ float2 from_e4m3x2(uint32_t v) {
   return __half22float2(__half2(h));
 }
 
+// y rounded to four significant bits (half a unit of the fourth bit added to the pattern, the
+// lower bits cleared: the carry moves into the exponent when needed), or 0 below 2^-6; an E4M3
+// value whenever |y| < 448.  Non-finite y stays non-finite (such rows are resolved exactly).
+__device__ __forceinline__ float split4(float y) {
+  const uint32_t b = __float_as_uint(y);
+  const float h = __uint_as_float((b + 0x00080000u) & 0xFFF00000u);
+  return fabsf(y) < 0.015625f ? 0.f : h;
+}
+
 __device__ __forceinline__ void tma_prefetch(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
@@ -370,13 +379,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           if constexpr (F8) {
-            // Convert row r's k-block to E4M3 planes: y = 2^s x (exact), X1 = e4m3(y),
-            // X2 = e4m3(y - X1) (pass 0 only), X3 = y - X1 - X2 (the differences are exact in
-            // binary32 while |y| < 2^15).  The scale comes from the row's first k-block: its
-            // largest |x| maps to [32, 64), leaving a factor 7 below the E4M3 maximum 448; an
-            // element beyond that is saturated and its excess lands in X3 (a wider band).
+            // Convert row r's k-block to E4M3 planes.  y = 2^s x (exact).  X1 = y rounded to
+            // four significant bits by integer arithmetic on its binary32 pattern (add half a
+            // unit of the fourth bit, clear the rest: round half away from zero), or 0 where
+            // |y| < 2^-6 (below E4M3's normal range); so X1 is an E4M3 value and its conversion
+            // is exact.  X2 = y - X1 is exact in binary32 and has at most four significant bits:
+            // its conversion is exact too, except in E4M3's subnormal range (spacing 2^-9),
+            // where the rounding error X3 = (y - X1) - e4m3(y - X1) is measured.  Only the
+            // conversions themselves use the conversion unit, one per pair of values and plane.
+            // The scale comes from the row's first k-block (its largest |x| to [32, 64)); a row
+            // with |y| >= 448 anywhere (beyond E4M3's range) has every column resolved exactly.
             // During pass 0 of the first unit the row is also measured: the norms of y's blocks
-            // (E, as in the bfloat16 path), ||X2|| and ||X3||.
+            // (E, as in the bfloat16 path), ||e4m3(X2)|| and ||X3||.
             uint8_t* const stg = smem + static_cast<uint32_t>(s) * SB;
             const uint8_t* arow = stg + roff;
             const bool small = ks < nkb, first = un == 0 && small;
@@ -406,12 +420,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                   const float y0 = bf16_lo(w[e]) * sc, y1 = bf16_hi(w[e]) * sc;
-                  const uint32_t b1 = to_e4m3x2(y0, y1);
-                  const float2 f1 = from_e4m3x2(b1);
-                  const float r0 = y0 - f1.x, r1 = y1 - f1.y;
+                  const float h0 = split4(y0), h1 = split4(y1);
+                  const uint32_t b1 = to_e4m3x2(h0, h1);
                   // elements 8 hh + 2e and 8 hh + 2e + 1 of the chunk: bytes of word 2 hh + e / 2
                   o1[2 * hh + (e >> 1)] |= b1 << (16 * (e & 1));
                   if (small) {
+                    const float r0 = y0 - h0, r1 = y1 - h1;
                     const uint32_t b2 = to_e4m3x2(r0, r1);
                     o2[2 * hh + (e >> 1)] |= b2 << (16 * (e & 1));
                     if (first) {
@@ -424,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                       q3 = __fmaf_ru(t0, t0, q3);
                       q3 = __fmaf_ru(t1, t1, q3);
                       nz |= w[e] & 0x7FFF7FFFu;
-                      big |= !(fabsf(y0) < 32768.f) || !(fabsf(y1) < 32768.f);
+                      big |= !(fabsf(y0) < 448.f) || !(fabsf(y1) < 448.f);
                     }
                   }
                 }

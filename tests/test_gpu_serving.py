@@ -85,3 +85,53 @@ def test_server_matches_oracle_and_alone():
     for a, m in zip(outs_alone, mixed_outs):
         if a[0] is not None:
             assert np.array_equal(a[0], m[0]) and np.array_equal(a[1], m[1]) and np.array_equal(a[2], m[2])
+
+
+def test_consecutive_inserts_are_coalesced_exactly():
+    """A burst of small inserts to one detector, with scores between some of them, from a
+    server with several scheduler threads: the inserts that queue up behind the two in flight
+    are admitted as one launch set (the server reports them), and every score, the counts and
+    the statistics equal the oracle's replay of the requests one by one."""
+    d, K, L = 128, 15, 50
+    dets = [ace.Detector(d, K, L, seed=70 + i) for i in range(6)]
+    srv = ace.Server(dets, mem_budget_bytes=64 << 20)
+    assert srv.info()["threads"] == 4
+    refs = [oracle.Detector(d, K, L, W=dd.projection()) for dd in dets]
+    rng = np.random.default_rng(5)
+    reqs, start = [], 0
+    for k in range(120):
+        det = 0 if k % 3 else int(rng.integers(0, 6))
+        n = int(rng.integers(1, 400))
+        X = torch.from_numpy(workloads.stream_chunk(9, start, n, total=10_000_000, d=d)).pin_memory().numpy()
+        start += n
+        op = ace.OP_SCORE if k % 17 == 16 else ace.OP_INSERT
+        reqs.append((det, op, X))
+    tickets, outs = [], []
+    for det, op, X in reqs:
+        n = X.shape[0]
+        o = (_pinned(n, np.float64), _pinned(n, np.uint32), _pinned(n, np.uint8)) if op == ace.OP_SCORE else (None,) * 3
+        tickets.append(srv.submit(det, op, X, 1.0, *o))
+        outs.append(o)
+    for t in tickets:
+        srv.wait(t)
+    info = srv.info()
+    srv.close()
+    assert info["coalesced"] > 0, info
+    for (det, op, X), o in zip(reqs, outs):
+        if op == ace.OP_INSERT:
+            refs[det].insert(X)
+        else:
+            rs, ru, rf = refs[det].score(X, 1.0)
+            assert np.array_equal(o[1], ru) and np.array_equal(o[0], rs) and np.array_equal(o[2], rf)
+    for dd, ref in zip(dets, refs):
+        assert np.array_equal(dd.counts(), ref.counts)
+        s, r = dd.stats(), ref.stats()
+        for k in ("n_ins", "n_scored", "Q", "S1", "S2", "mu_ins", "mu", "sigma"):
+            assert s[k] == r[k], k
+
+
+def test_server_refuses_a_detector_twice():
+    a = ace.Detector(20, 10, 4, seed=1)
+    with pytest.raises(ace.AceError) as e:
+        ace.Server([a, a])
+    assert e.value.code == ace.ACE_ERR_ARG
