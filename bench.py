@@ -273,9 +273,10 @@ def per_config(cases) -> dict:
         variants = [("fp32", ace.ACE_PROJ_FP32, False), ("bf16", ace.ACE_PROJ_BF16, False)]
         if w.get("w_bf16_variant"):
             variants.append(("bf16_w_bf16", ace.ACE_PROJ_BF16, True))
+            variants.append(("fp8_w_bf16", ace.ACE_PROJ_FP8, True))
         for prec, want, wb in variants:
             try:
-                det = ace.Detector(w["d"], w["K"], w["L"], seed=11, precision=prec[:4], w_bf16=wb)
+                det = ace.Detector(w["d"], w["K"], w["L"], seed=11, precision=prec.split("_")[0], w_bf16=wb)
             except ace.AceError as e:
                 if e.code == ace.ACE_ERR_UNSUPPORTED:
                     res[prec] = "engine not available for this shape"
@@ -316,12 +317,17 @@ def per_config(cases) -> dict:
                                               "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                                               "frac": flop / th / 1e12 / peaks["bf16_tflops"],
                                               "peak_src": f"bf16 burst, {peaks['src']}"}
+                elif prec.startswith("fp8"):
+                    pk = 2.0 * peaks["bf16_tflops"]
+                    entry["hash_roofline"] = {"bound": "tensor", "achieved": flop / th / 1e12, "peak": pk,
+                                              "unit": "TFLOP/s", "frac": flop / th / 1e12 / pk,
+                                              "peak_src": f"fp8 dense = 2 x bf16 burst ({peaks['src']}; nominal ratio)"}
                 else:
                     entry["hash_roofline"] = {"bound": "alu", "achieved": flop / th / 1e12, "peak": FP32_ALU_PEAK_TFLOPS,
                                               "unit": "TFLOP/s", "frac": flop / th / 1e12 / FP32_ALU_PEAK_TFLOPS,
                                               "peak_src": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"}
             res[prec] = entry
-        for v in ("bf16", "bf16_w_bf16"):
+        for v in ("bf16", "bf16_w_bf16", "fp8_w_bf16"):
             if isinstance(res.get(v), dict) and isinstance(res.get("fp32"), dict):
                 res[f"{v}_vs_fp32"] = res[v]["points_per_s"] / res["fp32"]["points_per_s"]
         out[name] = res
@@ -490,7 +496,8 @@ def projection_errors() -> dict:
     from paper_1706_06664_gb300 import ace, workloads
     cases = [("small", workloads.small(seed=1, n=4000), ("fp32", "bf16")),
              ("kdd-shaped", workloads.kdd(seed=2, n=20000), ("fp32", "bf16")),
-             ("high-dimensional (d=1024, bf16 input)", workloads.highdim(seed=3, n=1000), ("fp32", "bf16"))]
+             ("high-dimensional (d=1024, bf16 input)", workloads.highdim(seed=3, n=1000),
+              ("fp32", "bf16", "bf16_w_bf16", "fp8_w_bf16"))]
     out = {}
     for name, w, precs in cases:
         X = w["X"]
@@ -498,7 +505,8 @@ def projection_errors() -> dict:
         Xf = workloads.bf16_bits_to_f32(X) if X.dtype == np.uint16 else X
         res = {}
         for prec in precs:
-            det = ace.Detector(w["d"], w["K"], w["L"], seed=5, precision=prec)
+            det = ace.Detector(w["d"], w["K"], w["L"], seed=5, precision=prec.split("_")[0],
+                               w_bf16=prec.endswith("w_bf16"))
             est = det.project(Xd).cpu().numpy().astype(np.float64)
             W = det.projection()
             s64 = oracle.project(X, W)

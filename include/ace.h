@@ -258,7 +258,8 @@ enum { ACE_OP_INSERT = 0, ACE_OP_SCORE = 1, ACE_OP_INSERT_SCORE = 2 };
  * ACE_OP_SCORE (query phase and §5.3 rule) or ACE_OP_INSERT_SCORE — on detector `det` with
  * X_host (n x d, pinned for asynchrony) and optional output buffers (ignored for inserts),
  * and returns a ticket at once; X_host and the outputs must stay valid until the ticket is
- * waited for.  Up to four scheduler threads (detector i belongs to thread i mod their number)
+ * waited for.  One scheduler thread (the environment variable ACE_SERVER_THREADS, 1 to 4, sets
+ * more; detector i then belongs to thread i mod their number)
  * admit queued requests as slots (two per detector) and memory free up; each detector's
  * requests run in submission order on its own stream, so every result is the same as in a
  * run of that detector's requests alone, while different detectors overlap on the device.

@@ -5,10 +5,12 @@
 #include <condition_variable>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
 #include <cmath>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -1671,7 +1673,7 @@ int ace_insert_score_host(ace_handle h, const void* X_host, int64_t n, int dtype
 
 // ---------------------------------------------------------------------------------------
 // Request server (continuous batching over several detectors).  The detectors are divided
-// among a few scheduler threads (detector i belongs to thread i mod W), each with its own
+// among the scheduler threads (one by default; detector i belongs to thread i mod W), each with its own
 // queue of requests in submission order; a thread admits the first admissible request of its
 // queue whenever a slot or memory frees up: at most two per detector are in flight (its two
 // staging slots), the staged bytes of all threads stay within the budget, and a detector whose
@@ -1713,10 +1715,15 @@ struct ace_server_s {
   uint64_t next_id = 1;
   int device = 0;
   std::mutex mu;
-  std::condition_variable cv;
+  std::condition_variable cv;  // waiters (ace_server_wait / drain)
+  std::vector<std::unique_ptr<std::condition_variable>> wcv;  // one per scheduler thread
   std::vector<std::thread> workers;
   bool stop = false;
   uint64_t coalesced = 0;  // requests admitted as part of another's launch set
+
+  void wake_workers() {
+    for (auto& c : wcv) c->notify_one();
+  }
 
   int nworkers() const { return static_cast<int>(pending.size()); }
 
@@ -1735,6 +1742,7 @@ struct ace_server_s {
       q->done = true;
     }
     s->cv.notify_all();
+    s->wake_workers();  // a slot and memory are free again
   }
 
   // The first admissible waiting request of thread w's queue (caller holds mu), or nullptr;
@@ -1788,6 +1796,7 @@ struct ace_server_s {
       q->done = true;
     }
     cv.notify_all();
+    wake_workers();
   }
 
   void run(int w) {
@@ -1796,7 +1805,7 @@ struct ace_server_s {
     std::unique_lock<std::mutex> lk(mu);
     for (;;) {
       Req* r = nullptr;
-      cv.wait(lk, [&] { return (r = pick(w)) != nullptr || (stop && pending[w].empty()); });
+      wcv[w]->wait(lk, [&] { return (r = pick(w)) != nullptr || (stop && pending[w].empty()); });
       if (!r) break;
       inflight[r->det] += 1;
       bytes_inflight += r->bytes;
@@ -1839,7 +1848,13 @@ int ace_server_create(const ace_handle* dets, int n_dets, size_t mem_budget_byte
   s->dets.assign(dets, dets + n_dets);
   s->inflight.assign(n_dets, 0);
   s->budget = mem_budget_bytes;
-  s->pending.resize(std::min(n_dets, ace_server_s::kMaxWorkers));
+  // scheduler threads: ACE_SERVER_THREADS (1 .. 4) if set, else 1 (measured: four threads
+  // issuing CUDA calls at once gave 0.7x the capacity of one), at most one per detector
+  int nw = 1;
+  if (const char* env = std::getenv("ACE_SERVER_THREADS"))
+    nw = std::max(1, std::min(ace_server_s::kMaxWorkers, std::atoi(env)));
+  s->pending.resize(std::min(n_dets, nw));
+  for (size_t w = 0; w < s->pending.size(); ++w) s->wcv.emplace_back(new std::condition_variable());
   cudaGetDevice(&s->device);
   s->streams.assign(n_dets, nullptr);
   for (int i = 0; i < n_dets; ++i) {
@@ -1884,7 +1899,7 @@ int ace_server_submit(ace_server s, int det, int op, const void* X_host, int64_t
     s->reqs[r->id] = r;
     s->pending[det % s->nworkers()].push_back(r);
   }
-  s->cv.notify_all();
+  s->wcv[det % s->nworkers()]->notify_one();
   *ticket = r->id;
   return ACE_OK;
 }
@@ -1932,7 +1947,7 @@ int ace_server_destroy(ace_server s) {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;
   }
-  s->cv.notify_all();
+  s->wake_workers();
   for (auto& t : s->workers)
     if (t.joinable()) t.join();
   for (auto st : s->streams) {

@@ -125,13 +125,15 @@ __device__ __forceinline__ float2 from_e4m3x2(uint32_t v) {
   return __half22float2(__half2(h));
 }
 
-// y rounded to four significant bits (half a unit of the fourth bit added to the pattern, the
-// lower bits cleared: the carry moves into the exponent when needed), or 0 below 2^-6; an E4M3
-// value whenever |y| < 448.  Non-finite y stays non-finite (such rows are resolved exactly).
+// The leading four significant bits of y by Veltkamp's splitting (Dekker, "A floating-point
+// technique for extending the available precision", 1971): with c = RN((2^20 + 1) y),
+// h = RN(c - RN(c - y)) has at most 24 - 20 = 4 significant bits and y - h is exact in
+// binary32.  Three FMA-pipe operations instead of integer ones.  Where |y| < 2^-6 (E4M3's
+// subnormal range) h need not be an E4M3 value: its conversion then rounds, and the measuring
+// pass takes the converted values, so the remainder X3 is still exact.
 __device__ __forceinline__ float split4(float y) {
-  const uint32_t b = __float_as_uint(y);
-  const float h = __uint_as_float((b + 0x00080000u) & 0xFFF00000u);
-  return fabsf(y) < 0.015625f ? 0.f : h;
+  const float c = __fmul_rn(y, 1048577.0f);
+  return __fsub_rn(c, __fsub_rn(c, y));
 }
 
 __device__ __forceinline__ void tma_prefetch(const CUtensorMap* map) {
@@ -379,18 +381,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           if constexpr (F8) {
-            // Convert row r's k-block to E4M3 planes.  y = 2^s x (exact).  X1 = y rounded to
-            // four significant bits by integer arithmetic on its binary32 pattern (add half a
-            // unit of the fourth bit, clear the rest: round half away from zero), or 0 where
-            // |y| < 2^-6 (below E4M3's normal range); so X1 is an E4M3 value and its conversion
-            // is exact.  X2 = y - X1 is exact in binary32 and has at most four significant bits:
-            // its conversion is exact too, except in E4M3's subnormal range (spacing 2^-9),
-            // where the rounding error X3 = (y - X1) - e4m3(y - X1) is measured.  Only the
-            // conversions themselves use the conversion unit, one per pair of values and plane.
-            // The scale comes from the row's first k-block (its largest |x| to [32, 64)); a row
-            // with |y| >= 448 anywhere (beyond E4M3's range) has every column resolved exactly.
-            // During pass 0 of the first unit the row is also measured: the norms of y's blocks
-            // (E, as in the bfloat16 path), ||e4m3(X2)|| and ||X3||.
+            // Convert row r's k-block to E4M3 planes.  y = 2^s x (exact).  h = y split to four
+            // significant bits (split4), X1 = e4m3(h) (exact where |y| >= 2^-6), X2 =
+            // e4m3(y - h) (y - h is exact with at most four significant bits: its conversion is
+            // exact too, except in E4M3's subnormal range, spacing 2^-9), X3 = y - X1 - X2, the
+            // part the products miss.  The scale comes from the row's first k-block (its largest
+            // |x| to [32, 64)); a row with |y| >= 448 anywhere (beyond E4M3's range) has every
+            // column resolved exactly.  During pass 0 of the first unit the row is also
+            // measured: the norms of y's blocks (E, as in the bfloat16 path), ||X2|| and ||X3||
+            // from the converted values (exact differences in binary32).
             uint8_t* const stg = smem + static_cast<uint32_t>(s) * SB;
             const uint8_t* arow = stg + roff;
             const bool small = ks < nkb, first = un == 0 && small;
@@ -429,8 +428,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t b2 = to_e4m3x2(r0, r1);
                     o2[2 * hh + (e >> 1)] |= b2 << (16 * (e & 1));
                     if (first) {
-                      const float2 f2 = from_e4m3x2(b2);
-                      const float t0 = r0 - f2.x, t1 = r1 - f2.y;
+                      const float2 f1 = from_e4m3x2(b1), f2 = from_e4m3x2(b2);
+                      const float t0 = (y0 - f1.x) - f2.x, t1 = (y1 - f1.y) - f2.y;
                       bq[j >> 1] = fmaf(y0, y0, bq[j >> 1]);
                       bq[j >> 1] = fmaf(y1, y1, bq[j >> 1]);
                       q2 = __fmaf_ru(f2.x, f2.x, q2);

@@ -41,12 +41,11 @@ def e4m3(v):
 
 
 def split4(y):
-    """The kernel's X1: y rounded to four significant bits (half a unit of the fourth bit added
-    to the binary32 pattern, the rest cleared), 0 below 2^-6."""
-    y = np.asarray(y, dtype=np.float64)
-    b = y.astype(np.float32).view(np.uint32).astype(np.uint64)
-    h = ((b + 0x80000) & 0xFFF00000).astype(np.uint32).view(np.float32).astype(np.float64)
-    return np.where(np.abs(y) < 2.0**-6, 0.0, h)
+    """The kernel's leading part of y: Veltkamp's split to four significant bits in binary32,
+    c = RN((2^20 + 1) y), h = RN(c - RN(c - y))."""
+    y = np.asarray(y, dtype=np.float32)
+    c = (y * np.float32(1048577.0)).astype(np.float32)
+    return (c - (c - y).astype(np.float32)).astype(np.float32).astype(np.float64)
 
 
 def _row_scale(Xf):
@@ -84,8 +83,9 @@ def _row_band_fp8(W, Xf):
     sumw = (np.sqrt(wp) + np.sqrt(wb)).sum()
     Y = np.zeros((Xf.shape[0], dp))
     Y[:, :d] = Xf * _row_scale(Xf)[:, None]
-    X1 = split4(Y)
-    X2 = e4m3(Y - X1)
+    H = split4(Y)
+    X1 = e4m3(H)
+    X2 = e4m3(Y - H)
     X3 = Y - X1 - X2
     yk = (Y.reshape(-1, nkb, 64) ** 2).sum(axis=2)
     E = np.sqrt(np.cumsum(yk, axis=1)) @ WPk + np.sqrt(yk) @ WBk

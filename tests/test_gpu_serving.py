@@ -87,15 +87,17 @@ def test_server_matches_oracle_and_alone():
             assert np.array_equal(a[0], m[0]) and np.array_equal(a[1], m[1]) and np.array_equal(a[2], m[2])
 
 
-def test_consecutive_inserts_are_coalesced_exactly():
+@pytest.mark.parametrize("threads", ["1", "4"])
+def test_consecutive_inserts_are_coalesced_exactly(threads, monkeypatch):
     """A burst of small inserts to one detector, with scores between some of them, from a
-    server with several scheduler threads: the inserts that queue up behind the two in flight
-    are admitted as one launch set (the server reports them), and every score, the counts and
-    the statistics equal the oracle's replay of the requests one by one."""
+    server with one and with four scheduler threads: the inserts that queue up behind the two
+    in flight are admitted as one launch set (the server reports them), and every score, the
+    counts and the statistics equal the oracle's replay of the requests one by one."""
+    monkeypatch.setenv("ACE_SERVER_THREADS", threads)
     d, K, L = 128, 15, 50
     dets = [ace.Detector(d, K, L, seed=70 + i) for i in range(6)]
     srv = ace.Server(dets, mem_budget_bytes=64 << 20)
-    assert srv.info()["threads"] == 4
+    assert srv.info()["threads"] == int(threads)
     refs = [oracle.Detector(d, K, L, W=dd.projection()) for dd in dets]
     rng = np.random.default_rng(5)
     reqs, start = [], 0
