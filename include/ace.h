@@ -100,7 +100,8 @@ typedef struct {
 
 /* Creation flags (ace_create_ex). */
 enum {
-  ACE_W_BF16 = 1u /* round every drawn W entry to bfloat16 (nearest even), kept as binary32 */
+  ACE_W_BF16 = 1u,   /* round every drawn W entry to bfloat16 (nearest even), kept as binary32 */
+  ACE_W_COUNTER = 2u /* integer-only entries regenerated from the seed inside the kernels   */
 };
 
 /*
@@ -127,6 +128,19 @@ int ace_create(int d, int K, int L, uint64_t seed, ace_handle* out);
  * Errors: as ace_create; ACE_ERR_ARG for unknown flags.
  */
 int ace_create_ex(int d, int K, int L, uint64_t seed, unsigned flags, ace_handle* out);
+/*
+ * ACE_W_COUNTER (ace_create_ex; §3.4 keeps the seeds of the projections and regenerates them
+ * instead of storing them): W.flat[i*K*L + c] = (popcount(draw_f) - 32) / 4 with draw_f the
+ * SplitMix64 draw of index f = i*K*L + c in the counter mode above: an integer-only
+ * generator whose entries have mean 0 and variance 1 (Binomial(64, 1/2) - 32, over 4) and are
+ * bfloat16 values.  SRP's collision probability 1 - theta/pi holds for such a W approximately
+ * (exactly for Gaussian entries).  The binary32 engine (single calls and batches) regenerates
+ * its W tiles from the seed inside the kernel instead of reading a stored W; the exact recheck
+ * tiers and the tensor-core images still use a materialised copy.  Ids, counts and scores are
+ * the binary64 definition's for this W.  Takes precedence over ACE_W_BF16 (its entries are
+ * bfloat16 values already).  A checkpoint of such a detector (ace_save) loads as a detector
+ * with the same W stored (ace_load): the results are the same.
+ */
 
 /* As ace_create, with an explicit host d x (K*L) row-major binary32 W (copied). */
 int ace_create_with_projection(int d, int K, int L, const float* W_host, ace_handle* out);

@@ -60,6 +60,7 @@ def _load():
         i32, i64, u64, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
         lib.oracle_projection_from_seed.argtypes = [i32, i32, i32, u64, P]
         lib.oracle_projection_from_seed_bf16.argtypes = [i32, i32, i32, u64, P]
+        lib.oracle_projection_counter.argtypes = [i32, i32, i32, u64, P]
         lib.oracle_splitmix64_draw.argtypes = [u64, u64]
         lib.oracle_splitmix64_draw.restype = u64
         lib.oracle_hash.argtypes = [P, i32, i64, i32, P, i32, i32, P]
@@ -104,11 +105,15 @@ def splitmix64_draw(seed: int, t: int) -> int:
     return int(_load().oracle_splitmix64_draw(ctypes.c_uint64(seed), ctypes.c_uint64(t)))
 
 
-def projection_from_seed(d: int, K: int, L: int, seed: int, w_bf16: bool = False) -> np.ndarray:
+def projection_from_seed(d: int, K: int, L: int, seed: int, w_bf16: bool = False, counter: bool = False) -> np.ndarray:
     """d x (K*L) binary32 Gaussian matrix (SplitMix64 counter mode + Box-Muller); with w_bf16
-    every value is then rounded to bfloat16 (nearest even)."""
+    every value is then rounded to bfloat16 (nearest even); with counter, the integer-only
+    matrix (popcount of each draw - 32) / 4 instead."""
     W = np.empty((d, K * L), dtype=np.float32)
-    fn = _load().oracle_projection_from_seed_bf16 if w_bf16 else _load().oracle_projection_from_seed
+    if counter:
+        fn = _load().oracle_projection_counter
+    else:
+        fn = _load().oracle_projection_from_seed_bf16 if w_bf16 else _load().oracle_projection_from_seed
     fn(d, K, L, ctypes.c_uint64(seed & (2**64 - 1)), _ptr(W))
     return W
 

@@ -14,6 +14,9 @@
  *   oracle_projection_from_seed  Algorithm 1's hash initialisation: K*L independent Gaussian
  *                                projection vectors, w_i ~ N(0,1) (§2.1).  Generator:
  *                                SplitMix64 in counter mode + Box-Muller (see below).
+ *   oracle_projection_counter    the integer-only projection (§3.4 regenerates projections
+ *                                from stored seeds): W.flat[f] = (popcount(draw_f) - 32) / 4
+ *                                with the same SplitMix64 counter-mode draws.
  *   oracle_hash                  Eq. 1 (SRP bit h_w(x) = sign(w^T x)) and Eq. 2
  *                                (K bits concatenated into the meta-hash H_j), §3.2.
  *   oracle_insert                Algorithm 1 pre-processing phase; §3.2 (counting phase).
@@ -80,6 +83,27 @@ void oracle_projection_from_seed(int d, int K, int L, uint64_t seed, float* W) {
     double ang = two_pi * u2;
     double g = (f % 2u == 0u) ? r * cos(ang) : r * sin(ang);
     W[f] = (float)g;
+  }
+}
+
+/* Number of one bits of v, one bit cleared per step (v & (v - 1) drops the lowest one).    */
+static int ones64(uint64_t v) {
+  int c = 0;
+  while (v) {
+    v &= v - 1u;
+    ++c;
+  }
+  return c;
+}
+
+/* Integer-only projection: entry f is (ones(draw_f) - 32) / 4, draw_f the f-th SplitMix64  */
+/* draw of the seed.  The number of ones of 64 fair bits is Binomial(64, 1/2): mean 0,      */
+/* variance 16/16 = 1 after the shift and the division (exact in binary32).                 */
+void oracle_projection_counter(int d, int K, int L, uint64_t seed, float* W) {
+  const uint64_t total = (uint64_t)d * (uint64_t)K * (uint64_t)L;
+  for (uint64_t f = 0; f < total; ++f) {
+    int k = ones64(splitmix64_draw(seed, f)) - 32;
+    W[f] = (float)k / 4.0f;
   }
 }
 

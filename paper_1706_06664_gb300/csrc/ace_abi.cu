@@ -108,6 +108,8 @@ struct ace_detector {
   cudaStream_t rstream = nullptr;
   cudaEvent_t ev_hashed = nullptr, ev_resolved = nullptr;
   // streaming tensor-core path (large d, bfloat16 input; hash_gemm.cu)
+  bool wgen = false;             // ACE_W_COUNTER: the SIMT engine regenerates W tiles from wseed
+  uint64_t wseed = 0;
   bool gemm_ok = false;
   ace::GemmArgs gm{};           // constant part of the launch
   uint16_t* gimg = nullptr;     // [2 klp][dp] bfloat16 image of W' (hi rows, then lo rows)
@@ -835,7 +837,9 @@ int make_detector(int d, int K, int L, const float* Wsrc, uint64_t seed, bool fr
                   ace_handle* out) {
   if (!out) return fail(ACE_ERR_ARG, "out is NULL");
   *out = nullptr;
-  if (flags & ~static_cast<unsigned>(ACE_W_BF16)) return fail(ACE_ERR_ARG, "unknown creation flags 0x%x", flags);
+  if (flags & ~static_cast<unsigned>(ACE_W_BF16 | ACE_W_COUNTER))
+    return fail(ACE_ERR_ARG, "unknown creation flags 0x%x", flags);
+  if ((flags & ACE_W_COUNTER) && !from_seed) return fail(ACE_ERR_ARG, "ACE_W_COUNTER needs a seed");
   if (d < 1 || K < 1 || K > 24 || L < 1 || static_cast<long long>(K) * L > 65536)
     return fail(ACE_ERR_ARG, "invalid shape d=%d K=%d L=%d (need d>=1, 1<=K<=24, L>=1, K*L<=65536)", d, K, L);
   if (!from_seed && !Wsrc) return fail(ACE_ERR_ARG, "W_host is NULL");
@@ -858,9 +862,17 @@ int make_detector(int d, int K, int L, const float* Wsrc, uint64_t seed, bool fr
     delete h;
     return fail(ACE_ERR_OOM, "host allocation of W failed");
   }
-  if (from_seed) ace::generate_projection(d, K, L, seed, h->Wh.data());
-  else std::memcpy(h->Wh.data(), Wsrc, dkl * sizeof(float));
-  if (flags & ACE_W_BF16) ace::round_projection_bf16(h->Wh.data(), dkl);
+  if (flags & ACE_W_COUNTER) {
+    ace::generate_projection_counter(d, K, L, seed, h->Wh.data());
+    h->wgen = true;
+    h->wseed = seed;
+  } else if (from_seed) {
+    ace::generate_projection(d, K, L, seed, h->Wh.data());
+    if (flags & ACE_W_BF16) ace::round_projection_bf16(h->Wh.data(), dkl);
+  } else {
+    std::memcpy(h->Wh.data(), Wsrc, dkl * sizeof(float));
+    if (flags & ACE_W_BF16) ace::round_projection_bf16(h->Wh.data(), dkl);
+  }
   for (size_t i = 0; i < dkl; ++i)
     if (!std::isfinite(h->Wh[i])) {
       delete h;
@@ -878,12 +890,13 @@ int make_detector(int d, int K, int L, const float* Wsrc, uint64_t seed, bool fr
     return err == cudaErrorMemoryAllocation ? fail(ACE_ERR_OOM, "%s: out of device memory", what)
                                             : cuda_fail(err, what);
   };
-  if ((e = cudaMalloc(&h->W, dkl * sizeof(float))) != cudaSuccess) return bad(e, "cudaMalloc W");
+  // (a regenerated W needs no row-major device copy: only the SIMT engine's tiles read it)
+  if (!h->wgen && (e = cudaMalloc(&h->W, dkl * sizeof(float))) != cudaSuccess) return bad(e, "cudaMalloc W");
   if ((e = cudaMalloc(&h->Wt, dkl * sizeof(float))) != cudaSuccess) return bad(e, "cudaMalloc Wt");
   if ((e = cudaMalloc(&h->cB, h->KL * sizeof(float))) != cudaSuccess) return bad(e, "cudaMalloc cB");
   if ((e = cudaMalloc(&h->counts, count_elems(h) * sizeof(uint32_t))) != cudaSuccess) return bad(e, "cudaMalloc counts");
   if ((e = cudaMalloc(&h->st, sizeof(ace::DevStats))) != cudaSuccess) return bad(e, "cudaMalloc stats");
-  if ((e = cudaMemcpy(h->W, h->Wh.data(), dkl * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+  if (h->W && (e = cudaMemcpy(h->W, h->Wh.data(), dkl * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
     return bad(e, "copy W");
   if ((e = cudaMemcpy(h->Wt, Wt.data(), dkl * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
     return bad(e, "copy Wt");
@@ -955,6 +968,8 @@ ace::HashArgs hash_args(ace_handle h, const void* X, long long n, int dtype, int
   a.L = h->L;
   a.KL = h->KL;
   a.W = h->W;
+  a.wseed = h->wseed;
+  a.wgen = h->wgen ? 1 : 0;
   a.Wt = h->Wt;
   a.cB = h->cB;
   a.xfac = h->xfac;

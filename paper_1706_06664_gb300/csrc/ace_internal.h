@@ -37,13 +37,35 @@ enum HashMode : int {
   kTagDeferred = 16
 };
 
+// The integer-only projection entry of ACE_W_COUNTER detectors (§3.4 regenerates projections
+// from stored seeds instead of storing them): W.flat[f] = (popcount(z_f) - 32) / 4, z_f the
+// SplitMix64 draw t = f of the detector's seed (the same counter-mode definition as the
+// Box-Muller generator: finaliser of seed + (f + 1) * 0x9E3779B97F4A7C15).  popcount of 64
+// fair bits is Binomial(64, 1/2): the entry has mean 0 and variance exactly 1, takes the 65
+// values k/4, |k| <= 32 (all bfloat16 values), and is computed exactly on host and device
+// alike, so kernels can regenerate W tiles instead of reading them.
+__host__ __device__ inline float counter_w(uint64_t seed, uint64_t f) {
+  uint64_t z = seed + (f + 1u) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+#ifdef __CUDA_ARCH__
+  const int pc = __popcll(z);
+#else
+  const int pc = __builtin_popcountll(z);
+#endif
+  return static_cast<float>(pc - 32) * 0.25f;
+}
+
 // Everything a hash kernel needs.  Columns c = j*K + k; W is d x KL row-major.
 struct HashArgs {
   const void* X;        // n x d, binary32 or bfloat16 bits
   int x_bf16;           // 0: binary32, 1: bfloat16
   long long n;
   int d, K, L, KL;
-  const float* W;       // [d][KL] binary32
+  const float* W;       // [d][KL] binary32 (null when wgen: the tiles are regenerated)
+  unsigned long long wseed;  // ACE_W_COUNTER: the seed of counter_w
+  int wgen;             // 1: W tiles are regenerated from wseed (counter_w) instead of read
   const float* Wt;      // [KL][d] binary32 (columns contiguous, for the binary64 recheck)
   const float* cB;      // [KL] guard coefficient: margin * gamma * ||w_c|| (rounded up)
   float xfac;           // squared-norm inflation (1 + 2 gamma_d + slack)
@@ -104,6 +126,7 @@ cudaError_t launch_tc_probe(const void* A, const void* B, int kd, int N, bool fp
 
 // Host-side generator of the projection matrix (SplitMix64 counter mode + Box-Muller).
 void generate_projection(int d, int K, int L, uint64_t seed, float* W);
+void generate_projection_counter(int d, int K, int L, uint64_t seed, float* W);
 // Rounds every entry to bfloat16 (round to nearest even), keeping binary32 storage.
 void round_projection_bf16(float* W, uint64_t total);
 

@@ -81,7 +81,10 @@ __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int 
     for (int e = threadIdx.x; e < DK * BN; e += NT) {
       const int k = e / BN, c = e % BN;
       float v = 0.f;
-      if (c < ncol && kc + k < a.d) v = __ldg(a.W + static_cast<size_t>(kc + k) * a.KL + c0 + c);
+      if (c < ncol && kc + k < a.d) {
+        const size_t f = static_cast<size_t>(kc + k) * a.KL + c0 + c;
+        v = a.wgen ? counter_w(a.wseed, f) : __ldg(a.W + f);
+      }
       Ws[k][c] = v;
     }
     __syncthreads();

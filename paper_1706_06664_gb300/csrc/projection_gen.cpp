@@ -49,6 +49,11 @@ void round_projection_bf16(float* W, uint64_t total) {
   }
 }
 
+void generate_projection_counter(int d, int K, int L, uint64_t seed, float* W) {
+  const uint64_t total = static_cast<uint64_t>(d) * static_cast<uint64_t>(K) * static_cast<uint64_t>(L);
+  for (uint64_t f = 0; f < total; ++f) W[f] = counter_w(seed, f);
+}
+
 void generate_projection(int d, int K, int L, uint64_t seed, float* W) {
   const uint64_t total = static_cast<uint64_t>(d) * static_cast<uint64_t>(K) * static_cast<uint64_t>(L);
   const double two_pi = 2.0 * 3.14159265358979323846;

@@ -460,3 +460,62 @@ def test_window_equals_plain_detector_on_the_last_points():
         assert np.array_equal(det.counts, plain.counts) and det.n_ins == last.shape[0]
     with pytest.raises(ValueError):
         det.insert(rng.standard_normal((win + 1, d)).astype(np.float32))
+
+
+# ------------------------------------------------------------------------------------------
+# Integer-only projection (ACE_W_COUNTER)
+# ------------------------------------------------------------------------------------------
+def test_counter_projection_from_published_draws():
+    """Entries (popcount(draw_f) - 32) / 4 for the published SplitMix64 outputs
+    (tests/golden/splitmix64.json: seed 0 draw 0, seed 1234567 draws 0 to 2), the ones counted
+    by Python's own integer routine."""
+    vec = {(v["seed"], v["t"]): v["out"] for v in _load("splitmix64.json")["vectors"]}
+    W = oracle.projection_from_seed(1, 3, 1, seed=1234567, counter=True).ravel()
+    for t in range(3):
+        assert W[t] == (bin(vec[(1234567, t)]).count("1") - 32) / 4, t
+    assert oracle.projection_from_seed(1, 1, 1, seed=0, counter=True).ravel()[0] == (bin(vec[(0, 0)]).count("1") - 32) / 4
+    # flat index f = i K L + c: entry (i, c) is draw i K L + c
+    W2 = oracle.projection_from_seed(3, 2, 2, seed=1234567, counter=True)
+    assert W2[0, 1] == W.ravel()[1] and W2[0, 2] == W.ravel()[2]
+
+
+def test_counter_projection_is_binomial():
+    """4 w + 32 follows Binomial(64, 1/2) over a million entries (chi-square over the 65 values,
+    sparse tails merged), so w has mean 0 and variance 1; every entry is a bfloat16 value."""
+    W = oracle.projection_from_seed(64, 16, 1024, seed=777, counter=True).astype(np.float64).ravel()
+    k = W * 4 + 32
+    assert np.array_equal(k, np.rint(k)) and k.min() >= 0 and k.max() <= 64
+    assert np.array_equal(workloads.bf16_bits_to_f32(workloads.to_bf16_bits(W.astype(np.float32))), W.astype(np.float32))
+    obs = np.bincount(k.astype(int), minlength=65).astype(np.float64)
+    pmf = np.array([math.comb(64, i) for i in range(65)], dtype=np.float64) / 2.0**64
+    exp = pmf * k.size
+    lo, hi = 20, 44  # merge the tails (expected counts below ~100 outside)
+    o = np.concatenate([[obs[:lo].sum()], obs[lo:hi + 1], [obs[hi + 1:].sum()]])
+    e = np.concatenate([[exp[:lo].sum()], exp[lo:hi + 1], [exp[hi + 1:].sum()]])
+    chi2 = float(((o - e) ** 2 / e).sum())
+    scipy_stats = pytest.importorskip("scipy.stats")
+    assert scipy_stats.chi2.sf(chi2, len(o) - 1) > 1e-4, chi2
+    se = 1.0 / math.sqrt(W.size)
+    assert abs(W.mean()) < 5 * se and abs(W.var() - 1.0) < 5 * math.sqrt(2.0) * se
+
+
+@pytest.mark.parametrize("theta", [math.pi / 6, math.pi / 2, 5 * math.pi / 6])
+def test_counter_projection_collision_probability(theta):
+    """SRP with the integer-only W: two points at angle theta in d = 16 (random directions)
+    get the same bit on a fraction 1 - theta/pi of 2^17 columns, within sampling error and a
+    0.005 allowance (Binomial(64, 1/2) entries are nearly, not exactly, rotation-invariant)."""
+    d, M = 16, 1 << 17
+    rng = np.random.default_rng(int(theta * 1000))
+    x = rng.standard_normal(d)
+    x /= np.linalg.norm(x)
+    z = rng.standard_normal(d)
+    z -= (z @ x) * x
+    z /= np.linalg.norm(z)
+    X = np.stack([x, math.cos(theta) * x + math.sin(theta) * z]).astype(np.float32)
+    W = oracle.projection_from_seed(d, 1, M, seed=4242, counter=True)
+    ids = oracle.hash_ids(X, W, 1, M)
+    xd, yd = X.astype(np.float64)
+    th = math.acos(float(xd @ yd) / (np.linalg.norm(xd) * np.linalg.norm(yd)))
+    p = 1.0 - th / math.pi
+    frac = float(np.mean(ids[0] == ids[1]))
+    assert abs(frac - p) < 5 * math.sqrt(p * (1 - p) / M) + 0.005, (frac, p)
