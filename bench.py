@@ -521,6 +521,40 @@ def projection_errors() -> dict:
     return out
 
 
+def estimator_accuracy(seed: int = 12, m: int = 50, Ls=(10, 25, 50, 100, 200)) -> dict:
+    """Estimator-accuracy workload (§4.2; stand-ins for the paper's datasets, which are not
+    available): for 50 queries drawn from each dataset, the exact S(q, D) of Eq. 3 on the GPU
+    (ace_exact_score, binary64), ACE's estimate at L arrays and RSE with L samples (20 draws);
+    mean square error against L.  Also the exact-score kernel's rate: 4 d binary64 flop per
+    (query, point) pair (dot product and the point's squared norm), against the nominal 1.25
+    TFLOP/s binary64 rate of the part."""
+    import torch
+    from paper_1706_06664_gb300 import accuracy, ace, workloads
+    sets = [("small-shaped (n=10000, d=32)", workloads.small(seed=1)["X"], 15),
+            ("kdd-shaped (n=100000, d=41)", workloads.kdd(seed=2, n=100_000)["X"], 15),
+            ("high-dimensional (n=100000, d=1024 bf16)", workloads.highdim(seed=3, n=100_000)["X"], 15)]
+    out = {}
+    for name, X, K in sets:
+        Xd = torch.from_numpy(X.view(np.int16) if X.dtype == np.uint16 else X).cuda()
+        rng = np.random.default_rng(seed)
+        Q = Xd[torch.from_numpy(rng.choice(X.shape[0], size=m, replace=False)).cuda()]
+        res = accuracy.estimator_mse(Xd, Q, K, Ls, seed=seed, rse_draws=20)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ace.exact_score(Q, Xd, K)
+        e0.record()
+        ace.exact_score(Q, Xd, K)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        pairs = m * X.shape[0]
+        out[name] = {"K": K, "queries": m, "mean_S": float(np.mean(res["S"])),
+                     "mse": {str(L): {"ace": v["ace_mse"], "rse": v["rse_mse"]} for L, v in res["L"].items()},
+                     "exact_score": {"pairs_per_s": pairs / t, "ms": t * 1e3,
+                                     "fp64_tflops": 4.0 * X.shape[1] * pairs / t / 1e12,
+                                     "frac_of_nominal_fp64": 4.0 * X.shape[1] * pairs / t / 1.25e12}}
+    return out
+
+
 def batched(n_det: int = 2048, seed: int = 4) -> dict:
     """Batched-detectors shape: 2048 detectors, d log-uniform in [16, 512], n log-uniform in
     [100, 100000], K=12, L=32, Gaussian-mixture points (8 clusters N(m_c, I), m_c ~ N(0, 4I),
@@ -731,6 +765,8 @@ def run_ours(args):
         line["batched"] = section(batched)
     if rank == 0 and ws == 1 and args.proj_error:
         line["projection_error"] = section(projection_errors)
+    if rank == 0 and ws == 1 and args.accuracy:
+        line["estimator_accuracy"] = section(estimator_accuracy)
     if rank == 0:
         print(json.dumps(line), flush=True)
     det.close()
@@ -759,6 +795,7 @@ def main():
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-projection-error", dest="proj_error", action="store_false")
     ap.add_argument("--no-per-config", dest="per_config", action="store_false")
+    ap.add_argument("--no-accuracy", dest="accuracy", action="store_false")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     global D, KH, LT, WORKLOAD

@@ -414,6 +414,22 @@ int ace_insert_score_noalloc(ace_handle h, const void* X_dev, int64_t n, int dty
                              double* scores_dev, uint32_t* sums_dev, uint8_t* flags_dev, void* stream);
 
 /*
+ * ace_exact_score — the score family ACE estimates, computed exactly (Eq. 3 with SRP's
+ * collision probability, §3): S_dev[q] = sum_i p(q, x_i)^K, p(q, x) = 1 - acos(q.x / (||q||
+ * ||x||)) / pi, for nq queries Q_dev (nq x d) against nd points D_dev (nd x d), both binary32
+ * or both bfloat16 (dtype).  Theorem 1 makes ACE's score (1/L) sum_j A_j[H_j(q)] of a detector
+ * holding D an unbiased estimator of S(q, D); the random sampling estimator RSE (Eq. 10) is this
+ * sum over a sample of D scaled by nd / (sample size).  Binary64 arithmetic throughout (dot
+ * products and norms in index order, cos clamped to [-1, 1]); a zero vector has p = 1/2 against
+ * a non-zero one (its SRP bits are all 0) and p = 1 against another zero vector.  The sum over
+ * the points is taken in a fixed order, so the result does not depend on scheduling.
+ * nq <= 65535, 1 <= K <= 64.  Synchronous on `stream` (it allocates and frees a scratch of
+ * 8 nq ceil(nd / 256) bytes).  Errors: ACE_ERR_ARG, ACE_ERR_OOM, ACE_ERR_CUDA.
+ */
+int ace_exact_score(const void* Q_dev, int64_t nq, const void* D_dev, int64_t nd, int d, int dtype, int K,
+                    double* S_dev, void* stream);
+
+/*
  * ace_tc_probe — measurement hook for the tensor-core engines' error model.  Computes
  * D = A . B^T (A: 128 x kdim, B: ncols x kdim, bfloat16 bit patterns, row-major, host; D:
  * 128 x ncols binary32, host) on the tcgen05 tensor cores as kdim/16 MMA instructions of

@@ -300,3 +300,32 @@ class WindowDetector(Detector):
     def insert_score(self, X, alpha: float = 1.0):
         ids = self.insert(X)
         return self._score_ids(ids, alpha)
+
+
+def exact_score(Q: np.ndarray, D: np.ndarray, K: int) -> np.ndarray:
+    """Eq. 3 with SRP's collision probability (§3): S(q, D) = sum_i p(q, x_i)^K,
+    p(q, x) = 1 - acos(q.x / (||q|| ||x||)) / pi, in binary64, for every row q of Q (binary32
+    or bfloat16 bits).  A zero vector has no angle; its SRP bits are all 0 (sign(0) = 0), so
+    against a non-zero point each of its bits agrees with probability 1/2: p = 1/2 (and p = 1
+    between two zero vectors)."""
+    def f64(A):
+        A = np.asarray(A)
+        if A.dtype == np.uint16:
+            return (A.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+        return A.astype(np.float64)
+    Qd, Dd = f64(Q), f64(D)
+    qq = (Qd * Qd).sum(axis=1)
+    xx = (Dd * Dd).sum(axis=1)
+    dot = Qd @ Dd.T
+    with np.errstate(divide="ignore", invalid="ignore"):
+        c = dot / np.sqrt(qq[:, None] * xx[None, :])
+    p = 1.0 - np.arccos(np.clip(c, -1.0, 1.0)) / np.pi
+    zq, zx = (qq == 0)[:, None], (xx == 0)[None, :]
+    p = np.where(zq & zx, 1.0, np.where(zq | zx, 0.5, p))
+    return (p ** K).sum(axis=1)
+
+
+def rse(Q: np.ndarray, D: np.ndarray, K: int, idx: np.ndarray) -> np.ndarray:
+    """The random sampling estimator (Eq. 10): n / |S| times sum over the sample S = D[idx]
+    of p(q, x_i)^K."""
+    return exact_score(Q, np.asarray(D)[idx], K) * (len(D) / len(idx))

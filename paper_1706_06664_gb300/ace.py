@@ -29,7 +29,7 @@ EXPORTS = [
     "ace_batch_insert_score", "ace_server_create", "ace_server_submit", "ace_server_wait", "ace_server_drain", "ace_server_destroy", "ace_server_info", "ace_stats",
     "ace_get_counts", "ace_get_projection", "ace_get_shape", "ace_last_error", "ace_version",
     "ace_profile_enable", "ace_profile_phases", "ace_profile_read", "ace_insert_score_noalloc",
-    "ace_tc_probe", "ace_tc_probe_fp8", "ace_save_size", "ace_save", "ace_load", "ace_window_enable", "ace_set_graph",
+    "ace_tc_probe", "ace_tc_probe_fp8", "ace_exact_score", "ace_save_size", "ace_save", "ace_load", "ace_window_enable", "ace_set_graph",
     "ace_batch_tile",
 ]
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
@@ -107,6 +107,7 @@ def load_library(path: str = LIB_PATH):
             "ace_profile_read": ([H, ctypes.POINTER(ace_profile_t)], i32),
             "ace_tc_probe": ([P, P, i32, i32, P], i32),
             "ace_tc_probe_fp8": ([P, P, i32, i32, P], i32),
+            "ace_exact_score": ([P, i64, P, i64, i32, i32, i32, P, P], i32),
             "ace_window_enable": ([H, i64], i32),
             "ace_set_graph": ([H, i32], i32),
             "ace_batch_tile": ([i32, i32, i32, i32, P, P], i32),
@@ -469,6 +470,18 @@ def tc_probe(A: np.ndarray, B: np.ndarray) -> np.ndarray:
     _check(load_library().ace_tc_probe(ctypes.c_void_p(A.ctypes.data), ctypes.c_void_p(B.ctypes.data), A.shape[1],
                                        B.shape[0], ctypes.c_void_p(D.ctypes.data)))
     return D
+
+
+def exact_score(Q, D, K: int, stream=None):
+    """ace_exact_score: S(q, D) = sum_i p(q, x_i)^K (Eq. 3, SRP's p) for every row q of Q, in
+    binary64 (Q and D device tensors of the same dtype, binary32 or bfloat16)."""
+    torch = _torch()
+    if Q.dtype != D.dtype:
+        raise TypeError("Q and D must have the same dtype")
+    S = torch.empty(Q.shape[0], dtype=torch.float64, device=Q.device)
+    _check(load_library().ace_exact_score(_ptr(Q), Q.shape[0], _ptr(D), D.shape[0], Q.shape[1], _x_dtype(Q), int(K),
+                                          _ptr(S), _stream_ptr(stream)))
+    return S
 
 
 def tc_probe_fp8(A: np.ndarray, B: np.ndarray) -> np.ndarray:

@@ -2414,6 +2414,31 @@ int tc_probe_any(const void* A_host, const void* B_host, int kdim, int ncols, fl
 }
 }  // namespace
 
+int ace_exact_score(const void* Q_dev, int64_t nq, const void* D_dev, int64_t nd, int d, int dtype, int K,
+                    double* S_dev, void* stream) {
+  if (nq < 0 || nd < 0) return fail(ACE_ERR_ARG, "nq and nd must be >= 0");
+  if (nq == 0) return ACE_OK;
+  if (!Q_dev || !S_dev || (nd > 0 && !D_dev)) return fail(ACE_ERR_ARG, "NULL argument");
+  if (d < 1 || K < 1 || K > 64) return fail(ACE_ERR_ARG, "need d >= 1 and 1 <= K <= 64 (got d=%d K=%d)", d, K);
+  if (dtype != ACE_F32 && dtype != ACE_BF16) return fail(ACE_ERR_ARG, "unknown dtype %d", dtype);
+  if (nq > 65535) return fail(ACE_ERR_ARG, "at most 65535 queries per call (got %lld)", static_cast<long long>(nq));
+  if (nd > (1LL << 38)) return fail(ACE_ERR_ARG, "nd too large");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void* part = nullptr;
+  const size_t bytes = std::max<size_t>(ace::exact_score_scratch(nq, nd), 8);
+  cudaError_t e = cudaMalloc(&part, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ACE_ERR_OOM, "exact score scratch: %s", cudaGetErrorString(e));
+  }
+  e = ace::launch_exact_score(Q_dev, nq, D_dev, nd, d, dtype == ACE_BF16 ? 1 : 0, K, static_cast<double*>(part),
+                              S_dev, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(part);
+  if (e != cudaSuccess) return cuda_fail(e, "exact score");
+  return ACE_OK;
+}
+
 int ace_tc_probe(const uint16_t* A_host, const uint16_t* B_host, int kdim, int ncols, float* D_host) {
   return tc_probe_any(A_host, B_host, kdim, ncols, D_host, false);
 }

@@ -125,6 +125,12 @@ cudaError_t launch_tc_probe(const void* A, const void* B, int kd, int N, bool fp
                             cudaStream_t s);
 
 // Host-side generator of the projection matrix (SplitMix64 counter mode + Box-Muller).
+// Exact S(q, D) = sum_i p(q, x_i)^K for nq queries (exact_score.cu); part holds
+// exact_score_scratch(nq, nd) bytes.
+size_t exact_score_scratch(long long nq, long long nd);
+cudaError_t launch_exact_score(const void* Q, long long nq, const void* D, long long nd, int d, int bf16, int K,
+                               double* part, double* S, cudaStream_t s);
+
 void generate_projection(int d, int K, int L, uint64_t seed, float* W);
 void generate_projection_counter(int d, int K, int L, uint64_t seed, float* W);
 // Rounds every entry to bfloat16 (round to nearest even), keeping binary32 storage.

@@ -78,14 +78,18 @@ __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int 
       if (p < npt && kc + k < a.d) v = load_x<BF16>(a.X, (i0 + p) * a.d + kc + k);
       Xs[p][k] = v;
     }
-    for (int e = threadIdx.x; e < DK * BN; e += NT) {
-      const int k = e / BN, c = e % BN;
-      float v = 0.f;
-      if (c < ncol && kc + k < a.d) {
-        const size_t f = static_cast<size_t>(kc + k) * a.KL + c0 + c;
-        v = a.wgen ? counter_w(a.wseed, f) : __ldg(a.W + f);
+    if (a.wgen) {  // ACE_W_COUNTER: the tile is regenerated from the seed
+      for (int e = threadIdx.x; e < DK * BN; e += NT) {
+        const int k = e / BN, c = e % BN;
+        Ws[k][c] = (c < ncol && kc + k < a.d) ? counter_w(a.wseed, static_cast<size_t>(kc + k) * a.KL + c0 + c) : 0.f;
       }
-      Ws[k][c] = v;
+    } else {
+      for (int e = threadIdx.x; e < DK * BN; e += NT) {
+        const int k = e / BN, c = e % BN;
+        float v = 0.f;
+        if (c < ncol && kc + k < a.d) v = __ldg(a.W + static_cast<size_t>(kc + k) * a.KL + c0 + c);
+        Ws[k][c] = v;
+      }
     }
     __syncthreads();
     if (threadIdx.x < BM) {

@@ -519,3 +519,48 @@ def test_counter_projection_collision_probability(theta):
     p = 1.0 - th / math.pi
     frac = float(np.mean(ids[0] == ids[1]))
     assert abs(frac - p) < 5 * math.sqrt(p * (1 - p) / M) + 0.005, (frac, p)
+
+
+
+# ------------------------------------------------------------------------------------------
+# Eq. 3 computed exactly (the estimator-accuracy workload)
+# ------------------------------------------------------------------------------------------
+def test_exact_score_closed_forms():
+    """S(q, D) = sum_i p_i^K with p = 1 - theta/pi: a copy of q gives 1 (any scale), its
+    negation 0, an orthogonal point 2^-K, a point at angle theta (1 - theta/pi)^K, a zero point
+    2^-K (p = 1/2), and two zero vectors 1; the sum over a set is the sum of those."""
+    K = 7
+    q = np.array([[1.0, 2.0, -2.0]], dtype=np.float32)  # ||q|| = 3
+    u = q[0] / 3.0
+    v = np.array([2.0, 1.0, 2.0], dtype=np.float32) / 3.0  # u . v = 0
+    th = 0.7
+    at = (math.cos(th) * u + math.sin(th) * v).astype(np.float32)
+    Dset = np.stack([5 * q[0], -q[0], v, at, np.zeros(3, np.float32)]).astype(np.float32)
+    per = [1.0, 0.0, 2.0**-K, None, 2.0**-K]
+    xd = at.astype(np.float64)
+    thd = math.acos(float(xd @ u.astype(np.float64)) / (np.linalg.norm(xd) * np.linalg.norm(u.astype(np.float64))))
+    per[3] = (1 - thd / math.pi) ** K
+    for i, want in enumerate(per):
+        got = float(oracle.exact_score(q, Dset[i:i + 1], K)[0])
+        assert math.isclose(got, want, rel_tol=1e-12, abs_tol=1e-15), (i, got, want)
+    assert math.isclose(float(oracle.exact_score(q, Dset, K)[0]), sum(per), rel_tol=1e-12)
+    z = np.zeros((1, 3), dtype=np.float32)
+    assert float(oracle.exact_score(z, z, K)[0]) == 1.0
+    # RSE over the whole set is S itself
+    assert math.isclose(float(oracle.rse(q, Dset, K, np.arange(5))[0]), sum(per), rel_tol=1e-12)
+
+
+def test_theorem1_with_exact_score():
+    """The oracle detector's score averages, over L arrays, to S(q, D) of Eq. 3 (Theorem 1):
+    within five standard errors at L = 60,000 for three queries on a small clustered set."""
+    rng = np.random.default_rng(9)
+    d, K, L = 4, 3, 60_000
+    D = (rng.standard_normal((12, d)) + np.array([2.0, 0, 0, 0])).astype(np.float32)
+    Q = rng.standard_normal((3, d)).astype(np.float32)
+    det = oracle.Detector(d, K, L, seed=5)
+    det.insert(D)
+    scores, _, _ = det.score(Q, 1.0)
+    S = oracle.exact_score(Q, D, K)
+    for j in range(3):
+        se = math.sqrt(len(D) * S[j] / L)
+        assert abs(scores[j] - S[j]) < 5 * se + 1e-12, (j, scores[j], S[j])
