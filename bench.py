@@ -270,13 +270,15 @@ def per_config(cases) -> dict:
         xb = 2 if w.get("dtype") == "bf16" else 4
         flop = 2.0 * n * w["d"] * w["K"] * w["L"]
         res = {"n": n, "d": w["d"], "K": w["K"], "L": w["L"], "x_dtype": "bf16" if xb == 2 else "f32"}
-        variants = [("fp32", ace.ACE_PROJ_FP32, False), ("bf16", ace.ACE_PROJ_BF16, False)]
+        variants = [("fp32", ace.ACE_PROJ_FP32, {}), ("bf16", ace.ACE_PROJ_BF16, {})]
         if w.get("w_bf16_variant"):
-            variants.append(("bf16_w_bf16", ace.ACE_PROJ_BF16, True))
-            variants.append(("fp8_w_bf16", ace.ACE_PROJ_FP8, True))
-        for prec, want, wb in variants:
+            variants.append(("bf16_w_bf16", ace.ACE_PROJ_BF16, {"w_bf16": True}))
+            variants.append(("fp8_w_bf16", ace.ACE_PROJ_FP8, {"w_bf16": True}))
+        # the structured +-1 projection (a different hash family: other ids, its own roofline)
+        variants.append(("fwht_hadamard", ace.ACE_PROJ_FWHT, {"w_hadamard": True}))
+        for prec, want, kw in variants:
             try:
-                det = ace.Detector(w["d"], w["K"], w["L"], seed=11, precision=prec.split("_")[0], w_bf16=wb)
+                det = ace.Detector(w["d"], w["K"], w["L"], seed=11, precision=prec.split("_")[0], **kw)
             except ace.AceError as e:
                 if e.code == ace.ACE_ERR_UNSUPPORTED:
                     res[prec] = "engine not available for this shape"
@@ -317,6 +319,12 @@ def per_config(cases) -> dict:
                                               "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                                               "frac": flop / th / 1e12 / peaks["bf16_tflops"],
                                               "peak_src": f"bf16 burst, {peaks['src']}"}
+                elif prec.startswith("fwht"):
+                    # HBM-bound: X read once, ids written once (2 or 4 bytes per table)
+                    byts = n * (w["d"] * xb + w["L"] * (2 if w["K"] <= 16 else 4))
+                    entry["hash_roofline"] = {"bound": "hbm", "achieved": byts / th / 1e9, "peak": peaks["hbm_gbs"],
+                                              "unit": "GB/s", "frac": byts / th / 1e9 / peaks["hbm_gbs"],
+                                              "peak_src": f"HBM copy, {peaks['src']}"}
                 elif prec.startswith("fp8"):
                     pk = 2.0 * peaks["bf16_tflops"]
                     entry["hash_roofline"] = {"bound": "tensor", "achieved": flop / th / 1e12, "peak": pk,
@@ -327,7 +335,7 @@ def per_config(cases) -> dict:
                                               "unit": "TFLOP/s", "frac": flop / th / 1e12 / FP32_ALU_PEAK_TFLOPS,
                                               "peak_src": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"}
             res[prec] = entry
-        for v in ("bf16", "bf16_w_bf16", "fp8_w_bf16"):
+        for v in ("bf16", "bf16_w_bf16", "fp8_w_bf16", "fwht_hadamard"):
             if isinstance(res.get(v), dict) and isinstance(res.get("fp32"), dict):
                 res[f"{v}_vs_fp32"] = res[v]["points_per_s"] / res["fp32"]["points_per_s"]
         out[name] = res
@@ -629,7 +637,7 @@ def run_ours(args):
         host_batches = _batches(rank, n)
         X = [torch.from_numpy(b).to(dev) for b in host_batches]
     seed = 1234 + rank
-    det = ace.Detector(D, KH, LT, seed=seed, precision=args.precision, w_bf16=args.w_bf16)
+    det = ace.Detector(D, KH, LT, seed=seed, precision=args.precision, w_bf16=args.w_bf16, w_hadamard=args.w_hadamard)
     stream = torch.cuda.current_stream(dev)
     sc = torch.empty(n, dtype=torch.float64, device=dev)
     su = torch.empty(n, dtype=torch.int32, device=dev)
@@ -701,6 +709,11 @@ def run_ours(args):
             kkey = "hash_tc" if D <= 64 else "hash_gemm"
             roof = {"bound": "tensor", "achieved": flops / t / 1e12, "peak": peaks["bf16_tflops"],
                     "unit": "TFLOP/s", "peak_src": f"bf16 burst, {peaks['src']}"}
+        elif precision == ace.ACE_PROJ_FWHT:
+            kkey = "hash_fwht"
+            byts = n * (D * (2 if args.workload == "highdim" else 4) + LT * (2 if KH <= 16 else 4))
+            roof = {"bound": "hbm", "achieved": byts / t / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "peak_src": f"HBM copy, {peaks['src']}"}
         elif precision == ace.ACE_PROJ_FP8:
             kkey = "hash_gemm_fp8"
             roof = {"bound": "tensor", "achieved": flops / t / 1e12, "peak": 2.0 * peaks["bf16_tflops"],
@@ -723,10 +736,10 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {ace.ACE_PROJ_BF16: "bf16", ace.ACE_PROJ_FP8: "e4m3"}.get(precision, "f32"), "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": ["fp32", "bf16", "fp8"][precision] if precision in (0, 1, 2) else precision,
+        "config": {"workload": WORKLOAD, "precision": ["fp32", "bf16", "fp8", "fwht"][precision] if precision in (0, 1, 2, 3) else precision,
                    "l2": ("inputs rotate over 2 resident batches (2 x 2 GB > 129 MB L2)" if args.workload == "highdim"
                           else "inputs rotate over 3 resident batches (246 MB > 129 MB L2)"),
-                   "w": "bfloat16-valued" if args.w_bf16 else "binary32",
+                   "w": "structured +-1 (Hadamard rows, random signs)" if args.w_hadamard else ("bfloat16-valued" if args.w_bf16 else "binary32"),
                    "parallelism": f"replicas x{ws} (independent detectors, no collective)"},
         "roofline": roof,
         "step_roofline": _step_roofline(n, D, KH, LT, 2 if args.workload == "highdim" else 4, ms_max / args.steps,
@@ -782,11 +795,13 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16", "fp8"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16", "fp8", "fwht"])
     ap.add_argument("--n", type=int, default=None, help="points per batch (profiling runs only)")
     ap.add_argument("--workload", default="kdd", choices=["kdd", "highdim"],
                     help="kdd: the headline KDD-shaped workload; highdim: d = 1024 bfloat16 (profiling runs)")
     ap.add_argument("--w-bf16", dest="w_bf16", action="store_true", help="draw W in bfloat16 (ace_create_ex)")
+    ap.add_argument("--w-hadamard", dest="w_hadamard", action="store_true",
+                    help="structured +-1 W (ACE_W_HADAMARD); with --precision fwht or auto, the transform engine")
     ap.add_argument("--ref-sample", type=int, default=100_000, help="points per reference step")
     ap.add_argument("--ref-budget", type=float, default=REF_BUDGET_S, help="seconds of timed reference work")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

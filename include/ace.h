@@ -64,6 +64,8 @@ enum {
   ACE_PROJ_AUTO = -1, /* fastest available path for the detector's shape (default)       */
   ACE_PROJ_FP32 = 0,  /* binary32 FMA on the SIMT cores                                   */
   ACE_PROJ_BF16 = 1,  /* bfloat16 split operands on tcgen05 tensor cores, binary32 accum.  */
+  ACE_PROJ_FWHT = 3,  /* structured engine of ACE_W_HADAMARD detectors: fast Walsh-Hadamard
+                         transforms, O(dp log dp) additions per block of dp projections     */
   ACE_PROJ_FP8 = 2    /* E4M3 split operands (X = X1 + X2 per row with a power-of-two row
                          scale, W = W1 + W2 per column), four kind::f8f6f4 products in binary32:
                          streaming engine and bfloat16-valued W (ACE_W_BF16) only          */
@@ -101,7 +103,8 @@ typedef struct {
 /* Creation flags (ace_create_ex). */
 enum {
   ACE_W_BF16 = 1u,   /* round every drawn W entry to bfloat16 (nearest even), kept as binary32 */
-  ACE_W_COUNTER = 2u /* integer-only entries regenerated from the seed inside the kernels   */
+  ACE_W_COUNTER = 2u, /* integer-only entries regenerated from the seed inside the kernels  */
+  ACE_W_HADAMARD = 4u /* structured +-1 projections: Walsh-Hadamard rows with random signs  */
 };
 
 /*
@@ -140,6 +143,18 @@ int ace_create_ex(int d, int K, int L, uint64_t seed, unsigned flags, ace_handle
  * the binary64 definition's for this W.  Takes precedence over ACE_W_BF16 (its entries are
  * bfloat16 values already).  A checkpoint of such a detector (ace_save) loads as a detector
  * with the same W stored (ace_load): the results are the same.
+ *
+ * ACE_W_HADAMARD (§2.2: Fast-JL projections, O(d log d + m) hashes): W[i][c] = D_b[i] H[j][i]
+ * for column c = b dp + j, with dp the power of two >= max(d, 32), H the Sylvester-Hadamard
+ * matrix of order dp (H[j][i] = (-1)^popcount(i & j)), and D_b[i] = -1 when the SplitMix64
+ * draw of index b dp + i (the counter mode above) has its lowest bit set, +1 otherwise.  Each
+ * block of dp projections of a point is then one Walsh-Hadamard transform of the point with
+ * random signs; the structured engine (ACE_PROJ_FWHT, chosen by ACE_PROJ_AUTO when d <= 1024
+ * and ceil(K*L / dp) dp <= 5120) computes it with O(dp log dp) additions per block and resolves every
+ * sign inside its rounding bound by the binary64 definition.  The entries are +-1 (bfloat16
+ * values), so every other engine computes the same ids from the stored W.  SRP's collision
+ * probability 1 - theta/pi holds for one column; columns of one block are orthogonal rather
+ * than independent.  Excludes ACE_W_COUNTER.
  */
 
 /* As ace_create, with an explicit host d x (K*L) row-major binary32 W (copied). */

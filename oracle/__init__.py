@@ -61,6 +61,7 @@ def _load():
         lib.oracle_projection_from_seed.argtypes = [i32, i32, i32, u64, P]
         lib.oracle_projection_from_seed_bf16.argtypes = [i32, i32, i32, u64, P]
         lib.oracle_projection_counter.argtypes = [i32, i32, i32, u64, P]
+        lib.oracle_projection_hadamard.argtypes = [i32, i32, i32, u64, P]
         lib.oracle_splitmix64_draw.argtypes = [u64, u64]
         lib.oracle_splitmix64_draw.restype = u64
         lib.oracle_hash.argtypes = [P, i32, i64, i32, P, i32, i32, P]
@@ -105,12 +106,16 @@ def splitmix64_draw(seed: int, t: int) -> int:
     return int(_load().oracle_splitmix64_draw(ctypes.c_uint64(seed), ctypes.c_uint64(t)))
 
 
-def projection_from_seed(d: int, K: int, L: int, seed: int, w_bf16: bool = False, counter: bool = False) -> np.ndarray:
+def projection_from_seed(d: int, K: int, L: int, seed: int, w_bf16: bool = False, counter: bool = False,
+                         hadamard: bool = False) -> np.ndarray:
     """d x (K*L) binary32 Gaussian matrix (SplitMix64 counter mode + Box-Muller); with w_bf16
     every value is then rounded to bfloat16 (nearest even); with counter, the integer-only
-    matrix (popcount of each draw - 32) / 4 instead."""
+    matrix (popcount of each draw - 32) / 4 instead; with hadamard, the structured +-1 matrix
+    (Sylvester-Hadamard rows with random signs per block of columns)."""
     W = np.empty((d, K * L), dtype=np.float32)
-    if counter:
+    if hadamard:
+        fn = _load().oracle_projection_hadamard
+    elif counter:
         fn = _load().oracle_projection_counter
     else:
         fn = _load().oracle_projection_from_seed_bf16 if w_bf16 else _load().oracle_projection_from_seed

@@ -17,6 +17,8 @@
  *   oracle_projection_counter    the integer-only projection (§3.4 regenerates projections
  *                                from stored seeds): W.flat[f] = (popcount(draw_f) - 32) / 4
  *                                with the same SplitMix64 counter-mode draws.
+ *   oracle_projection_hadamard   the structured +-1 projection (Fast-JL family, §2.2): rows of
+ *                                a Sylvester-Hadamard matrix with random signs per block.
  *   oracle_hash                  Eq. 1 (SRP bit h_w(x) = sign(w^T x)) and Eq. 2
  *                                (K bits concatenated into the meta-hash H_j), §3.2.
  *   oracle_insert                Algorithm 1 pre-processing phase; §3.2 (counting phase).
@@ -104,6 +106,24 @@ void oracle_projection_counter(int d, int K, int L, uint64_t seed, float* W) {
   for (uint64_t f = 0; f < total; ++f) {
     int k = ones64(splitmix64_draw(seed, f)) - 32;
     W[f] = (float)k / 4.0f;
+  }
+}
+
+/* Structured projection (ACE_W_HADAMARD; the Fast-JL family of §2.2): dp = the power of    */
+/* two >= max(d, 32); column c = b dp + j has W[i][c] = D_b[i] * H[j][i] with the Sylvester  */
+/* Hadamard entry H[j][i] = (-1)^(number of ones of i AND j) and D_b[i] = -1 when draw        */
+/* b dp + i of the seed is odd, +1 otherwise.                                                  */
+void oracle_projection_hadamard(int d, int K, int L, uint64_t seed, float* W) {
+  const int KL = K * L;
+  int dp = 32;
+  while (dp < d) dp *= 2;
+  for (int i = 0; i < d; ++i) {
+    for (int c = 0; c < KL; ++c) {
+      const int b = c / dp, j = c % dp;
+      const int dneg = (int)(splitmix64_draw(seed, (uint64_t)b * (uint64_t)dp + (uint64_t)i) & 1u);
+      const int hneg = ones64((uint64_t)(i & j)) & 1;
+      W[(size_t)i * KL + c] = (dneg ^ hneg) ? -1.0f : 1.0f;
+    }
   }
 }
 

@@ -16,10 +16,12 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libace_gb300.so")
 
 ACE_OK, ACE_ERR_ARG, ACE_ERR_OOM, ACE_ERR_OVERFLOW, ACE_ERR_TIMEOUT, ACE_ERR_CUDA, ACE_ERR_UNSUPPORTED = range(7)
 ACE_F32, ACE_BF16 = 0, 1
-ACE_PROJ_AUTO, ACE_PROJ_FP32, ACE_PROJ_BF16, ACE_PROJ_FP8 = -1, 0, 1, 2
+ACE_PROJ_AUTO, ACE_PROJ_FP32, ACE_PROJ_BF16, ACE_PROJ_FP8, ACE_PROJ_FWHT = -1, 0, 1, 2, 3
 ACE_W_BF16 = 1
 ACE_W_COUNTER = 2
-PRECISIONS = {"auto": ACE_PROJ_AUTO, "fp32": ACE_PROJ_FP32, "bf16": ACE_PROJ_BF16, "fp8": ACE_PROJ_FP8}
+ACE_W_HADAMARD = 4
+PRECISIONS = {"auto": ACE_PROJ_AUTO, "fp32": ACE_PROJ_FP32, "bf16": ACE_PROJ_BF16, "fp8": ACE_PROJ_FP8,
+              "fwht": ACE_PROJ_FWHT}
 
 # Every symbol include/ace.h declares (checked by the tests).
 EXPORTS = [
@@ -160,12 +162,13 @@ class Detector:
     current CUDA device."""
 
     def __init__(self, d: int, K: int, L: int, seed: int = 0, W: np.ndarray | None = None,
-                 precision: str = "auto", w_bf16: bool = False, w_counter: bool = False):
+                 precision: str = "auto", w_bf16: bool = False, w_counter: bool = False, w_hadamard: bool = False):
         lib = load_library()
         self.d, self.K, self.L = int(d), int(K), int(L)
         h = ctypes.c_void_p()
         if W is None:
-            flags = (ACE_W_BF16 if w_bf16 else 0) | (ACE_W_COUNTER if w_counter else 0)
+            flags = (ACE_W_BF16 if w_bf16 else 0) | (ACE_W_COUNTER if w_counter else 0) | \
+                (ACE_W_HADAMARD if w_hadamard else 0)
             _check(lib.ace_create_ex(self.d, self.K, self.L, ctypes.c_uint64(int(seed) & (2**64 - 1)),
                                      flags, ctypes.byref(h)))
         else:

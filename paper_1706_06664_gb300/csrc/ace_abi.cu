@@ -25,6 +25,7 @@
 #include "gemm_plan.h"
 #include "tc_plan.h"
 #include "tc_ptx.cuh"
+#include "fwht_plan.h"
 
 namespace {
 
@@ -108,6 +109,10 @@ struct ace_detector {
   cudaStream_t rstream = nullptr;
   cudaEvent_t ev_hashed = nullptr, ev_resolved = nullptr;
   // streaming tensor-core path (large d, bfloat16 input; hash_gemm.cu)
+  // ACE_W_HADAMARD: the structured engine (hash_fwht.cu)
+  bool hadamard = false, fwht_ok = false;
+  ace::FwhtArgs fw{};
+  uint32_t* gdsign = nullptr;   // [nblk][dp/32] sign words of the blocks' diagonals
   bool wgen = false;             // ACE_W_COUNTER: the SIMT engine regenerates W tiles from wseed
   uint64_t wseed = 0;
   bool gemm_ok = false;
@@ -211,6 +216,7 @@ void free_all(ace_detector* h) {
   cudaFree(h->gprof);
   cudaFree(h->gcolf);
   cudaFree(h->gwt16);
+  cudaFree(h->gdsign);
   cudaFree(h->gimg8);
   cudaFree(h->gprof8);
   cudaFree(h->gcolf8);
@@ -837,9 +843,12 @@ int make_detector(int d, int K, int L, const float* Wsrc, uint64_t seed, bool fr
                   ace_handle* out) {
   if (!out) return fail(ACE_ERR_ARG, "out is NULL");
   *out = nullptr;
-  if (flags & ~static_cast<unsigned>(ACE_W_BF16 | ACE_W_COUNTER))
+  if (flags & ~static_cast<unsigned>(ACE_W_BF16 | ACE_W_COUNTER | ACE_W_HADAMARD))
     return fail(ACE_ERR_ARG, "unknown creation flags 0x%x", flags);
-  if ((flags & ACE_W_COUNTER) && !from_seed) return fail(ACE_ERR_ARG, "ACE_W_COUNTER needs a seed");
+  if ((flags & (ACE_W_COUNTER | ACE_W_HADAMARD)) && !from_seed)
+    return fail(ACE_ERR_ARG, "ACE_W_COUNTER and ACE_W_HADAMARD need a seed");
+  if ((flags & ACE_W_COUNTER) && (flags & ACE_W_HADAMARD))
+    return fail(ACE_ERR_ARG, "ACE_W_COUNTER and ACE_W_HADAMARD exclude each other");
   if (d < 1 || K < 1 || K > 24 || L < 1 || static_cast<long long>(K) * L > 65536)
     return fail(ACE_ERR_ARG, "invalid shape d=%d K=%d L=%d (need d>=1, 1<=K<=24, L>=1, K*L<=65536)", d, K, L);
   if (!from_seed && !Wsrc) return fail(ACE_ERR_ARG, "W_host is NULL");
@@ -862,7 +871,13 @@ int make_detector(int d, int K, int L, const float* Wsrc, uint64_t seed, bool fr
     delete h;
     return fail(ACE_ERR_OOM, "host allocation of W failed");
   }
-  if (flags & ACE_W_COUNTER) {
+  std::vector<uint32_t> dsign;
+  if (flags & ACE_W_HADAMARD) {
+    const int dp = ace::fwht_order(d);
+    dsign.assign(static_cast<size_t>((h->KL + dp - 1) / dp) * (dp / 32), 0u);
+    ace::generate_projection_hadamard(d, K, L, seed, h->Wh.data(), dsign.data());
+    h->hadamard = true;
+  } else if (flags & ACE_W_COUNTER) {
     ace::generate_projection_counter(d, K, L, seed, h->Wh.data());
     h->wgen = true;
     h->wseed = seed;
@@ -914,6 +929,32 @@ int make_detector(int d, int K, int L, const float* Wsrc, uint64_t seed, bool fr
     free_all(h);
     delete h;
     return rc;
+  }
+  if (h->hadamard) {
+    // the structured engine: the transform's order dp, its sign words, and the guard constant
+    // (gamma_m of the m-level addition tree + gamma64_d of the binary64 definition, 1 % margin)
+    ace::FwhtArgs& f = h->fw;
+    f = ace::FwhtArgs{};
+    f.d = d;
+    f.dp = ace::fwht_order(d);
+    f.m = 0;
+    while ((1 << f.m) < f.dp) ++f.m;
+    f.K = K;
+    f.L = L;
+    f.KL = h->KL;
+    f.nblk = (h->KL + f.dp - 1) / f.dp;
+    const double u = std::ldexp(1.0, -24), u64 = std::ldexp(1.0, -53);
+    const double gm = f.m * u / (1.0 - f.m * u), g64 = d * u64 / (1.0 - d * u64);
+    f.cband = std::nextafter(static_cast<float>((gm + g64) * 1.01), FLT_MAX);
+    f.babs = static_cast<float>(f.m * std::ldexp(1.0, -146));
+    f.Wt = h->Wt;
+    f.st = h->st;
+    h->fwht_ok = f.dp <= ace::kFwhtMaxDp && f.nblk * (f.dp / 32) <= ace::kFwhtMaxWords;
+    if ((e = cudaMalloc(&h->gdsign, dsign.size() * sizeof(uint32_t))) != cudaSuccess) return bad(e, "cudaMalloc signs");
+    if ((e = cudaMemcpy(h->gdsign, dsign.data(), dsign.size() * sizeof(uint32_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bad(e, "copy signs");
+    f.dsign = h->gdsign;
+    if (h->fwht_ok) h->precision = ACE_PROJ_AUTO;
   }
   if (h->tc_ok) {
     if ((e = cudaStreamCreateWithFlags(&h->rstream, cudaStreamNonBlocking)) != cudaSuccess) return bad(e, "recheck stream");
@@ -994,13 +1035,14 @@ size_t id_bytes(ace_handle h) { return h->K <= 16 ? 2 : 4; }
 // Hashes a.n points into the ids scratch (a.ids, leading dimension a.ld).  With kInsert the
 // counts are incremented too: fused in the SIMT engine; on the tensor-core path by a pass over
 // the stored ids, which `tc_insert` = false leaves to the caller (chunked hashing of one batch).
-enum class Engine { kSimt, kResident, kStreaming };
+enum class Engine { kSimt, kResident, kStreaming, kFwht };
 
 // The engine that hashes X: binary32 SIMT when asked for, or when no tensor-core design fits;
 // the resident tensor-core design for d <= 64 (any input type); the streaming one for larger
 // d with bfloat16 input at a 16-byte-aligned address (the TMA engine's rule).
 Engine pick_engine(ace_handle h, int x_bf16, const void* X) {
   if (h->precision == ACE_PROJ_FP32) return Engine::kSimt;
+  if (h->precision == ACE_PROJ_FWHT || (h->precision == ACE_PROJ_AUTO && h->fwht_ok)) return Engine::kFwht;
   if (h->precision == ACE_PROJ_FP8)
     return h->gemm8_ok && x_bf16 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0 ? Engine::kStreaming : Engine::kSimt;
   if (h->tc_ok) return Engine::kResident;
@@ -1121,6 +1163,39 @@ int run_hash(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_inser
     return ACE_OK;
   }
   if (eng == Engine::kStreaming) return run_gemm(h, a, s, tc_insert);
+  if (eng == Engine::kFwht) {  // structured engine: ids (or projections), then the count increments
+    const bool insert = (a.mode & ace::kInsert) != 0;
+    void* ids = a.ids;
+    if (insert && (!ids || ids == h->ids)) {
+      if (int rc = grow(&h->ids, &h->ids_cap, ids_need(h, a.n), s, "ids scratch")) return rc;
+      ids = h->ids;
+    }
+    ace::FwhtArgs f = h->fw;
+    f.X = a.X;
+    f.x_bf16 = a.x_bf16;
+    f.n = a.n;
+    f.mode = (a.mode & ~ace::kInsert) | (insert ? ace::kStoreIds : 0);
+    f.ids = ids;
+    f.ld = a.ld;
+    f.ids_rm = a.ids_rm;
+    f.proj = a.proj;
+    if (!(a.mode & ace::kStoreProj)) {
+      h->last_precision = ACE_PROJ_FWHT;
+      h->last_products = 0;
+    }
+    cudaError_t e;
+    {
+      PhaseScope ps(h, ACE_PHASE_HASH, s);
+      e = ace::launch_hash_fwht(f, h->num_sms, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "structured hash kernel launch");
+    if (insert && tc_insert) {
+      PhaseScope ps(h, ACE_PHASE_INSERT, s);
+      e = ace::launch_insert_from_ids(ids, h->K <= 16, a.ld, a.n, h->K, h->L, h->counts, h->num_sms, s);
+      if (e != cudaSuccess) return cuda_fail(e, "insert kernel launch");
+    }
+    return ACE_OK;
+  }
   // tensor-core engine (ids only), the binary64 resolution of the deferred tables, then the
   // count increments from the stored ids.  With 16-bit ids and K <= 15 the deferred tables are
   // tagged (kTagDeferred): their resolution, which counts them too, runs on rstream while the
@@ -1463,8 +1538,12 @@ int ace_set_graph(ace_handle h, int enable) {
 int ace_set_precision(ace_handle h, int precision) {
   if (!h) return fail(ACE_ERR_ARG, "handle is NULL");
   if (precision != ACE_PROJ_AUTO && precision != ACE_PROJ_FP32 && precision != ACE_PROJ_BF16 &&
-      precision != ACE_PROJ_FP8)
+      precision != ACE_PROJ_FP8 && precision != ACE_PROJ_FWHT)
     return fail(ACE_ERR_ARG, "unknown precision %d", precision);
+  if (precision == ACE_PROJ_FWHT && !h->fwht_ok)
+    return fail(ACE_ERR_UNSUPPORTED, "the structured engine needs a detector created with ACE_W_HADAMARD, d <= %d "
+                                     "and ceil(K*L / dp) dp <= %d (d=%d K=%d L=%d)", ace::kFwhtMaxDp,
+                ace::kFwhtMaxWords * 32, h->d, h->K, h->L);
   if (precision == ACE_PROJ_FP8 && !h->gemm8_ok)
     return fail(ACE_ERR_UNSUPPORTED, "the E4M3 projection needs the streaming tensor-core engine (an sm_103 device, "
                                      "d > 64 and a multiple of 8) and a W whose entries are all bfloat16 values "

@@ -17,6 +17,7 @@
 #include <cstring>
 
 #include "ace_internal.h"
+#include "fwht_plan.h"
 
 namespace ace {
 
@@ -47,6 +48,24 @@ void round_projection_bf16(float* W, uint64_t total) {
     const uint32_t u = static_cast<uint32_t>(to_bf16(W[i])) << 16;
     std::memcpy(&W[i], &u, 4);
   }
+}
+
+void generate_projection_hadamard(int d, int K, int L, uint64_t seed, float* W, uint32_t* dsign) {
+  const int KL = K * L, dp = fwht_order(d), nblk = (KL + dp - 1) / dp;
+  for (int b = 0; b < nblk; ++b)
+    for (int w = 0; w < dp / 32; ++w) {
+      uint32_t word = 0;
+      for (int t = 0; t < 32; ++t)
+        if (draw(seed, static_cast<uint64_t>(b) * dp + 32u * w + t) & 1u) word |= 1u << t;
+      dsign[b * (dp / 32) + w] = word;
+    }
+  for (int i = 0; i < d; ++i)
+    for (int c = 0; c < KL; ++c) {
+      const int b = c / dp, j = c % dp;
+      const bool neg_d = (dsign[b * (dp / 32) + i / 32] >> (i % 32)) & 1u;
+      const bool neg_h = __builtin_popcount(static_cast<unsigned>(i & j)) & 1;
+      W[static_cast<size_t>(i) * KL + c] = (neg_d != neg_h) ? -1.0f : 1.0f;
+    }
 }
 
 void generate_projection_counter(int d, int K, int L, uint64_t seed, float* W) {

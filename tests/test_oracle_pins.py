@@ -564,3 +564,52 @@ def test_theorem1_with_exact_score():
     for j in range(3):
         se = math.sqrt(len(D) * S[j] / L)
         assert abs(scores[j] - S[j]) < 5 * se + 1e-12, (j, scores[j], S[j])
+
+
+# ------------------------------------------------------------------------------------------
+# Structured projection (ACE_W_HADAMARD)
+# ------------------------------------------------------------------------------------------
+def test_hadamard_projection_definition():
+    """W[i][c] = D_b[i] H[j][i] (c = b dp + j): scipy's Sylvester-Hadamard matrix and the sign
+    of each SplitMix64 draw (whose values the published vectors pin) give the same matrix, for
+    a d that needs padding (41 -> 64) and several blocks (K L = 750)."""
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    d, K, L, seed = 41, 15, 50, 99
+    W = oracle.projection_from_seed(d, K, L, seed, hadamard=True)
+    dp, KL = 64, K * L
+    H = scipy_linalg.hadamard(dp)
+    ref = np.zeros((d, KL), dtype=np.float32)
+    for c in range(KL):
+        b, j = divmod(c, dp)
+        for i in range(d):
+            ref[i, c] = (-1.0 if oracle.splitmix64_draw(seed, b * dp + i) & 1 else 1.0) * H[j, i]
+    assert np.array_equal(W, ref)
+
+
+def test_hadamard_blocks_are_orthogonal():
+    """With d = dp (no padding) the dp columns of one block are orthogonal: W_b^T W_b = dp I."""
+    d = 64
+    W = oracle.projection_from_seed(d, 16, 12, 7, hadamard=True).astype(np.int64)
+    for b in range(W.shape[1] // d):
+        Wb = W[:, b * d:(b + 1) * d]
+        assert np.array_equal(Wb.T @ Wb, d * np.eye(d, dtype=np.int64)), b
+
+
+@pytest.mark.parametrize("theta", [math.pi / 6, math.pi / 2, 5 * math.pi / 6])
+def test_hadamard_collision_probability(theta):
+    """Each column is a random +-1 vector (a Hadamard row times random signs), so one SRP bit
+    of two points at angle theta agrees with probability close to 1 - theta/pi: within 0.01
+    over 2^17 columns (4,096 blocks with independent signs) in d = 16."""
+    d, M = 16, 1 << 17
+    rng = np.random.default_rng(int(theta * 1000))
+    x = rng.standard_normal(d)
+    x /= np.linalg.norm(x)
+    z = rng.standard_normal(d)
+    z -= (z @ x) * x
+    z /= np.linalg.norm(z)
+    X = np.stack([x, math.cos(theta) * x + math.sin(theta) * z]).astype(np.float32)
+    W = oracle.projection_from_seed(d, 1, M, seed=4242, hadamard=True)
+    ids = oracle.hash_ids(X, W, 1, M)
+    xd, yd = X.astype(np.float64)
+    th = math.acos(float(xd @ yd) / (np.linalg.norm(xd) * np.linalg.norm(yd)))
+    assert abs(float(np.mean(ids[0] == ids[1])) - (1.0 - th / math.pi)) < 0.01
