@@ -27,10 +27,26 @@ namespace {
 // stored as it is finished.
 constexpr int kIdBufBytes = 4096;
 
+// Dynamic shared memory of one 8-warp block: per warp the sign words of its current point and
+// an id buffer; the per-lane sign masks of every block of columns; for dp = 1024 a 32 x 33
+// transpose tile per warp.
+template <int E>
+struct FwhtSmem {
+  static constexpr size_t words = 0;                                         // uint32 [8][kFwhtMaxWords]
+  static constexpr size_t idbuf = words + 8 * kFwhtMaxWords * 4;             // bytes [8][kIdBufBytes]
+  static constexpr size_t smask = idbuf + 8 * kIdBufBytes;                   // uint32 [kFwhtMaxWords / E][32]
+  static constexpr size_t tbuf = smask + (kFwhtMaxWords / E) * 32 * 4;       // float [8][32 * 33] (E = 32)
+  static constexpr size_t bytes = tbuf + (E == 32 ? 8 * 32 * 33 * 4 : 0);
+};
+
 template <bool BF16, typename IdT, int E>
 __global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ FwhtArgs a) {
-  __shared__ uint32_t words[8][kFwhtMaxWords];
-  __shared__ __align__(16) unsigned char idbuf[8][kIdBufBytes];
+  extern __shared__ __align__(16) unsigned char fsm[];
+  using SM = FwhtSmem<E>;
+  uint32_t (*words)[kFwhtMaxWords] = reinterpret_cast<uint32_t (*)[kFwhtMaxWords]>(fsm + SM::words);
+  unsigned char (*idbuf)[kIdBufBytes] = reinterpret_cast<unsigned char (*)[kIdBufBytes]>(fsm + SM::idbuf);
+  uint32_t* const smask = reinterpret_cast<uint32_t*>(fsm + SM::smask);  // [nblk][32]: lane l's flip bits of block b
+  float (*tbuf)[32 * 33] = reinterpret_cast<float (*)[32 * 33]>(fsm + SM::tbuf);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int d = a.d, dp = a.dp, K = a.K, L = a.L, KL = a.KL, nblk = a.nblk, mode = a.mode;
   const long long n = a.n, ld = a.ld;
@@ -40,6 +56,15 @@ __global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ 
   const bool gather = static_cast<long long>(L) * 32 * static_cast<long long>(sizeof(IdT)) <= kIdBufBytes &&
                       (mode & kStoreIds) && !(mode & kStoreProj);
   const int nwords = nblk * E;
+  // per-lane sign masks, the same for every point: bit e of smask[b][l] is the sign bit of
+  // coordinate 32 e + l in block b
+  for (int t = threadIdx.x; t < nblk * 32; t += blockDim.x) {
+    const int b = t / 32, l = t % 32;
+    uint32_t mk = 0u;
+    for (int e = 0; e < E; ++e) mk |= ((__ldg(a.dsign + b * E + e) >> l) & 1u) << e;
+    smask[t] = mk;
+  }
+  __syncthreads();
   unsigned long long nre = 0;
   // each warp takes groups of 32 consecutive points
   const long long ngroups = (n + 31) / 32;
@@ -85,22 +110,12 @@ __global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ 
       if (lane == 0 && !isfinite(q) && !(mode & kStoreProj)) atomicAdd(&a.st->nonfinite, 1ull);
       const float B = __fmaf_ru(cband, sa, babs);  // +inf or NaN for a non-finite row: all exact
       for (int b = 0; b < nblk; ++b) {
+        // sign flips: bit e of this lane's mask for block b flips coordinate 32 e + lane
+        const uint32_t fm = smask[b * 32 + lane];
         float v[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const uint32_t sw = __ldg(a.dsign + b * E + e);
-          v[e] = ((sw >> lane) & 1u) ? -x[e] : x[e];
-        }
-        // butterflies on the lane bits (coordinates differing in bit 0..4 of t = 32 e + lane)
-#pragma unroll
-        for (int h = 1; h < 32; h <<= 1) {
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            const float o = __shfl_xor_sync(0xFFFFFFFFu, v[e], h);
-            v[e] = (lane & h) ? __fsub_rn(o, v[e]) : __fadd_rn(v[e], o);
-          }
-        }
-        // butterflies on the slot bits (bit 5.. of t)
+        for (int e = 0; e < E; ++e) v[e] = __uint_as_float(__float_as_uint(x[e]) ^ (((fm >> e) & 1u) << 31));
+        // butterflies on the slot bits (bit 5.. of t = 32 e + lane), within the lane
 #pragma unroll
         for (int h = 1; h < E; h <<= 1) {
 #pragma unroll
@@ -112,17 +127,65 @@ __global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ 
             }
           }
         }
+        if constexpr (E == 32) {
+          // dp = 1024: transpose through shared memory (lane l then holds t = 32 l .. 32 l + 31),
+          // so the five stages on the low bits are within the lane too, and the lane's 32
+          // outputs are the 32 columns of one sign word
+          float* const tile = tbuf[wib];  // [32][33]
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int col = b * dp + e * 32 + lane;
-          bool bit = v[e] > 0.f;
-          if (!(fabsf(v[e]) > B) && col < KL && !(mode & kStoreProj)) {  // inside the bound (or NaN)
-            bit = exact_bit<BF16>(a.X, i, d, a.Wt, col);
-            ++nre;
+          for (int e = 0; e < 32; ++e) tile[e * 33 + lane] = v[e];
+          __syncwarp();
+#pragma unroll
+          for (int e = 0; e < 32; ++e) v[e] = tile[lane * 33 + e];
+          __syncwarp();
+#pragma unroll
+          for (int h = 1; h < 32; h <<= 1) {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              if ((e & h) == 0) {
+                const float lo = v[e], hi = v[e + h];
+                v[e] = __fadd_rn(lo, hi);
+                v[e + h] = __fsub_rn(lo, hi);
+              }
+            }
           }
-          if ((mode & kStoreProj) && col < KL) a.proj[i * static_cast<long long>(KL) + col] = v[e];
-          const uint32_t wv = __ballot_sync(0xFFFFFFFFu, bit);
-          if (lane == 0) wrow[b * E + e] = wv;
+          uint32_t wv = 0u;
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            const int col = b * dp + lane * 32 + e;
+            bool bit = v[e] > 0.f;
+            if (!(fabsf(v[e]) > B) && col < KL && !(mode & kStoreProj)) {  // inside the bound (or NaN)
+              bit = exact_bit<BF16>(a.X, i, d, a.Wt, col);
+              ++nre;
+            }
+            if ((mode & kStoreProj) && col < KL) a.proj[i * static_cast<long long>(KL) + col] = v[e];
+            wv |= (bit ? 1u : 0u) << e;
+          }
+          wrow[b * 32 + lane] = wv;
+        } else {
+          // butterflies on the lane bits: o + s v with s = -1 on the upper lane of each pair
+          // (one rounded operation, the same as the sum or the difference)
+#pragma unroll
+          for (int h = 1; h < 32; h <<= 1) {
+            const float sg = (lane & h) ? -1.f : 1.f;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              const float o = __shfl_xor_sync(0xFFFFFFFFu, v[e], h);
+              v[e] = __fmaf_rn(sg, v[e], o);
+            }
+          }
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int col = b * dp + e * 32 + lane;
+            bool bit = v[e] > 0.f;
+            if (!(fabsf(v[e]) > B) && col < KL && !(mode & kStoreProj)) {  // inside the bound (or NaN)
+              bit = exact_bit<BF16>(a.X, i, d, a.Wt, col);
+              ++nre;
+            }
+            if ((mode & kStoreProj) && col < KL) a.proj[i * static_cast<long long>(KL) + col] = v[e];
+            const uint32_t wv = __ballot_sync(0xFFFFFFFFu, bit);
+            if (lane == 0) wrow[b * E + e] = wv;
+          }
         }
       }
       __syncwarp();
@@ -156,15 +219,20 @@ cudaError_t launch_hash_fwht(const FwhtArgs& a, int num_sms, cudaStream_t s) {
     return cudaErrorInvalidValue;
   const long long want = ((a.n + 31) / 32 + 7) / 8;  // groups of 32 points, 8 warps per block
   const unsigned grid = static_cast<unsigned>(std::min<long long>(want, static_cast<long long>(num_sms) * 8));
-  auto go = [&](auto kern) -> cudaError_t {
-    kern<<<grid, 256, 0, s>>>(a);
+  auto go = [&](auto kern, size_t smem) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 256, smem, s>>>(a);
     return cudaGetLastError();
   };
   const bool b16 = a.x_bf16 != 0, id16 = a.K <= 16;
 #define ACE_FWHT_CASE(EV)                                                                          \
   case EV:                                                                                         \
-    if (b16) return id16 ? go(hash_fwht_kernel<true, uint16_t, EV>) : go(hash_fwht_kernel<true, uint32_t, EV>); \
-    return id16 ? go(hash_fwht_kernel<false, uint16_t, EV>) : go(hash_fwht_kernel<false, uint32_t, EV>);
+    if (b16)                                                                                       \
+      return id16 ? go(hash_fwht_kernel<true, uint16_t, EV>, FwhtSmem<EV>::bytes)                  \
+                  : go(hash_fwht_kernel<true, uint32_t, EV>, FwhtSmem<EV>::bytes);                 \
+    return id16 ? go(hash_fwht_kernel<false, uint16_t, EV>, FwhtSmem<EV>::bytes)                   \
+                : go(hash_fwht_kernel<false, uint32_t, EV>, FwhtSmem<EV>::bytes);
   switch (E) {
     ACE_FWHT_CASE(1)
     ACE_FWHT_CASE(2)
