@@ -30,19 +30,30 @@ constexpr int kIdBufBytes = 4096;
 // Dynamic shared memory of one 8-warp block: per warp the sign words of its current point and
 // an id buffer; the per-lane sign masks of every block of columns; for dp = 1024 a 32 x 33
 // transpose tile per warp.
-template <int E>
+template <int E, int ESZ>
 struct FwhtSmem {
   static constexpr size_t words = 0;                                         // uint32 [8][kFwhtMaxWords]
   static constexpr size_t idbuf = words + 8 * kFwhtMaxWords * 4;             // bytes [8][kIdBufBytes]
   static constexpr size_t smask = idbuf + 8 * kIdBufBytes;                   // uint32 [kFwhtMaxWords / E][32]
   static constexpr size_t tbuf = smask + (kFwhtMaxWords / E) * 32 * 4;       // float [8][32 * 33] (E = 32)
-  static constexpr size_t bytes = tbuf + (E == 32 ? 8 * 32 * 33 * 4 : 0);
+  static constexpr size_t xrow = tbuf + (E == 32 ? 8 * 32 * 33 * 4 : 0);     // bytes [8][2][dp * ESZ] (E >= 16)
+  static constexpr size_t bytes = xrow + (E >= 16 ? 8 * 2 * (E * 32) * ESZ : 0);
 };
+
+// Asynchronous 16-byte copy global -> shared (cp.async, completion by group).
+__device__ __forceinline__ void cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 template <bool BF16, typename IdT, int E>
 __global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ FwhtArgs a) {
   extern __shared__ __align__(16) unsigned char fsm[];
-  using SM = FwhtSmem<E>;
+  using SM = FwhtSmem<E, BF16 ? 2 : 4>;
   uint32_t (*words)[kFwhtMaxWords] = reinterpret_cast<uint32_t (*)[kFwhtMaxWords]>(fsm + SM::words);
   unsigned char (*idbuf)[kIdBufBytes] = reinterpret_cast<unsigned char (*)[kIdBufBytes]>(fsm + SM::idbuf);
   uint32_t* const smask = reinterpret_cast<uint32_t*>(fsm + SM::smask);  // [nblk][32]: lane l's flip bits of block b
@@ -69,9 +80,28 @@ __global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ 
   // each warp takes groups of 32 consecutive points
   const long long ngroups = (n + 31) / 32;
   const long long nwarps = static_cast<long long>(gridDim.x) * (blockDim.x >> 5);
+  // Long rows (E >= 16) whose byte length is a multiple of 16 are staged in shared memory by
+  // asynchronous copies, double-buffered per warp: the next point's row is in flight while the
+  // current one is transformed.  The padding beyond d stays zero (it is never copied).
+  constexpr int kEsz = BF16 ? 2 : 4;
+  const bool staged = E >= 16 && (static_cast<long long>(d) * kEsz) % 16 == 0 &&
+                      (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0;
+  unsigned char* const xr = fsm + SM::xrow + static_cast<size_t>(wib) * 2 * (E * 32) * kEsz;
+  const int rbytes = d * kEsz, nchunk = rbytes / 16;
+  if (E >= 16) {
+    for (int t = lane; t < 2 * E * 32 * kEsz / 4; t += 32) reinterpret_cast<uint32_t*>(xr)[t] = 0u;  // zero padding
+    __syncwarp();
+  }
+  auto stage = [&](long long ii, int buf) {  // row ii into buffer buf (one copy group)
+    const unsigned char* src = static_cast<const unsigned char*>(a.X) + ii * rbytes;
+    unsigned char* dst = xr + buf * (E * 32) * kEsz;
+    for (int c = lane; c < nchunk; c += 32) cp16(dst + c * 16, src + c * 16);
+    cp_commit();
+  };
   for (long long g = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + wib; g < ngroups; g += nwarps) {
     const long long i0 = g * 32;
     const int np = static_cast<int>(min(32LL, n - i0));
+    if (staged) stage(i0, 0);
     // For short rows (E <= 8) each point's loads are issued for the next point while it is
     // transformed; for long rows the registers are better spent on resident warps.
     constexpr bool kPrefetch = E <= 8;
@@ -92,9 +122,26 @@ __global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ 
         if constexpr (kPrefetch) {
           x[e] = xn[e];
           if (p + 1 < np) xn[e] = t < d ? load_x<BF16>(a.X, (i + 1) * d + t) : 0.f;
-        } else {
+        } else if (!staged) {
           x[e] = t < d ? load_x<BF16>(a.X, i * d + t) : 0.f;
         }
+      }
+      if (staged) {
+        if (p + 1 < np) {
+          stage(i + 1, (p + 1) & 1);
+          cp_wait1();  // this point's group has landed
+        } else {
+          cp_wait0();
+        }
+        __syncwarp();
+        const unsigned char* row = xr + (p & 1) * (E * 32) * kEsz;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int t = e * 32 + lane;
+          if constexpr (BF16) x[e] = __uint_as_float(static_cast<uint32_t>(reinterpret_cast<const uint16_t*>(row)[t]) << 16);
+          else x[e] = reinterpret_cast<const float*>(row)[t];
+        }
+        __syncwarp();  // (the buffer is refilled two points later)
       }
       float sa = 0.f, q = 0.f;
 #pragma unroll
@@ -229,10 +276,10 @@ cudaError_t launch_hash_fwht(const FwhtArgs& a, int num_sms, cudaStream_t s) {
 #define ACE_FWHT_CASE(EV)                                                                          \
   case EV:                                                                                         \
     if (b16)                                                                                       \
-      return id16 ? go(hash_fwht_kernel<true, uint16_t, EV>, FwhtSmem<EV>::bytes)                  \
-                  : go(hash_fwht_kernel<true, uint32_t, EV>, FwhtSmem<EV>::bytes);                 \
-    return id16 ? go(hash_fwht_kernel<false, uint16_t, EV>, FwhtSmem<EV>::bytes)                   \
-                : go(hash_fwht_kernel<false, uint32_t, EV>, FwhtSmem<EV>::bytes);
+      return id16 ? go(hash_fwht_kernel<true, uint16_t, EV>, FwhtSmem<EV, 2>::bytes)               \
+                  : go(hash_fwht_kernel<true, uint32_t, EV>, FwhtSmem<EV, 2>::bytes);              \
+    return id16 ? go(hash_fwht_kernel<false, uint16_t, EV>, FwhtSmem<EV, 4>::bytes)                \
+                : go(hash_fwht_kernel<false, uint32_t, EV>, FwhtSmem<EV, 4>::bytes);
   switch (E) {
     ACE_FWHT_CASE(1)
     ACE_FWHT_CASE(2)

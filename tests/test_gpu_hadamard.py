@@ -39,7 +39,8 @@ def _check(det, ref, X):
         assert s[k] == r[k], k
 
 
-@pytest.mark.parametrize("shape", [(32, 10, 20), (41, 15, 50), (100, 12, 7), (256, 20, 8), (1024, 16, 64)])
+@pytest.mark.parametrize("shape", [(32, 10, 20), (41, 15, 50), (100, 12, 7), (256, 20, 8), (520, 16, 8), (1001, 12, 10),
+                                   (1024, 16, 64)])
 def test_structured_engine_parity(shape):
     d, K, L = shape
     det, ref = _pair(d, K, L, seed=d * 3 + K)
