@@ -50,7 +50,8 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-template <bool BF16, typename IdT, int E>
+// PROJ: the measurement path (the transform's binary32 outputs, no ids).
+template <bool BF16, typename IdT, int E, bool PROJ>
 __global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ FwhtArgs a) {
   extern __shared__ __align__(16) unsigned char fsm[];
   using SM = FwhtSmem<E, BF16 ? 2 : 4>;
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ 
   uint32_t* const wrow = words[wib];
   IdT* const ibuf = reinterpret_cast<IdT*>(idbuf[wib]);  // [L][32]
   const bool gather = static_cast<long long>(L) * 32 * static_cast<long long>(sizeof(IdT)) <= kIdBufBytes &&
-                      (mode & kStoreIds) && !(mode & kStoreProj);
+                      (mode & kStoreIds) && !PROJ;
   const int nwords = nblk * E;
   // per-lane sign masks, the same for every point: bit e of smask[b][l] is the sign bit of
   // coordinate 32 e + l in block b
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ 
         sa = __fadd_ru(sa, __shfl_xor_sync(0xFFFFFFFFu, sa, off));
         q += __shfl_xor_sync(0xFFFFFFFFu, q, off);
       }
-      if (lane == 0 && !isfinite(q) && !(mode & kStoreProj)) atomicAdd(&a.st->nonfinite, 1ull);
+      if (lane == 0 && !isfinite(q) && !PROJ) atomicAdd(&a.st->nonfinite, 1ull);
       const float B = __fmaf_ru(cband, sa, babs);  // +inf or NaN for a non-finite row: all exact
       for (int b = 0; b < nblk; ++b) {
         // sign flips: bit e of this lane's mask for block b flips coordinate 32 e + lane
@@ -201,11 +202,11 @@ __global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ 
           for (int e = 0; e < 32; ++e) {
             const int col = b * dp + lane * 32 + e;
             bool bit = v[e] > 0.f;
-            if (!(fabsf(v[e]) > B) && col < KL && !(mode & kStoreProj)) {  // inside the bound (or NaN)
+            if (!PROJ && !(fabsf(v[e]) > B) && col < KL) {  // inside the bound (or NaN)
               bit = exact_bit<BF16>(a.X, i, d, a.Wt, col);
               ++nre;
             }
-            if ((mode & kStoreProj) && col < KL) a.proj[i * static_cast<long long>(KL) + col] = v[e];
+            if (PROJ && col < KL) a.proj[i * static_cast<long long>(KL) + col] = v[e];
             wv |= (bit ? 1u : 0u) << e;
           }
           wrow[b * 32 + lane] = wv;
@@ -225,18 +226,18 @@ __global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ 
           for (int e = 0; e < E; ++e) {
             const int col = b * dp + e * 32 + lane;
             bool bit = v[e] > 0.f;
-            if (!(fabsf(v[e]) > B) && col < KL && !(mode & kStoreProj)) {  // inside the bound (or NaN)
+            if (!PROJ && !(fabsf(v[e]) > B) && col < KL) {  // inside the bound (or NaN)
               bit = exact_bit<BF16>(a.X, i, d, a.Wt, col);
               ++nre;
             }
-            if ((mode & kStoreProj) && col < KL) a.proj[i * static_cast<long long>(KL) + col] = v[e];
+            if (PROJ && col < KL) a.proj[i * static_cast<long long>(KL) + col] = v[e];
             const uint32_t wv = __ballot_sync(0xFFFFFFFFu, bit);
             if (lane == 0) wrow[b * E + e] = wv;
           }
         }
       }
       __syncwarp();
-      if (!(mode & kStoreProj)) {
+      if (!PROJ) {
         for (int j = lane; j < L; j += 32) {
           const uint32_t id = extract_bits(wrow, nwords, j * K, K);
           if (gather) ibuf[j * 32 + p] = static_cast<IdT>(id);
@@ -265,21 +266,30 @@ cudaError_t launch_hash_fwht(const FwhtArgs& a, int num_sms, cudaStream_t s) {
   if (a.dp < 32 || a.dp > kFwhtMaxDp || (a.dp & (a.dp - 1)) || a.nblk * E > kFwhtMaxWords)
     return cudaErrorInvalidValue;
   const long long want = ((a.n + 31) / 32 + 7) / 8;  // groups of 32 points, 8 warps per block
-  const unsigned grid = static_cast<unsigned>(std::min<long long>(want, static_cast<long long>(num_sms) * 8));
+  // one wave of resident blocks, each looping over groups (no tail waves, one prologue each)
   auto go = [&](auto kern, size_t smem) -> cudaError_t {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    if (e != cudaSuccess) return e;
+    const unsigned grid =
+        static_cast<unsigned>(std::min<long long>(want, static_cast<long long>(num_sms) * std::max(1, per_sm)));
     kern<<<grid, 256, smem, s>>>(a);
     return cudaGetLastError();
   };
+  const bool proj = (a.mode & kStoreProj) != 0;
   const bool b16 = a.x_bf16 != 0, id16 = a.K <= 16;
 #define ACE_FWHT_CASE(EV)                                                                          \
   case EV:                                                                                         \
+    if (proj)                                                                                      \
+      return b16 ? go(hash_fwht_kernel<true, uint32_t, EV, true>, FwhtSmem<EV, 2>::bytes)          \
+                 : go(hash_fwht_kernel<false, uint32_t, EV, true>, FwhtSmem<EV, 4>::bytes);        \
     if (b16)                                                                                       \
-      return id16 ? go(hash_fwht_kernel<true, uint16_t, EV>, FwhtSmem<EV, 2>::bytes)               \
-                  : go(hash_fwht_kernel<true, uint32_t, EV>, FwhtSmem<EV, 2>::bytes);              \
-    return id16 ? go(hash_fwht_kernel<false, uint16_t, EV>, FwhtSmem<EV, 4>::bytes)                \
-                : go(hash_fwht_kernel<false, uint32_t, EV>, FwhtSmem<EV, 4>::bytes);
+      return id16 ? go(hash_fwht_kernel<true, uint16_t, EV, false>, FwhtSmem<EV, 2>::bytes)        \
+                  : go(hash_fwht_kernel<true, uint32_t, EV, false>, FwhtSmem<EV, 2>::bytes);       \
+    return id16 ? go(hash_fwht_kernel<false, uint16_t, EV, false>, FwhtSmem<EV, 4>::bytes)         \
+                : go(hash_fwht_kernel<false, uint32_t, EV, false>, FwhtSmem<EV, 4>::bytes);
   switch (E) {
     ACE_FWHT_CASE(1)
     ACE_FWHT_CASE(2)
