@@ -248,6 +248,9 @@ def _step_roofline(n, d, K, L, x_bytes, ms, peaks):
             "peaks": f"{peaks['hbm_gbs']:.0f} GB/s, {peaks['bf16_tflops']:.0f} TFLOP/s bf16 ({peaks['src']})"}
 
 
+PRIVACY_SIGMA = 1.0
+
+
 def per_config(cases) -> dict:
     """insert+score points/s per config on each engine it runs on, against the plain binary32
     (FP32) engine: CUDA events on the launching stream around each call, median of 10 calls
@@ -276,9 +279,16 @@ def per_config(cases) -> dict:
             variants.append(("fp8_w_bf16", ace.ACE_PROJ_FP8, {"w_bf16": True}))
         # the structured +-1 projection (a different hash family: other ids, its own roofline)
         variants.append(("fwht_hadamard", ace.ACE_PROJ_FWHT, {"w_hadamard": True}))
+        # §4.5 privacy noise before the sign (sigma = 1): the cost of drawing and adding it
+        variants.append(("fp32_privacy", ace.ACE_PROJ_FP32, {"privacy": PRIVACY_SIGMA}))
+        variants.append(("fwht_hadamard_privacy", ace.ACE_PROJ_FWHT, {"w_hadamard": True, "privacy": PRIVACY_SIGMA}))
         for prec, want, kw in variants:
+            kw = dict(kw)
+            sigma = kw.pop("privacy", 0.0)
             try:
                 det = ace.Detector(w["d"], w["K"], w["L"], seed=11, precision=prec.split("_")[0], **kw)
+                if sigma:
+                    det.set_privacy(sigma, 12)
             except ace.AceError as e:
                 if e.code == ace.ACE_ERR_UNSUPPORTED:
                     res[prec] = "engine not available for this shape"
@@ -312,6 +322,8 @@ def per_config(cases) -> dict:
                      "phases_ms": phases, "rechecks_per_point": st["rechecks"] / (n * reps),
                      "deferred_per_point": st["deferred"] / (n * reps),
                      "step_roofline": _step_roofline(n, w["d"], w["K"], w["L"], xb, t * 1e3, peaks)}
+            if sigma:
+                entry["privacy_sigma"] = sigma
             if "hash" in phases:
                 th = phases["hash"] / 1e3
                 if prec.startswith("bf16"):
@@ -335,9 +347,12 @@ def per_config(cases) -> dict:
                                               "unit": "TFLOP/s", "frac": flop / th / 1e12 / FP32_ALU_PEAK_TFLOPS,
                                               "peak_src": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"}
             res[prec] = entry
-        for v in ("bf16", "bf16_w_bf16", "fp8_w_bf16", "fwht_hadamard"):
+        for v in ("bf16", "bf16_w_bf16", "fp8_w_bf16", "fwht_hadamard", "fp32_privacy"):
             if isinstance(res.get(v), dict) and isinstance(res.get("fp32"), dict):
                 res[f"{v}_vs_fp32"] = res[v]["points_per_s"] / res["fp32"]["points_per_s"]
+        if isinstance(res.get("fwht_hadamard_privacy"), dict) and isinstance(res.get("fwht_hadamard"), dict):
+            res["fwht_hadamard_privacy_vs_fwht_hadamard"] = (res["fwht_hadamard_privacy"]["points_per_s"] /
+                                                             res["fwht_hadamard"]["points_per_s"])
         out[name] = res
         del Xd
     return out

@@ -188,6 +188,37 @@ int ace_set_graph(ace_handle h, int enable);
 int ace_set_precision(ace_handle h, int precision);
 
 /*
+ * ace_set_privacy — privacy-preserving hashing (§4.5): the bits of a point are the signs of
+ * its projections with noise added after the projection and before the sign, so the data
+ * never leaves the hashing step (the ids carry the noise; everything after them is
+ * unchanged).  From this call on, bit c of a point hashed by ace_insert, ace_score,
+ * ace_insert_score or ace_hash (and the host-buffer, batched, serving and allocation-free
+ * forms) is [x.w_c + eta > 0] (the binary64 sum of Eq. 1 plus eta, exactly; ties are 0),
+ * with
+ *   eta = sigma * g,  g = (number of one bits of SplitMix64 draw t of noise_seed - 32) / 4,
+ *   t = (m + i) * K L + c,
+ * m the number of points this detector hashed with noise before the call and i the point's
+ * row in the batch.  g is Binomial(64, 1/2) centred and scaled: mean 0, variance 1, values
+ * k / 4 for |k| <= 32 — a stand-in for the paper's N(0, 1) that is exactly representable, so
+ * every bit has one binary64 definition that the engines reproduce.  A point gets fresh
+ * noise each time it is hashed (an insert_score call hashes once for both).  sigma = 0 turns
+ * the noise off.  Each call restarts m at 0.  While the noise is on: the engines are the
+ * binary32 SIMT one and, for ACE_W_HADAMARD detectors, the structured one (ACE_PROJ_AUTO
+ * picks between them; ACE_PROJ_BF16 and ACE_PROJ_FP8 are refused); ace_delete returns
+ * ACE_ERR_UNSUPPORTED (a point does not hash to the ids it was inserted with; a window
+ * removes points by their stored ids and stays exact); graph replay is not used; ace_project
+ * returns the noise-free projections.  ace_save keeps sigma, the seed and m.
+ * Errors: ACE_ERR_ARG (sigma not 0 and outside [2^-60, 2^60] or not a number; noise_seed
+ * equal to the seed the detector was created from), ACE_ERR_UNSUPPORTED (precision set to
+ * ACE_PROJ_BF16 or ACE_PROJ_FP8).
+ */
+int ace_set_privacy(ace_handle h, float sigma, uint64_t noise_seed);
+
+/* The privacy settings: sigma (0: off), the noise seed and m, the noise index of the next
+ * point (any pointer may be NULL). */
+int ace_get_privacy(ace_handle h, float* sigma, uint64_t* noise_seed, uint64_t* next_index);
+
+/*
  * ace_insert — counting phase (Algorithm 1 pre-processing; §3.2, counting phase):
  * for every point x of X (n x d), A_j[H_j(x)] += 1 for j = 1..L.  The result does not
  * depend on the order of the points.  n = 0 is a no-op.
@@ -359,8 +390,10 @@ int ace_get_projection(ace_handle h, float* W_host);
 /*
  * Checkpoint of a detector (the paper keeps its arrays in memory; saving and restoring them
  * lets a long stream be scored across process restarts).  The blob holds everything that
- * determines later results: the shape, W, the L x 2^K counts, n_ins, and the running score
- * statistics N, S1, S2 (and the recheck/status counters), with a checksum.
+ * determines later results: the shape, W, the L x 2^K counts, n_ins, the running score
+ * statistics N, S1, S2 (and the recheck/status counters) and the privacy settings
+ * (ace_set_privacy), with a checksum.  ace_load also reads the earlier layout without the
+ * privacy settings.
  *   ace_save_size — bytes of the blob for this detector.
  *   ace_save — writes the blob to host memory buf (cap bytes, at least ace_save_size);
  *              synchronises `stream` (to read the counts as of all work enqueued on it).

@@ -65,6 +65,7 @@ def _load():
         lib.oracle_splitmix64_draw.argtypes = [u64, u64]
         lib.oracle_splitmix64_draw.restype = u64
         lib.oracle_hash.argtypes = [P, i32, i64, i32, P, i32, i32, P]
+        lib.oracle_hash_noisy.argtypes = [P, i32, i64, i32, P, i32, i32, ctypes.c_float, u64, u64, P]
         lib.oracle_project.argtypes = [P, i32, i64, i32, P, i32, P]
         lib.oracle_insert.argtypes = [P, i64, i32, i32, P]
         lib.oracle_insert.restype = i32
@@ -142,6 +143,20 @@ def hash_ids(X: np.ndarray, W: np.ndarray, K: int, L: int) -> np.ndarray:
     return ids
 
 
+def hash_ids_noisy(X: np.ndarray, W: np.ndarray, K: int, L: int, sigma: float, noise_seed: int,
+                   nbase: int) -> np.ndarray:
+    """§4.5 privacy-preserving SRP: bit c of row i is [w_c^T x + eta > 0] with
+    eta = sigma * (popcount(draw (nbase + i) K L + c of noise_seed) - 32) / 4."""
+    Xc, dt = _x_args(X)
+    n, d = Xc.shape
+    Wc = np.ascontiguousarray(W, dtype=np.float32)
+    assert Wc.shape == (d, K * L)
+    ids = np.empty((n, L), dtype=np.uint32)
+    _load().oracle_hash_noisy(_ptr(Xc), dt, n, d, _ptr(Wc), K, L, ctypes.c_float(sigma),
+                              ctypes.c_uint64(noise_seed & (2**64 - 1)), ctypes.c_uint64(nbase), _ptr(ids))
+    return ids
+
+
 def project(X: np.ndarray, W: np.ndarray) -> np.ndarray:
     """Binary64 projections in index order, n x KL."""
     Xc, dt = _x_args(X)
@@ -215,9 +230,18 @@ class Detector:
         self.counts = np.zeros((L, 1 << K), dtype=np.uint32)
         self.n_ins = 0
         self.st = np.zeros(5, dtype=np.uint64)  # N, S1 lo/hi, S2 lo/hi
+        self.sigma, self.noise_seed, self.nbase = 0.0, 0, 0
+
+    def set_privacy(self, sigma: float, noise_seed: int = 0):
+        """§4.5: noise before the sign from now on; the noise index restarts at 0."""
+        self.sigma, self.noise_seed, self.nbase = float(np.float32(sigma)), noise_seed, 0
 
     def hash(self, X):
-        return hash_ids(X, self.W, self.K, self.L)
+        if self.sigma == 0.0:
+            return hash_ids(X, self.W, self.K, self.L)
+        ids = hash_ids_noisy(X, self.W, self.K, self.L, self.sigma, self.noise_seed, self.nbase)
+        self.nbase += ids.shape[0]
+        return ids
 
     def insert(self, X):
         ids = self.hash(X)
@@ -227,6 +251,8 @@ class Detector:
 
     def delete(self, X):
         """Removes the batch's points from the arrays (§3.4.1); all or nothing."""
+        if self.sigma != 0.0:
+            raise ValueError("with privacy noise a point does not hash to its inserted ids")
         ids = self.hash(X)
         if ids.shape[0] > self.n_ins:
             raise ValueError("deleting more points than were inserted")

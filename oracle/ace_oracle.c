@@ -186,6 +186,43 @@ void oracle_hash(const void* X, int x_dtype, int64_t n, int d, const float* W, i
   }
 }
 
+/*
+ * §4.5, privacy-preserving SRP: the sign is taken of the projection plus noise,
+ * bit = [ s + eta > 0 ] with s the binary64 index-order sum of Eq. 1 and
+ * eta = sigma * (ones(draw t of noise_seed) - 32) / 4, t = (nbase + i) * KL + c: centred,
+ * scaled Binomial(64, 1/2) noise of variance sigma^2 (the library's Gaussian stand-in),
+ * exact in binary64 (sigma has 24 significant bits, (ones - 32) / 4 at most 6).
+ */
+void oracle_hash_noisy(const void* X, int x_dtype, int64_t n, int d, const float* W, int K, int L,
+                       float sigma, uint64_t noise_seed, uint64_t nbase, uint32_t* ids) {
+  const int KL = K * L;
+#pragma omp parallel
+  {
+    double* x = (double*)malloc(sizeof(double) * (size_t)(d > 0 ? d : 1));
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      for (int t = 0; t < d; ++t) {
+        size_t at = (size_t)i * (size_t)d + (size_t)t;
+        x[t] = x_dtype == 0 ? (double)((const float*)X)[at] : bf16_bits_to_double(((const uint16_t*)X)[at]);
+      }
+      for (int j = 0; j < L; ++j) {
+        uint32_t h = 0;
+        for (int k = 0; k < K; ++k) {
+          const int c = j * K + k;
+          double s = 0.0;
+          for (int t = 0; t < d; ++t) s += x[t] * (double)W[(size_t)t * KL + c];
+          const uint64_t idx = (nbase + (uint64_t)i) * (uint64_t)KL + (uint64_t)c;
+          const double g = (double)(ones64(splitmix64_draw(noise_seed, idx)) - 32) / 4.0;
+          const double eta = (double)sigma * g;
+          h |= (uint32_t)(s + eta > 0.0) << k;
+        }
+        ids[(size_t)i * L + j] = h;
+      }
+    }
+    free(x);
+  }
+}
+
 /* Raw projections s[i*KL + c] (binary64, index order) for tests that look at margins. */
 void oracle_project(const void* X, int x_dtype, int64_t n, int d, const float* W, int KL, double* s) {
   for (int64_t i = 0; i < n; ++i)

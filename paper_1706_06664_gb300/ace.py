@@ -26,6 +26,7 @@ PRECISIONS = {"auto": ACE_PROJ_AUTO, "fp32": ACE_PROJ_FP32, "bf16": ACE_PROJ_BF1
 # Every symbol include/ace.h declares (checked by the tests).
 EXPORTS = [
     "ace_create", "ace_create_ex", "ace_create_with_projection", "ace_destroy", "ace_reset", "ace_set_precision",
+    "ace_set_privacy", "ace_get_privacy",
     "ace_insert", "ace_score", "ace_insert_score", "ace_insert_score_host",
     "ace_insert_score_host_async", "ace_host_wait", "ace_delete", "ace_project", "ace_hash",
     "ace_batch_insert_score", "ace_server_create", "ace_server_submit", "ace_server_wait", "ace_server_drain", "ace_server_destroy", "ace_server_info", "ace_stats",
@@ -83,6 +84,9 @@ def load_library(path: str = LIB_PATH):
             "ace_destroy": ([H], i32),
             "ace_reset": ([H, P], i32),
             "ace_set_precision": ([H, i32], i32),
+            "ace_set_privacy": ([H, ctypes.c_float, ctypes.c_uint64], i32),
+            "ace_get_privacy": ([H, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64),
+                                 ctypes.POINTER(ctypes.c_uint64)], i32),
             "ace_insert": ([H, P, i64, i32, P], i32),
             "ace_score": ([H, P, i64, i32, f64, P, P, P, P], i32),
             "ace_insert_score": ([H, P, i64, i32, f64, P, P, P, P], i32),
@@ -200,6 +204,16 @@ class Detector:
     def set_precision(self, precision):
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         _check(load_library().ace_set_precision(self._h, p))
+
+    def set_privacy(self, sigma: float, noise_seed: int = 0):
+        """§4.5 privacy noise before the sign (ace_set_privacy); sigma = 0 turns it off."""
+        _check(load_library().ace_set_privacy(self._h, ctypes.c_float(sigma), ctypes.c_uint64(noise_seed & (2**64 - 1))))
+
+    def privacy(self) -> dict:
+        """{"sigma", "noise_seed", "next_index"} (ace_get_privacy)."""
+        sg, sd, nx = ctypes.c_float(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load_library().ace_get_privacy(self._h, ctypes.byref(sg), ctypes.byref(sd), ctypes.byref(nx)))
+        return {"sigma": sg.value, "noise_seed": sd.value, "next_index": nx.value}
 
     def reset(self, stream=None):
         _check(load_library().ace_reset(self._h, _stream_ptr(stream)))

@@ -115,6 +115,12 @@ struct ace_detector {
   uint32_t* gdsign = nullptr;   // [nblk][dp/32] sign words of the blocks' diagonals
   bool wgen = false;             // ACE_W_COUNTER: the SIMT engine regenerates W tiles from wseed
   uint64_t wseed = 0;
+  bool seeded = false;           // created from a seed (the seed kept to refuse it as a noise seed)
+  uint64_t seed = 0;
+  // privacy noise (ace_set_privacy): sigma, the noise seed, and the noise index of the next
+  // point hashed (points hashed with noise so far)
+  float nsig = 0.f;
+  uint64_t nseed = 0, nbase = 0;
   bool gemm_ok = false;
   ace::GemmArgs gm{};           // constant part of the launch
   uint16_t* gimg = nullptr;     // [2 klp][dp] bfloat16 image of W' (hi rows, then lo rows)
@@ -858,6 +864,8 @@ int make_detector(int d, int K, int L, const float* Wsrc, uint64_t seed, bool fr
   h->K = K;
   h->L = L;
   h->KL = K * L;
+  h->seeded = from_seed;
+  h->seed = from_seed ? seed : 0u;
   h->div = ace::make_div_const(static_cast<uint32_t>(L));
   cudaError_t e = cudaGetDevice(&h->device);
   if (e != cudaSuccess) {
@@ -999,8 +1007,17 @@ int grow(void** p, size_t* cap, size_t need, cudaStream_t s, const char* what) {
   return ACE_OK;
 }
 
-ace::HashArgs hash_args(ace_handle h, const void* X, long long n, int dtype, int mode) {
+// Launch arguments for hashing n points of X.  With privacy noise on (and ids, not
+// projections, asked for) the next n noise indices are reserved for these points, in order;
+// `noise` = false (the autotuner's scratch runs) reserves none and adds no noise.
+ace::HashArgs hash_args(ace_handle h, const void* X, long long n, int dtype, int mode, bool noise = true) {
   ace::HashArgs a{};
+  if (noise && h->nsig != 0.f && !(mode & ace::kStoreProj)) {
+    a.nsig = h->nsig;
+    a.nseed = h->nseed;
+    a.nbase = static_cast<long long>(h->nbase);
+    h->nbase += static_cast<uint64_t>(n);
+  }
   a.X = X;
   a.x_bf16 = dtype == ACE_BF16;
   a.n = n;
@@ -1043,6 +1060,7 @@ enum class Engine { kSimt, kResident, kStreaming, kFwht };
 Engine pick_engine(ace_handle h, int x_bf16, const void* X) {
   if (h->precision == ACE_PROJ_FP32) return Engine::kSimt;
   if (h->precision == ACE_PROJ_FWHT || (h->precision == ACE_PROJ_AUTO && h->fwht_ok)) return Engine::kFwht;
+  if (h->nsig != 0.f) return Engine::kSimt;  // privacy noise: the tensor-core engines add none
   if (h->precision == ACE_PROJ_FP8)
     return h->gemm8_ok && x_bf16 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0 ? Engine::kStreaming : Engine::kSimt;
   if (h->tc_ok) return Engine::kResident;
@@ -1179,6 +1197,9 @@ int run_hash(ace_handle h, const ace::HashArgs& a, cudaStream_t s, bool tc_inser
     f.ld = a.ld;
     f.ids_rm = a.ids_rm;
     f.proj = a.proj;
+    f.nsig = a.nsig;
+    f.nseed = a.nseed;
+    f.nbase = a.nbase;
     if (!(a.mode & ace::kStoreProj)) {
       h->last_precision = ACE_PROJ_FWHT;
       h->last_products = 0;
@@ -1290,7 +1311,7 @@ int score_common(ace_handle h, const void* X, long long n, int dtype, double alp
   // (the legacy default stream cannot be captured, and a stream someone is capturing already
   // records these launches in that capture)
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  if (!h || !h->graph_on || h->ring || h->prof || n <= 0 || s == nullptr || s == cudaStreamLegacy ||
+  if (!h || !h->graph_on || h->ring || h->prof || h->nsig != 0.f || n <= 0 || s == nullptr || s == cudaStreamLegacy ||
       s == cudaStreamPerThread || cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
     return score_common_direct(h, X, n, dtype, alpha, scores, sums, flags, s, insert);
   int rc = check_x(h, X, n, dtype);
@@ -1439,7 +1460,7 @@ int tuned_tile(ace_handle h, const void* X, long long n, int dtype, cudaStream_t
   int best = 0;
   float best_ms = 0.f;
   for (int t = 0; t < 4 && e == cudaSuccess; ++t) {
-    ace::HashArgs a = hash_args(h, buf + ib, nt, dtype, ace::kStoreIds);
+    ace::HashArgs a = hash_args(h, buf + ib, nt, dtype, ace::kStoreIds, false);
     a.ids = buf;
     a.ld = nt;
     a.st = reinterpret_cast<ace::DevStats*>(buf + ib + xb);
@@ -1551,7 +1572,35 @@ int ace_set_precision(ace_handle h, int precision) {
   if (precision == ACE_PROJ_BF16 && !h->tc_ok && !h->gemm_ok)
     return fail(ACE_ERR_UNSUPPORTED, "the tensor-core paths need an sm_103 device and either d <= 64 or d a multiple "
                                      "of 8 (d=%d K=%d L=%d)", h->d, h->K, h->L);
+  if ((precision == ACE_PROJ_BF16 || precision == ACE_PROJ_FP8) && h->nsig != 0.f)
+    return fail(ACE_ERR_UNSUPPORTED, "privacy noise is on: the tensor-core engines add no noise");
   h->precision = precision;
+  return ACE_OK;
+}
+
+int ace_set_privacy(ace_handle h, float sigma, uint64_t noise_seed) {
+  if (!h) return fail(ACE_ERR_ARG, "handle is NULL");
+  if (!(sigma == 0.f || (sigma >= 0x1p-60f && sigma <= 0x1p60f)))
+    return fail(ACE_ERR_ARG, "sigma must be 0 or in [2^-60, 2^60] (got %g)", static_cast<double>(sigma));
+  if (sigma != 0.f && h->seeded && noise_seed == h->seed)
+    return fail(ACE_ERR_ARG, "the noise seed must differ from the detector's projection seed");
+  if (sigma != 0.f && (h->precision == ACE_PROJ_BF16 || h->precision == ACE_PROJ_FP8))
+    return fail(ACE_ERR_UNSUPPORTED, "the tensor-core engines add no noise: set ACE_PROJ_AUTO, ACE_PROJ_FP32 or "
+                                     "ACE_PROJ_FWHT first");
+  h->nsig = sigma;
+  h->nseed = sigma != 0.f ? noise_seed : 0u;
+  h->nbase = 0;
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);  // a captured call holds the noise-free arguments
+  h->gexec = nullptr;
+  h->gseen = false;
+  return ACE_OK;
+}
+
+int ace_get_privacy(ace_handle h, float* sigma, uint64_t* noise_seed, uint64_t* next_index) {
+  if (!h) return fail(ACE_ERR_ARG, "handle is NULL");
+  if (sigma) *sigma = h->nsig;
+  if (noise_seed) *noise_seed = h->nseed;
+  if (next_index) *next_index = h->nbase;
   return ACE_OK;
 }
 
@@ -2057,6 +2106,8 @@ int ace_delete(ace_handle h, const void* X_dev, int64_t n, int dtype, void* stre
   int rc = check_x(h, X_dev, n, dtype);
   if (rc) return rc;
   if (h->ring) return fail(ACE_ERR_ARG, "a windowed detector removes its oldest points itself");
+  if (h->nsig != 0.f)
+    return fail(ACE_ERR_UNSUPPORTED, "privacy noise is on: a point hashes to other ids than when it was inserted");
   if (n == 0) return ACE_OK;
   if (static_cast<uint64_t>(n) > h->n_ins)
     return fail(ACE_ERR_ARG, "deleting %lld points from a detector holding %llu", static_cast<long long>(n),
@@ -2169,10 +2220,12 @@ int ace_batch_insert_score(const ace_handle* dets, int count, const void* const*
   auto* d_hdone = reinterpret_cast<unsigned int*>(dev + b_ha + b_sj + 2 * b_st + 8);
   auto* d_sready = d_hdone + count;
   const int sms = dets[0]->num_sms > 0 ? dets[0]->num_sms : 152;
+  bool noisy = false;
+  for (const auto& a : ha) noisy = noisy || a.nsig != 0.f;
   if (e == cudaSuccess) {
     ace_detector* h0 = dets[0];
     PhaseScope ps(h0, ACE_PHASE_HASH, s);  // the one launch (all phases of all detectors)
-    e = ace::launch_batch(d_ha, d_sj, d_hs, d_ss, count, d_next, d_hdone, d_sready, dtype == ACE_BF16, id16, sms, s);
+    e = ace::launch_batch(d_ha, d_sj, d_hs, d_ss, count, d_next, d_hdone, d_sready, dtype == ACE_BF16, id16, noisy, sms, s);
   }
   cudaFreeAsync(dev, s);
   if (e != cudaSuccess) return cuda_fail(e, "batched launch");
@@ -2290,13 +2343,16 @@ int ace_get_projection(ace_handle h, float* W_host) {
 
 // ---------------------------------------------------------------------------------------
 // Checkpoint blob (ace_save / ace_load).  Little-endian, 8-byte fields:
-//   "ACEDET01", version 1, d, K, L, flags (bit 0: W is bfloat16-valued), n_ins,
-//   n_scored, S1 lo/hi, S2 lo/hi, rechecks, nonfinite, deferred, status,
+//   "ACEDET01", version, d, K, L, flags (bit 0: W is bfloat16-valued), n_ins,
+//   n_scored, S1 lo/hi, S2 lo/hi, rechecks, nonfinite, deferred, status, 0,
+//   [version 2: the privacy noise's sigma (binary32 bits), noise seed, next noise index, 0,]
 //   W (d*K*L binary32, row-major), counts (L*2^K uint32), FNV-1a 64 of everything before it.
+// ace_save writes version 2; ace_load reads both.
 // ---------------------------------------------------------------------------------------
 namespace {
 constexpr char kBlobMagic[8] = {'A', 'C', 'E', 'D', 'E', 'T', '0', '1'};
-constexpr int kBlobHeaderWords = 16;  // after the magic
+constexpr int kBlobHeaderWords1 = 16;  // after the magic, version 1
+constexpr int kBlobHeaderWords = 20;   // version 2
 
 uint64_t fnv1a64(const unsigned char* p, size_t n) {
   uint64_t h = 0xCBF29CE484222325ull;
@@ -2307,8 +2363,9 @@ uint64_t fnv1a64(const unsigned char* p, size_t n) {
   return h;
 }
 
-size_t blob_bytes(int d, int K, int L) {
-  return 8 + 8 * kBlobHeaderWords + static_cast<size_t>(d) * K * L * 4 + (static_cast<size_t>(1) << K) * L * 4 + 8;
+size_t blob_bytes(int d, int K, int L, int words = kBlobHeaderWords) {
+  return 8 + 8 * static_cast<size_t>(words) + static_cast<size_t>(d) * K * L * 4 +
+         (static_cast<size_t>(1) << K) * L * 4 + 8;
 }
 }  // namespace
 
@@ -2333,7 +2390,9 @@ int ace_save(ace_handle h, void* buf, size_t cap, void* stream) {
   ACE_CUDA(cudaStreamSynchronize(s));
   bool wb = true;
   for (float w : h->Wh) wb = wb && bf16_value(bf16_rn(w)) == w;
-  uint64_t hdr[kBlobHeaderWords] = {1u,
+  uint32_t nsig_bits;
+  std::memcpy(&nsig_bits, &h->nsig, 4);
+  uint64_t hdr[kBlobHeaderWords] = {2u,
                                     static_cast<uint64_t>(h->d),
                                     static_cast<uint64_t>(h->K),
                                     static_cast<uint64_t>(h->L),
@@ -2348,6 +2407,10 @@ int ace_save(ace_handle h, void* buf, size_t cap, void* stream) {
                                     st.nonfinite,
                                     st.deferred,
                                     st.status,
+                                    0u,
+                                    nsig_bits,
+                                    h->nseed,
+                                    h->nbase,
                                     0u};
   std::memcpy(out, kBlobMagic, 8);
   std::memcpy(out + 8, hdr, sizeof hdr);
@@ -2361,24 +2424,37 @@ int ace_load(const void* buf, size_t bytes, ace_handle* out) {
   if (!buf || !out) return fail(ACE_ERR_ARG, "NULL argument");
   *out = nullptr;
   const unsigned char* in = static_cast<const unsigned char*>(buf);
-  if (bytes < 8 + 8 * kBlobHeaderWords + 8 || std::memcmp(in, kBlobMagic, 8) != 0)
+  if (bytes < 8 + 8 * kBlobHeaderWords1 + 8 || std::memcmp(in, kBlobMagic, 8) != 0)
     return fail(ACE_ERR_ARG, "not an ACE checkpoint");
-  uint64_t hdr[kBlobHeaderWords];
-  std::memcpy(hdr, in + 8, sizeof hdr);
-  if (hdr[0] != 1u) return fail(ACE_ERR_ARG, "checkpoint version %llu is not supported",
-                                static_cast<unsigned long long>(hdr[0]));
+  uint64_t hdr[kBlobHeaderWords] = {};
+  std::memcpy(hdr, in + 8, 8 * kBlobHeaderWords1);
+  if (hdr[0] != 1u && hdr[0] != 2u)
+    return fail(ACE_ERR_ARG, "checkpoint version %llu is not supported", static_cast<unsigned long long>(hdr[0]));
+  const int words = hdr[0] == 1u ? kBlobHeaderWords1 : kBlobHeaderWords;
+  if (words > kBlobHeaderWords1) {
+    if (bytes < 8 + 8 * static_cast<size_t>(words) + 8) return fail(ACE_ERR_ARG, "checkpoint header truncated");
+    std::memcpy(hdr, in + 8, 8 * static_cast<size_t>(words));
+  }
   const uint64_t d = hdr[1], K = hdr[2], L = hdr[3];
   if (d < 1 || d > (1u << 30) || K < 1 || K > 24 || L < 1 || K * L > 65536)
     return fail(ACE_ERR_ARG, "checkpoint shape d=%llu K=%llu L=%llu is invalid", static_cast<unsigned long long>(d),
                 static_cast<unsigned long long>(K), static_cast<unsigned long long>(L));
-  const size_t need = blob_bytes(static_cast<int>(d), static_cast<int>(K), static_cast<int>(L));
+  const size_t need = blob_bytes(static_cast<int>(d), static_cast<int>(K), static_cast<int>(L), words);
   if (bytes != need) return fail(ACE_ERR_ARG, "checkpoint of %zu bytes; its shape needs %zu", bytes, need);
+  float nsig = 0.f;
+  if (words > kBlobHeaderWords1) {
+    const uint32_t nb = static_cast<uint32_t>(hdr[16]);
+    std::memcpy(&nsig, &nb, 4);
+    if (!(nsig == 0.f || (nsig >= 0x1p-60f && nsig <= 0x1p60f)) || hdr[16] > 0xFFFFFFFFull)
+      return fail(ACE_ERR_ARG, "checkpoint privacy sigma is invalid");
+  }
   uint64_t sum;
   std::memcpy(&sum, in + need - 8, 8);
   if (sum != fnv1a64(in, need - 8)) return fail(ACE_ERR_ARG, "checkpoint checksum mismatch (corrupted blob)");
   const size_t wbytes = static_cast<size_t>(d) * K * L * 4;
   std::vector<float> W(static_cast<size_t>(d) * K * L);
-  std::memcpy(W.data(), in + 8 + 8 * kBlobHeaderWords, wbytes);
+  const size_t hbytes = 8 + 8 * static_cast<size_t>(words);
+  std::memcpy(W.data(), in + hbytes, wbytes);
   ace_handle h = nullptr;
   if (int rc = make_detector(static_cast<int>(d), static_cast<int>(K), static_cast<int>(L), W.data(), 0, false, 0u, &h))
     return rc;
@@ -2392,14 +2468,16 @@ int ace_load(const void* buf, size_t bytes, ace_handle* out) {
   st.nonfinite = hdr[12];
   st.deferred = hdr[13];
   st.status = static_cast<unsigned int>(hdr[14]);
-  cudaError_t e = cudaMemcpy(h->counts, in + 8 + 8 * kBlobHeaderWords + wbytes, count_elems(h) * 4,
-                             cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMemcpy(h->counts, in + hbytes + wbytes, count_elems(h) * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->st, &st, sizeof st, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     ace_destroy(h);
     return cuda_fail(e, "checkpoint upload");
   }
   h->n_ins = hdr[5];
+  h->nsig = nsig;
+  h->nseed = nsig != 0.f ? hdr[17] : 0u;
+  h->nbase = nsig != 0.f ? hdr[18] : 0u;
   *out = h;
   return ACE_OK;
 }

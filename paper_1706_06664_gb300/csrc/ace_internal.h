@@ -82,6 +82,11 @@ struct HashArgs {
   float* proj;          // [n][KL] (kStoreProj)
   int tile;             // SIMT tile variant (0: 128 points x 128 columns per block; 1: 128 x 64;
                         // 2: 64 x 128; 3: 64 x 64)
+  // privacy noise (§4.5; ace_set_privacy): projection c of point p is x.w_c + eta with
+  // eta = nsig * counter_w(nseed, (nbase + p) * KL + c); nsig = 0: no noise
+  float nsig;
+  unsigned long long nseed;
+  long long nbase;
 };
 
 // One detector's share of a batched query phase and flags pass.
@@ -113,7 +118,7 @@ int simt_tile_cols(int tile);
 // Every detector's hash + insert, query phase and flags in one persistent launch (hash_simt.cu).
 cudaError_t launch_batch(const HashArgs* args_dev, const ScoreJob* jobs_dev, const long long* hstart_dev,
                          const long long* sstart_dev, int ndet, unsigned long long* next, unsigned int* hdone,
-                         unsigned int* sready, bool bf16, bool id16, int num_sms, cudaStream_t s);
+                         unsigned int* sready, bool bf16, bool id16, bool noisy, int num_sms, cudaStream_t s);
 cudaError_t launch_delete_check(const uint32_t* hist, const uint32_t* counts, long long total, unsigned int* flag,
                                 int num_sms, cudaStream_t s);
 cudaError_t launch_window_evict(const void* ring, int ids16, long long cap, long long start, long long m, int K, int L,

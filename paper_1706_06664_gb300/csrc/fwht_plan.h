@@ -37,6 +37,11 @@ struct FwhtArgs {
   uint32_t* ids_rm;           // [n][L] (kStoreIdsRowMajor)
   float* proj;                // [n][KL] (kStoreProj)
   DevStats* st;
+  // privacy noise (§4.5): output c of point p is y_c + nsig * counter_w(nseed, (nbase + p) KL + c);
+  // nsig = 0: no noise
+  float nsig;
+  unsigned long long nseed;
+  long long nbase;
 };
 
 cudaError_t launch_hash_fwht(const FwhtArgs& a, int num_sms, cudaStream_t s);

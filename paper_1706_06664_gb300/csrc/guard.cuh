@@ -22,33 +22,42 @@ __device__ __forceinline__ float load_x(const void* X, long long idx) {
   }
 }
 
-// Exact SRP bit of point i on column col: binary64, index order, Wt is [KL][d].
+// Binary64 sum of x_i w_i in index order (the definition's sum, Eq. 1); Wt is [KL][d].
 template <bool BF16>
-__device__ __noinline__ bool exact_bit(const void* X, long long i, int d, const float* Wt, int col) {
+__device__ __forceinline__ double exact_sum(const void* X, long long i, int d, const float* Wt, int col) {
   const long long base = i * static_cast<long long>(d);
   const float* w = Wt + static_cast<size_t>(col) * static_cast<size_t>(d);
   double s = 0.0;
 #pragma unroll 8
   for (int k = 0; k < d; ++k)  // unrolled so that the loads run ahead; the order of the sum is kept
     s = fma(static_cast<double>(load_x<BF16>(X, base + k)), static_cast<double>(__ldg(w + k)), s);
-  return s > 0.0;
+  return s;
 }
 
-// Sign of the exact dot product x.w by Dot2 (Ogita, Rump & Oishi, "Accurate sum and dot
-// product", SIAM J. Sci. Comput. 26(6), 2005): binary32 error-free transformations
-// (TwoProduct by FMA, Knuth's TwoSum) carry the sum in about twice the working precision, and
-// without underflow the result satisfies |res - x.w| <= u |x.w| + gamma_d^2 sum|x_i w_i|.
-// When |res| exceeds gamma_d^2 sum|x_i w_i| plus the binary64 sum's own error gamma64_d
-// sum|x_i w_i|, the exact value and the binary64 definition both have the sign of res and are
-// non-zero.  c2 covers those terms together with the rounding of the computed sum of |x_i w_i|;
-// cabs covers underflow.  Returns +1 or -1 when decided, 0 when only binary64 can tell
-// (exact ties, NaN, overflow).  Every operation is an explicitly rounded intrinsic, so no
-// contraction into an FMA can break the transformations.  w is read with stride ws.
+// Exact SRP bit of point i on column col: binary64, index order.
 template <bool BF16>
-__device__ __noinline__ int dot2_sign(const void* X, long long i, int d, const float* w, long long ws, float c2,
-                                      float cabs) {
+__device__ __noinline__ bool exact_bit(const void* X, long long i, int d, const float* Wt, int col) {
+  return exact_sum<BF16>(X, i, d, Wt, col) > 0.0;
+}
+
+// The same bit with a binary64 term added to the sum at the end (the privacy noise of §4.5):
+// [RN(s + add) > 0], which has the sign of s + add.
+template <bool BF16>
+__device__ __noinline__ bool exact_bit_add(const void* X, long long i, int d, const float* Wt, int col, double add) {
+  return __dadd_rn(exact_sum<BF16>(X, i, d, Wt, col), add) > 0.0;
+}
+
+// Dot2 (Ogita, Rump & Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26(6),
+// 2005): binary32 error-free transformations (TwoProduct by FMA, Knuth's TwoSum) carry the
+// sum of x_i w_i in about twice the working precision; without underflow the result res
+// satisfies |res - x.w| <= u |x.w| + gamma_d^2 sum|x_i w_i|.  Returns res; a = the computed
+// sum of |x_i w_i|.  Every operation is an explicitly rounded intrinsic, so no contraction
+// into an FMA can break the transformations.  w is read with stride ws.
+template <bool BF16>
+__device__ __forceinline__ float dot2_sum(const void* X, long long i, int d, const float* w, long long ws, float& a) {
   const long long base = i * static_cast<long long>(d);
-  float p = 0.f, e = 0.f, a = 0.f;
+  float p = 0.f, e = 0.f;
+  a = 0.f;
 #pragma unroll 4
   for (int k = 0; k < d; ++k) {
     const float x = load_x<BF16>(X, base + k);
@@ -62,9 +71,38 @@ __device__ __noinline__ int dot2_sign(const void* X, long long i, int d, const f
     e = __fadd_rn(e, __fadd_rn(q, r));
     a = __fadd_rn(a, fabsf(h));
   }
-  const float res = __fadd_rn(p, e);
+  return __fadd_rn(p, e);
+}
+
+// Sign of the exact dot product x.w by Dot2.  When |res| exceeds gamma_d^2 sum|x_i w_i| plus
+// the binary64 sum's own error gamma64_d sum|x_i w_i|, the exact value and the binary64
+// definition both have the sign of res and are non-zero (the relative term u |x.w| cannot
+// change a sign).  c2 covers those terms together with the rounding of the computed sum of
+// |x_i w_i|; cabs covers underflow.  Returns +1 or -1 when decided, 0 when only binary64 can
+// tell (exact ties, NaN, overflow).
+template <bool BF16>
+__device__ __noinline__ int dot2_sign(const void* X, long long i, int d, const float* w, long long ws, float c2,
+                                      float cabs) {
+  float a;
+  const float res = dot2_sum<BF16>(X, i, d, w, ws, a);
   const float T = __fmaf_ru(c2, a, cabs);
   if (fabsf(res) > T) return res > 0.f ? 1 : -1;  // false for NaN, and for any res when T = inf
+  return 0;
+}
+
+// Sign of x.w + add (the privacy noise of §4.5: add is the binary32 eta, whose binary64 value
+// differs by at most 2^-24 |add|).  The relative term of Dot2's bound now matters (u |x.w| <=
+// u |res| (1 + 2u)), and the final addition rounds once more (2^-24 |res + add|): the bound
+// gains 2^-23 (|res| + |add| + |res + add|), twice those terms.
+template <bool BF16>
+__device__ __noinline__ int dot2_sign_add(const void* X, long long i, int d, const float* w, long long ws, float c2,
+                                          float cabs, float add) {
+  float a;
+  const float res = dot2_sum<BF16>(X, i, d, w, ws, a);
+  const float v = __fadd_rn(res, add);
+  float T = __fmaf_ru(c2, a, cabs);
+  T = __fmaf_ru(1.1920928955078125e-07f, __fadd_ru(__fadd_ru(fabsf(res), fabsf(add)), fabsf(v)), T);
+  if (fabsf(v) > T) return v > 0.f ? 1 : -1;
   return 0;
 }
 

@@ -50,9 +50,19 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// PROJ: the measurement path (the transform's binary32 outputs, no ids).
-template <bool BF16, typename IdT, int E, bool PROJ>
+// The definition of a bit under privacy noise (§4.5), in binary64: the index-order sum plus
+// eta exactly (a binary32 times k / 4, |k| <= 32).
+template <bool BF16>
+__device__ __noinline__ bool noisy_exact_bit(const FwhtArgs& a, long long i, int col) {
+  const float cw = counter_w(a.nseed, static_cast<uint64_t>(a.nbase + i) * a.KL + col);
+  return exact_bit_add<BF16>(a.X, i, a.d, a.Wt, col, static_cast<double>(a.nsig) * static_cast<double>(cw));
+}
+
+// OUT: 0 ids; 1 the measurement path (the transform's binary32 outputs, no ids); 2 ids with
+// privacy noise (a separate instantiation, so that the others carry none of its registers).
+template <bool BF16, typename IdT, int E, int OUT>
 __global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ FwhtArgs a) {
+  constexpr bool PROJ = OUT == 1;
   extern __shared__ __align__(16) unsigned char fsm[];
   using SM = FwhtSmem<E, BF16 ? 2 : 4>;
   uint32_t (*words)[kFwhtMaxWords] = reinterpret_cast<uint32_t (*)[kFwhtMaxWords]>(fsm + SM::words);
@@ -63,6 +73,11 @@ __global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ 
   const int d = a.d, dp = a.dp, K = a.K, L = a.L, KL = a.KL, nblk = a.nblk, mode = a.mode;
   const long long n = a.n, ld = a.ld;
   const float cband = a.cband, babs = a.babs;
+  // privacy noise (§4.5): eta is added to each output in place (outputs col >= KL are padding
+  // and never become bits); its binary32 rounding and the addition's stay within 2^-24 (8 nsig
+  // + |y|) (|eta| <= 8 nsig), allowed for with a factor 2
+  constexpr bool noisy = OUT == 2;
+  const float nall = __fmul_ru(8.f, a.nsig);
   uint32_t* const wrow = words[wib];
   IdT* const ibuf = reinterpret_cast<IdT*>(idbuf[wib]);  // [L][32]
   const bool gather = static_cast<long long>(L) * 32 * static_cast<long long>(sizeof(IdT)) <= kIdBufBytes &&
@@ -197,13 +212,19 @@ __global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ 
               }
             }
           }
+          if (noisy) {
+            const uint64_t rb = static_cast<uint64_t>(a.nbase + i) * KL + b * dp + lane * 32;
+#pragma unroll
+            for (int e = 0; e < 32; ++e) v[e] = __fadd_rn(v[e], __fmul_rn(a.nsig, counter_w(a.nseed, rb + e)));
+          }
           uint32_t wv = 0u;
 #pragma unroll
           for (int e = 0; e < 32; ++e) {
             const int col = b * dp + lane * 32 + e;
             bool bit = v[e] > 0.f;
-            if (!PROJ && !(fabsf(v[e]) > B) && col < KL) {  // inside the bound (or NaN)
-              bit = exact_bit<BF16>(a.X, i, d, a.Wt, col);
+            const float Be = noisy ? __fmaf_ru(1.1920928955078125e-07f, __fadd_ru(nall, fabsf(v[e])), B) : B;
+            if (!PROJ && !(fabsf(v[e]) > Be) && col < KL) {  // inside the bound (or NaN)
+              bit = noisy ? noisy_exact_bit<BF16>(a, i, col) : exact_bit<BF16>(a.X, i, d, a.Wt, col);
               ++nre;
             }
             if (PROJ && col < KL) a.proj[i * static_cast<long long>(KL) + col] = v[e];
@@ -222,12 +243,18 @@ __global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ 
               v[e] = __fmaf_rn(sg, v[e], o);
             }
           }
+          if (noisy) {
+            const uint64_t rb = static_cast<uint64_t>(a.nbase + i) * KL + b * dp + lane;
+#pragma unroll
+            for (int e = 0; e < E; ++e) v[e] = __fadd_rn(v[e], __fmul_rn(a.nsig, counter_w(a.nseed, rb + 32 * e)));
+          }
 #pragma unroll
           for (int e = 0; e < E; ++e) {
             const int col = b * dp + e * 32 + lane;
             bool bit = v[e] > 0.f;
-            if (!PROJ && !(fabsf(v[e]) > B) && col < KL) {  // inside the bound (or NaN)
-              bit = exact_bit<BF16>(a.X, i, d, a.Wt, col);
+            const float Be = noisy ? __fmaf_ru(1.1920928955078125e-07f, __fadd_ru(nall, fabsf(v[e])), B) : B;
+            if (!PROJ && !(fabsf(v[e]) > Be) && col < KL) {  // inside the bound (or NaN)
+              bit = noisy ? noisy_exact_bit<BF16>(a, i, col) : exact_bit<BF16>(a.X, i, d, a.Wt, col);
               ++nre;
             }
             if (PROJ && col < KL) a.proj[i * static_cast<long long>(KL) + col] = v[e];
@@ -280,16 +307,24 @@ cudaError_t launch_hash_fwht(const FwhtArgs& a, int num_sms, cudaStream_t s) {
   };
   const bool proj = (a.mode & kStoreProj) != 0;
   const bool b16 = a.x_bf16 != 0, id16 = a.K <= 16;
+  const bool noisy = !proj && a.nsig != 0.f;
 #define ACE_FWHT_CASE(EV)                                                                          \
   case EV:                                                                                         \
     if (proj)                                                                                      \
-      return b16 ? go(hash_fwht_kernel<true, uint32_t, EV, true>, FwhtSmem<EV, 2>::bytes)          \
-                 : go(hash_fwht_kernel<false, uint32_t, EV, true>, FwhtSmem<EV, 4>::bytes);        \
+      return b16 ? go(hash_fwht_kernel<true, uint32_t, EV, 1>, FwhtSmem<EV, 2>::bytes)             \
+                 : go(hash_fwht_kernel<false, uint32_t, EV, 1>, FwhtSmem<EV, 4>::bytes);           \
+    if (noisy) {                                                                                   \
+      if (b16)                                                                                     \
+        return id16 ? go(hash_fwht_kernel<true, uint16_t, EV, 2>, FwhtSmem<EV, 2>::bytes)          \
+                    : go(hash_fwht_kernel<true, uint32_t, EV, 2>, FwhtSmem<EV, 2>::bytes);         \
+      return id16 ? go(hash_fwht_kernel<false, uint16_t, EV, 2>, FwhtSmem<EV, 4>::bytes)           \
+                  : go(hash_fwht_kernel<false, uint32_t, EV, 2>, FwhtSmem<EV, 4>::bytes);          \
+    }                                                                                              \
     if (b16)                                                                                       \
-      return id16 ? go(hash_fwht_kernel<true, uint16_t, EV, false>, FwhtSmem<EV, 2>::bytes)        \
-                  : go(hash_fwht_kernel<true, uint32_t, EV, false>, FwhtSmem<EV, 2>::bytes);       \
-    return id16 ? go(hash_fwht_kernel<false, uint16_t, EV, false>, FwhtSmem<EV, 4>::bytes)         \
-                : go(hash_fwht_kernel<false, uint32_t, EV, false>, FwhtSmem<EV, 4>::bytes);
+      return id16 ? go(hash_fwht_kernel<true, uint16_t, EV, 0>, FwhtSmem<EV, 2>::bytes)            \
+                  : go(hash_fwht_kernel<true, uint32_t, EV, 0>, FwhtSmem<EV, 2>::bytes);           \
+    return id16 ? go(hash_fwht_kernel<false, uint16_t, EV, 0>, FwhtSmem<EV, 4>::bytes)             \
+                : go(hash_fwht_kernel<false, uint32_t, EV, 0>, FwhtSmem<EV, 4>::bytes);
   switch (E) {
     ACE_FWHT_CASE(1)
     ACE_FWHT_CASE(2)

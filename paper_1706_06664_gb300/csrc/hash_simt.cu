@@ -42,7 +42,9 @@ constexpr size_t kSimtSmemMax = SimtTile<8, 8>::bytes;
 static_assert(SimtTile<8, 4>::bytes <= kSimtSmemMax && SimtTile<4, 8>::bytes <= kSimtSmemMax, "smem");
 
 // Block `blk` of one detector's hash: tile blk / ntb of BM points, table block blk % ntb.
-template <bool BF16, typename IdT, int RM, int NC>
+// NOISY: the variant that can add privacy noise (used when a detector of the launch has it on;
+// a separate instantiation, so that the noise-free kernel carries none of its registers).
+template <bool BF16, typename IdT, int RM, int NC, bool NOISY>
 __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int ntb, long long blk, uint8_t* sbuf) {
   using T = SimtTile<RM, NC>;
   constexpr int BM = T::BM, BN = T::BN, NW = T::NW;
@@ -148,6 +150,21 @@ __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int 
     cb[c] = col < ncol ? __ldg(a.cB + c0 + col) : 0.f;
   }
   __syncthreads();
+  // privacy noise (§4.5): the sign of x.w_c + eta is taken.  eta is added in place; its
+  // binary32 rounding and the addition's add at most 2^-24 (|eta| + |sum|) <= 2^-24 (8 nsig +
+  // |sum|) to the distance from the definition (|eta| <= 8 nsig), allowed for with a factor 2.
+  const bool noisy = NOISY && a.nsig != 0.f;
+  float nall = 0.f;
+  if (noisy) {
+    nall = __fmul_ru(8.f, a.nsig);
+#pragma unroll
+    for (int r = 0; r < RM; ++r) {
+      const uint64_t rb = static_cast<uint64_t>(a.nbase + i0 + prow(r)) * a.KL + c0;
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+        acc[r][c] = __fadd_rn(acc[r][c], __fmul_rn(a.nsig, counter_w(a.nseed, rb + pcol(c))));
+    }
+  }
 #pragma unroll
   for (int r = 0; r < RM; ++r) {
     const int p = prow(r);
@@ -160,7 +177,8 @@ __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int 
         const int col = g * 64 + tx * 4 + c;
         if (col < ncol) {
           const float sv = acc[r][g * 4 + c];
-          const float B = fmaf(cb[g * 4 + c], xu, a.babs);
+          float B = fmaf(cb[g * 4 + c], xu, a.babs);
+          if (noisy) B = __fmaf_ru(1.1920928955078125e-07f, __fadd_ru(nall, fabsf(sv)), B);
           if (fabsf(sv) > B) sb |= (sv > 0.f ? 1u : 0u) << c;
           else ab |= 1u << c;
         }
@@ -211,7 +229,12 @@ __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int 
           s = __fadd_rn(s, so);
           r = __fadd_rn(__fadd_rn(r, ro), fabsf(s));
         }
-        const float bound = __fmaf_ru(a.runc, r, __fmaf_ru(__fmul_ru(a.run64, __ldg(a.cB + col)), xu, a.runabs));
+        float bound = __fmaf_ru(a.runc, r, __fmaf_ru(__fmul_ru(a.run64, __ldg(a.cB + col)), xu, a.runabs));
+        if (noisy) {
+          const float eta = __fmul_rn(a.nsig, counter_w(a.nseed, static_cast<uint64_t>(a.nbase + i0 + p) * a.KL + col));
+          s = __fadd_rn(s, eta);
+          bound = __fmaf_ru(1.1920928955078125e-07f, __fadd_ru(fabsf(eta), fabsf(s)), bound);
+        }
         if (fabsf(s) > bound) {
           done |= 1u << b;
           if (s > 0.f) set |= 1u << b;
@@ -241,8 +264,17 @@ __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int 
         const int k = __ffs(m) - 1;
         m &= m - 1u;
         const int col = c0 + cbit + k;
-        const int sg = dot2_sign<BF16>(a.X, i, a.d, a.Wt + static_cast<size_t>(col) * a.d, 1, a.dot2c, a.dot2abs);
-        if (sg != 0 ? sg > 0 : exact_bit<BF16>(a.X, i, a.d, a.Wt, col)) id |= 1u << k;
+        const float* wc = a.Wt + static_cast<size_t>(col) * a.d;
+        if (noisy) {  // eta in binary32 for Dot2; exactly in binary64 (a binary32 times k/4, |k| <= 32)
+          const float cw = counter_w(a.nseed, static_cast<uint64_t>(a.nbase + i) * a.KL + col);
+          const int sg = dot2_sign_add<BF16>(a.X, i, a.d, wc, 1, a.dot2c, a.dot2abs, __fmul_rn(a.nsig, cw));
+          if (sg != 0 ? sg > 0
+                      : exact_bit_add<BF16>(a.X, i, a.d, a.Wt, col, static_cast<double>(a.nsig) * static_cast<double>(cw)))
+            id |= 1u << k;
+        } else {
+          const int sg = dot2_sign<BF16>(a.X, i, a.d, wc, 1, a.dot2c, a.dot2abs);
+          if (sg != 0 ? sg > 0 : exact_bit<BF16>(a.X, i, a.d, a.Wt, col)) id |= 1u << k;
+        }
         ++nre;
       }
       atomicAdd(&a.st->rechecks, nre);
@@ -271,22 +303,22 @@ __host__ __device__ inline void tile_blocks(const HashArgs& a, int t, int& tpb, 
   ntb = (a.L + tpb - 1) / tpb;
 }
 
-template <bool BF16, typename IdT>
+template <bool BF16, typename IdT, bool NOISY>
 __device__ __forceinline__ void hash_block_any(const HashArgs& a, long long blk, uint8_t* sbuf) {
   int tpb, ntb;
   tile_blocks(a, a.tile, tpb, ntb);
   switch (a.tile) {
-    case 1: hash_simt_block<BF16, IdT, 8, 4>(a, tpb, ntb, blk, sbuf); break;
-    case 2: hash_simt_block<BF16, IdT, 4, 8>(a, tpb, ntb, blk, sbuf); break;
-    case 3: hash_simt_block<BF16, IdT, 4, 4>(a, tpb, ntb, blk, sbuf); break;
-    default: hash_simt_block<BF16, IdT, 8, 8>(a, tpb, ntb, blk, sbuf); break;
+    case 1: hash_simt_block<BF16, IdT, 8, 4, NOISY>(a, tpb, ntb, blk, sbuf); break;
+    case 2: hash_simt_block<BF16, IdT, 4, 8, NOISY>(a, tpb, ntb, blk, sbuf); break;
+    case 3: hash_simt_block<BF16, IdT, 4, 4, NOISY>(a, tpb, ntb, blk, sbuf); break;
+    default: hash_simt_block<BF16, IdT, 8, 8, NOISY>(a, tpb, ntb, blk, sbuf); break;
   }
 }
 
-template <bool BF16, typename IdT>
+template <bool BF16, typename IdT, bool NOISY>
 __global__ void __launch_bounds__(NT, 2) hash_simt_kernel(HashArgs a) {
   extern __shared__ __align__(16) uint8_t sbuf[];
-  hash_block_any<BF16, IdT>(a, blockIdx.x, sbuf);
+  hash_block_any<BF16, IdT, NOISY>(a, blockIdx.x, sbuf);
 }
 
 constexpr long long kBatchWait = 4000000000LL;  // about 2 s at 2 GHz
@@ -325,7 +357,7 @@ __device__ __forceinline__ int find_det(const T* start, int ndet, long long b) {
   return lo;
 }
 
-template <bool BF16, typename IdT>
+template <bool BF16, typename IdT, bool NOISY>
 __global__ void __launch_bounds__(NT, 2)
     batch_kernel(const HashArgs* __restrict__ args, const ScoreJob* __restrict__ jobs,
                  const long long* __restrict__ hstart, const long long* __restrict__ sstart, int ndet,
@@ -356,7 +388,7 @@ __global__ void __launch_bounds__(NT, 2)
     if (it < H) {
       const int g = hdet(it);
       const HashArgs a = args[g];  // a copy: the block's loops read these fields many times
-      hash_block_any<BF16, IdT>(a, it - (pre_smem ? static_cast<long long>(hs32[g]) : hstart[g]), sbuf);
+      hash_block_any<BF16, IdT, NOISY>(a, it - (pre_smem ? static_cast<long long>(hs32[g]) : hstart[g]), sbuf);
       __syncthreads();
       if (threadIdx.x == 0) {
         __threadfence();
@@ -400,7 +432,7 @@ long long hash_simt_blocks(const HashArgs& a) {
 
 cudaError_t launch_batch(const HashArgs* args_dev, const ScoreJob* jobs_dev, const long long* hstart_dev,
                          const long long* sstart_dev, int ndet, unsigned long long* next, unsigned int* hdone,
-                         unsigned int* sready, bool bf16, bool id16, int num_sms, cudaStream_t s) {
+                         unsigned int* sready, bool bf16, bool id16, bool noisy, int num_sms, cudaStream_t s) {
   const size_t smem = kSimtSmemMax + 2 * sizeof(unsigned int) * (kBatchSmemDets + 1);
   auto go = [&](auto kern) -> cudaError_t {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -412,8 +444,12 @@ cudaError_t launch_batch(const HashArgs* args_dev, const ScoreJob* jobs_dev, con
                                                                           ndet, next, hdone, sready);
     return cudaGetLastError();
   };
-  if (bf16) return id16 ? go(batch_kernel<true, uint16_t>) : go(batch_kernel<true, uint32_t>);
-  return id16 ? go(batch_kernel<false, uint16_t>) : go(batch_kernel<false, uint32_t>);
+  if (noisy) {
+    if (bf16) return id16 ? go(batch_kernel<true, uint16_t, true>) : go(batch_kernel<true, uint32_t, true>);
+    return id16 ? go(batch_kernel<false, uint16_t, true>) : go(batch_kernel<false, uint32_t, true>);
+  }
+  if (bf16) return id16 ? go(batch_kernel<true, uint16_t, false>) : go(batch_kernel<true, uint32_t, false>);
+  return id16 ? go(batch_kernel<false, uint16_t, false>) : go(batch_kernel<false, uint32_t, false>);
 }
 
 cudaError_t launch_hash_simt(const HashArgs& a, cudaStream_t s) {
@@ -428,8 +464,12 @@ cudaError_t launch_hash_simt(const HashArgs& a, cudaStream_t s) {
     return cudaGetLastError();
   };
   const bool id16 = a.K <= 16;
-  if (a.x_bf16) return id16 ? go(hash_simt_kernel<true, uint16_t>) : go(hash_simt_kernel<true, uint32_t>);
-  return id16 ? go(hash_simt_kernel<false, uint16_t>) : go(hash_simt_kernel<false, uint32_t>);
+  if (a.nsig != 0.f) {
+    if (a.x_bf16) return id16 ? go(hash_simt_kernel<true, uint16_t, true>) : go(hash_simt_kernel<true, uint32_t, true>);
+    return id16 ? go(hash_simt_kernel<false, uint16_t, true>) : go(hash_simt_kernel<false, uint32_t, true>);
+  }
+  if (a.x_bf16) return id16 ? go(hash_simt_kernel<true, uint16_t, false>) : go(hash_simt_kernel<true, uint32_t, false>);
+  return id16 ? go(hash_simt_kernel<false, uint16_t, false>) : go(hash_simt_kernel<false, uint32_t, false>);
 }
 
 }  // namespace ace
