@@ -63,9 +63,10 @@ def _peaks():
 # sources that determine each timed kernel's code (its traffic figure is void once one changes)
 KERNEL_SOURCES = {
     "hash_tc": ("hash_tc.cu", "tc_ptx.cuh", "tc_plan.h", "guard.cuh", "ace_internal.h", "exact_div.h"),
-    "hash_simt": ("hash_simt.cu", "guard.cuh", "ace_internal.h", "exact_div.h", "score_block.cuh"),
+    "hash_simt": ("hash_simt.cu", "guard.cuh", "ace_internal.h", "exact_div.h", "score_block.cuh", "flag_wait.cuh"),
     "hash_gemm": ("hash_gemm.cu", "gemm_plan.h", "tc_ptx.cuh", "guard.cuh", "ace_internal.h", "exact_div.h"),
     "hash_gemm_fp8": ("hash_gemm.cu", "gemm_plan.h", "tc_ptx.cuh", "guard.cuh", "ace_internal.h", "exact_div.h"),
+    "hash_fwht": ("hash_fwht.cu", "fwht_plan.h", "guard.cuh", "ace_internal.h", "exact_div.h"),
 }
 
 

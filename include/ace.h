@@ -478,6 +478,20 @@ int ace_exact_score(const void* Q_dev, int64_t nq, const void* D_dev, int64_t nd
                     double* S_dev, void* stream);
 
 /*
+ * ace_wait_probe — failure detection without a GPU fault: runs one of the library's bounded
+ * device waits on an event that never happens, with nothing in flight, and reports how it
+ * gave up.  kind 0: the tensor-core kernels' barrier wait, in a CTA that holds tensor memory
+ * as the hash kernels do (it frees it after giving up; a second wait, with the abort flag
+ * already set, returns at once); kind 1: the batched launch's wait on a device flag.
+ * limit_cycles in [1e5, 1e9] SM cycles.  *status = ACE_STATUS_TIMEOUT when the wait gave up;
+ * cycles_out (2 entries, may be NULL): the cycles the wait took and, for kind 0, those of the
+ * aborted wait.  Synchronises the device; the context stays usable.  No counterpart in the
+ * paper (an execution detail).  Errors: ACE_ERR_ARG, ACE_ERR_UNSUPPORTED (kind 0 needs an
+ * sm_103 device), ACE_ERR_CUDA.
+ */
+int ace_wait_probe(int kind, int64_t limit_cycles, uint32_t* status, int64_t* cycles_out);
+
+/*
  * ace_tc_probe — measurement hook for the tensor-core engines' error model.  Computes
  * D = A . B^T (A: 128 x kdim, B: ncols x kdim, bfloat16 bit patterns, row-major, host; D:
  * 128 x ncols binary32, host) on the tcgen05 tensor cores as kdim/16 MMA instructions of

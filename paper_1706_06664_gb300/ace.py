@@ -15,6 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libace_gb300.so")
 
 ACE_OK, ACE_ERR_ARG, ACE_ERR_OOM, ACE_ERR_OVERFLOW, ACE_ERR_TIMEOUT, ACE_ERR_CUDA, ACE_ERR_UNSUPPORTED = range(7)
+ACE_STATUS_TIMEOUT = 2  # a bounded device wait gave up (ace_stats status bits)
 ACE_F32, ACE_BF16 = 0, 1
 ACE_PROJ_AUTO, ACE_PROJ_FP32, ACE_PROJ_BF16, ACE_PROJ_FP8, ACE_PROJ_FWHT = -1, 0, 1, 2, 3
 ACE_W_BF16 = 1
@@ -32,7 +33,7 @@ EXPORTS = [
     "ace_batch_insert_score", "ace_server_create", "ace_server_submit", "ace_server_wait", "ace_server_drain", "ace_server_destroy", "ace_server_info", "ace_stats",
     "ace_get_counts", "ace_get_projection", "ace_get_shape", "ace_last_error", "ace_version",
     "ace_profile_enable", "ace_profile_phases", "ace_profile_read", "ace_insert_score_noalloc",
-    "ace_tc_probe", "ace_tc_probe_fp8", "ace_exact_score", "ace_save_size", "ace_save", "ace_load", "ace_window_enable", "ace_set_graph",
+    "ace_tc_probe", "ace_tc_probe_fp8", "ace_wait_probe", "ace_exact_score", "ace_save_size", "ace_save", "ace_load", "ace_window_enable", "ace_set_graph",
     "ace_batch_tile",
 ]
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
@@ -84,6 +85,7 @@ def load_library(path: str = LIB_PATH):
             "ace_destroy": ([H], i32),
             "ace_reset": ([H, P], i32),
             "ace_set_precision": ([H, i32], i32),
+            "ace_wait_probe": ([i32, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_int64)], i32),
             "ace_set_privacy": ([H, ctypes.c_float, ctypes.c_uint64], i32),
             "ace_get_privacy": ([H, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64),
                                  ctypes.POINTER(ctypes.c_uint64)], i32),
@@ -499,6 +501,14 @@ def exact_score(Q, D, K: int, stream=None):
     _check(load_library().ace_exact_score(_ptr(Q), Q.shape[0], _ptr(D), D.shape[0], Q.shape[1], _x_dtype(Q), int(K),
                                           _ptr(S), _stream_ptr(stream)))
     return S
+
+
+def wait_probe(kind: int, limit_cycles: int) -> dict:
+    """ace_wait_probe: {"status", "cycles", "aborted_cycles"} of a bounded wait made to run out."""
+    st = ctypes.c_uint32()
+    cyc = (ctypes.c_int64 * 2)()
+    _check(load_library().ace_wait_probe(int(kind), int(limit_cycles), ctypes.byref(st), cyc))
+    return {"status": st.value, "cycles": cyc[0], "aborted_cycles": cyc[1]}
 
 
 def tc_probe_fp8(A: np.ndarray, B: np.ndarray) -> np.ndarray:

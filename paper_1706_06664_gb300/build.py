@@ -21,7 +21,8 @@ LIB = os.path.join(LIBDIR, "libace_gb300.so")
 CU_SOURCES = ["ace_abi.cu", "hash_simt.cu", "hash_tc.cu", "hash_gemm.cu", "tc_probe.cu", "recheck.cu", "count_kernels.cu",
               "exact_score.cu", "hash_fwht.cu"]
 CPP_SOURCES = ["projection_gen.cpp"]
-HEADERS = ["ace_internal.h", "exact_div.h", "guard.cuh", "tc_ptx.cuh", "tc_plan.h", "gemm_plan.h", "fwht_plan.h"]
+HEADERS = ["ace_internal.h", "exact_div.h", "guard.cuh", "tc_ptx.cuh", "tc_plan.h", "gemm_plan.h", "fwht_plan.h",
+           "flag_wait.cuh", "score_block.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

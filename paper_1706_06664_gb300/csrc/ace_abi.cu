@@ -2596,6 +2596,38 @@ int ace_exact_score(const void* Q_dev, int64_t nq, const void* D_dev, int64_t nd
   return ACE_OK;
 }
 
+int ace_wait_probe(int kind, int64_t limit_cycles, uint32_t* status, int64_t* cycles_out) {
+  if (!status || (kind != 0 && kind != 1) || limit_cycles < 100000 || limit_cycles > 1000000000)
+    return fail(ACE_ERR_ARG, "kind must be 0 or 1, limit_cycles in [1e5, 1e9] and status non-NULL");
+  int dev = 0;
+  ACE_CUDA(cudaGetDevice(&dev));
+  cudaDeviceProp p;
+  ACE_CUDA(cudaGetDeviceProperties(&p, dev));
+  if (kind == 0 && (p.major != 10 || p.minor != 3))
+    return fail(ACE_ERR_UNSUPPORTED, "the tensor-core wait probe needs an sm_103 device");
+  unsigned char* buf = nullptr;
+  const size_t bytes = 16 + sizeof(ace::DevStats) + 2 * sizeof(long long);
+  ACE_CUDA(cudaMalloc(&buf, bytes));
+  unsigned int* flag = reinterpret_cast<unsigned int*>(buf);
+  auto* st = reinterpret_cast<ace::DevStats*>(buf + 16);
+  auto* cyc = reinterpret_cast<long long*>(buf + 16 + sizeof(ace::DevStats));
+  cudaError_t e = cudaMemset(buf, 0, bytes);
+  if (e == cudaSuccess) e = ace::launch_wait_probe(kind, limit_cycles, flag, st, cyc, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  ace::DevStats hs{};
+  long long hc[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(&hs, st, sizeof hs, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(hc, cyc, sizeof hc, cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_fail(e, "wait probe");
+  *status = hs.status;
+  if (cycles_out) {
+    cycles_out[0] = hc[0];
+    cycles_out[1] = hc[1];
+  }
+  return ACE_OK;
+}
+
 int ace_tc_probe(const uint16_t* A_host, const uint16_t* B_host, int kdim, int ncols, float* D_host) {
   return tc_probe_any(A_host, B_host, kdim, ncols, D_host, false);
 }

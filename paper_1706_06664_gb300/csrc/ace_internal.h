@@ -128,6 +128,8 @@ cudaError_t launch_delete_apply(const uint32_t* hist, uint32_t* counts, long lon
 // Measurement hook: D = A . B^T as kd/16 tcgen05 MMAs of 128 x N x 16 (tc_probe.cu).
 cudaError_t launch_tc_probe(const void* A, const void* B, int kd, int N, bool fp8, float* D, int* status,
                             cudaStream_t s);
+cudaError_t launch_wait_probe(int kind, long long limit, const unsigned int* flag, DevStats* st, long long* cycles,
+                              cudaStream_t s);
 
 // Host-side generator of the projection matrix (SplitMix64 counter mode + Box-Muller).
 // Exact S(q, D) = sum_i p(q, x_i)^K for nq queries (exact_score.cu); part holds

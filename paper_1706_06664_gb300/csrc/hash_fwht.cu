@@ -58,10 +58,112 @@ __device__ __noinline__ bool noisy_exact_bit(const FwhtArgs& a, long long i, int
   return exact_bit_add<BF16>(a.X, i, a.d, a.Wt, col, static_cast<double>(a.nsig) * static_cast<double>(cw));
 }
 
+// Packed pairs of binary32 values (one 64-bit register) and the paired operations of sm_100
+// and later: each half is rounded on its own, exactly as the scalar operation would be, so
+// the results are those of two __fadd_rn / __fsub_rn / __fmaf_rn, in half the instructions.
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void unpk2(uint64_t r, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {  // a b + c
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// Walsh-Hadamard stages on the bits of the register index e (v[e] +- v[e + h] for h = 1, 2, ..,
+// E / 2): the first within adjacent registers, the others on register pairs at once.
+template <int E>
+__device__ __forceinline__ void inlane_stages(float (&v)[E]) {
+  if constexpr (E >= 2) {
+#pragma unroll
+    for (int e = 0; e < E; e += 2) {
+      const float lo = v[e], hi = v[e + 1];
+      v[e] = __fadd_rn(lo, hi);
+      v[e + 1] = __fsub_rn(lo, hi);
+    }
+  }
+#pragma unroll
+  for (int h = 2; h < E; h <<= 1) {
+#pragma unroll
+    for (int e = 0; e < E; e += 2) {
+      if ((e & h) == 0) {
+        const uint64_t lo = pk2(v[e], v[e + 1]), hi = pk2(v[e + h], v[e + h + 1]);
+        unpk2(add2(lo, hi), v[e], v[e + 1]);
+        unpk2(sub2(lo, hi), v[e + h], v[e + h + 1]);
+      }
+    }
+  }
+}
+
+// Whether every binary64 sum of +-x_t (t < dp) is exact for this row: all coordinates finite,
+// and the sums' bits, from the lowest significant bit of the smallest non-zero |x_t|
+// (2^(E_t - 150), or 2^(E_t - 134) for bfloat16 values, with the biased exponent E_t >= 1) to
+// the top of dp 2^(E_max - 126), fit binary64's 53.  Then the sum's value does not depend on the
+// order of the additions: a warp can split it.  (The warp's x registers hold the row.)
+template <bool BF16, int E>
+__device__ __forceinline__ bool exact_tier_applies(const float (&x)[E], int m) {
+  uint32_t emax = 0u, emin = 255u;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t u = __float_as_uint(x[e]) & 0x7FFFFFFFu;
+    const uint32_t ef = u >> 23;
+    emax = max(emax, ef);
+    if (u) emin = min(emin, max(ef, 1u));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    emax = max(emax, __shfl_xor_sync(0xFFFFFFFFu, emax, off));
+    emin = min(emin, __shfl_xor_sync(0xFFFFFFFFu, emin, off));
+  }
+  if (emax >= 255u) return false;  // inf or NaN
+  if (emax == 0u && emin == 255u) return true;  // a zero row
+  const int lo = static_cast<int>(emin) - (BF16 ? 134 : 150);
+  const int hi = static_cast<int>(emax) - 126 + m;
+  return hi - lo <= 53;
+}
+
+// The sum over t of W[t][b dp + j] x_t with W[t][c] = D_b[t] H[j][t] (fm: this lane's sign bits
+// of block b, bit e for t = 32 e + lane), in binary64: each lane adds its E terms, the warp
+// joins the lanes' sums.  Exact when exact_tier_applies; every lane returns the same value.
+template <int E>
+__device__ __forceinline__ double coop_sum(const float (&x)[E], uint32_t fm, int j, int lane) {
+  const uint32_t lp = static_cast<uint32_t>(__popc(static_cast<uint32_t>(j & 31) & static_cast<uint32_t>(lane))) & 1u;
+  const uint32_t jh = static_cast<uint32_t>(j) >> 5;
+  double s = 0.0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t neg = ((fm >> e) ^ lp ^ static_cast<uint32_t>(__popc(jh & static_cast<uint32_t>(e)))) & 1u;
+    s = __dadd_rn(s, neg ? -static_cast<double>(x[e]) : static_cast<double>(x[e]));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xFFFFFFFFu, s, off));
+  return s;
+}
+
 // OUT: 0 ids; 1 the measurement path (the transform's binary32 outputs, no ids); 2 ids with
 // privacy noise (a separate instantiation, so that the others carry none of its registers).
+// Blocks per SM the register budget is sized for: short rows need few registers, and more
+// resident warps hide the latency of their shuffles.
+template <int E>
+constexpr int kFwhtMinBlocks = E <= 4 ? 4 : (E == 8 ? 3 : 2);
+
 template <bool BF16, typename IdT, int E, int OUT>
-__global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ FwhtArgs a) {
+__global__ void __launch_bounds__(256, kFwhtMinBlocks<E>) hash_fwht_kernel(const __grid_constant__ FwhtArgs a) {
   constexpr bool PROJ = OUT == 1;
   extern __shared__ __align__(16) unsigned char fsm[];
   using SM = FwhtSmem<E, BF16 ? 2 : 4>;
@@ -159,12 +261,27 @@ __global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ 
         }
         __syncwarp();  // (the buffer is refilled two points later)
       }
-      float sa = 0.f, q = 0.f;
+      // sum|x_t| rounded upwards and the squared norm, four chains each (any order of upward
+      // roundings bounds the sum from above)
+      float sa4[4] = {0.f, 0.f, 0.f, 0.f}, q4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        sa = __fadd_ru(sa, fabsf(x[e]));
-        q = fmaf(x[e], x[e], q);
+      for (int e = 0; e < E; ++e) sa4[e & 3] = __fadd_ru(sa4[e & 3], fabsf(x[e]));
+      if constexpr (E >= 4) {
+        uint64_t qa = pk2(0.f, 0.f), qb = pk2(0.f, 0.f);
+#pragma unroll
+        for (int e = 0; e < E; e += 4) {
+          const uint64_t xa = pk2(x[e], x[e + 1]), xb = pk2(x[e + 2], x[e + 3]);
+          qa = fma2(xa, xa, qa);
+          qb = fma2(xb, xb, qb);
+        }
+        unpk2(qa, q4[0], q4[1]);
+        unpk2(qb, q4[2], q4[3]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) q4[e] = x[e] * x[e];
       }
+      float sa = __fadd_ru(__fadd_ru(sa4[0], sa4[1]), __fadd_ru(sa4[2], sa4[3]));
+      float q = (q4[0] + q4[1]) + (q4[2] + q4[3]);
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
         sa = __fadd_ru(sa, __shfl_xor_sync(0xFFFFFFFFu, sa, off));
@@ -172,6 +289,9 @@ __global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ 
       }
       if (lane == 0 && !isfinite(q) && !PROJ) atomicAdd(&a.st->nonfinite, 1ull);
       const float B = __fmaf_ru(cband, sa, babs);  // +inf or NaN for a non-finite row: all exact
+      // uniform threshold: with noise, |v| > Bt implies |v| > B + 2^-23 (nall + |v|)
+      const float Bt = noisy ? __fmul_ru(__fmaf_ru(1.1920928955078125e-07f, nall, B), 1.0000002384185791f) : B;
+      int exact_ok = -1;  // the cooperative exact tier applies to this row (computed when first needed)
       for (int b = 0; b < nblk; ++b) {
         // sign flips: bit e of this lane's mask for block b flips coordinate 32 e + lane
         const uint32_t fm = smask[b * 32 + lane];
@@ -179,17 +299,7 @@ __global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ 
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = __uint_as_float(__float_as_uint(x[e]) ^ (((fm >> e) & 1u) << 31));
         // butterflies on the slot bits (bit 5.. of t = 32 e + lane), within the lane
-#pragma unroll
-        for (int h = 1; h < E; h <<= 1) {
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            if ((e & h) == 0) {
-              const float lo = v[e], hi = v[e + h];
-              v[e] = __fadd_rn(lo, hi);
-              v[e + h] = __fsub_rn(lo, hi);
-            }
-          }
-        }
+        inlane_stages<E>(v);
         if constexpr (E == 32) {
           // dp = 1024: transpose through shared memory (lane l then holds t = 32 l .. 32 l + 31),
           // so the five stages on the low bits are within the lane too, and the lane's 32
@@ -201,65 +311,109 @@ __global__ void __launch_bounds__(256) hash_fwht_kernel(const __grid_constant__ 
 #pragma unroll
           for (int e = 0; e < 32; ++e) v[e] = tile[lane * 33 + e];
           __syncwarp();
-#pragma unroll
-          for (int h = 1; h < 32; h <<= 1) {
-#pragma unroll
-            for (int e = 0; e < 32; ++e) {
-              if ((e & h) == 0) {
-                const float lo = v[e], hi = v[e + h];
-                v[e] = __fadd_rn(lo, hi);
-                v[e + h] = __fsub_rn(lo, hi);
-              }
-            }
-          }
-          if (noisy) {
-            const uint64_t rb = static_cast<uint64_t>(a.nbase + i) * KL + b * dp + lane * 32;
-#pragma unroll
-            for (int e = 0; e < 32; ++e) v[e] = __fadd_rn(v[e], __fmul_rn(a.nsig, counter_w(a.nseed, rb + e)));
-          }
-          uint32_t wv = 0u;
-#pragma unroll
-          for (int e = 0; e < 32; ++e) {
-            const int col = b * dp + lane * 32 + e;
-            bool bit = v[e] > 0.f;
-            const float Be = noisy ? __fmaf_ru(1.1920928955078125e-07f, __fadd_ru(nall, fabsf(v[e])), B) : B;
-            if (!PROJ && !(fabsf(v[e]) > Be) && col < KL) {  // inside the bound (or NaN)
-              bit = noisy ? noisy_exact_bit<BF16>(a, i, col) : exact_bit<BF16>(a.X, i, d, a.Wt, col);
-              ++nre;
-            }
-            if (PROJ && col < KL) a.proj[i * static_cast<long long>(KL) + col] = v[e];
-            wv |= (bit ? 1u : 0u) << e;
-          }
-          wrow[b * 32 + lane] = wv;
+          inlane_stages<32>(v);
         } else {
           // butterflies on the lane bits: o + s v with s = -1 on the upper lane of each pair
           // (one rounded operation, the same as the sum or the difference)
 #pragma unroll
           for (int h = 1; h < 32; h <<= 1) {
             const float sg = (lane & h) ? -1.f : 1.f;
+            float o[E];
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-              const float o = __shfl_xor_sync(0xFFFFFFFFu, v[e], h);
-              v[e] = __fmaf_rn(sg, v[e], o);
+            for (int e = 0; e < E; ++e) o[e] = __shfl_xor_sync(0xFFFFFFFFu, v[e], h);
+            if constexpr (E == 1) {
+              v[0] = __fmaf_rn(sg, v[0], o[0]);
+            } else {
+              const uint64_t sg2 = pk2(sg, sg);
+#pragma unroll
+              for (int e = 0; e < E; e += 2) unpk2(fma2(sg2, pk2(v[e], v[e + 1]), pk2(o[e], o[e + 1])), v[e], v[e + 1]);
             }
           }
-          if (noisy) {
-            const uint64_t rb = static_cast<uint64_t>(a.nbase + i) * KL + b * dp + lane;
-#pragma unroll
-            for (int e = 0; e < E; ++e) v[e] = __fadd_rn(v[e], __fmul_rn(a.nsig, counter_w(a.nseed, rb + 32 * e)));
-          }
+        }
+        // output e of this lane is column b dp + cofs(e)
+        auto cofs = [&](int e) { return E == 32 ? lane * 32 + e : e * 32 + lane; };
+        if constexpr (PROJ) {
 #pragma unroll
           for (int e = 0; e < E; ++e) {
-            const int col = b * dp + e * 32 + lane;
-            bool bit = v[e] > 0.f;
-            const float Be = noisy ? __fmaf_ru(1.1920928955078125e-07f, __fadd_ru(nall, fabsf(v[e])), B) : B;
-            if (!PROJ && !(fabsf(v[e]) > Be) && col < KL) {  // inside the bound (or NaN)
-              bit = noisy ? noisy_exact_bit<BF16>(a, i, col) : exact_bit<BF16>(a.X, i, d, a.Wt, col);
+            const int col = b * dp + cofs(e);
+            if (col < KL) a.proj[i * static_cast<long long>(KL) + col] = v[e];
+          }
+          continue;
+        }
+        if constexpr (noisy) {
+          const uint64_t rb = static_cast<uint64_t>(a.nbase + i) * KL + b * dp;
+#pragma unroll
+          for (int e = 0; e < E; ++e) v[e] = __fadd_rn(v[e], __fmul_rn(a.nsig, counter_w(a.nseed, rb + cofs(e))));
+        }
+        // sign words (bit = [v > 0]; the outputs inside the bound are corrected below)
+        float mv = fabsf(v[0]);
+#pragma unroll
+        for (int e = 1; e < E; ++e) mv = fminf(mv, fabsf(v[e]));  // (a NaN output makes the row's bound NaN)
+        if constexpr (E == 32) {
+          // outside the bound v is neither 0 nor NaN, so [v > 0] is the complement of the sign
+          // bit: the sign bits are funnelled into four bytes, one shift per output
+          uint32_t c[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int e = 8 * k + 7; e >= 8 * k; --e) c[k] = __funnelshift_l(__float_as_uint(v[e]), c[k], 1);
+          wrow[b * 32 + lane] = ~((c[0] | (c[1] << 8)) | ((c[2] << 16) | (c[3] << 24)));
+        } else {
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const uint32_t wv = __ballot_sync(0xFFFFFFFFu, v[e] > 0.f);
+            if (lane == 0) wrow[b * E + e] = wv;
+          }
+        }
+        uint32_t amb = 0u;  // bit e: output e is inside the bound (or NaN), a column < KL
+        if (!(mv > Bt)) {
+#pragma unroll
+          for (int e = 0; e < E; ++e)
+            if (!(fabsf(v[e]) > Bt) && b * dp + cofs(e) < KL) amb |= 1u << e;
+        }
+        uint32_t any = __ballot_sync(0xFFFFFFFFu, amb != 0u);
+        if (any) {
+          __syncwarp();
+          if (exact_ok < 0) exact_ok = exact_tier_applies<BF16, E>(x, a.m) ? 1 : 0;
+          if (exact_ok) {
+            // one output at a time, by the whole warp: the binary64 sum of +-x_t is exact, so
+            // it is the definition's index-order sum
+            while (any) {
+              const int src = __ffs(any) - 1;
+              const uint32_t am = __shfl_sync(0xFFFFFFFFu, amb, src);
+              const int e = __ffs(am) - 1;
+              const int j = E == 32 ? src * 32 + e : e * 32 + src;
+              double sum = coop_sum<E>(x, fm, j, lane);
+              bool bit;
+              if constexpr (noisy) {
+                const float cw = counter_w(a.nseed, static_cast<uint64_t>(a.nbase + i) * KL + b * dp + j);
+                bit = __dadd_rn(sum, static_cast<double>(a.nsig) * static_cast<double>(cw)) > 0.0;
+              } else {
+                bit = sum > 0.0;
+              }
+              if (lane == 0) {
+                const int c = b * dp + j;
+                wrow[c >> 5] = (wrow[c >> 5] & ~(1u << (c & 31))) | ((bit ? 1u : 0u) << (c & 31));
+                ++nre;
+              }
+              if (lane == src) amb &= amb - 1u;
+              any = __ballot_sync(0xFFFFFFFFu, amb != 0u);
+              __syncwarp();
+            }
+          } else {
+            // rows whose exponent range is too wide (or not finite): each lane evaluates the
+            // definition in index order
+            while (amb) {
+              const int e = __ffs(amb) - 1;
+              amb &= amb - 1u;
+              const int c = b * dp + cofs(e);
+              bool bit;
+              if constexpr (noisy) bit = noisy_exact_bit<BF16>(a, i, c);
+              else bit = exact_bit<BF16>(a.X, i, d, a.Wt, c);
+              if (bit) atomicOr(&wrow[c >> 5], 1u << (c & 31));
+              else atomicAnd(&wrow[c >> 5], ~(1u << (c & 31)));
               ++nre;
             }
-            if (PROJ && col < KL) a.proj[i * static_cast<long long>(KL) + col] = v[e];
-            const uint32_t wv = __ballot_sync(0xFFFFFFFFu, bit);
-            if (lane == 0) wrow[b * E + e] = wv;
           }
         }
       }

@@ -15,6 +15,7 @@
 // definition only what Dot2 cannot (exact ties, NaN, overflow).  At d = 1024 about 1.6
 // columns per point land inside the binary32 bound; a binary64 chain of 1024 dependent FMAs
 // per such column cost four times the projection itself on GB300.
+#include "flag_wait.cuh"
 #include "guard.cuh"
 #include "score_block.cuh"
 
@@ -319,22 +320,6 @@ template <bool BF16, typename IdT, bool NOISY>
 __global__ void __launch_bounds__(NT, 2) hash_simt_kernel(HashArgs a) {
   extern __shared__ __align__(16) uint8_t sbuf[];
   hash_block_any<BF16, IdT, NOISY>(a, blockIdx.x, sbuf);
-}
-
-constexpr long long kBatchWait = 4000000000LL;  // about 2 s at 2 GHz
-
-// Waits (thread 0) until *flag >= want, bounded; on time-out it raises the detector's timeout
-// status and gives up (the detector's results are then not to be used).
-__device__ __forceinline__ void wait_at_least(const unsigned int* flag, unsigned int want, DevStats* st) {
-  const long long t0 = clock64();
-  while (*reinterpret_cast<const volatile unsigned int*>(flag) < want) {
-    if (clock64() - t0 > kBatchWait) {
-      atomicOr(&st->status, static_cast<unsigned>(ACE_STATUS_TIMEOUT));
-      break;
-    }
-    __nanosleep(256);
-  }
-  __threadfence();
 }
 
 // Every detector's insert_score in one persistent launch.  Work items are dispensed in order

@@ -7,6 +7,7 @@
 // the hardware: bfloat16 operands as kd/16 kind::f16 MMAs of 128 x N x 16, or E4M3 operands
 // as kd/32 kind::f8f6f4 MMAs of 128 x N x 32.
 #include "ace_internal.h"
+#include "flag_wait.cuh"
 #include "tc_ptx.cuh"
 
 namespace ace {
@@ -92,7 +93,65 @@ __global__ void __launch_bounds__(128, 1)
   }
 }
 
+// Failure-detection probe: the library's bounded waits, made to run out on events that never
+// happen, with nothing in flight.  kind 0 (the tensor-core kernels' wait): the CTA holds TMEM
+// as the hash kernels do, waits for a barrier phase that expects two arrivals and gets one,
+// gives up after `limit` cycles (raising ACE_STATUS_TIMEOUT), then waits once more with the
+// abort flag already set (which returns at once), frees its TMEM and returns.  kind 1 (the
+// batched launch's wait): thread 0 waits for a device flag that nothing sets.  cycles[0]: the
+// cycles the first wait took; cycles[1]: those of the aborted wait (kind 0).
+__global__ void __launch_bounds__(128, 1)
+    wait_probe_kernel(int kind, long long limit, const unsigned int* flag, DevStats* st, long long* cycles) {
+  __shared__ uint64_t bar;
+  __shared__ uint32_t taddr;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (kind == 1) {
+    if (tid == 0) {
+      const long long t0 = clock64();
+      wait_at_least(flag, 1u, st, limit);
+      cycles[0] = clock64() - t0;
+      cycles[1] = 0;
+    }
+    return;
+  }
+  if (tid == 0) {
+    mbar_init(&bar, 2);
+    mbar_fence_init();
+    abort_flag = 0;
+  }
+  if (warp == 0) {
+    tmem_alloc(&taddr, 32);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid == 0) {
+    mbar_arrive(&bar);  // one of the two arrivals the phase needs
+    long long t0 = clock64();
+    if (!mbar_wait(&bar, 0, &abort_flag, limit)) {
+      atomicOr(&st->status, static_cast<unsigned>(ACE_STATUS_TIMEOUT));
+      abort_flag = 1;
+    }
+    cycles[0] = clock64() - t0;
+    t0 = clock64();
+    mbar_wait(&bar, 0, &abort_flag, limit);  // returns at once: the abort flag is set
+    cycles[1] = clock64() - t0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(taddr, 32);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_probe(int kind, long long limit, const unsigned int* flag, DevStats* st, long long* cycles,
+                              cudaStream_t s) {
+  wait_probe_kernel<<<1, 128, 0, s>>>(kind, limit, flag, st, cycles);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_tc_probe(const void* A, const void* B, int kd, int N, bool fp8, float* D, int* status,
                             cudaStream_t s) {

@@ -95,5 +95,5 @@ def test_counter_w_checkpoint_and_unknown_flags():
     _check(det2, ref, X2, torch.from_numpy(X2).cuda())
     import ctypes
     h = ctypes.c_void_p()
-    rc = ace.load_library().ace_create_ex(d, K, L, ctypes.c_uint64(1), 0x4, ctypes.byref(h))
+    rc = ace.load_library().ace_create_ex(d, K, L, ctypes.c_uint64(1), 0x8, ctypes.byref(h))
     assert rc == ace.ACE_ERR_ARG and not h.value
