@@ -16,6 +16,7 @@
 // index order) from the stored +-1 W.
 #include <algorithm>
 
+#include "f32x2.cuh"
 #include "fwht_plan.h"
 #include "guard.cuh"
 
@@ -56,33 +57,6 @@ template <bool BF16>
 __device__ __noinline__ bool noisy_exact_bit(const FwhtArgs& a, long long i, int col) {
   const float cw = counter_w(a.nseed, static_cast<uint64_t>(a.nbase + i) * a.KL + col);
   return exact_bit_add<BF16>(a.X, i, a.d, a.Wt, col, static_cast<double>(a.nsig) * static_cast<double>(cw));
-}
-
-// Packed pairs of binary32 values (one 64-bit register) and the paired operations of sm_100
-// and later: each half is rounded on its own, exactly as the scalar operation would be, so
-// the results are those of two __fadd_rn / __fsub_rn / __fmaf_rn, in half the instructions.
-__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void unpk2(uint64_t r, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
-}
-__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
-  uint64_t r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
-  uint64_t r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {  // a b + c
-  uint64_t r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
 }
 
 // Walsh-Hadamard stages on the bits of the register index e (v[e] +- v[e + h] for h = 1, 2, ..,
