@@ -706,6 +706,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+constexpr int kMaxDeferSegs = 1024;  // deferral segments (one per hash CTA)
+
 // Exact resolution of the deferred (point, column) entries.  One warp per entry: the lanes
 // split the dot product (lane l: 16-byte chunks l, l + 32, ... of the bfloat16 row and the
 // matching binary32 W column), each as a binary32 FMA chain, join the sums by a butterfly of
@@ -715,24 +717,41 @@ __global__ void __launch_bounds__(kThreads, 1)
 // and the a priori gamma_d bound holds as well; the smaller decides.  What neither decides
 // goes to Dot2 and then to the binary64 definition (one lane).  A bit that differs from the
 // stored one is flipped in the id with an atomic XOR (other columns of the same id may be
-// resolved by other warps at the same time).
+// resolved by other warps at the same time).  The entries of all segments form one index
+// space (segment prefixes in shared memory) that every warp strides through, so that the work
+// is balanced whatever the segments' sizes.
 template <typename IdT, bool W16>
-__global__ void __launch_bounds__(256) recheck_cols_kernel(const __grid_constant__ GemmArgs a, int nseg) {
+__global__ void __launch_bounds__(256, W16 ? 3 : 2) recheck_cols_kernel(const __grid_constant__ GemmArgs a, int nseg) {
+  __shared__ unsigned long long pre[kMaxDeferSegs + 1];  // pre[s]: entries of segments < s
   const int lane = threadIdx.x & 31;
   const unsigned nwarps = gridDim.x * (blockDim.x >> 5);
   const unsigned gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const unsigned per_seg = max(1u, nwarps / static_cast<unsigned>(nseg));
-  if (gw >= per_seg * static_cast<unsigned>(nseg)) return;
-  const int seg = static_cast<int>(gw % static_cast<unsigned>(nseg));
-  const unsigned lw = gw / static_cast<unsigned>(nseg);
-  const unsigned long long cnt = a.defer_counts[seg];
-  const unsigned long long* const list = a.defer + a.seg_cap * static_cast<unsigned long long>(seg);
+  if (threadIdx.x < 32) {  // warp 0: inclusive scan of the segment counts, 32 at a time
+    unsigned long long run = 0;
+    if (lane == 0) pre[0] = 0;
+    for (int b = 0; b < nseg; b += 32) {
+      const int sg = b + lane;
+      unsigned long long v =
+          sg < nseg ? min(static_cast<unsigned long long>(a.defer_counts[sg]), a.seg_cap) : 0ull;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long o = __shfl_up_sync(0xFFFFFFFFu, v, off);
+        if (lane >= off) v += o;
+      }
+      if (sg < nseg) pre[sg + 1] = run + v;
+      run += __shfl_sync(0xFFFFFFFFu, v, 31);
+    }
+  }
+  __syncthreads();
+  const unsigned long long total = pre[nseg];
   const int d = a.d, K = a.K, L = a.L, mode = a.mode;
   const int nch = d / 8;
   const long long ld = a.ld;
   unsigned long long nre = 0;
-  for (unsigned long long e = lw; e < cnt; e += per_seg) {
-    const unsigned long long w = list[e];
+  int lo = 0;  // the segment holding g (pre[lo] <= g < pre[lo + 1]); g only grows
+  for (unsigned long long g = gw; g < total; g += nwarps) {
+    while (pre[lo + 1] <= g) ++lo;
+    const unsigned long long w = a.defer[a.seg_cap * static_cast<unsigned long long>(lo) + (g - pre[lo])];
     const long long i = static_cast<long long>(w >> kGemmEntryShift);
     const int c = static_cast<int>((w >> 1) & 0xFFFFull);
     const uint32_t tb = static_cast<uint32_t>(w & 1ull);
@@ -740,29 +759,46 @@ __global__ void __launch_bounds__(256) recheck_cols_kernel(const __grid_constant
     const float4* wr = reinterpret_cast<const float4*>(a.Wt + static_cast<size_t>(c) * d);
     const uint4* wr16 = reinterpret_cast<const uint4*>(a.Wt16) + static_cast<size_t>(c) * nch;
     float s = 0.f, run = 0.f, q = 0.f;
-    for (int ch = lane; ch < nch; ch += 32) {
-      const uint4 xv = __ldg(xr + ch);
-      float ws[8];
-      if constexpr (W16) {  // bfloat16-valued W: the same binary32 values from half the bytes
-        const uint4 wv = __ldg(wr16 + ch);
-        const uint32_t u[4] = {wv.x, wv.y, wv.z, wv.w};
+    // lane l's chunks l, l + 32, ..., four at a time: the loads of a round are all issued
+    // before its arithmetic (one memory latency per round instead of one per chunk)
+    constexpr int kRound = 4;
+    for (int c0 = lane; c0 < nch; c0 += 32 * kRound) {
+      uint4 xv[kRound], wa[kRound], wb[kRound];  // wb: the second half of a binary32 W chunk
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          ws[2 * e] = bf16_lo(u[e]);
-          ws[2 * e + 1] = bf16_hi(u[e]);
+      for (int u = 0; u < kRound; ++u) {
+        const int ch = c0 + 32 * u;
+        if (ch < nch) {
+          xv[u] = __ldg(xr + ch);
+          if constexpr (W16) {  // bfloat16-valued W: the same binary32 values from half the bytes
+            wa[u] = __ldg(wr16 + ch);
+          } else {
+            wa[u] = __ldg(reinterpret_cast<const uint4*>(wr) + 2 * ch);
+            wb[u] = __ldg(reinterpret_cast<const uint4*>(wr) + 2 * ch + 1);
+          }
         }
-      } else {
-        const float4 w0 = __ldg(wr + 2 * ch), w1 = __ldg(wr + 2 * ch + 1);
-        ws[0] = w0.x; ws[1] = w0.y; ws[2] = w0.z; ws[3] = w0.w;
-        ws[4] = w1.x; ws[5] = w1.y; ws[6] = w1.z; ws[7] = w1.w;
       }
-      const float xs[8] = {bf16_lo(xv.x), bf16_hi(xv.x), bf16_lo(xv.y), bf16_hi(xv.y),
-                           bf16_lo(xv.z), bf16_hi(xv.z), bf16_lo(xv.w), bf16_hi(xv.w)};
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        s = fmaf(xs[k], ws[k], s);
-        run = __fadd_rn(run, fabsf(s));
-        q = fmaf(xs[k], xs[k], q);
+      for (int u = 0; u < kRound; ++u) {
+        if (c0 + 32 * u < nch) {
+          float ws[8];
+          if constexpr (W16) {
+            ws[0] = bf16_lo(wa[u].x); ws[1] = bf16_hi(wa[u].x); ws[2] = bf16_lo(wa[u].y); ws[3] = bf16_hi(wa[u].y);
+            ws[4] = bf16_lo(wa[u].z); ws[5] = bf16_hi(wa[u].z); ws[6] = bf16_lo(wa[u].w); ws[7] = bf16_hi(wa[u].w);
+          } else {
+            ws[0] = __uint_as_float(wa[u].x); ws[1] = __uint_as_float(wa[u].y);
+            ws[2] = __uint_as_float(wa[u].z); ws[3] = __uint_as_float(wa[u].w);
+            ws[4] = __uint_as_float(wb[u].x); ws[5] = __uint_as_float(wb[u].y);
+            ws[6] = __uint_as_float(wb[u].z); ws[7] = __uint_as_float(wb[u].w);
+          }
+          const float xs[8] = {bf16_lo(xv[u].x), bf16_hi(xv[u].x), bf16_lo(xv[u].y), bf16_hi(xv[u].y),
+                               bf16_lo(xv[u].z), bf16_hi(xv[u].z), bf16_lo(xv[u].w), bf16_hi(xv[u].w)};
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            s = fmaf(xs[k], ws[k], s);
+            run = __fadd_rn(run, fabsf(s));
+            q = fmaf(xs[k], xs[k], q);
+          }
+        }
       }
     }
 #pragma unroll
@@ -781,13 +817,87 @@ __global__ void __launch_bounds__(256) recheck_cols_kernel(const __grid_constant
     if (fabsf(s) > fminf(brun, bpri)) {
       bit = s > 0.f;
     } else {
-      int sg = 0;
-      bool eb = false;
-      if (lane == 0) {
-        sg = dot2_sign<true>(a.X, i, d, a.Wt + static_cast<size_t>(c) * d, 1, a.dot2c, a.dot2abs);
-        eb = sg != 0 ? sg > 0 : exact_bit<true>(a.X, i, d, a.Wt, c);
+      // Warp-cooperative exact sum.  x is bfloat16 (8 significant bits); a bfloat16-valued w
+      // makes every product x_t w_t exact in binary64, and a binary32 w is split into w_hi =
+      // its bfloat16 rounding and w_lo = w - w_hi (exact), whose products are summed apart.
+      // When the bits from the lowest set bit of any product of a sum up to d times its largest
+      // product fit in 53, every binary64 sum of those products is exact, in any order: the
+      // lanes' sums joined by a butterfly are exact, and so is the sign of their total (one
+      // rounded addition keeps it) -- the definition's.  Otherwise (products spanning too many
+      // binades) Dot2 and the binary64 definition on one lane.
+      double sh = 0.0, sl = 0.0;
+      int emh = -4096, elh = 4096, eml = -4096, ell = 4096;
+      // em: the largest biased exponent; el: the lowest set bit of any product is 2^(el - 1023)
+      auto track = [](double pr, int& em, int& el) {
+        const long long b = __double_as_longlong(pr);
+        const int ef = static_cast<int>((b >> 52) & 0x7FF);
+        if (ef == 0x7FF) {
+          em = 1 << 20;  // inf or NaN: not this tier
+        } else if (pr != 0.0) {
+          const long long sig = (b & 0xFFFFFFFFFFFFFLL) | (ef ? (1LL << 52) : 0LL);
+          em = max(em, ef);
+          el = min(el, max(ef, 1) - 52 + (__ffsll(sig) - 1));
+        }
+      };
+      for (int ch = lane; ch < nch; ch += 32) {
+        const uint4 xv = __ldg(xr + ch);
+        float ws[8];
+        if constexpr (W16) {
+          const uint4 wv = __ldg(wr16 + ch);
+          ws[0] = bf16_lo(wv.x); ws[1] = bf16_hi(wv.x); ws[2] = bf16_lo(wv.y); ws[3] = bf16_hi(wv.y);
+          ws[4] = bf16_lo(wv.z); ws[5] = bf16_hi(wv.z); ws[6] = bf16_lo(wv.w); ws[7] = bf16_hi(wv.w);
+        } else {
+          const float4 w0 = __ldg(wr + 2 * ch), w1 = __ldg(wr + 2 * ch + 1);
+          ws[0] = w0.x; ws[1] = w0.y; ws[2] = w0.z; ws[3] = w0.w;
+          ws[4] = w1.x; ws[5] = w1.y; ws[6] = w1.z; ws[7] = w1.w;
+        }
+        const float xs[8] = {bf16_lo(xv.x), bf16_hi(xv.x), bf16_lo(xv.y), bf16_hi(xv.y),
+                             bf16_lo(xv.z), bf16_hi(xv.z), bf16_lo(xv.w), bf16_hi(xv.w)};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const double xd = static_cast<double>(xs[k]);
+          if constexpr (W16) {
+            const double pr = __dmul_rn(xd, static_cast<double>(ws[k]));
+            sh = __dadd_rn(sh, pr);
+            track(pr, emh, elh);
+          } else {
+            const float whi = __bfloat162float(__float2bfloat16_rn(ws[k]));
+            const double ph = __dmul_rn(xd, static_cast<double>(whi));
+            const double pl = __dmul_rn(xd, static_cast<double>(__fsub_rn(ws[k], whi)));
+            sh = __dadd_rn(sh, ph);
+            sl = __dadd_rn(sl, pl);
+            track(ph, emh, elh);
+            track(pl, eml, ell);
+          }
+        }
       }
-      bit = __shfl_sync(0xFFFFFFFFu, eb ? 1 : 0, 0) != 0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        sh = __dadd_rn(sh, __shfl_xor_sync(0xFFFFFFFFu, sh, off));
+        emh = max(emh, __shfl_xor_sync(0xFFFFFFFFu, emh, off));
+        elh = min(elh, __shfl_xor_sync(0xFFFFFFFFu, elh, off));
+        if constexpr (!W16) {
+          sl = __dadd_rn(sl, __shfl_xor_sync(0xFFFFFFFFu, sl, off));
+          eml = max(eml, __shfl_xor_sync(0xFFFFFFFFu, eml, off));
+          ell = min(ell, __shfl_xor_sync(0xFFFFFFFFu, ell, off));
+        }
+      }
+      // (biased exponents) every partial sum is below d 2^(em - 1022) <= 2^(em - 1022 + lg) and a
+      // multiple of 2^(el - 1023): at most em - el + lg + 1 bits
+      const int lg = 32 - __clz(d - 1);
+      const bool exh = emh < 0 || emh - elh + lg + 1 <= 53;
+      const bool exl = W16 || eml < 0 || eml - ell + lg + 1 <= 53;
+      if (exh && exl) {
+        bit = __dadd_rn(sh, sl) > 0.0;
+      } else {
+        int sg = 0;
+        bool eb = false;
+        if (lane == 0) {
+          sg = dot2_sign<true>(a.X, i, d, a.Wt + static_cast<size_t>(c) * d, 1, a.dot2c, a.dot2abs);
+          eb = sg != 0 ? sg > 0 : exact_bit<true>(a.X, i, d, a.Wt, c);
+        }
+        bit = __shfl_sync(0xFFFFFFFFu, eb ? 1 : 0, 0) != 0;
+      }
     }
     if (lane == 0) {
       ++nre;
@@ -846,7 +956,7 @@ cudaError_t launch_recheck_cols(const GemmArgs& a, int nseg, int num_sms, cudaSt
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
     if (e != cudaSuccess) return e;
     const unsigned grid = static_cast<unsigned>(num_sms * max(1, per_sm));
-    if (grid * 8u < static_cast<unsigned>(nseg)) return cudaErrorInvalidConfiguration;
+    if (nseg > kMaxDeferSegs) return cudaErrorInvalidConfiguration;
     kern<<<grid, 256, 0, s>>>(a, nseg);
     return cudaGetLastError();
   };

@@ -99,3 +99,36 @@ def test_structured_engine_refusals_and_other_engines():
         det = ace.Detector(d, K, L, seed=2, precision=prec, w_hadamard=True)
         ids[prec] = ace.u32(det.hash(_dev(X)))
     assert np.array_equal(ids["fwht"], ids["fp32"]) and np.array_equal(ids["fwht"], ids["bf16"])
+
+
+def test_structured_engine_full_size_sampled():
+    """C3's shape at its full size (n = 1,000,000 bfloat16 points drawn on the device, d = 1024,
+    K = 16, L = 64) in the bench's launch configuration (one insert_score call on the
+    structured engine): the ids of 2,000 sampled points (first and last included) against the
+    oracle, and at full size the properties that tie every output to the ids."""
+    d, K, L = 1024, 16, 64
+    Xd, _ = workloads.highdim_device(seed=3, n=1_000_000)
+    n = Xd.shape[0]
+    det = ace.Detector(d, K, L, seed=9, w_hadamard=True)
+    ids = ace.u32(det.hash(Xd))
+    rng = np.random.default_rng(1)
+    sample = np.unique(np.concatenate([rng.choice(n, size=2000, replace=False), [0, n - 1]]))
+    Xs = Xd[torch.from_numpy(sample).cuda()].cpu().numpy().view(np.uint16)
+    ref = oracle.Detector(d, K, L, W=oracle.projection_from_seed(d, K, L, 9, hadamard=True))
+    assert np.array_equal(ids[sample], ref.hash(Xs))
+    sc, su, fl = det.insert_score(Xd, 1.0)
+    torch.cuda.synchronize()
+    counts = det.counts()
+    for j in range(L):
+        assert np.array_equal(counts[j], np.bincount(ids[:, j], minlength=1 << K)), j
+    expect = np.zeros(n, dtype=np.int64)
+    for j in range(L):
+        expect += counts[j][ids[:, j]]
+    assert np.array_equal(ace.u32(su).astype(np.int64), expect)
+    assert np.array_equal(sc.cpu().numpy(), expect / L)
+    st = det.stats()
+    assert st["precision"] == ace.ACE_PROJ_FWHT and st["status"] == 0 and st["rechecks"] > 0
+    ref.counts[:] = counts
+    ref.n_ins = n
+    _, _, ref_fl = ref._score_ids(ids, 1.0)
+    assert np.array_equal(fl.cpu().numpy(), ref_fl)
