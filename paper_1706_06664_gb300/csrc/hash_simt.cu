@@ -31,16 +31,28 @@ constexpr int NT = 256;  // threads: 16 column groups x 16 point groups
 template <int RM, int NC>
 struct SimtTile {
   static constexpr int BM = 16 * RM, BN = 16 * NC, NW = BN / 32 > 0 ? BN / 32 : 1;
-  // shared-memory layout (bytes), carved from one dynamic buffer
-  static constexpr size_t off_ws = 0;                                         // float [DK][BN]
-  static constexpr size_t off_xs = off_ws + sizeof(float) * DK * BN;          // float [BM][DK + 1]
-  static constexpr size_t off_bits = off_xs + sizeof(float) * BM * (DK + 1);  // uint32 [BM][NW]
+  // shared-memory layout (bytes), carved from one dynamic buffer; the W and X chunks are
+  // double-buffered (the next chunk's copies are in flight while this one is multiplied)
+  static constexpr size_t ws_bytes = sizeof(float) * DK * BN, xs_bytes = sizeof(float) * BM * (DK + 1);
+  static constexpr size_t off_ws = 0;                                         // float [2][DK][BN]
+  static constexpr size_t off_xs = off_ws + 2 * ws_bytes;                     // float [2][BM][DK + 1]
+  static constexpr size_t off_bits = off_xs + 2 * xs_bytes;                   // uint32 [BM][NW]
   static constexpr size_t off_amb = off_bits + sizeof(uint32_t) * BM * NW;    // uint32 [BM][NW]
   static constexpr size_t off_xn = off_amb + sizeof(uint32_t) * BM * NW;      // float [BM]
   static constexpr size_t bytes = off_xn + sizeof(float) * BM;
 };
 constexpr size_t kSimtSmemMax = SimtTile<8, 8>::bytes;
 static_assert(SimtTile<8, 4>::bytes <= kSimtSmemMax && SimtTile<4, 8>::bytes <= kSimtSmemMax, "smem");
+
+// Asynchronous 4-byte copy global -> shared (cp.async, completion by group).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Block `blk` of one detector's hash: tile blk / ntb of BM points, table block blk % ntb.
 // NOISY: the variant that can add privacy noise (used when a detector of the launch has it on;
@@ -49,8 +61,8 @@ template <bool BF16, typename IdT, int RM, int NC, bool NOISY>
 __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int ntb, long long blk, uint8_t* sbuf) {
   using T = SimtTile<RM, NC>;
   constexpr int BM = T::BM, BN = T::BN, NW = T::NW;
-  float (*Ws)[BN] = reinterpret_cast<float (*)[BN]>(sbuf + T::off_ws);
-  float (*Xs)[DK + 1] = reinterpret_cast<float (*)[DK + 1]>(sbuf + T::off_xs);
+  auto Wbuf = [&](int b) { return reinterpret_cast<float (*)[BN]>(sbuf + T::off_ws + b * T::ws_bytes); };
+  auto Xbuf = [&](int b) { return reinterpret_cast<float (*)[DK + 1]>(sbuf + T::off_xs + b * T::xs_bytes); };
   uint32_t (*bits)[NW] = reinterpret_cast<uint32_t (*)[NW]>(sbuf + T::off_bits);
   uint32_t (*amb)[NW] = reinterpret_cast<uint32_t (*)[NW]>(sbuf + T::off_amb);
   float* xn = reinterpret_cast<float*>(sbuf + T::off_xn);
@@ -74,12 +86,20 @@ __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int 
     for (int c = 0; c < NC; ++c) acc[r][c] = 0.f;
   float q = 0.f;
 
-  for (int kc = 0; kc < a.d; kc += DK) {
+  // Chunk kc of X and W into buffer b: binary32 elements by asynchronous 4-byte copies (one
+  // group per chunk), zeros and bfloat16 or regenerated values by plain stores.
+  auto stage = [&](int kc, int b) {
+    float (*Xs)[DK + 1] = Xbuf(b);
+    float (*Ws)[BN] = Wbuf(b);
     for (int e = threadIdx.x; e < BM * DK; e += NT) {
       const int p = e / DK, k = e % DK;
-      float v = 0.f;
-      if (p < npt && kc + k < a.d) v = load_x<BF16>(a.X, (i0 + p) * a.d + kc + k);
-      Xs[p][k] = v;
+      const bool in = p < npt && kc + k < a.d;
+      if constexpr (BF16) {
+        Xs[p][k] = in ? load_x<true>(a.X, (i0 + p) * a.d + kc + k) : 0.f;
+      } else {
+        if (in) cp_async4(&Xs[p][k], static_cast<const float*>(a.X) + (i0 + p) * a.d + kc + k);
+        else Xs[p][k] = 0.f;
+      }
     }
     if (a.wgen) {  // ACE_W_COUNTER: the tile is regenerated from the seed
       for (int e = threadIdx.x; e < DK * BN; e += NT) {
@@ -89,18 +109,32 @@ __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int 
     } else {
       for (int e = threadIdx.x; e < DK * BN; e += NT) {
         const int k = e / BN, c = e % BN;
-        float v = 0.f;
-        if (c < ncol && kc + k < a.d) v = __ldg(a.W + static_cast<size_t>(kc + k) * a.KL + c0 + c);
-        Ws[k][c] = v;
+        if (c < ncol && kc + k < a.d) cp_async4(&Ws[k][c], a.W + static_cast<size_t>(kc + k) * a.KL + c0 + c);
+        else Ws[k][c] = 0.f;
       }
     }
+    cp_async_commit();
+  };
+  stage(0, 0);
+  for (int kc = 0, b = 0; kc < a.d; kc += DK, b ^= 1) {
+    if (kc + DK < a.d) {
+      stage(kc + DK, b ^ 1);  // its buffer was last read before the previous chunk's closing barrier
+      cp_async_wait1();       // this chunk's copies (the older group) have landed
+    } else {
+      cp_async_wait0();
+    }
     __syncthreads();
+    float (*Xs)[DK + 1] = Xbuf(b);
+    float (*Ws)[BN] = Wbuf(b);
+    // the chunk's coordinates below d only (the zero padding of the last chunk would add exact
+    // zeros: skipping it changes no sum)
+    const int kn = min(DK, a.d - kc);
     if (threadIdx.x < BM) {
 #pragma unroll 8
-      for (int k = 0; k < DK; ++k) q = fmaf(Xs[threadIdx.x][k], Xs[threadIdx.x][k], q);
+      for (int k = 0; k < kn; ++k) q = fmaf(Xs[threadIdx.x][k], Xs[threadIdx.x][k], q);
     }
 #pragma unroll 4
-    for (int k = 0; k < DK; ++k) {
+    for (int k = 0; k < kn; ++k) {
       float xa[RM], wb[NC];
 #pragma unroll
       for (int r = 0; r < RM; ++r) xa[r] = Xs[prow(r)][k];
