@@ -33,9 +33,10 @@ struct SimtTile {
   static constexpr int BM = 16 * RM, BN = 16 * NC, NW = BN / 32 > 0 ? BN / 32 : 1;
   // shared-memory layout (bytes), carved from one dynamic buffer; the W and X chunks are
   // double-buffered (the next chunk's copies are in flight while this one is multiplied)
-  static constexpr size_t ws_bytes = sizeof(float) * DK * BN, xs_bytes = sizeof(float) * BM * (DK + 1);
+  static constexpr int XLD = BM + 4;  // X chunk stored k-major: 16-byte rows of four points per load
+  static constexpr size_t ws_bytes = sizeof(float) * DK * BN, xs_bytes = sizeof(float) * DK * XLD;
   static constexpr size_t off_ws = 0;                                         // float [2][DK][BN]
-  static constexpr size_t off_xs = off_ws + 2 * ws_bytes;                     // float [2][BM][DK + 1]
+  static constexpr size_t off_xs = off_ws + 2 * ws_bytes;                     // float [2][DK][XLD]
   static constexpr size_t off_bits = off_xs + 2 * xs_bytes;                   // uint32 [BM][NW]
   static constexpr size_t off_amb = off_bits + sizeof(uint32_t) * BM * NW;    // uint32 [BM][NW]
   static constexpr size_t off_xn = off_amb + sizeof(uint32_t) * BM * NW;      // float [BM]
@@ -62,7 +63,8 @@ __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int 
   using T = SimtTile<RM, NC>;
   constexpr int BM = T::BM, BN = T::BN, NW = T::NW;
   auto Wbuf = [&](int b) { return reinterpret_cast<float (*)[BN]>(sbuf + T::off_ws + b * T::ws_bytes); };
-  auto Xbuf = [&](int b) { return reinterpret_cast<float (*)[DK + 1]>(sbuf + T::off_xs + b * T::xs_bytes); };
+  constexpr int XLD = T::XLD;
+  auto Xbuf = [&](int b) { return reinterpret_cast<float (*)[XLD]>(sbuf + T::off_xs + b * T::xs_bytes); };
   uint32_t (*bits)[NW] = reinterpret_cast<uint32_t (*)[NW]>(sbuf + T::off_bits);
   uint32_t (*amb)[NW] = reinterpret_cast<uint32_t (*)[NW]>(sbuf + T::off_amb);
   float* xn = reinterpret_cast<float*>(sbuf + T::off_xn);
@@ -89,16 +91,16 @@ __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int 
   // Chunk kc of X and W into buffer b: binary32 elements by asynchronous 4-byte copies (one
   // group per chunk), zeros and bfloat16 or regenerated values by plain stores.
   auto stage = [&](int kc, int b) {
-    float (*Xs)[DK + 1] = Xbuf(b);
+    float (*Xs)[XLD] = Xbuf(b);
     float (*Ws)[BN] = Wbuf(b);
     for (int e = threadIdx.x; e < BM * DK; e += NT) {
       const int p = e / DK, k = e % DK;
       const bool in = p < npt && kc + k < a.d;
       if constexpr (BF16) {
-        Xs[p][k] = in ? load_x<true>(a.X, (i0 + p) * a.d + kc + k) : 0.f;
+        Xs[k][p] = in ? load_x<true>(a.X, (i0 + p) * a.d + kc + k) : 0.f;
       } else {
-        if (in) cp_async4(&Xs[p][k], static_cast<const float*>(a.X) + (i0 + p) * a.d + kc + k);
-        else Xs[p][k] = 0.f;
+        if (in) cp_async4(&Xs[k][p], static_cast<const float*>(a.X) + (i0 + p) * a.d + kc + k);
+        else Xs[k][p] = 0.f;
       }
     }
     if (a.wgen) {  // ACE_W_COUNTER: the tile is regenerated from the seed
@@ -124,20 +126,26 @@ __device__ __forceinline__ void hash_simt_block(const HashArgs& a, int tpb, int 
       cp_async_wait0();
     }
     __syncthreads();
-    float (*Xs)[DK + 1] = Xbuf(b);
+    float (*Xs)[XLD] = Xbuf(b);
     float (*Ws)[BN] = Wbuf(b);
     // the chunk's coordinates below d only (the zero padding of the last chunk would add exact
     // zeros: skipping it changes no sum)
     const int kn = min(DK, a.d - kc);
     if (threadIdx.x < BM) {
 #pragma unroll 8
-      for (int k = 0; k < kn; ++k) q = fmaf(Xs[threadIdx.x][k], Xs[threadIdx.x][k], q);
+      for (int k = 0; k < kn; ++k) q = fmaf(Xs[k][threadIdx.x], Xs[k][threadIdx.x], q);
     }
 #pragma unroll 4
     for (int k = 0; k < kn; ++k) {
       float xa[RM], wb[NC];
 #pragma unroll
-      for (int r = 0; r < RM; ++r) xa[r] = Xs[prow(r)][k];
+      for (int g = 0; g < RM / 4; ++g) {  // rows 4 g .. 4 g + 3 are points g 64 + 4 ty .. + 3
+        const float4 x4 = *reinterpret_cast<const float4*>(&Xs[k][g * 64 + ty * 4]);
+        xa[4 * g] = x4.x;
+        xa[4 * g + 1] = x4.y;
+        xa[4 * g + 2] = x4.z;
+        xa[4 * g + 3] = x4.w;
+      }
 #pragma unroll
       for (int g = 0; g < NC / 4; ++g) {
         const float4 w = *reinterpret_cast<const float4*>(&Ws[k][g * 64 + tx * 4]);
