@@ -3,17 +3,21 @@
 // y = H D_b x, computed in O(dp log dp) additions by one warp per point.
 //
 // Layout: lane l holds coordinates e * 32 + l (e < E = dp / 32), so the loads of a row are
-// coalesced, the five butterfly stages on the low index bits are shuffles across lanes and the
-// rest are between a lane's own registers, and after the transform the ballot of slot e over
-// the lanes is exactly the 32-bit sign word of columns b dp + 32 e .. + 31.
+// coalesced; the stages on the slot bits run within the lane (on register pairs, with the
+// paired binary32 operations); for dp <= 512 the five stages on the low index bits are
+// shuffles across lanes and after the transform the ballot of slot e over the lanes is
+// exactly the 32-bit sign word of columns b dp + 32 e .. + 31; for dp = 1024 a transpose
+// through shared memory makes those stages in-lane too, and each lane packs one sign word.
 //
 // Exactness: each output is a sum of dp terms +-x_i formed by a tree of m = log2(dp) rounded
 // additions, so |y^ - y| <= gamma_m sum|x_i| (Higham, Accuracy and Stability of Numerical
 // Algorithms, §4.2: any summation tree of height m), and the binary64 definition (Eq. 1 with
 // this W: index-order sum of x_i w_i) is within gamma64_d sum|x_i| of y.  An output with
 // |y^| > cband sum|x_i| + babs (upper bounds of both, with sum|x_i| rounded upwards) has the
-// sign of the definition; the others are evaluated by the definition itself (exact_bit, binary64,
-// index order) from the stored +-1 W.
+// sign of the definition; a point whose smallest output clears that bound needs no per-output
+// test.  The others are evaluated by the definition: by the whole warp, as a binary64 sum that
+// is exact in any order, when the row's coordinates span few enough binades
+// (exact_tier_applies); otherwise by each lane in index order from the stored +-1 W.
 #include <algorithm>
 
 #include "f32x2.cuh"

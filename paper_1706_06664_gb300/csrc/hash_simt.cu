@@ -15,6 +15,10 @@
 // definition only what Dot2 cannot (exact ties, NaN, overflow).  At d = 1024 about 1.6
 // columns per point land inside the binary32 bound; a binary64 chain of 1024 dependent FMAs
 // per such column cost four times the projection itself on GB300.
+//
+// Staging: d is walked in chunks of DK coordinates; each chunk of X (k-major) and of the
+// block's W columns is double-buffered in shared memory and filled by asynchronous copies
+// while the previous chunk is multiplied.
 #include "flag_wait.cuh"
 #include "guard.cuh"
 #include "score_block.cuh"
