@@ -66,7 +66,8 @@ KERNEL_SOURCES = {
     "hash_simt": ("hash_simt.cu", "guard.cuh", "ace_internal.h", "exact_div.h", "score_block.cuh", "flag_wait.cuh"),
     "hash_gemm": ("hash_gemm.cu", "gemm_plan.h", "tc_ptx.cuh", "guard.cuh", "ace_internal.h", "exact_div.h"),
     "hash_gemm_fp8": ("hash_gemm.cu", "gemm_plan.h", "tc_ptx.cuh", "guard.cuh", "ace_internal.h", "exact_div.h"),
-    "hash_fwht": ("hash_fwht.cu", "fwht_plan.h", "guard.cuh", "ace_internal.h", "exact_div.h", "f32x2.cuh"),
+    "hash_fwht": ("hash_fwht.cu", "fwht_plan.h", "guard.cuh", "ace_internal.h", "exact_div.h", "f32x2.cuh",
+                  "fwht_exact.cuh"),
 }
 
 
