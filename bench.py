@@ -239,6 +239,49 @@ def oracle_per_config(cases, budget_s: float = 1.5) -> dict:
     return out
 
 
+def count_phases(n: int, K: int, L: int, phases_ms: dict) -> dict:
+    """The counting and query phases against library baselines of the same work, probed in the
+    same run: the insert's n L count increments against uniformly random 32-bit atomic
+    additions straight into the L2-resident L 2^K counts (torch index_add_: the L2-atomic way
+    of counting, at its no-contention rate), and the score's n L gathers against uniformly
+    random 4-byte loads from that array (torch take, 64-bit indices, one output per load).
+    ratio > 1: the library kernels' way is slower (the insert uses privatised shared-memory
+    histograms instead of L2 atomics).  CUDA events, median of 5 after 2 warm-up runs."""
+    import torch
+    dev = torch.device("cuda")
+    m = n * L
+    counts = torch.zeros(L << K, dtype=torch.int32, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    idx = torch.randint(0, L << K, (m,), device=dev, generator=g)
+    ones = torch.ones(m, dtype=torch.int32, device=dev)
+
+    def timed(fn):
+        ts = []
+        for r in range(7):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            if r >= 2:
+                ts.append(e0.elapsed_time(e1) / 1e3)
+        return statistics.median(ts)
+
+    t_atom = timed(lambda: counts.index_add_(0, idx, ones))
+    t_take = timed(lambda: torch.take(counts, idx))
+    out = {"increments_or_gathers_per_step": m,
+           "probe_note": "library baselines probed in this run on uniformly random addresses of an "
+                         f"L2-resident array of {L << K} counts ({(L << K) * 4 / 1e6:.1f} MB)"}
+    for name, key, tp, pk in (("insert", "insert", t_atom, "l2_atomic_probe_per_s"),
+                              ("score_gather", "score", t_take, "library_gather_probe_per_s")):
+        if key in phases_ms and phases_ms[key] > 0:
+            ach = m / (phases_ms[key] / 1e3)
+            out[name] = {"achieved_per_s": ach, pk: m / tp, "ratio": ach / (m / tp)}
+    del counts, idx, ones
+    return out
+
+
 def _step_roofline(n, d, K, L, x_bytes, ms, peaks):
     """The whole call against the spec roofline: t_roof = max((X + W bytes) / HBM,
     projection flop / bf16 peak), with the measured peaks; frac = t_roof / measured time."""
@@ -778,6 +821,8 @@ def run_ours(args):
         except Exception as e:  # noqa: BLE001 - reported in the JSON line
             return {"error": f"{type(e).__name__}: {e}"[:300]}
 
+    if rank == 0 and ws == 1:
+        line["count_phases"] = section(count_phases, n, KH, LT, line["phases_ms_per_step"])
     cases = None
     if rank == 0 and ws == 1 and (args.per_config or args.cpu_baseline):
         cases = section(_config_cases)
