@@ -324,12 +324,16 @@ def per_config(cases) -> dict:
             variants.append(("fp8_w_bf16", ace.ACE_PROJ_FP8, {"w_bf16": True}))
         # the structured +-1 projection (a different hash family: other ids, its own roofline)
         variants.append(("fwht_hadamard", ace.ACE_PROJ_FWHT, {"w_hadamard": True}))
+        if n <= 100_000:  # launch-bound batches: repeated calls replayed as a captured CUDA graph
+            variants.append(("fp32_graph", ace.ACE_PROJ_FP32, {"graph": True}))
+            variants.append(("bf16_graph", ace.ACE_PROJ_BF16, {"graph": True}))
         # §4.5 privacy noise before the sign (sigma = 1): the cost of drawing and adding it
         variants.append(("fp32_privacy", ace.ACE_PROJ_FP32, {"privacy": PRIVACY_SIGMA}))
         variants.append(("fwht_hadamard_privacy", ace.ACE_PROJ_FWHT, {"w_hadamard": True, "privacy": PRIVACY_SIGMA}))
         for prec, want, kw in variants:
             kw = dict(kw)
             sigma = kw.pop("privacy", 0.0)
+            graph = kw.pop("graph", False)
             try:
                 det = ace.Detector(w["d"], w["K"], w["L"], seed=11, precision=prec.split("_")[0], **kw)
                 if sigma:
@@ -341,17 +345,35 @@ def per_config(cases) -> dict:
                 raise
             reps = 13 if not (prec == "fp32" and n * w["d"] * w["K"] * w["L"] > 1e11) else 5
             times = []
-            for r in range(reps):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                if r == 3:
-                    det.profile_read()
-                    det.profile(True)
-                e0.record(stream)
-                det.insert_score(Xd, ALPHA, stream=stream)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                if r >= 3:
-                    times.append(e0.elapsed_time(e1) / 1e3)
+            if graph:
+                # replay needs the same arguments every call (fixed outputs) on a stream of its
+                # own; the timing hook would turn it off, so no phases are read
+                det.set_graph(True)
+                gs = torch.cuda.Stream()
+                outs = (torch.empty(n, dtype=torch.float64, device=Xd.device),
+                        torch.empty(n, dtype=torch.int32, device=Xd.device),
+                        torch.empty(n, dtype=torch.uint8, device=Xd.device))
+                reps = 23
+                for r in range(reps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(gs)
+                    det.insert_score(Xd, ALPHA, *outs, stream=gs)
+                    e1.record(gs)
+                    torch.cuda.synchronize()
+                    if r >= 3:
+                        times.append(e0.elapsed_time(e1) / 1e3)
+            else:
+                for r in range(reps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    if r == 3:
+                        det.profile_read()
+                        det.profile(True)
+                    e0.record(stream)
+                    det.insert_score(Xd, ALPHA, stream=stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    if r >= 3:
+                        times.append(e0.elapsed_time(e1) / 1e3)
             det.profile(False)
             prof = det.profile_read()
             st = det.stats()
@@ -392,7 +414,7 @@ def per_config(cases) -> dict:
                                               "unit": "TFLOP/s", "frac": flop / th / 1e12 / FP32_ALU_PEAK_TFLOPS,
                                               "peak_src": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"}
             res[prec] = entry
-        for v in ("bf16", "bf16_w_bf16", "fp8_w_bf16", "fwht_hadamard", "fp32_privacy"):
+        for v in ("bf16", "bf16_w_bf16", "fp8_w_bf16", "fwht_hadamard", "fp32_privacy", "fp32_graph", "bf16_graph"):
             if isinstance(res.get(v), dict) and isinstance(res.get("fp32"), dict):
                 res[f"{v}_vs_fp32"] = res[v]["points_per_s"] / res["fp32"]["points_per_s"]
         if isinstance(res.get("fwht_hadamard_privacy"), dict) and isinstance(res.get("fwht_hadamard"), dict):
