@@ -1749,23 +1749,32 @@ static int enqueue_host_batch(ace_handle h, int op, const void* X_host, int64_t 
   if (do_insert && h->ring && n > h->win_cap)
     return fail(ACE_ERR_ARG, "a batch of %lld points is larger than the window of %lld", static_cast<long long>(n),
                 h->win_cap);
-  ACE_CUDA(cudaStreamWaitEvent(h->cstream, sl.done, 0));
+  // A small single-chunk batch copies X on `s` itself: there is no later chunk whose copy
+  // could overlap its hashing, and the copy stream would cost three more driver calls (two
+  // waits and an event) per batch, which is what limits the rate of small requests.  The
+  // slot's staging buffer is free on `s`: its previous batch ran on `s` (a change of stream
+  // waits for every batch above), and that batch's hashing, its last use of the buffer, came
+  // after its copy on either stream.
+  constexpr size_t kDirectCopyMax = size_t(4) << 20;
+  const bool direct = nch == 1 && xbytes <= kDirectCopyMax;
+  cudaStream_t xs = direct ? s : h->cstream;
+  if (!direct) ACE_CUDA(cudaStreamWaitEvent(h->cstream, sl.done, 0));
   if (segs) {
     size_t off = 0;
     for (int i = 0; i < nseg; ++i) {
       if (segs[i].n > 0)
         ACE_CUDA(cudaMemcpyAsync(static_cast<char*>(sl.x) + off, segs[i].X, static_cast<size_t>(segs[i].n) * row,
-                                 cudaMemcpyHostToDevice, h->cstream));
+                                 cudaMemcpyHostToDevice, xs));
       off += static_cast<size_t>(segs[i].n) * row;
     }
-    ACE_CUDA(cudaEventRecord(sl.chunk[0], h->cstream));
+    if (!direct) ACE_CUDA(cudaEventRecord(sl.chunk[0], h->cstream));
   } else {
     for (int c = 0; c < nch; ++c) {
       const long long c0 = c * chunk, nc = std::min<long long>(chunk, n - c0);
       if (nc <= 0) break;
       ACE_CUDA(cudaMemcpyAsync(static_cast<char*>(sl.x) + c0 * row, static_cast<const char*>(X_host) + c0 * row,
-                               static_cast<size_t>(nc) * row, cudaMemcpyHostToDevice, h->cstream));
-      ACE_CUDA(cudaEventRecord(sl.chunk[c], h->cstream));
+                               static_cast<size_t>(nc) * row, cudaMemcpyHostToDevice, xs));
+      if (!direct) ACE_CUDA(cudaEventRecord(sl.chunk[c], h->cstream));
     }
   }
   const bool simt = pick_engine(h, dtype == ACE_BF16, sl.x) == Engine::kSimt;
@@ -1773,7 +1782,7 @@ static int enqueue_host_batch(ace_handle h, int op, const void* X_host, int64_t 
   for (int c = 0; c < nch; ++c) {
     const long long c0 = c * chunk, nc = std::min<long long>(chunk, n - c0);
     if (nc <= 0) break;
-    ACE_CUDA(cudaStreamWaitEvent(s, sl.chunk[c], 0));
+    if (!direct) ACE_CUDA(cudaStreamWaitEvent(s, sl.chunk[c], 0));
     ace::HashArgs a = hash_args(h, static_cast<const char*>(sl.x) + c0 * row, nc, dtype,
                                 ace::kStoreIds | (simt && do_insert ? ace::kInsert : 0));
     a.ids = static_cast<char*>(h->ids) + static_cast<size_t>(c0) * id_bytes(h);
@@ -1816,12 +1825,13 @@ int ace_insert_score_host(ace_handle h, const void* X_host, int64_t n, int dtype
 
 // ---------------------------------------------------------------------------------------
 // Request server (continuous batching over several detectors).  The detectors are divided
-// among the scheduler threads (one by default; detector i belongs to thread i mod W), each with its own
-// queue of requests in submission order; a thread admits the first admissible request of its
-// queue whenever a slot or memory frees up: at most two per detector are in flight (its two
-// staging slots), the staged bytes of all threads stay within the budget, and a detector whose
-// oldest waiting request cannot start keeps its later requests waiting too, so each detector
-// sees its requests in submission order — its results are the same alone and in any mix.
+// among the scheduler threads (one by default; detector i belongs to thread i mod W); each
+// detector keeps its waiting requests in submission order, and a thread admits the earliest
+// admissible one among its detectors whenever a slot or memory frees up: at most two per
+// detector are in flight (its two staging slots), the staged bytes of all threads stay within
+// the budget, and a detector whose oldest waiting request cannot start keeps its later
+// requests waiting too, so each detector sees its requests in submission order — its results
+// are the same alone and in any mix.
 // Inserts that follow one another in a detector's order (no other request of that detector
 // between them) are admitted together as one launch set (their points copied side by side,
 // hashed and counted once), which gives the same counts as inserting them one by one.  Each
@@ -1853,7 +1863,8 @@ struct ace_server_s {
   std::vector<cudaStream_t> streams;
   std::vector<int> inflight;
   size_t budget = 0, bytes_inflight = 0;
-  std::vector<std::deque<Req*>> pending;  // per scheduler thread
+  std::vector<std::deque<Req*>> waiting;  // per detector, in submission order
+  std::vector<int64_t> npending;          // requests waiting, per scheduler thread
   std::unordered_map<uint64_t, Req*> reqs;
   uint64_t next_id = 1;
   int device = 0;
@@ -1868,7 +1879,7 @@ struct ace_server_s {
     for (auto& c : wcv) c->notify_one();
   }
 
-  int nworkers() const { return static_cast<int>(pending.size()); }
+  int nworkers() const { return static_cast<int>(npending.size()); }
 
   static void CUDART_CB on_done(void* p) {
     Req* r = static_cast<Req*>(p);
@@ -1888,41 +1899,39 @@ struct ace_server_s {
     s->wake_workers();  // a slot and memory are free again
   }
 
-  // The first admissible waiting request of thread w's queue (caller holds mu), or nullptr;
-  // for an insert, the inserts that directly follow it in its detector's order join it.
+  // The first admissible waiting request of thread w's detectors in submission order (caller
+  // holds mu), or nullptr; for an insert, the inserts that directly follow it in its
+  // detector's order join it.  Only the head of a detector's queue can be admitted (its later
+  // requests wait behind it), so the choice is the admissible head with the smallest ticket:
+  // a scan over the thread's detectors, not over every waiting request.
   Req* pick(int w) {
-    std::deque<Req*>& q = pending[w];
-    std::vector<char> held(dets.size(), 0);
-    for (auto it = q.begin(); it != q.end(); ++it) {
-      Req* r = *it;
-      if (held[r->det]) continue;
-      const bool slot = inflight[r->det] < 2;
-      const bool mem = bytes_inflight == 0 || bytes_inflight + r->bytes <= budget;
-      if (!(slot && mem)) {
-        held[r->det] = 1;  // keep this detector's later requests behind this one
-        continue;
-      }
-      const auto first = it;
-      size_t bytes = r->bytes;
-      int64_t n = r->n;
-      if (r->op == ACE_OP_INSERT && !dets[r->det]->ring) {
-        for (auto jt = std::next(it); jt != q.end(); ++jt) {
-          Req* o = *jt;
-          if (o->det != r->det) continue;
-          if (o->op != ACE_OP_INSERT || o->dtype != r->dtype || n + o->n > kMergeMax ||
-              bytes_inflight + bytes + o->bytes > budget)
-            break;
-          r->merged.push_back(o);
-          bytes += o->bytes;
-          n += o->n;
-        }
-      }
-      q.erase(first);
-      for (Req* o : r->merged) q.erase(std::find(q.begin(), q.end(), o));
-      coalesced += r->merged.size();
-      return r;
+    Req* r = nullptr;
+    for (size_t d = static_cast<size_t>(w); d < dets.size(); d += static_cast<size_t>(nworkers())) {
+      if (waiting[d].empty() || inflight[d] >= 2) continue;
+      Req* h = waiting[d].front();
+      if (bytes_inflight != 0 && bytes_inflight + h->bytes > budget) continue;
+      if (!r || h->id < r->id) r = h;
     }
-    return nullptr;
+    if (!r) return nullptr;
+    std::deque<Req*>& q = waiting[r->det];
+    q.pop_front();
+    size_t bytes = r->bytes;
+    int64_t n = r->n;
+    if (r->op == ACE_OP_INSERT && !dets[r->det]->ring) {
+      while (!q.empty()) {
+        Req* o = q.front();
+        if (o->op != ACE_OP_INSERT || o->dtype != r->dtype || n + o->n > kMergeMax ||
+            bytes_inflight + bytes + o->bytes > budget)
+          break;
+        r->merged.push_back(o);
+        bytes += o->bytes;
+        n += o->n;
+        q.pop_front();
+      }
+    }
+    npending[w] -= 1 + static_cast<int64_t>(r->merged.size());
+    coalesced += r->merged.size();
+    return r;
   }
 
   void release(Req* r, int rc) {  // caller holds mu: a request that could not be enqueued
@@ -1948,7 +1957,7 @@ struct ace_server_s {
     std::unique_lock<std::mutex> lk(mu);
     for (;;) {
       Req* r = nullptr;
-      wcv[w]->wait(lk, [&] { return (r = pick(w)) != nullptr || (stop && pending[w].empty()); });
+      wcv[w]->wait(lk, [&] { return (r = pick(w)) != nullptr || (stop && npending[w] == 0); });
       if (!r) break;
       inflight[r->det] += 1;
       bytes_inflight += r->bytes;
@@ -1996,8 +2005,9 @@ int ace_server_create(const ace_handle* dets, int n_dets, size_t mem_budget_byte
   int nw = 1;
   if (const char* env = std::getenv("ACE_SERVER_THREADS"))
     nw = std::max(1, std::min(ace_server_s::kMaxWorkers, std::atoi(env)));
-  s->pending.resize(std::min(n_dets, nw));
-  for (size_t w = 0; w < s->pending.size(); ++w) s->wcv.emplace_back(new std::condition_variable());
+  s->npending.assign(std::min(n_dets, nw), 0);
+  s->waiting.resize(n_dets);
+  for (size_t w = 0; w < s->npending.size(); ++w) s->wcv.emplace_back(new std::condition_variable());
   cudaGetDevice(&s->device);
   s->streams.assign(n_dets, nullptr);
   for (int i = 0; i < n_dets; ++i) {
@@ -2040,7 +2050,8 @@ int ace_server_submit(ace_server s, int det, int op, const void* X_host, int64_t
     std::lock_guard<std::mutex> lk(s->mu);
     r->id = s->next_id++;
     s->reqs[r->id] = r;
-    s->pending[det % s->nworkers()].push_back(r);
+    s->waiting[det].push_back(r);
+    s->npending[det % s->nworkers()] += 1;
   }
   s->wcv[det % s->nworkers()]->notify_one();
   *ticket = r->id;
@@ -2066,8 +2077,8 @@ int ace_server_drain(ace_server s) {
   if (!s) return fail(ACE_ERR_ARG, "server is NULL");
   std::unique_lock<std::mutex> lk(s->mu);
   s->cv.wait(lk, [&] {
-    for (const auto& q : s->pending)
-      if (!q.empty()) return false;
+    for (int64_t v : s->npending)
+      if (v) return false;
     for (int v : s->inflight)
       if (v) return false;
     return true;

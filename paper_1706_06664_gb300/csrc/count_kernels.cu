@@ -12,6 +12,7 @@
 
 #include "ace_internal.h"
 #include "score_block.cuh"
+#include "launch_cache.h"
 
 namespace ace {
 namespace {
@@ -213,10 +214,10 @@ cudaError_t launch_insert_from_ids(const void* ids, int ids16, long long ld, lon
     const int bins = (1 << K) / nparts;
     const size_t smem = static_cast<size_t>(bins) * sizeof(uint32_t);
     auto go = [&](auto kern, const auto* typed) -> cudaError_t {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+      cudaError_t e = smem_limit(kern, static_cast<int>(smem));
       if (e != cudaSuccess) return e;
       int per_sm = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 1024, smem);
+      e = blocks_per_sm(&per_sm, kern, 1024, smem);
       if (e != cudaSuccess) return e;
       // one wave: split each (table, slice) into point ranges until the SMs are covered
       const long long units = static_cast<long long>(L) * nparts;

@@ -24,6 +24,7 @@
 #include "fwht_exact.cuh"
 #include "fwht_plan.h"
 #include "guard.cuh"
+#include "launch_cache.h"
 
 namespace ace {
 namespace {
@@ -383,10 +384,10 @@ cudaError_t launch_hash_fwht(const FwhtArgs& a, int num_sms, cudaStream_t s) {
   const long long want = ((a.n + 31) / 32 + 7) / 8;  // groups of 32 points, 8 warps per block
   // one wave of resident blocks, each looping over groups (no tail waves, one prologue each)
   auto go = [&](auto kern, size_t smem) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t e = smem_limit(kern, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    e = blocks_per_sm(&per_sm, kern, 256, smem);
     if (e != cudaSuccess) return e;
     const unsigned grid =
         static_cast<unsigned>(std::min<long long>(want, static_cast<long long>(num_sms) * std::max(1, per_sm)));

@@ -46,6 +46,7 @@
 #include "gemm_plan.h"
 #include "guard.cuh"
 #include "tc_ptx.cuh"
+#include "launch_cache.h"
 
 namespace ace {
 namespace {
@@ -930,7 +931,7 @@ cudaError_t launch_hash_gemm(const GemmArgs& a, const void* tmX, const void* tmW
   const CUtensorMap& mx = *static_cast<const CUtensorMap*>(tmX);
   const CUtensorMap& mw = *static_cast<const CUtensorMap*>(tmW);
   auto go = [&](auto kern) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaError_t e = smem_limit(kern, kSmemBytes);
     if (e != cudaSuccess) return e;
     kern<<<static_cast<unsigned>(grid), kThreads, kSmemBytes, s>>>(a, mx, mw);
     return cudaGetLastError();
@@ -953,7 +954,7 @@ cudaError_t launch_recheck_cols(const GemmArgs& a, int nseg, int num_sms, cudaSt
   if (a.n <= 0 || nseg <= 0) return cudaSuccess;
   auto go = [&](auto kern) -> cudaError_t {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+    cudaError_t e = blocks_per_sm(&per_sm, kern, 256, 0);
     if (e != cudaSuccess) return e;
     const unsigned grid = static_cast<unsigned>(num_sms * max(1, per_sm));
     if (nseg > kMaxDeferSegs) return cudaErrorInvalidConfiguration;

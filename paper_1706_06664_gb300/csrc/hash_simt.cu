@@ -22,6 +22,7 @@
 #include "flag_wait.cuh"
 #include "guard.cuh"
 #include "score_block.cuh"
+#include "launch_cache.h"
 
 namespace ace {
 namespace {
@@ -466,10 +467,10 @@ cudaError_t launch_batch(const HashArgs* args_dev, const ScoreJob* jobs_dev, con
                          unsigned int* sready, bool bf16, bool id16, bool noisy, int num_sms, cudaStream_t s) {
   const size_t smem = kSimtSmemMax + 2 * sizeof(unsigned int) * (kBatchSmemDets + 1);
   auto go = [&](auto kern) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t e = smem_limit(kern, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+    e = blocks_per_sm(&per_sm, kern, NT, smem);
     if (e != cudaSuccess) return e;
     kern<<<static_cast<unsigned>(num_sms * max(1, per_sm)), NT, smem, s>>>(args_dev, jobs_dev, hstart_dev, sstart_dev,
                                                                           ndet, next, hdone, sready);
@@ -489,7 +490,7 @@ cudaError_t launch_hash_simt(const HashArgs& a, cudaStream_t s) {
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   const dim3 grid(static_cast<unsigned>(blocks));
   auto go = [&](auto kern) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSimtSmemMax));
+    cudaError_t e = smem_limit(kern, static_cast<int>(kSimtSmemMax));
     if (e != cudaSuccess) return e;
     kern<<<grid, NT, kSimtSmemMax, s>>>(a);
     return cudaGetLastError();

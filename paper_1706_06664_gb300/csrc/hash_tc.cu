@@ -37,6 +37,7 @@
 #include "tc_plan.h"
 
 #include <type_traits>
+#include "launch_cache.h"
 
 namespace ace {
 namespace {
@@ -608,7 +609,7 @@ cudaError_t launch_hash_tc(const TcArgs& a, int num_sms, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
   const long long grid = min(static_cast<long long>(num_sms), a.ntiles);
   auto go = [&](auto kern) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes);
+    cudaError_t e = smem_limit(kern, a.smem_bytes);
     if (e != cudaSuccess) return e;
     kern<<<static_cast<unsigned>(grid), kThreads, a.smem_bytes, s>>>(a);
     return cudaGetLastError();

@@ -360,6 +360,32 @@ def test_host_async_batches_in_order(precision):
     _compare_stats(a, ref)
 
 
+@pytest.mark.parametrize("precision", PRECS)
+def test_host_async_small_and_chunked_batches_mixed(precision):
+    """Small single-chunk batches (their copy runs on the caller's stream) and chunked ones
+    (copy stream, two chunks or more) alternate over the two staging slots with no wait in
+    between: each batch's outputs equal the oracle's run of the same batches in order."""
+    w = workloads.kdd(seed=11, n=200000)
+    a, ref = _pair(w["d"], w["K"], w["L"], seed=7, precision=precision)
+    sizes = [1, 5000, 40000, 300, 70000, 2, 9000, 33000, 128, 17]
+    cuts = np.concatenate([[0], np.cumsum(sizes)])
+    parts = [w["X"][cuts[i]:cuts[i + 1]] for i in range(len(sizes))]
+    outs = []
+    for X in parts:
+        n = X.shape[0]
+        o = (torch.empty(n, dtype=torch.float64).pin_memory().numpy(),
+             torch.empty(n, dtype=torch.int32).pin_memory().numpy().view(np.uint32),
+             torch.empty(n, dtype=torch.uint8).pin_memory().numpy())
+        a.insert_score_host_async(X, 1.0, *o)
+        outs.append(o)
+    a.host_wait()
+    for X, (sc, su, fl) in zip(parts, outs):
+        rs, ru, rf = ref.insert_score(X, 1.0)
+        assert np.array_equal(su, ru) and np.array_equal(sc, rs) and np.array_equal(fl, rf)
+    _engine_used(a, precision)
+    _compare_stats(a, ref)
+
+
 def test_kdd_full_size_against_oracle():
     """KDD-shaped recipe at its full size (n=500,000, d=41, K=15, L=50) in the bench's launch
     configuration (one insert_score call on the whole batch), on both engines: every id,
