@@ -237,6 +237,50 @@ def test_near_orthogonal_points_are_exact(precision):
     _engine_used(det, precision)
 
 
+def test_cancelling_instructions_next_to_the_band():
+    """The tensor-core engine's accumulation model under stress, next to the edge of its band
+    (B = tau ||x||_up; at d = 41, tau = 5.1019e-5: the bfloat16 split's 3 2^-16, the
+    accumulation term over three plus six instructions, 1 % margin).  Each point is x = a (t_i w_i) along its chosen unit
+    column w = w_c / ||w_c||, with t_i = +1 on the first 16 coordinates (one MMA instruction),
+    -1 on the next 16 and balancing signs on the rest: every instruction's addends then add up
+    to about ||x|| (the Cauchy-Schwarz worst case the bound is built on), the accumulator swings
+    out and back, and the small products are truncated against it.  One coordinate then places
+    x.w at r tau ||x|| for r from 0.5 to 10, either sign, so many bits are decided just outside
+    the band, on the model alone.  Every id, count and score must equal the oracle's; the
+    points with r < 1 are deferred, the far ones (r >= 1.5) are not."""
+    d, K, L = 41, 15, 50
+    det, ref = _pair(d, K, L, seed=33, precision="bf16")
+    W = det.projection().astype(np.float64)
+    rng = np.random.default_rng(41)
+    tau = 5.10191e-5
+    ratios = [0.5, 0.9, 0.99, 1.01, 1.02, 1.05, 1.1, 1.2, 1.5, 2.0, 3.0, 10.0]
+    n = 24 * len(ratios) * 10
+    X = np.zeros((n, d))
+    for i in range(n):
+        c = int(rng.integers(0, K * L))
+        w = W[:, c] / np.linalg.norm(W[:, c])
+        t = np.where(np.arange(d) < 16, 1.0, -1.0)
+        acc = float((t[:32] * w[:32] ** 2).sum())
+        for k in range(32, d):  # the last coordinates bring the sum back towards 0
+            t[k] = -1.0 if acc > 0 else 1.0
+            acc += t[k] * w[k] ** 2
+        x = t * w * 2.0 ** rng.uniform(-4, 8)
+        k = 32 + int(np.argmax(np.abs(w[32:])))
+        sign = 1.0 if (i // len(ratios)) % 2 == 0 else -1.0
+        for _ in range(6):  # the norm moves with x[k]: a few rounds settle the ratio
+            x[k] += (sign * ratios[i % len(ratios)] * tau * np.linalg.norm(x) - x @ w) / w[k]
+        X[i] = x
+    X = X.astype(np.float32)
+    _compare_score(det.insert_score(_dev(X), 1.0), ref.insert_score(X, 1.0))
+    assert np.array_equal(det.counts(), ref.counts)
+    _compare_stats(det, ref)
+    _engine_used(det, "bf16")
+    inside = sum(1 for i in range(n) if ratios[i % len(ratios)] < 1.0)
+    far = sum(1 for i in range(n) if ratios[i % len(ratios)] >= 1.5)
+    deferred = det.stats()["deferred"]
+    assert inside <= deferred <= n - far + n // 3, (inside, deferred, far)
+
+
 def test_near_orthogonal_points_high_d_are_exact():
     """d = 1024 on the binary32 engine, where the warp recheck, Dot2 and the binary64
     definition each decide some bits: points whose projection on a chosen column is 1e-3 down
