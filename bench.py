@@ -482,8 +482,24 @@ def _e2e(args, det, host_batches, stream, dist, dev, n, ws):
         det.insert_score_host_async(hx[i % len(hx)], ALPHA, o_sc, o_su, o_fl, stream=stream)
     det.host_wait()
     e2e_s = _max_over_ranks(time.perf_counter() - t0, dist, dev)
+    # the host link's own rate for the same bytes: one plain pinned copy of a batch, best of 10
+    dst = torch.empty(pin_x[0].numel(), dtype=pin_x[0].dtype, device=dev)
+    with torch.cuda.stream(stream):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        link = []
+        for _ in range(10):
+            ev0.record(stream)
+            dst.view(-1).copy_(pin_x[0].view(-1), non_blocking=True)
+            ev1.record(stream)
+            ev1.synchronize()
+            link.append(ev0.elapsed_time(ev1))
+    link_gbs = pin_x[0].nbytes / (min(link) / 1e3) / 1e9
+    x_gbs = pin_x[0].nbytes * args.steps / e2e_s / 1e9
     return {"value": n * args.steps * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(hx[0].nbytes),
-            "d2h_bytes_per_step": int(o_sc.nbytes + o_su.nbytes + o_fl.nbytes)}
+            "d2h_bytes_per_step": int(o_sc.nbytes + o_su.nbytes + o_fl.nbytes),
+            "x_gbs": x_gbs, "host_link_gbs": link_gbs, "of_link": x_gbs / link_gbs,
+            "link_note": "x_gbs: X bytes moved per second end to end (per rank); host_link_gbs: one plain "
+                         "pinned host-to-device copy of a batch on the same stream, best of 10"}
 
 
 def serving(seed: int = 31, window_points: int = 1 << 20, n_windows: int = 4, n_det: int = 64,

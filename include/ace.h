@@ -344,8 +344,9 @@ int ace_server_info(ace_server s, int* threads, uint64_t* coalesced);
 
 /*
  * ace_insert_score_host_async — ace_insert_score_host without the wait: enqueues the copy
- * of X_host (in chunks, each hashed as soon as it has arrived), the insert, the query phase
- * and the copies of the outputs back to the host buffers on `stream`, and returns.  Batches
+ * of X_host (in chunks, each hashed as soon as it has arrived; in one copy when an earlier
+ * batch is still in flight, whose work then overlaps it), the insert, the query phase and
+ * the copies of the outputs back to the host buffers on `stream`, and returns.  Batches
  * are processed in call order with the same results as synchronous calls.  Until
  * ace_host_wait returns, X_host must not change and the outputs are not valid.  At most two
  * batches are in flight per detector (a third call first waits for the oldest); the copy of

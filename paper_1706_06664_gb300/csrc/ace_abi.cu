@@ -1742,6 +1742,13 @@ static int enqueue_host_batch(ace_handle h, int op, const void* X_host, int64_t 
   int nch = static_cast<int>(std::min<long long>((n + chunk - 1) / chunk, kMaxChunks));
   chunk = (n + nch - 1) / nch;
   chunk = (chunk + 127) / 128 * 128;
+  // With the other slot's batch still in flight, that batch's work overlaps this batch's copy
+  // already, and chunks would only cost link time (measured end to end at 500,000 points:
+  // 1.05 G points/s with eight chunks, 1.21 with two, 1.24 with one copy): one copy.
+  if (h->hs[h->hs_next ^ 1].busy) {
+    nch = 1;
+    chunk = n;
+  }
   if (segs) {  // pieces: one copy each, then the batch is hashed as one chunk
     nch = 1;
     chunk = n;
