@@ -432,6 +432,7 @@ class Server:
         h = ctypes.c_void_p()
         _check(load_library().ace_server_create(arr, len(self._dets), int(mem_budget_bytes), ctypes.byref(h)))
         self._h = h
+        self._submit = load_library().ace_server_submit
         self._live = {}
 
     def submit(self, det: int, op: int, X: np.ndarray, alpha: float = 1.0, scores=None, sums=None, flags=None) -> int:
@@ -439,12 +440,12 @@ class Server:
             raise TypeError("X must be float32 or uint16 bfloat16 bits")
         dt = ACE_F32 if X.dtype == np.float32 else ACE_BF16
 
-        def p(a):
-            return ctypes.c_void_p(a.ctypes.data) if a is not None else ctypes.c_void_p(0)
+        def p(a):  # argtypes turn an int or None into the pointer argument
+            return a.ctypes.data if a is not None else None
 
         t = ctypes.c_uint64()
-        _check(load_library().ace_server_submit(self._h, int(det), int(op), ctypes.c_void_p(X.ctypes.data), X.shape[0],
-                                                dt, float(alpha), p(scores), p(sums), p(flags), ctypes.byref(t)))
+        _check(self._submit(self._h, int(det), int(op), X.ctypes.data, X.shape[0], dt, float(alpha), p(scores), p(sums),
+                            p(flags), ctypes.byref(t)))
         self._live[t.value] = (X, scores, sums, flags)
         return t.value
 
