@@ -199,9 +199,10 @@ def cpu_baseline(X: np.ndarray, detector_seed: int, budget_s: float = 12.0) -> d
 
 
 def _config_cases():
-    """C1 and C2 at full size (host batches) and C3 at its full size, n = 1,000,000, drawn on the
-    device (its host generator takes minutes at that size); the CPU oracle times C3 on a host
-    draw of the same recipe (its rate per point does not depend on n)."""
+    """The small and KDD-shaped configs at full size (host batches) and the high-dimensional one
+    at its full size, n = 1,000,000, drawn on the device (its host generator takes minutes at
+    that size); the CPU oracle times the high-dimensional config on a host draw of the same
+    recipe (its rate per point does not depend on n)."""
     from paper_1706_06664_gb300 import workloads
     Xd, _ = workloads.highdim_device(seed=3, n=1_000_000)
     c3 = {"X_dev": Xd, "d": 1024, "K": 16, "L": 64, "dtype": "bf16", "w_bf16_variant": True,
@@ -283,8 +284,9 @@ def count_phases(n: int, K: int, L: int, phases_ms: dict) -> dict:
 
 
 def _step_roofline(n, d, K, L, x_bytes, ms, peaks):
-    """The whole call against the spec roofline: t_roof = max((X + W bytes) / HBM,
-    projection flop / bf16 peak), with the measured peaks; frac = t_roof / measured time."""
+    """The whole call against its roofline, the slower of its bytes and its flop:
+    t_roof = max((X + W bytes) / HBM, projection flop / bf16 peak), with the measured peaks;
+    frac = t_roof / measured time."""
     flop = 2.0 * n * d * K * L
     byt = n * d * x_bytes + d * K * L * 4
     t_roof = max(byt / (peaks["hbm_gbs"] * 1e9), flop / (peaks["bf16_tflops"] * 1e12))
@@ -301,8 +303,8 @@ def per_config(cases) -> dict:
     (FP32) engine: CUDA events on the launching stream around each call, median of 10 calls
     after 3 warm-up calls on one detector per engine, the batch resident in HBM; the hash
     kernel's own time from the library's timing hook (its roofline fraction in algorithmic
-    flop against the measured bf16 peak), and the whole call against the spec roofline.
-    The batched (C4) and streaming (C5) configs have sections of their own."""
+    flop against the measured bf16 peak), and the whole call against its roofline
+    (_step_roofline).  The batched and streaming configs have sections of their own."""
     import torch
     from paper_1706_06664_gb300 import ace
     stream = torch.cuda.current_stream()

@@ -102,9 +102,9 @@ def test_structured_engine_refusals_and_other_engines():
 
 
 def test_structured_engine_full_size_sampled():
-    """C3's shape at its full size (n = 1,000,000 bfloat16 points drawn on the device, d = 1024,
-    K = 16, L = 64) in the bench's launch configuration (one insert_score call on the
-    structured engine): the ids of 2,000 sampled points (first and last included) against the
+    """The high-dimensional shape at its full size (n = 1,000,000 bfloat16 points drawn on the
+    device, d = 1024, K = 16, L = 64) in the bench's launch configuration (one insert_score call
+    on the structured engine): the ids of 2,000 sampled points (first and last included) against the
     oracle, and at full size the properties that tie every output to the ids."""
     d, K, L = 1024, 16, 64
     Xd, _ = workloads.highdim_device(seed=3, n=1_000_000)
