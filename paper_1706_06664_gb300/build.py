@@ -22,7 +22,8 @@ CU_SOURCES = ["ace_abi.cu", "hash_simt.cu", "hash_tc.cu", "hash_gemm.cu", "tc_pr
               "exact_score.cu", "hash_fwht.cu"]
 CPP_SOURCES = ["projection_gen.cpp"]
 HEADERS = ["ace_internal.h", "exact_div.h", "guard.cuh", "tc_ptx.cuh", "tc_plan.h", "gemm_plan.h", "fwht_plan.h",
-           "flag_wait.cuh", "score_block.cuh", "f32x2.cuh", "fwht_exact.cuh", "launch_cache.h"]
+           "flag_wait.cuh", "score_block.cuh", "f32x2.cuh", "fwht_exact.cuh", "launch_cache.h",
+           "admission.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -26,6 +26,7 @@
 #include "tc_plan.h"
 #include "tc_ptx.cuh"
 #include "fwht_plan.h"
+#include "admission.h"
 
 namespace {
 
@@ -1865,13 +1866,9 @@ struct ace_server_s {
     std::vector<Req*> merged;  // inserts admitted with this one (completed with it)
   };
   static constexpr int kMaxWorkers = 4;
-  static constexpr int64_t kMergeMax = 65536;  // points of one coalesced insert
   std::vector<ace_handle> dets;
   std::vector<cudaStream_t> streams;
-  std::vector<int> inflight;
-  size_t budget = 0, bytes_inflight = 0;
-  std::vector<std::deque<Req*>> waiting;  // per detector, in submission order
-  std::vector<int64_t> npending;          // requests waiting, per scheduler thread
+  ace::Admission<Req> adm;  // queues, slots and the memory budget (admission.h)
   std::unordered_map<uint64_t, Req*> reqs;
   uint64_t next_id = 1;
   int device = 0;
@@ -1880,25 +1877,22 @@ struct ace_server_s {
   std::vector<std::unique_ptr<std::condition_variable>> wcv;  // one per scheduler thread
   std::vector<std::thread> workers;
   bool stop = false;
-  uint64_t coalesced = 0;  // requests admitted as part of another's launch set
 
   void wake_workers() {
     for (auto& c : wcv) c->notify_one();
   }
 
-  int nworkers() const { return static_cast<int>(npending.size()); }
+  int nworkers() const { return adm.nthreads(); }
 
   static void CUDART_CB on_done(void* p) {
     Req* r = static_cast<Req*>(p);
     ace_server_s* s = r->srv;
     std::lock_guard<std::mutex> lk(s->mu);
     const auto now = std::chrono::steady_clock::now();
-    s->inflight[r->det] -= 1;
-    s->bytes_inflight -= r->bytes;
+    s->adm.finish(r);
     r->t_done = now;
     r->done = true;
     for (Req* q : r->merged) {
-      s->bytes_inflight -= q->bytes;
       q->t_done = now;
       q->done = true;
     }
@@ -1906,50 +1900,18 @@ struct ace_server_s {
     s->wake_workers();  // a slot and memory are free again
   }
 
-  // The first admissible waiting request of thread w's detectors in submission order (caller
-  // holds mu), or nullptr; for an insert, the inserts that directly follow it in its
-  // detector's order join it.  Only the head of a detector's queue can be admitted (its later
-  // requests wait behind it), so the choice is the admissible head with the smallest ticket:
-  // a scan over the thread's detectors, not over every waiting request.
+  // The request thread w starts next (caller holds mu), with the inserts that join it.
   Req* pick(int w) {
-    Req* r = nullptr;
-    for (size_t d = static_cast<size_t>(w); d < dets.size(); d += static_cast<size_t>(nworkers())) {
-      if (waiting[d].empty() || inflight[d] >= 2) continue;
-      Req* h = waiting[d].front();
-      if (bytes_inflight != 0 && bytes_inflight + h->bytes > budget) continue;
-      if (!r || h->id < r->id) r = h;
-    }
-    if (!r) return nullptr;
-    std::deque<Req*>& q = waiting[r->det];
-    q.pop_front();
-    size_t bytes = r->bytes;
-    int64_t n = r->n;
-    if (r->op == ACE_OP_INSERT && !dets[r->det]->ring) {
-      while (!q.empty()) {
-        Req* o = q.front();
-        if (o->op != ACE_OP_INSERT || o->dtype != r->dtype || n + o->n > kMergeMax ||
-            bytes_inflight + bytes + o->bytes > budget)
-          break;
-        r->merged.push_back(o);
-        bytes += o->bytes;
-        n += o->n;
-        q.pop_front();
-      }
-    }
-    npending[w] -= 1 + static_cast<int64_t>(r->merged.size());
-    coalesced += r->merged.size();
-    return r;
+    return adm.pick(w, ACE_OP_INSERT, [&](int d) { return !dets[static_cast<size_t>(d)]->ring; });
   }
 
   void release(Req* r, int rc) {  // caller holds mu: a request that could not be enqueued
     const auto now = std::chrono::steady_clock::now();
-    inflight[r->det] -= 1;
-    bytes_inflight -= r->bytes;
+    adm.finish(r);
     r->rc = rc;
     r->t_done = now;
     r->done = true;
     for (Req* q : r->merged) {
-      bytes_inflight -= q->bytes;
       q->rc = rc;
       q->t_done = now;
       q->done = true;
@@ -1964,11 +1926,11 @@ struct ace_server_s {
     std::unique_lock<std::mutex> lk(mu);
     for (;;) {
       Req* r = nullptr;
-      wcv[w]->wait(lk, [&] { return (r = pick(w)) != nullptr || (stop && npending[w] == 0); });
+      wcv[w]->wait(lk, [&] {
+        return (r = pick(w)) != nullptr || (stop && adm.npending[static_cast<size_t>(w)] == 0);
+      });
       if (!r) break;
-      inflight[r->det] += 1;
-      bytes_inflight += r->bytes;
-      for (Req* q : r->merged) bytes_inflight += q->bytes;
+      adm.start(r);
       lk.unlock();
       int rc;
       if (r->merged.empty()) {
@@ -2005,16 +1967,13 @@ int ace_server_create(const ace_handle* dets, int n_dets, size_t mem_budget_byte
   ace_server_s* s = new (std::nothrow) ace_server_s();
   if (!s) return fail(ACE_ERR_OOM, "host allocation failed");
   s->dets.assign(dets, dets + n_dets);
-  s->inflight.assign(n_dets, 0);
-  s->budget = mem_budget_bytes;
   // scheduler threads: ACE_SERVER_THREADS (1 .. 4) if set, else 1 (measured: four threads
   // issuing CUDA calls at once gave 0.7x the capacity of one), at most one per detector
   int nw = 1;
   if (const char* env = std::getenv("ACE_SERVER_THREADS"))
     nw = std::max(1, std::min(ace_server_s::kMaxWorkers, std::atoi(env)));
-  s->npending.assign(std::min(n_dets, nw), 0);
-  s->waiting.resize(n_dets);
-  for (size_t w = 0; w < s->npending.size(); ++w) s->wcv.emplace_back(new std::condition_variable());
+  s->adm.init(n_dets, std::min(n_dets, nw), mem_budget_bytes);
+  for (int w = 0; w < s->nworkers(); ++w) s->wcv.emplace_back(new std::condition_variable());
   cudaGetDevice(&s->device);
   s->streams.assign(n_dets, nullptr);
   for (int i = 0; i < n_dets; ++i) {
@@ -2057,8 +2016,7 @@ int ace_server_submit(ace_server s, int det, int op, const void* X_host, int64_t
     std::lock_guard<std::mutex> lk(s->mu);
     r->id = s->next_id++;
     s->reqs[r->id] = r;
-    s->waiting[det].push_back(r);
-    s->npending[det % s->nworkers()] += 1;
+    s->adm.submit(r);
   }
   s->wcv[det % s->nworkers()]->notify_one();
   *ticket = r->id;
@@ -2083,13 +2041,7 @@ int ace_server_wait(ace_server s, uint64_t ticket, double* latency_s) {
 int ace_server_drain(ace_server s) {
   if (!s) return fail(ACE_ERR_ARG, "server is NULL");
   std::unique_lock<std::mutex> lk(s->mu);
-  s->cv.wait(lk, [&] {
-    for (int64_t v : s->npending)
-      if (v) return false;
-    for (int v : s->inflight)
-      if (v) return false;
-    return true;
-  });
+  s->cv.wait(lk, [&] { return s->adm.idle(); });
   return ACE_OK;
 }
 
@@ -2097,7 +2049,7 @@ int ace_server_info(ace_server s, int* threads, uint64_t* coalesced) {
   if (!s) return fail(ACE_ERR_ARG, "server is NULL");
   std::lock_guard<std::mutex> lk(s->mu);
   if (threads) *threads = s->nworkers();
-  if (coalesced) *coalesced = s->coalesced;
+  if (coalesced) *coalesced = s->adm.coalesced;
   return ACE_OK;
 }
 
