@@ -319,8 +319,8 @@ enum { ACE_OP_INSERT = 0, ACE_OP_SCORE = 1, ACE_OP_INSERT_SCORE = 2 };
  * X_host (n x d, pinned for asynchrony) and optional output buffers (ignored for inserts),
  * and returns a ticket at once; X_host and the outputs must stay valid until the ticket is
  * waited for.  One scheduler thread (the environment variable ACE_SERVER_THREADS, 1 to 4, sets
- * more; detector i then belongs to thread i mod their number)
- * admit queued requests as slots (two per detector) and memory free up; each detector's
+ * more; detector i then belongs to thread i mod their number) admits queued requests, the
+ * earliest first, as slots (two per detector) and memory free up; each detector's
  * requests run in submission order on its own stream, so every result is the same as in a
  * run of that detector's requests alone, while different detectors overlap on the device.
  * Inserts that follow one another in a detector's order (no other request of it between them;
