@@ -50,3 +50,54 @@ def test_errors_without_device_work():
     assert lib.ace_create(4, 25, 4, 1, ctypes.byref(h)) == ace.ACE_ERR_ARG
     assert lib.ace_set_precision(None, 0) == ace.ACE_ERR_ARG
     assert lib.ace_insert(None, None, 0, 0, None) == ace.ACE_ERR_ARG
+
+
+def _fnv1a64(b: bytes) -> int:
+    h = 0xCBF29CE484222325
+    for c in b:
+        h = ((h ^ c) * 0x100000001B3) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def _blob(d=3, K=2, L=2, version=2, hdr_patch=None, extra=b"", payload=None):
+    """A checkpoint laid out as ace_save writes it: magic, header words (version, d, K, L, ...;
+    version 2 adds the privacy words 16-19), W (d x KL binary32), the L x 2^K counts (zeros,
+    or `payload` in their place), and the FNV-1a 64 checksum of everything before it."""
+    words = 16 if version == 1 else 20
+    hdr = [0] * words
+    hdr[0], hdr[1], hdr[2], hdr[3] = version, d, K, L
+    for k, v in (hdr_patch or {}).items():
+        hdr[k] = v
+    body = b"ACEDET01" + b"".join(int(v).to_bytes(8, "little") for v in hdr)
+    body += (b"\0" * (d * K * L * 4 + (1 << K) * L * 4) if payload is None else payload) + extra
+    return body + _fnv1a64(body).to_bytes(8, "little")
+
+
+def test_checkpoint_loader_rejects_malformed_blobs_before_device_work():
+    lib = ace.load_library()
+    h = ctypes.c_void_p()
+
+    def load(b):
+        buf = ctypes.create_string_buffer(b, len(b))
+        return lib.ace_load(buf, len(b), ctypes.byref(h)), lib.ace_last_error().decode()
+
+    assert lib.ace_load(None, 0, ctypes.byref(h)) == ace.ACE_ERR_ARG
+    good = _blob()
+    cases = [
+        (good[:100], "not an ACE checkpoint"),
+        (b"ACEDET02" + good[8:], "not an ACE checkpoint"),
+        (_blob(version=3), "version 3 is not supported"),
+        (_blob(K=25, payload=b""), "shape"),
+        (_blob(d=0, payload=b""), "shape"),
+        (_blob(K=16, L=4097, payload=b""), "shape"),
+        (_blob(extra=b"\0"), "needs"),
+        (_blob(hdr_patch={16: 0x7FC00000}), "privacy sigma"),  # sigma = NaN
+        (_blob(hdr_patch={16: 1 << 32}), "privacy sigma"),
+        (good[:-1] + bytes([good[-1] ^ 1]), "checksum"),
+        (good[:40] + bytes([good[40] ^ 1]) + good[41:], "checksum"),
+        (_blob(version=1)[:-1] + b"\0", "checksum"),  # the earlier layout, without privacy words
+    ]
+    # (the checksum is the last check: a blob that only fails it passed all the others)
+    for b, msg in cases:
+        rc, err = load(b)
+        assert rc == ace.ACE_ERR_ARG and msg in err, (msg, rc, err)
