@@ -50,6 +50,31 @@ def test_errors_without_device_work():
     assert lib.ace_create(4, 25, 4, 1, ctypes.byref(h)) == ace.ACE_ERR_ARG
     assert lib.ace_set_precision(None, 0) == ace.ACE_ERR_ARG
     assert lib.ace_insert(None, None, 0, 0, None) == ace.ACE_ERR_ARG
+    # every entry point checks its arguments before any CUDA call (ace.h's error contract)
+    E = ace.ACE_ERR_ARG
+    t = ctypes.c_uint64()
+    st = ctypes.c_uint32()
+    nbytes = ctypes.c_size_t()
+    one = ctypes.c_int64(1)
+    assert lib.ace_host_wait(None) == E
+    assert lib.ace_window_enable(None, 10) == E
+    assert lib.ace_set_privacy(None, ctypes.c_float(1.0), 1) == E
+    assert lib.ace_save_size(None, ctypes.byref(nbytes)) == E
+    assert lib.ace_save(None, None, 0, None) == E
+    assert lib.ace_batch_insert_score(None, 1, None, None, 0, 1.0, None, None, None, None) == E
+    assert lib.ace_server_create(None, 1, 1 << 20, ctypes.byref(t)) == E
+    assert lib.ace_server_submit(None, 0, 1, None, 1, 0, 1.0, None, None, None, ctypes.byref(t)) == E
+    assert lib.ace_server_wait(None, 1, None) == E
+    assert lib.ace_server_drain(None) == E
+    assert lib.ace_server_info(None, None, None) == E
+    assert lib.ace_server_destroy(None) == ace.ACE_OK  # destroying nothing is a no-op
+    assert lib.ace_exact_score(None, -1, None, 0, 4, 0, 4, None, None) == E
+    assert lib.ace_exact_score(ctypes.byref(one), 1, None, 0, 4, 0, 65, ctypes.byref(one), None) == E
+    assert b"K <= 64" in lib.ace_last_error()
+    assert lib.ace_exact_score(ctypes.byref(one), 1, None, 0, 4, 7, 4, ctypes.byref(one), None) == E
+    assert lib.ace_wait_probe(2, 1000000, ctypes.byref(st), None) == E
+    assert lib.ace_wait_probe(0, 10, ctypes.byref(st), None) == E
+    assert lib.ace_wait_probe(0, 1000000, None, None) == E
 
 
 def _fnv1a64(b: bytes) -> int:
